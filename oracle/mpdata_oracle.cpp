@@ -1,0 +1,432 @@
+/*
+ * MPDATA oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, slow, loop-by-loop FP64 CPU statement of one MPDATA time step on a
+ * structured, halo-padded 3D grid.  It exists to check the CUDA library; only
+ * the tests, the smoke check and the benchmark's CPU-baseline leg may load it.
+ * It shares no code, header or constant with the CUDA path.
+ *
+ * Storage: every field is [nz+2h][ny+2h][nx+2h], i fastest.  U[k][j][i] is
+ * the face i+1/2, V the face j+1/2, W the face k+1/2 (C-grid convention of
+ * Sec. 3.1.4.1).  U, V, W are G-weighted Courant numbers.
+ *
+ * Where the paper fixes the arithmetic it is followed directly:
+ *   - donor-cell (upwind) flux F(L,R,C) = max(C,0) L + min(C,0) R
+ *     (Listings 4 and 5);
+ *   - vertical flux with zero-flux top and bottom faces, i.e. the boundary
+ *     factor pivbz = 0 (Listing 7);
+ *   - flux divergence followed by the solution advance (Listings 8 and 9),
+ *     with the metric/density G in the role of the density rho.
+ * The paper defers the antidiffusive and non-oscillatory passes to another
+ * document (Sec. 5), so they follow the published MPDATA literature: the
+ * pseudo-velocity with A and B ratios (Smolarkiewicz 1984), the G-weighted
+ * form (Smolarkiewicz & Margolin 1998) and the non-oscillatory limiter
+ * (Smolarkiewicz & Grabowski 1990).  Step order:
+ *   1. halo fill: periodic in i and j, edge copy in k; zero-flux W faces;
+ *   2. donor-cell pass -> psi1;
+ *   3. for m = 2..iord: pseudo-velocities from psi^(m-1); optional limiter
+ *      (bounds over the 7-point stencil of psi^n and psi^(m-1), beta-up and
+ *      beta-down, limited velocities); donor-cell pass with them;
+ *   4. psi^(n+1) = psi^(iord).
+ * epsilon = 1e-15 in every ratio.  Ties: max(a,b) = a if a >= b, min(a,b) = a
+ * if a <= b, and |x| has derivative sign(x) with sign(0) = 0.
+ *
+ * The scalar type is a template parameter so that the same code, run on dual
+ * numbers, gives the exact tangent-linear model used to pin the adjoint.
+ */
+#include <cmath>
+#include <cstring>
+#include <cstdint>
+#include <algorithm>
+#include <vector>
+
+namespace {
+
+const double EPS = 1e-15;
+
+struct Grid {
+  int nx, ny, nz, h;
+  long px, py, pz;  // padded extents
+  Grid(int nx_, int ny_, int nz_, int h_) : nx(nx_), ny(ny_), nz(nz_), h(h_) {
+    px = nx + 2L * h; py = ny + 2L * h; pz = nz + 2L * h;
+  }
+  long size() const { return px * py * pz; }
+  long at(int i, int j, int k) const { return ((k + h) * py + (j + h)) * px + (i + h); }
+};
+
+/* ---------------------------------------------------------------- scalars */
+
+struct Dual {
+  double v, d;
+  Dual() : v(0), d(0) {}
+  Dual(double x) : v(x), d(0) {}
+  Dual(double x, double dx) : v(x), d(dx) {}
+};
+inline Dual operator+(Dual a, Dual b) { return Dual(a.v + b.v, a.d + b.d); }
+inline Dual operator-(Dual a, Dual b) { return Dual(a.v - b.v, a.d - b.d); }
+inline Dual operator-(Dual a) { return Dual(-a.v, -a.d); }
+inline Dual operator*(Dual a, Dual b) { return Dual(a.v * b.v, a.d * b.v + a.v * b.d); }
+inline Dual operator/(Dual a, Dual b) {
+  double q = a.v / b.v;
+  return Dual(q, (a.d - q * b.d) / b.v);
+}
+
+inline double val(double x) { return x; }
+inline double val(const Dual& x) { return x.v; }
+
+template <class T> inline T omax(T a, T b) { return val(a) >= val(b) ? a : b; }
+template <class T> inline T omin(T a, T b) { return val(a) <= val(b) ? a : b; }
+inline double oabs(double x) { return std::fabs(x); }
+inline Dual oabs(Dual x) {
+  return Dual(std::fabs(x.v), x.v > 0 ? x.d : (x.v < 0 ? -x.d : 0.0));
+}
+
+/* Donor-cell (upwind) flux through a face with left value L, right value R
+   and face Courant number C (Listings 4/5). */
+template <class T> inline T donor(T L, T R, T C) {
+  return omax(C, T(0.0)) * L + omin(C, T(0.0)) * R;
+}
+
+/* ------------------------------------------------------------------ halos */
+
+inline int wrap(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
+
+/* Cell-centred fields (psi, G) and the horizontal face fields (U, V):
+   periodic in i and j, corners included; the k halo copies the edge level. */
+template <class T> void fill_halo_periodic(T* f, const Grid& g) {
+  for (int k = 0; k < g.nz; ++k) {
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = -g.h; i < g.nx + g.h; ++i)
+        if (i < 0 || i >= g.nx) f[g.at(i, j, k)] = f[g.at(wrap(i, g.nx), j, k)];
+    for (int j = -g.h; j < g.ny + g.h; ++j)
+      if (j < 0 || j >= g.ny)
+        for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, wrap(j, g.ny), k)];
+  }
+  for (int k = -g.h; k < g.nz + g.h; ++k) {
+    if (k >= 0 && k < g.nz) continue;
+    int ks = k < 0 ? 0 : g.nz - 1;
+    for (int j = -g.h; j < g.ny + g.h; ++j)
+      for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, j, ks)];
+  }
+}
+
+/* Vertical face fields (W, its pseudo-velocity): periodic in i and j; the
+   bottom face (k = -1, i.e. -1/2) and the top face (k = nz-1, i.e. nz-1/2)
+   carry no flux (pivbz = 0 in Listing 7), nor does anything beyond them. */
+template <class T> void fill_halo_wface(T* f, const Grid& g) {
+  fill_halo_periodic(f, g);
+  for (int k = -g.h; k < g.nz + g.h; ++k) {
+    if (k >= 0 && k < g.nz - 1) continue;
+    for (int j = -g.h; j < g.ny + g.h; ++j)
+      for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = T(0.0);
+  }
+}
+
+/* -------------------------------------------------------------- the stages */
+
+/* Flux divergence and solution advance (Listings 8/9):
+   out = P - (1/G) * sum_d [F(P_c, P_c+d, C_c+d/2) - F(P_c-d, P_c, C_c-d/2)]. */
+template <class T>
+void advance(const Grid& g, const T* P, const T* u, const T* v, const T* w, const T* G, T* out) {
+  const long sx = 1, sy = g.px, sz = g.px * g.py;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        T fxp = donor(P[c], P[c + sx], u[c]);
+        T fxm = donor(P[c - sx], P[c], u[c - sx]);
+        T fyp = donor(P[c], P[c + sy], v[c]);
+        T fym = donor(P[c - sy], P[c], v[c - sy]);
+        T fzp = donor(P[c], P[c + sz], w[c]);
+        T fzm = donor(P[c - sz], P[c], w[c - sz]);
+        out[c] = P[c] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) / G[c];
+      }
+}
+
+/* Antidiffusive pseudo-velocity on the faces c+1/2 of every interior cell
+   (Smolarkiewicz 1984, G-weighted as in Smolarkiewicz & Margolin 1998):
+
+     Ut = (|U| - U^2/Gf) A - U (Vbar By + Wbar Bz) / Gf,
+     A  = (P_R - P_L) / (P_R + P_L + eps),
+     By = 1/2 (P_R,j+1 + P_L,j+1 - P_R,j-1 - P_L,j-1)
+              / (P_R,j+1 + P_L,j+1 + P_R,j-1 + P_L,j-1 + eps),
+     Vbar = 1/4 (V at the four j-faces around the face),  Gf = (G_L + G_R)/2,
+
+   and the same with the directions cycled for Vt and Wt.  Wt on the top
+   face is zero. */
+template <class T>
+void pseudo_velocity(const Grid& g, const T* P, const T* u, const T* v, const T* w, const T* G,
+                     T* ut, T* vt, T* wt) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+  const T eps(EPS), half(0.5), quarter(0.25);
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        {  // x face between c and c+X
+          long L = c, R = c + X;
+          T U = u[c];
+          T Gf = half * (G[L] + G[R]);
+          T A = (P[R] - P[L]) / (P[R] + P[L] + eps);
+          T By = half * (P[R + Y] + P[L + Y] - P[R - Y] - P[L - Y]) /
+                 (P[R + Y] + P[L + Y] + P[R - Y] + P[L - Y] + eps);
+          T Bz = half * (P[R + Z] + P[L + Z] - P[R - Z] - P[L - Z]) /
+                 (P[R + Z] + P[L + Z] + P[R - Z] + P[L - Z] + eps);
+          T Vb = quarter * (v[L] + v[R] + v[L - Y] + v[R - Y]);
+          T Wb = quarter * (w[L] + w[R] + w[L - Z] + w[R - Z]);
+          ut[c] = (oabs(U) - U * U / Gf) * A - U * (Vb * By + Wb * Bz) / Gf;
+        }
+        {  // y face between c and c+Y
+          long L = c, R = c + Y;
+          T V = v[c];
+          T Gf = half * (G[L] + G[R]);
+          T A = (P[R] - P[L]) / (P[R] + P[L] + eps);
+          T Bx = half * (P[R + X] + P[L + X] - P[R - X] - P[L - X]) /
+                 (P[R + X] + P[L + X] + P[R - X] + P[L - X] + eps);
+          T Bz = half * (P[R + Z] + P[L + Z] - P[R - Z] - P[L - Z]) /
+                 (P[R + Z] + P[L + Z] + P[R - Z] + P[L - Z] + eps);
+          T Ub = quarter * (u[L] + u[R] + u[L - X] + u[R - X]);
+          T Wb = quarter * (w[L] + w[R] + w[L - Z] + w[R - Z]);
+          vt[c] = (oabs(V) - V * V / Gf) * A - V * (Ub * Bx + Wb * Bz) / Gf;
+        }
+        if (k < g.nz - 1) {  // z face between c and c+Z (interior faces only)
+          long L = c, R = c + Z;
+          T W = w[c];
+          T Gf = half * (G[L] + G[R]);
+          T A = (P[R] - P[L]) / (P[R] + P[L] + eps);
+          T Bx = half * (P[R + X] + P[L + X] - P[R - X] - P[L - X]) /
+                 (P[R + X] + P[L + X] + P[R - X] + P[L - X] + eps);
+          T By = half * (P[R + Y] + P[L + Y] - P[R - Y] - P[L - Y]) /
+                 (P[R + Y] + P[L + Y] + P[R - Y] + P[L - Y] + eps);
+          T Ub = quarter * (u[L] + u[R] + u[L - X] + u[R - X]);
+          T Vb = quarter * (v[L] + v[R] + v[L - Y] + v[R - Y]);
+          wt[c] = (oabs(W) - W * W / Gf) * A - W * (Ub * Bx + Vb * By) / Gf;
+        } else {
+          wt[c] = T(0.0);
+        }
+      }
+}
+
+/* Non-oscillatory limiter (Smolarkiewicz & Grabowski 1990), G-weighted.
+   Bounds over the 7-point stencil of both psi^n (P0) and psi^(m-1) (P);
+   unlimited antidiffusive fluxes f = F(P_L, P_R, Ut); incoming and outgoing
+   flux sums; beta-up = (max - P) G / (in + eps), beta-down =
+   (P - min) G / (out + eps); output: betas (halo-filled) in bu, bd. */
+template <class T>
+void limiter_betas(const Grid& g, const T* P0, const T* P, const T* ut, const T* vt, const T* wt,
+                   const T* G, T* mx, T* mn, T* bu, T* bd) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+  const T eps(EPS), zero(0.0);
+  const long nb[6] = {-X, X, -Y, Y, -Z, Z};
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        T hi = P0[c], lo = P0[c];
+        hi = omax(hi, P[c]);
+        lo = omin(lo, P[c]);
+        for (int q = 0; q < 6; ++q) {
+          hi = omax(hi, P0[c + nb[q]]);
+          hi = omax(hi, P[c + nb[q]]);
+          lo = omin(lo, P0[c + nb[q]]);
+          lo = omin(lo, P[c + nb[q]]);
+        }
+        mx[c] = hi;
+        mn[c] = lo;
+        // fluxes through the six faces: the "+" faces and the "-" faces
+        T fxp = donor(P[c], P[c + X], ut[c]);
+        T fxm = donor(P[c - X], P[c], ut[c - X]);
+        T fyp = donor(P[c], P[c + Y], vt[c]);
+        T fym = donor(P[c - Y], P[c], vt[c - Y]);
+        T fzp = donor(P[c], P[c + Z], wt[c]);
+        T fzm = donor(P[c - Z], P[c], wt[c - Z]);
+        T in = (omax(fxm, zero) - omin(fxp, zero)) + (omax(fym, zero) - omin(fyp, zero)) +
+               (omax(fzm, zero) - omin(fzp, zero));
+        T out = (omax(fxp, zero) - omin(fxm, zero)) + (omax(fyp, zero) - omin(fym, zero)) +
+                (omax(fzp, zero) - omin(fzm, zero));
+        bu[c] = (hi - P[c]) * G[c] / (in + eps);
+        bd[c] = (P[c] - lo) * G[c] / (out + eps);
+      }
+  fill_halo_periodic(bu, g);
+  fill_halo_periodic(bd, g);
+}
+
+/* Limited velocity on the face between L and R:
+   min(1, bd_L, bu_R) max(Ut,0) + min(1, bu_L, bd_R) min(Ut,0). */
+template <class T> inline T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
+  const T one(1.0), zero(0.0);
+  T cpos = omin(omin(one, bdL), buR);
+  T cneg = omin(omin(one, buL), bdR);
+  return cpos * omax(Ut, zero) + cneg * omin(Ut, zero);
+}
+
+template <class T>
+void limit_velocities(const Grid& g, const T* ut, const T* vt, const T* wt, const T* bu,
+                      const T* bd, T* ul, T* vl, T* wl) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        ul[c] = limit_face(ut[c], bu[c], bd[c], bu[c + X], bd[c + X]);
+        vl[c] = limit_face(vt[c], bu[c], bd[c], bu[c + Y], bd[c + Y]);
+        wl[c] = (k < g.nz - 1) ? limit_face(wt[c], bu[c], bd[c], bu[c + Z], bd[c + Z]) : T(0.0);
+      }
+}
+
+/* Intermediates of the last corrective pass, for staged comparisons. */
+struct Stages {
+  double *psi1, *ut, *vt, *wt, *mx, *mn, *bu, *bd, *ul, *vl, *wl;
+};
+
+template <class T> void copy_out(double* dst, const std::vector<T>& src) {
+  if (!dst) return;
+  for (size_t q = 0; q < src.size(); ++q) dst[q] = val(src[q]);
+}
+
+/* One MPDATA step.  Inputs are read at their interior points only. */
+template <class T>
+void mpdata_step(const Grid& g, int iord, int nonosc, const T* psi_in, const T* Uin,
+                 const T* Vin, const T* Win, const T* Gin, T* psi_out, const Stages* st) {
+  const long n = g.size();
+  std::vector<T> P0(n), P(n), Pn(n), U(n), V(n), W(n), G(n);
+  std::vector<T> ut(n), vt(n), wt(n), ul(n), vl(n), wl(n), mx(n), mn(n), bu(n), bd(n);
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        P0[c] = psi_in[c]; U[c] = Uin[c]; V[c] = Vin[c]; W[c] = Win[c]; G[c] = Gin[c];
+      }
+  // 1. halos and the zero-flux vertical boundary
+  fill_halo_periodic(P0.data(), g);
+  fill_halo_periodic(U.data(), g);
+  fill_halo_periodic(V.data(), g);
+  fill_halo_periodic(G.data(), g);
+  fill_halo_wface(W.data(), g);
+  // 2. donor-cell pass
+  advance(g, P0.data(), U.data(), V.data(), W.data(), G.data(), P.data());
+  fill_halo_periodic(P.data(), g);
+  if (st) copy_out(st->psi1, P);
+  // 3. corrective passes
+  const T *cu = U.data(), *cv = V.data(), *cw = W.data();
+  for (int m = 2; m <= iord; ++m) {
+    pseudo_velocity(g, P.data(), cu, cv, cw, G.data(), ut.data(), vt.data(), wt.data());
+    fill_halo_periodic(ut.data(), g);
+    fill_halo_periodic(vt.data(), g);
+    fill_halo_wface(wt.data(), g);
+    if (nonosc) {
+      limiter_betas(g, P0.data(), P.data(), ut.data(), vt.data(), wt.data(), G.data(), mx.data(),
+                    mn.data(), bu.data(), bd.data());
+      limit_velocities(g, ut.data(), vt.data(), wt.data(), bu.data(), bd.data(), ul.data(),
+                       vl.data(), wl.data());
+    } else {
+      std::copy(ut.begin(), ut.end(), ul.begin());
+      std::copy(vt.begin(), vt.end(), vl.begin());
+      std::copy(wt.begin(), wt.end(), wl.begin());
+    }
+    fill_halo_periodic(ul.data(), g);
+    fill_halo_periodic(vl.data(), g);
+    fill_halo_wface(wl.data(), g);
+    advance(g, P.data(), ul.data(), vl.data(), wl.data(), G.data(), Pn.data());
+    fill_halo_periodic(Pn.data(), g);
+    if (st && m == iord) {
+      copy_out(st->ut, ut); copy_out(st->vt, vt); copy_out(st->wt, wt);
+      copy_out(st->mx, mx); copy_out(st->mn, mn); copy_out(st->bu, bu); copy_out(st->bd, bd);
+      copy_out(st->ul, ul); copy_out(st->vl, vl); copy_out(st->wl, wl);
+    }
+    P.swap(Pn);
+    // the next pass (iord >= 3) takes the limited velocities of this one
+    cu = ul.data(); cv = vl.data(); cw = wl.data();
+  }
+  for (long q = 0; q < n; ++q) psi_out[q] = P[q];
+}
+
+}  // namespace
+
+/* =============================================================== C ABI */
+
+extern "C" {
+
+int orc_version() { return 1; }
+
+/* Halo fill.  kind 0: cell/horizontal-face field (periodic i-j, k copy);
+   kind 1: vertical-face field (periodic i-j, zero boundary faces). */
+void orc_fill_halo(int nx, int ny, int nz, int h, int kind, double* f) {
+  Grid g(nx, ny, nz, h);
+  if (kind == 1) fill_halo_wface(f, g); else fill_halo_periodic(f, g);
+}
+
+/* nsteps MPDATA steps; psi_out gets the padded result with its halo filled.
+   The optional stage pointers (may be null) receive the intermediates of the
+   last corrective pass of the last step. */
+void orc_run(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps,
+             const double* psi_in, const double* U, const double* V, const double* W,
+             const double* G, double* psi_out, double* psi1, double* ut, double* vt, double* wt,
+             double* mx, double* mn, double* bu, double* bd, double* ul, double* vl, double* wl) {
+  Grid g(nx, ny, nz, h);
+  Stages st{psi1, ut, vt, wt, mx, mn, bu, bd, ul, vl, wl};
+  std::vector<double> cur(psi_in, psi_in + g.size()), nxt(g.size());
+  for (int s = 0; s < nsteps; ++s) {
+    mpdata_step<double>(g, iord, nonosc, cur.data(), U, V, W, G, nxt.data(),
+                        s == nsteps - 1 ? &st : nullptr);
+    cur.swap(nxt);
+  }
+  std::memcpy(psi_out, cur.data(), sizeof(double) * g.size());
+}
+
+/* Pseudo-velocities of a given field P with Courant fields U, V, W. */
+void orc_pseudo_velocity(int nx, int ny, int nz, int h, const double* Pin, const double* Uin,
+                         const double* Vin, const double* Win, const double* Gin, double* ut,
+                         double* vt, double* wt) {
+  Grid g(nx, ny, nz, h);
+  long n = g.size();
+  std::vector<double> P(Pin, Pin + n), U(Uin, Uin + n), V(Vin, Vin + n), W(Win, Win + n),
+      G(Gin, Gin + n);
+  fill_halo_periodic(P.data(), g);
+  fill_halo_periodic(U.data(), g);
+  fill_halo_periodic(V.data(), g);
+  fill_halo_periodic(G.data(), g);
+  fill_halo_wface(W.data(), g);
+  pseudo_velocity(g, P.data(), U.data(), V.data(), W.data(), G.data(), ut, vt, wt);
+}
+
+/* Mass sum_interior psi * G, summed in (k, j, i) order. */
+double orc_mass(int nx, int ny, int nz, int h, const double* psi, const double* G) {
+  Grid g(nx, ny, nz, h);
+  double s = 0.0;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) s += psi[g.at(i, j, k)] * G[g.at(i, j, k)];
+  return s;
+}
+
+/* Tangent-linear model of nsteps steps (dual numbers through the forward
+   code): returns psi_out and its directional derivative dpsi_out along
+   (dpsi, dU, dV, dW).  G is held fixed. */
+void orc_tlm(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps, const double* psi,
+             const double* U, const double* V, const double* W, const double* G,
+             const double* dpsi, const double* dU, const double* dV, const double* dW,
+             double* psi_out, double* dpsi_out) {
+  Grid g(nx, ny, nz, h);
+  long n = g.size();
+  std::vector<Dual> p(n), u(n), v(n), w(n), gg(n), o(n);
+  for (long q = 0; q < n; ++q) {
+    p[q] = Dual(psi[q], dpsi[q]);
+    u[q] = Dual(U[q], dU[q]);
+    v[q] = Dual(V[q], dV[q]);
+    w[q] = Dual(W[q], dW[q]);
+    gg[q] = Dual(G[q], 0.0);
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    mpdata_step<Dual>(g, iord, nonosc, p.data(), u.data(), v.data(), w.data(), gg.data(),
+                      o.data(), nullptr);
+    p.swap(o);
+  }
+  for (long q = 0; q < n; ++q) { psi_out[q] = p[q].v; dpsi_out[q] = p[q].d; }
+}
+
+}  // extern "C"
