@@ -1,3 +1,408 @@
-"""placeholder"""
-def table2_accesses(nodes, edges, fused):
-    return nodes * 5 if fused else edges * 2 + nodes * 10
+"""MPDATA step benchmark: grid-point updates per second on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload latlon256_f64|latlon512_f32] [--no-extras]
+
+A step is one MPDATA time step (donor cell + iord-1 limited corrective
+passes, halo of the result included) plus the FP64 mass reduction, on the
+3D lat-lon configuration: 256x256x64, halo 2, FP64, iord 2, non-oscillatory,
+G = cos(lat), deformational flow with weak w, Gaussian + step tracer
+(synthetic, seeded).  Inputs are resident in HBM when timing starts; the
+five input fields (5 x 36.8 MB) exceed the 126 MB L2, so no flush is used.
+
+Under torchrun each rank advances its own replica of the workload (the
+configurations are independent problems; no data-path collective), the
+timed region is bracketed by a barrier and device syncs, and the slowest
+rank's time is used: value = total updates of all ranks / max time.
+
+--impl reference times the CPU oracle (plain FP64 C++, OpenMP over k) on the
+host cores on the same workload, as the comparison arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MPDATA grid-point updates/s"
+UNIT = "updates/s"
+
+WORKLOADS = {
+    "latlon256_f64": dict(nx=256, ny=256, nz=64, halo=2, dtype="f64", iord=2, nonosc=1,
+                          config_steps=50),
+    "latlon512_f32": dict(nx=512, ny=512, nz=128, halo=2, dtype="f32", iord=2, nonosc=1,
+                          config_steps=100),
+}
+
+# Algorithmic words per interior point moved by each kernel stage (reads +
+# writes of whole fields the stage must touch; neighbour re-reads are not
+# counted).  The whole step needs 6 (read psi, U, V, W, G; write psi).
+STAGE_WORDS = {
+    "donor": 7,      # psi, U, V, W -> fx, fy, fz
+    "advance": 6,    # psi, fx, fy, fz, G -> psi'
+    "pseudo": 8,     # psi1, U, V, W, G -> Ut, Vt, Wt
+    "beta": 8,       # psi^n, psi1, Ut, Vt, Wt, G -> beta_up, beta_down
+    "limit": 9,      # psi1, Ut, Vt, Wt, beta x2 -> fx, fy, fz
+    "mass": 2,       # psi, G
+    "halo": 0,
+    "fused": 7,      # psi^n, psi1, U, V, W, G -> psi^(n+1)
+    "fused_donor": 6,  # psi^n, U, V, W, G -> psi1
+}
+STEP_WORDS = 6
+
+
+def table2_accesses(nodes: int, edges: int, fused: bool) -> int:
+    """Main-memory accesses per vertical plane for the MPDATA fluxes with the
+    counting of Table 2: unfused 1 r + 1 w per edge and 7 r + 3 w per node;
+    fused 4 r + 1 w per node."""
+    return nodes * (4 + 1) if fused else edges * (1 + 1) + nodes * (7 + 3)
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples, stamped with the host clock."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        rows = [p for (t, p) in self.samples if t0 <= t <= t1]
+        if not rows:   # region shorter than the sampling period: take the nearest
+            rows = [p for (t, p) in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[4 + q].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# -------------------------------------------------------------- our arm --
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1908_06094_b300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_from_profiles(stage: str, workload: str, src_hash: str):
+    """DRAM bytes per launch of a stage from a committed ncu summary, only if
+    it was taken on the current kernel sources (same source hash)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    try:
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            st, wl, h, b = line.split()[:4]
+            if st == stage and wl == workload and h == src_hash:
+                return float(b)
+    except OSError:
+        pass
+    return None
+
+
+def _oracle_rate(wl, seconds: float, psi, fields, h):
+    """Updates/s of the CPU oracle on the full workload grid, stepping until
+    ``seconds`` have passed (at least one step)."""
+    import oracle
+    n = wl["nx"] * wl["ny"] * wl["nz"]
+    cur = psi
+    steps = 0
+    t0 = time.perf_counter()
+    while True:
+        cur = oracle.run(cur, *fields, h=h, iord=wl["iord"], nonosc=wl["nonosc"], nsteps=1)
+        steps += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return steps * n / dt, steps
+
+
+def run_ours(args, wl_name):
+    import numpy as np
+    import torch
+    import synth
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+
+    from paper_1908_06094_b300 import MPDATA, _capi
+
+    wl = WORKLOADS[wl_name]
+    dt = torch.float64 if wl["dtype"] == "f64" else torch.float32
+    h = wl["halo"]
+    case = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=1234 + rank)
+    padded = [synth.pad(x, h) for x in (case.psi, case.u, case.v, case.w, case.g)]
+    if dt == torch.float32:
+        padded = [x.astype(np.float32) for x in padded]
+    d = [torch.from_numpy(x).to(dev).contiguous() for x in padded]
+    m = MPDATA(wl["nx"], wl["ny"], wl["nz"], halo=h, iord=wl["iord"],
+               nonoscillatory=wl["nonosc"], dtype=dt, device=dev)
+    if args.variant is not None:
+        m.set_variant(args.variant)
+    mass_out = torch.empty((), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    npts = wl["nx"] * wl["ny"] * wl["nz"]
+
+    def step():
+        m.step(*d, nsteps=1)
+        m.mass(d[0], d[4], out=mass_out)
+
+    m0 = m.mass(d[0], d[4]).item()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(dev.index or 0) if rank == 0 else None
+    time.sleep(0.3 if sampler else 0.0)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    launches0 = _capi.mpdata_launch_count(m._ctx)
+    _capi.mpdata_profile(m._ctx, True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    wall0 = time.time()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    wall1 = time.time()
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = _capi.mpdata_launch_count(m._ctx) - launches0
+    stage_ms = {}
+    for name, sid in _capi.STAGES.items():
+        t, k = _capi.mpdata_profile_read(m._ctx, sid)
+        if k:
+            stage_ms[name] = (t, k)
+    _capi.mpdata_profile(m._ctx, False)
+    m1 = mass_out.item()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    clocks = None
+    if sampler:
+        sampler.stop()
+        clocks = sampler.summary(wall0, wall1)
+
+    value = ws * npts * args.steps / (ms / 1e3)
+    out = None
+    if rank == 0:
+        hbm, peak_kind = _peaks()
+        dom = max(stage_ms, key=lambda s: stage_ms[s][0]) if stage_ms else None
+        esize = 8 if dt == torch.float64 else 4
+        roof = None
+        if dom:
+            t, k = stage_ms[dom]
+            per_launch_ms = t / k
+            bytes_launch = STAGE_WORDS[dom] * esize * npts
+            achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
+            src = _source_hash()
+            traffic = _traffic_from_profiles(dom, wl_name, src)
+            roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                    "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                    "traffic": traffic, "algorithmic_bytes": bytes_launch,
+                    "launch_ms": round(per_launch_ms, 5), "peak_source": peak_kind,
+                    "stage_share": {s: round(v[0] / sum(x[0] for x in stage_ms.values()), 4)
+                                    for s, v in stage_ms.items()}}
+        step_bytes = STEP_WORDS * esize * npts
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"],
+            "data": "synthetic (seeded lat-lon deformational flow, Gaussian + step tracer)",
+            "config": {"workload": f"latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']} halo {h} "
+                                   f"{wl['dtype']} iord={wl['iord']} nonoscillatory",
+                       "nx": wl["nx"], "ny": wl["ny"], "nz": wl["nz"], "halo": h,
+                       "iord": wl["iord"], "nonoscillatory": wl["nonosc"],
+                       "step": "one MPDATA step + FP64 mass reduction",
+                       "l2": "no flush: the 5 input fields (%.0f MB) exceed the 126 MB L2"
+                             % (5 * esize * padded[0].size / 1e6),
+                       "variant": "staged" if args.variant == 1 else "default",
+                       "parallelism": f"replicas x{ws}"},
+            "hbm_roofline_frac_step": round(value / ws * step_bytes / npts / 1e9 / hbm, 4),
+            "roofline": roof,
+            "gpu_launches": launches,
+            "mass_drift_rel": abs(m1 - m0) / abs(m0) if m0 else None,
+            "clocks": clocks,
+        }
+    # end-to-end through the HOST-buffer C call
+    if rank == 0 and not args.no_extras:
+        host = [torch.from_numpy(x.copy()).pin_memory() for x in padded]
+        k = max(3, min(args.steps, 20))
+        m.step_host(*host, nsteps=1)
+        t0 = time.perf_counter()
+        for _ in range(k):
+            m.step_host(*host, nsteps=1)
+        e2e_s = time.perf_counter() - t0
+        fb = padded[0].nbytes
+        out["e2e"] = {"value": npts * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 5 * fb,
+                      "d2h_bytes_per_step": fb,
+                      "path": "mpdata_step_host: pinned host psi,U,V,W,G -> device, 1 step, "
+                              "psi -> host, per step"}
+        # CPU baseline: the oracle as it stands, all host cores, bounded sample
+        ncores = os.cpu_count() or 1
+        cpu_rate, cpu_steps = _oracle_rate(wl, args.cpu_seconds, padded[0].astype("float64"),
+                                           [x.astype("float64") for x in padded[1:]], h)
+        out["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": ncores,
+                               "kind": "oracle",
+                               "sample": f"{cpu_steps} full steps of the same workload "
+                                         f"(OMP_NUM_THREADS={os.environ.get('OMP_NUM_THREADS', ncores)})"}
+    m.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+# --------------------------------------------------------- reference arm --
+
+def run_reference(args, wl_name):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle
+    import synth
+    wl = WORKLOADS[wl_name]
+    h = wl["halo"]
+    case = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=1234)
+    P = [synth.pad(x, h) for x in (case.psi, case.u, case.v, case.w, case.g)]
+    if wl["dtype"] == "f32":
+        P = [x.astype(np.float32).astype(np.float64) for x in P]
+    npts = wl["nx"] * wl["ny"] * wl["nz"]
+    # each step is a bounded sample of the workload: the full grid if one
+    # oracle step is short, else a slab of levels
+    nz_s = wl["nz"]
+    t0 = time.perf_counter()
+    oracle.run(*P, h=h, iord=wl["iord"], nonosc=wl["nonosc"], nsteps=1)
+    one = time.perf_counter() - t0
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    if one > budget:
+        nz_s = max(2, int(wl["nz"] * budget / one))
+        case = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=1234)
+        P = [synth.pad(x[:nz_s], h) for x in (case.psi, case.u, case.v, case.w, case.g)]
+        P[3][h + nz_s - 1] = 0.0
+    cur = P[0]
+    for _ in range(args.warmup):
+        cur = oracle.run(cur, *P[1:], h=h, iord=wl["iord"], nonosc=wl["nonosc"], nsteps=1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cur = oracle.run(cur, *P[1:], h=h, iord=wl["iord"], nonosc=wl["nonosc"], nsteps=1)
+    el = time.perf_counter() - t0
+    n_s = wl["nx"] * wl["ny"] * nz_s
+    value = n_s * args.steps / el
+    ncores = os.cpu_count() or 1
+    sample = (f"{'full grid' if nz_s == wl['nz'] else f'{nz_s}-level slab'} "
+              f"{wl['nx']}x{wl['ny']}x{nz_s}, one step per bench step")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)",
+            "config": {"workload": f"latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']} halo {h} "
+                                   f"{wl['dtype']} iord={wl['iord']} nonoscillatory",
+                       "nx": wl["nx"], "ny": wl["ny"], "nz": wl["nz"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="latlon256_f64", choices=sorted(WORKLOADS))
+    ap.add_argument("--variant", type=int, default=None, help="0 fused, 1 staged")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the e2e and CPU-baseline legs")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    out = run_reference(args, args.workload) if args.impl == "reference" else \
+        run_ours(args, args.workload)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

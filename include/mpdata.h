@@ -1,0 +1,173 @@
+/*
+ * mpdata.h -- C ABI of libmpdata_b300.so, a B300 (sm_103a) implementation of
+ * one MPDATA advection time step on a structured, halo-padded 3D grid.
+ *
+ * The step (what the paper's MPDATA dwarf computes; Sec. 5, Listings 4-9):
+ *   1. donor-cell pass: F(L,R,C) = max(C,0) L + min(C,0) R on the three face
+ *      families (Listings 4/5 horizontally, Listing 7 vertically), then the
+ *      flux divergence and solution advance psi1 = psi - (1/G) sum dF
+ *      (Listings 8/9, G in the role of the density);
+ *   2. iord-1 corrective passes: the antidiffusive pseudo-velocity
+ *      Ut = (|U| - U^2/Gf) A - U (Vbar By + Wbar Bz)/Gf (Smolarkiewicz 1984,
+ *      G-weighted per Smolarkiewicz & Margolin 1998; the paper defers these
+ *      formulas to its companion deliverable, Sec. 5), optionally limited by
+ *      the non-oscillatory option (Smolarkiewicz & Grabowski 1990), then the
+ *      same flux divergence and advance.
+ * Boundaries: periodic in i and j; the bottom face (k = -1/2) and the top
+ * face (k = nz-1/2) carry no flux (the boundary factor pivbz = 0 of
+ * Listing 7) whatever W holds there.  epsilon = 1e-15 in every ratio.
+ *
+ * Layout (every field, every call): a C-contiguous array
+ * [nz+2h][ny+2h][nx+2h] of the context's dtype, i fastest, interior point
+ * (i,j,k) at ((k+h)(ny+2h) + (j+h))(nx+2h) + (i+h).  Staggering follows the
+ * C-grid convention of Sec. 3.1.4.1: U[k][j][i] is the face i+1/2, V[k][j][i]
+ * the face j+1/2, W[k][j][i] the face k+1/2.  U, V, W are G-weighted Courant
+ * numbers (mass fluxes in Courant units: U = G_face u dt/dx).
+ *
+ * Inputs are read at interior points only: the library applies the periodic
+ * and closed boundaries itself, so input halos may hold anything.  Output
+ * psi is written at interior points and its halo is filled (periodic in i
+ * and j, edge copy in k), so the result is a consistent padded field.
+ *
+ * Pointers: field pointers are DEVICE pointers (cudaMalloc / torch CUDA
+ * tensors) on the context's device, 16-byte aligned, unless a function says
+ * HOST.  The caller owns every field buffer; the context owns only its
+ * scratch memory, allocated in mpdata_init and freed in mpdata_destroy.
+ *
+ * Streams and errors: every call is asynchronous on the stream given to
+ * mpdata_init (or mpdata_set_stream); none allocates or synchronises, except
+ * the HOST-buffer call.  Arguments are checked on the host before any
+ * launch; errors are negative return codes (never an abort or a device
+ * trap).  A failure reported by the CUDA runtime returns MPDATA_ECUDA and
+ * the runtime's message is kept for mpdata_last_error_string().
+ */
+#ifndef MPDATA_B300_H
+#define MPDATA_B300_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define MPDATA_API __attribute__((visibility("default")))
+#else
+#define MPDATA_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpdata_ctx mpdata_ctx; /* opaque, library-owned */
+
+enum mpdata_status {
+  MPDATA_OK = 0,
+  MPDATA_EINVAL = -1,  /* bad size, option or null pointer              */
+  MPDATA_ENOMEM = -2,  /* scratch allocation failed                     */
+  MPDATA_ECUDA = -3,   /* the CUDA runtime reported an error            */
+  MPDATA_EALIGN = -4,  /* a field pointer is not 16-byte aligned        */
+  MPDATA_EDEVICE = -5, /* no usable device                              */
+  MPDATA_ERANGE = -6   /* a size beyond a documented maximum            */
+};
+
+enum mpdata_dtype { MPDATA_F64 = 0, MPDATA_F32 = 1 };
+enum mpdata_kbc { MPDATA_K_ZEROFLUX = 0 };
+enum mpdata_halo_kind {
+  MPDATA_HALO_CELL = 0,  /* psi, G, U, V: periodic i-j, edge copy in k   */
+  MPDATA_HALO_WFACE = 1  /* W: periodic i-j, closed faces (zero) in k    */
+};
+enum mpdata_variant {
+  MPDATA_FUSED = 0,  /* default: fused kernels, intermediates on chip     */
+  MPDATA_STAGED = 1  /* one kernel per stage, intermediates in memory     */
+};
+
+/* Create a context for one grid.
+ *   nx, ny, nz  interior sizes, each >= 1 (nz = 1 is a 2D problem);
+ *   halo        h >= 1, and h >= 2 when iord >= 2 (the radius a corrective
+ *               pass reads, so the output stays usable by h-radius stencils);
+ *   iord        number of passes, 1 (donor cell only) to 8;
+ *   nonoscillatory  0 or 1 (the limiter of every corrective pass);
+ *   dtype       MPDATA_F64 or MPDATA_F32 (storage and arithmetic);
+ *   k_bc        MPDATA_K_ZEROFLUX (closed top and bottom, Listing 7);
+ *   cuda_stream a cudaStream_t (NULL = the legacy default stream).
+ * Allocates the scratch of one step on the current device.
+ * Errors: EINVAL (sizes/options/out == NULL), EDEVICE, ENOMEM. */
+MPDATA_API int mpdata_init(mpdata_ctx **out, int nx, int ny, int nz, int halo, int iord,
+                int nonoscillatory, int dtype, int k_bc, void *cuda_stream);
+
+/* Change the stream later calls are issued on. Errors: EINVAL. */
+MPDATA_API int mpdata_set_stream(mpdata_ctx *c, void *cuda_stream);
+
+/* Choose the kernel organisation (mpdata_variant); both give the same
+ * step to rounding.  Errors: EINVAL. */
+MPDATA_API int mpdata_set_variant(mpdata_ctx *c, int variant);
+
+/* Advance psi (in/out, device) by nsteps MPDATA steps with Courant fields
+ * u, v, w and metric g (device, read-only).  nsteps >= 0.
+ * Errors: EINVAL (null pointer, nsteps < 0), EALIGN, ECUDA. */
+MPDATA_API int mpdata_step(mpdata_ctx *c, void *psi, const void *u, const void *v, const void *w,
+                const void *g, int nsteps);
+
+/* The same from HOST buffers: copies psi, u, v, w, g (padded, HOST) to
+ * context-owned device buffers, runs nsteps steps, copies psi back to the
+ * HOST buffer and waits for the stream.  The device buffers are allocated on
+ * the first call (the only call besides init that allocates).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+MPDATA_API int mpdata_step_host(mpdata_ctx *c, void *psi_host, const void *u_host, const void *v_host,
+                     const void *w_host, const void *g_host, int nsteps);
+
+/* Fill the halo of a padded field in place (kind: mpdata_halo_kind).
+ * Periodic in i and j, corners included; in k an edge copy (CELL) or zero
+ * (WFACE, which also zeroes the top face k = nz-1).
+ * This is the boundary-condition component of Sec. 3.1.1, item 2.
+ * Errors: EINVAL, EALIGN, ECUDA. */
+MPDATA_API int mpdata_fill_halo(mpdata_ctx *c, void *field, int kind);
+
+/* Mass: the sum over the interior of psi*G, accumulated in FP64 for either
+ * dtype with a deterministic two-level reduction (fixed partition and fixed
+ * tree order, so repeated calls give identical bits); the result is written
+ * to *out_dev, a DEVICE double.  Errors: EINVAL, EALIGN, ECUDA. */
+MPDATA_API int mpdata_mass(mpdata_ctx *c, const void *psi, const void *g, double *out_dev);
+
+/* Instrumentation.  Stage ids of the kernels the library launches. */
+enum mpdata_stage {
+  MPDATA_STAGE_HALO = 0,     /* halo fill of psi (a1)                        */
+  MPDATA_STAGE_DONOR = 1,    /* donor-cell fluxes (a2)                       */
+  MPDATA_STAGE_ADVANCE = 2,  /* flux divergence + advance (a2, a6)           */
+  MPDATA_STAGE_PSEUDO = 3,   /* antidiffusive pseudo-velocities (a3)         */
+  MPDATA_STAGE_BETA = 4,     /* limiter bounds and beta (a4, a5)             */
+  MPDATA_STAGE_LIMIT = 5,    /* limited velocities and fluxes (a6)           */
+  MPDATA_STAGE_MASS = 6,     /* mass reduction (a7)                          */
+  MPDATA_STAGE_FUSED = 7,    /* fused corrective pass (a3-a6)                */
+  MPDATA_STAGE_FUSED_DONOR = 8, /* fused donor pass (a2)                     */
+  MPDATA_NSTAGES = 9
+};
+
+/* Number of kernels this context has launched since it was created. */
+MPDATA_API long long mpdata_launch_count(mpdata_ctx *c);
+
+/* Per-stage timing with CUDA events recorded on the context's stream around
+ * every launch while enabled (enable = 1; 0 stops).  Enabling clears the
+ * totals.  At most 65536 launches are timed; later ones are counted but not
+ * timed.  Errors: EINVAL, ENOMEM, ECUDA. */
+MPDATA_API int mpdata_profile(mpdata_ctx *c, int enable);
+
+/* Waits for the stream, then returns the summed event time (ms) and number
+ * of timed launches of one stage.  Errors: EINVAL, ECUDA. */
+MPDATA_API int mpdata_profile_read(mpdata_ctx *c, int stage, double *ms, int *launches);
+
+/* Destroy a context and free its scratch (NULL is ignored). */
+MPDATA_API void mpdata_destroy(mpdata_ctx *c);
+
+/* Static description of a status code. */
+MPDATA_API const char *mpdata_strerror(int code);
+
+/* The CUDA runtime's message for the last MPDATA_ECUDA on this context. */
+MPDATA_API const char *mpdata_last_error_string(mpdata_ctx *c);
+
+/* Library version (major*10000 + minor*100 + patch). */
+MPDATA_API int mpdata_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPDATA_B300_H */

@@ -1,0 +1,22 @@
+"""B300-native MPDATA step: a C-ABI CUDA library (libmpdata_b300.so) and a
+thin Python binding over it.
+
+* ``_capi``   -- ctypes binding, one function per C entry point;
+* ``MPDATA``  -- the same calls taking torch CUDA tensors (pointer and stream
+  marshalling only: every step of the method runs in the library's kernels).
+
+The library is loaded on first use of either; a missing or unloadable
+library raises ImportError (there is no fallback path).
+"""
+import importlib
+
+__all__ = ["_capi", "MPDATA", "padded_shape"]
+
+
+def __getattr__(name):
+    if name == "_capi":
+        return importlib.import_module("._capi", __name__)
+    if name in ("MPDATA", "padded_shape"):
+        mod = importlib.import_module(".mpdata", __name__)
+        return getattr(mod, name)
+    raise AttributeError(name)

@@ -1,0 +1,147 @@
+"""ctypes binding of libmpdata_b300.so: the C ABI of include/mpdata.h, one
+Python function per C function, same names, argument marshalling only.
+
+There is no fallback: if the library is missing or does not load, importing
+this module raises.  Build it with ``python -m paper_1908_06094_b300.build``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libmpdata_b300.so")
+
+MPDATA_OK = 0
+MPDATA_EINVAL = -1
+MPDATA_ENOMEM = -2
+MPDATA_ECUDA = -3
+MPDATA_EALIGN = -4
+MPDATA_EDEVICE = -5
+MPDATA_ERANGE = -6
+MPDATA_F64 = 0
+MPDATA_F32 = 1
+MPDATA_K_ZEROFLUX = 0
+MPDATA_HALO_CELL = 0
+MPDATA_HALO_WFACE = 1
+MPDATA_FUSED = 0
+MPDATA_STAGED = 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libmpdata_b300.so not built (expected at {LIB_PATH}); "
+                      "run `python -m paper_1908_06094_b300.build`")
+
+lib = ctypes.CDLL(LIB_PATH)
+
+_c = ctypes.c_void_p
+_i = ctypes.c_int
+_ctxpp = ctypes.POINTER(ctypes.c_void_p)
+
+# symbol -> (restype, argtypes); the list is the ABI that include/mpdata.h declares
+SIGNATURES = {
+    "mpdata_init": (_i, [_ctxpp, _i, _i, _i, _i, _i, _i, _i, _i, _c]),
+    "mpdata_set_stream": (_i, [_c, _c]),
+    "mpdata_set_variant": (_i, [_c, _i]),
+    "mpdata_step": (_i, [_c, _c, _c, _c, _c, _c, _i]),
+    "mpdata_step_host": (_i, [_c, _c, _c, _c, _c, _c, _i]),
+    "mpdata_fill_halo": (_i, [_c, _c, _i]),
+    "mpdata_mass": (_i, [_c, _c, _c, _c]),
+    "mpdata_destroy": (None, [_c]),
+    "mpdata_strerror": (ctypes.c_char_p, [_i]),
+    "mpdata_last_error_string": (ctypes.c_char_p, [_c]),
+    "mpdata_version": (_i, []),
+    "mpdata_launch_count": (ctypes.c_longlong, [_c]),
+    "mpdata_profile": (_i, [_c, _i]),
+    "mpdata_profile_read": (_i, [_c, _i, ctypes.POINTER(ctypes.c_double),
+                                 ctypes.POINTER(ctypes.c_int)]),
+}
+
+STAGES = {"halo": 0, "donor": 1, "advance": 2, "pseudo": 3, "beta": 4, "limit": 5, "mass": 6,
+          "fused": 7, "fused_donor": 8}
+
+for _name, (_res, _args) in SIGNATURES.items():
+    _f = getattr(lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+class MPDATAError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: {mpdata_strerror(code)} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+def _check(rc: int, where: str, ctx=None) -> None:
+    if rc != MPDATA_OK:
+        detail = mpdata_last_error_string(ctx) if (ctx and rc == MPDATA_ECUDA) else ""
+        raise MPDATAError(rc, where, detail)
+
+
+def mpdata_strerror(code: int) -> str:
+    return lib.mpdata_strerror(code).decode()
+
+
+def mpdata_last_error_string(ctx) -> str:
+    return lib.mpdata_last_error_string(ctx).decode()
+
+
+def mpdata_version() -> int:
+    return lib.mpdata_version()
+
+
+def mpdata_init(nx, ny, nz, halo, iord, nonoscillatory, dtype, k_bc=MPDATA_K_ZEROFLUX,
+                cuda_stream=0):
+    """Returns an opaque context handle (int); raises MPDATAError on failure."""
+    out = ctypes.c_void_p()
+    rc = lib.mpdata_init(ctypes.byref(out), nx, ny, nz, halo, iord, nonoscillatory, dtype, k_bc,
+                         cuda_stream)
+    _check(rc, "mpdata_init")
+    return out.value
+
+
+def mpdata_set_stream(ctx, cuda_stream):
+    _check(lib.mpdata_set_stream(ctx, cuda_stream), "mpdata_set_stream", ctx)
+
+
+def mpdata_set_variant(ctx, variant):
+    _check(lib.mpdata_set_variant(ctx, variant), "mpdata_set_variant", ctx)
+
+
+def mpdata_step(ctx, psi, u, v, w, g, nsteps):
+    _check(lib.mpdata_step(ctx, psi, u, v, w, g, nsteps), "mpdata_step", ctx)
+
+
+def mpdata_step_host(ctx, psi_h, u_h, v_h, w_h, g_h, nsteps):
+    _check(lib.mpdata_step_host(ctx, psi_h, u_h, v_h, w_h, g_h, nsteps), "mpdata_step_host", ctx)
+
+
+def mpdata_fill_halo(ctx, field, kind):
+    _check(lib.mpdata_fill_halo(ctx, field, kind), "mpdata_fill_halo", ctx)
+
+
+def mpdata_mass(ctx, psi, g, out_dev):
+    _check(lib.mpdata_mass(ctx, psi, g, out_dev), "mpdata_mass", ctx)
+
+
+def mpdata_destroy(ctx):
+    lib.mpdata_destroy(ctx)
+
+
+def mpdata_launch_count(ctx) -> int:
+    return lib.mpdata_launch_count(ctx)
+
+
+def mpdata_profile(ctx, enable: bool):
+    _check(lib.mpdata_profile(ctx, int(bool(enable))), "mpdata_profile", ctx)
+
+
+def mpdata_profile_read(ctx, stage: int):
+    """(total ms, timed launches) of one stage since profiling was enabled."""
+    ms = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(lib.mpdata_profile_read(ctx, stage, ctypes.byref(ms), ctypes.byref(n)),
+           "mpdata_profile_read", ctx)
+    return ms.value, n.value

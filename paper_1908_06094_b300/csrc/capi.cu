@@ -1,0 +1,356 @@
+// capi.cu -- the C ABI of libmpdata_b300.so (declared in include/mpdata.h):
+// the context, host-side argument checks, and the per-step launch sequence.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/mpdata.h"
+#include "grid.cuh"
+#include "mass.cuh"
+#include "staged.cuh"
+
+using mpd::Geo;
+
+struct mpdata_ctx {
+  Geo g;
+  int iord, nonosc, dtype, kbc, variant, device;
+  size_t esize;
+  cudaStream_t stream;
+  // scratch of one step (one allocation)
+  void* scratch;
+  void *psi1, *psi2, *fx, *fy, *fz, *ut, *vt, *wt, *bu, *bd, *ul, *vl, *wl;
+  double* part;
+  // device copies for the HOST-buffer call (allocated on its first use)
+  void* hbuf;
+  // instrumentation
+  long long launches;
+  bool prof_on;
+  int prof_n, prof_cap;
+  cudaEvent_t* prof_ev;
+  int* prof_stage;
+  char err[256];
+};
+
+namespace {
+
+int cuda_fail(mpdata_ctx* c, cudaError_t e, const char* where) {
+  if (c) std::snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
+  return MPDATA_ECUDA;
+}
+
+#define MPD_CHECK_LAUNCH(c, where)                      \
+  do {                                                  \
+    cudaError_t e_ = cudaGetLastError();                \
+    if (e_ != cudaSuccess) return cuda_fail(c, e_, where); \
+  } while (0)
+
+// Every kernel launch goes through MPD_LAUNCH: it is counted, and timed with
+// a pair of events on the context's stream while profiling is enabled.
+void prof_begin(mpdata_ctx* c) {
+  if (c->prof_on && c->prof_n < c->prof_cap) cudaEventRecord(c->prof_ev[2 * c->prof_n], c->stream);
+}
+void prof_end(mpdata_ctx* c, int stage) {
+  ++c->launches;
+  if (c->prof_on && c->prof_n < c->prof_cap) {
+    cudaEventRecord(c->prof_ev[2 * c->prof_n + 1], c->stream);
+    c->prof_stage[c->prof_n++] = stage;
+  }
+}
+#define MPD_LAUNCH(c, stage, ...) \
+  do {                            \
+    prof_begin(c);                \
+    __VA_ARGS__;                  \
+    prof_end(c, stage);           \
+  } while (0)
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+dim3 cell_grid(const Geo& g) { return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz); }
+const dim3 kCellBlock(32, 8, 1);
+
+template <class T>
+int halo_launch(mpdata_ctx* c, T* f, int kind) {
+  int64_t n = c->g.total;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_kernel<T><<<blocks, 256, 0, c->stream>>>(c->g, f, kind));
+  MPD_CHECK_LAUNCH(c, "halo_kernel");
+  return MPDATA_OK;
+}
+
+// One MPDATA step, staged organisation (one kernel per stage).
+template <class T>
+int step_staged(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G) {
+  using namespace mpd::staged;
+  const Geo& g = c->g;
+  const dim3 grid = cell_grid(g);
+  cudaStream_t s = c->stream;
+  T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
+  // pass 1: donor cell
+  T* cur = c->iord == 1 ? psi : (T*)c->psi1;
+  MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
+             flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
+  MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+             advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur));
+  MPD_CHECK_LAUNCH(c, "donor pass");
+  // corrective passes
+  const T *cu = U, *cv = V, *cw = W;
+  T* setA[3] = {(T*)c->ut, (T*)c->vt, (T*)c->wt};
+  T* setB[3] = {(T*)c->ul, (T*)c->vl, (T*)c->wl};
+  for (int m = 2; m <= c->iord; ++m) {
+    T** tset = (cu == setA[0]) ? setB : setA;  // unlimited pseudo-velocities
+    T** lset = (tset == setA) ? setB : setA;   // limited ones (next pass's input)
+    const bool more = m < c->iord;
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+               pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, cu, cv, cw, G, tset[0],
+                                                             tset[1], tset[2]));
+    if (c->nonosc) {
+      MPD_LAUNCH(c, MPDATA_STAGE_BETA,
+                 beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, cur, tset[0], tset[1],
+                                                             tset[2], G, (T*)c->bu, (T*)c->bd));
+      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
+                 limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                     g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
+                     more ? lset[0] : nullptr, more ? lset[1] : nullptr,
+                     more ? lset[2] : nullptr));
+    } else {
+      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
+                 flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, tset[0], tset[1], tset[2],
+                                                             fx, fy, fz));
+    }
+    T* dest = !more ? psi : (cur == (T*)c->psi1 ? (T*)c->psi2 : (T*)c->psi1);
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, fx, fy, fz, G, dest));
+    MPD_CHECK_LAUNCH(c, "corrective pass");
+    cur = dest;
+    T** vset = c->nonosc ? lset : tset;
+    cu = vset[0]; cv = vset[1]; cw = vset[2];
+  }
+  return MPDATA_OK;
+}
+
+template <class T>
+int step_n(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G, int nsteps) {
+  if (nsteps == 0) return MPDATA_OK;
+  for (int s = 0; s < nsteps; ++s) {
+    int rc = step_staged<T>(c, psi, U, V, W, G);
+    if (rc) return rc;
+  }
+  return halo_launch<T>(c, psi, MPDATA_HALO_CELL);
+}
+
+template <class T>
+int mass_launch(mpdata_ctx* c, const T* psi, const T* G, double* out) {
+  MPD_LAUNCH(c, MPDATA_STAGE_MASS,
+             mpd::mass_partial_kernel<T><<<mpd::MASS_BLOCKS, mpd::MASS_THREADS, 0, c->stream>>>(
+                 c->g, psi, G, c->part));
+  MPD_LAUNCH(c, MPDATA_STAGE_MASS,
+             mpd::mass_final_kernel<<<1, 1024, 0, c->stream>>>(c->part, mpd::MASS_BLOCKS, out));
+  MPD_CHECK_LAUNCH(c, "mass kernels");
+  return MPDATA_OK;
+}
+
+int check_fields(const void* const* ptrs, int n) {
+  for (int q = 0; q < n; ++q) {
+    if (!ptrs[q]) return MPDATA_EINVAL;
+    if (!aligned16(ptrs[q])) return MPDATA_EALIGN;
+  }
+  return MPDATA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpdata_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+const char* mpdata_strerror(int code) {
+  switch (code) {
+    case MPDATA_OK: return "ok";
+    case MPDATA_EINVAL: return "invalid argument (size, option or null pointer)";
+    case MPDATA_ENOMEM: return "device allocation failed";
+    case MPDATA_ECUDA: return "CUDA runtime error";
+    case MPDATA_EALIGN: return "field pointer not 16-byte aligned";
+    case MPDATA_EDEVICE: return "no usable CUDA device";
+    case MPDATA_ERANGE: return "size beyond the documented maximum";
+    default: return "unknown status";
+  }
+}
+
+const char* mpdata_last_error_string(mpdata_ctx* c) { return c ? c->err : ""; }
+
+int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, int nonosc,
+                int dtype, int k_bc, void* stream) {
+  if (!out) return MPDATA_EINVAL;
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || halo < 1 || iord < 1 || iord > 8) return MPDATA_EINVAL;
+  if (iord >= 2 && halo < 2) return MPDATA_EINVAL;
+  if (nonosc != 0 && nonosc != 1) return MPDATA_EINVAL;
+  if (dtype != MPDATA_F64 && dtype != MPDATA_F32) return MPDATA_EINVAL;
+  if (k_bc != MPDATA_K_ZEROFLUX) return MPDATA_EINVAL;
+  if (nz > 65535) return MPDATA_ERANGE;
+  // padded extents must fit the 32-bit index arithmetic of a row/plane
+  if ((int64_t)(nx + 2 * halo) * (ny + 2 * halo) > (int64_t)1 << 31) return MPDATA_ERANGE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return MPDATA_EDEVICE;
+  mpdata_ctx* c = new (std::nothrow) mpdata_ctx();
+  if (!c) return MPDATA_ENOMEM;
+  std::memset(c, 0, sizeof(*c));
+  c->g = mpd::make_geo(nx, ny, nz, halo);
+  c->iord = iord;
+  c->nonosc = nonosc;
+  c->dtype = dtype;
+  c->kbc = k_bc;
+  c->variant = MPDATA_STAGED;
+  c->device = dev;
+  c->esize = dtype == MPDATA_F64 ? 8 : 4;
+  c->stream = (cudaStream_t)stream;
+  const size_t fbytes = ((size_t)c->g.total * c->esize + 255) & ~(size_t)255;
+  const int nfields = iord >= 2 ? (iord >= 3 ? 13 : 9) : 3;
+  const size_t bytes = fbytes * nfields + sizeof(double) * mpd::MASS_BLOCKS;
+  if (cudaMalloc(&c->scratch, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return MPDATA_ENOMEM;
+  }
+  char* p = (char*)c->scratch;
+  void** slots[13] = {&c->fx, &c->fy, &c->fz, &c->psi1, &c->ut, &c->vt, &c->wt, &c->bu,
+                      &c->bd, &c->psi2, &c->ul, &c->vl, &c->wl};
+  for (int q = 0; q < nfields; ++q) *slots[q] = p + q * fbytes;
+  c->part = (double*)(p + nfields * fbytes);
+  *out = c;
+  return MPDATA_OK;
+}
+
+int mpdata_set_stream(mpdata_ctx* c, void* stream) {
+  if (!c) return MPDATA_EINVAL;
+  c->stream = (cudaStream_t)stream;
+  return MPDATA_OK;
+}
+
+int mpdata_set_variant(mpdata_ctx* c, int variant) {
+  if (!c || (variant != MPDATA_STAGED && variant != MPDATA_FUSED)) return MPDATA_EINVAL;
+  if (variant == MPDATA_FUSED) return MPDATA_EINVAL;  // not available in this build
+  c->variant = variant;
+  return MPDATA_OK;
+}
+
+int mpdata_step(mpdata_ctx* c, void* psi, const void* u, const void* v, const void* w,
+                const void* g, int nsteps) {
+  if (!c || nsteps < 0) return MPDATA_EINVAL;
+  const void* f[5] = {psi, u, v, w, g};
+  int rc = check_fields(f, 5);
+  if (rc) return rc;
+  if (c->dtype == MPDATA_F64)
+    return step_n<double>(c, (double*)psi, (const double*)u, (const double*)v,
+                          (const double*)w, (const double*)g, nsteps);
+  return step_n<float>(c, (float*)psi, (const float*)u, (const float*)v, (const float*)w,
+                       (const float*)g, nsteps);
+}
+
+int mpdata_step_host(mpdata_ctx* c, void* psi_h, const void* u_h, const void* v_h,
+                     const void* w_h, const void* g_h, int nsteps) {
+  if (!c || nsteps < 0 || !psi_h || !u_h || !v_h || !w_h || !g_h) return MPDATA_EINVAL;
+  const size_t fbytes = (size_t)c->g.total * c->esize;
+  const size_t fpad = (fbytes + 255) & ~(size_t)255;
+  if (!c->hbuf) {
+    if (cudaMalloc(&c->hbuf, 5 * fpad) != cudaSuccess) {
+      cudaGetLastError();
+      c->hbuf = nullptr;
+      return MPDATA_ENOMEM;
+    }
+  }
+  char* d = (char*)c->hbuf;
+  const void* src[5] = {psi_h, u_h, v_h, w_h, g_h};
+  for (int q = 0; q < 5; ++q) {
+    cudaError_t e = cudaMemcpyAsync(d + q * fpad, src[q], fbytes, cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  }
+  int rc = mpdata_step(c, d, d + fpad, d + 2 * fpad, d + 3 * fpad, d + 4 * fpad, nsteps);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(psi_h, d, fbytes, cudaMemcpyDeviceToHost, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  return MPDATA_OK;
+}
+
+int mpdata_fill_halo(mpdata_ctx* c, void* field, int kind) {
+  if (!c || (kind != MPDATA_HALO_CELL && kind != MPDATA_HALO_WFACE)) return MPDATA_EINVAL;
+  const void* f[1] = {field};
+  int rc = check_fields(f, 1);
+  if (rc) return rc;
+  if (c->dtype == MPDATA_F64) return halo_launch<double>(c, (double*)field, kind);
+  return halo_launch<float>(c, (float*)field, kind);
+}
+
+int mpdata_mass(mpdata_ctx* c, const void* psi, const void* g, double* out_dev) {
+  if (!c || !out_dev) return MPDATA_EINVAL;
+  const void* f[2] = {psi, g};
+  int rc = check_fields(f, 2);
+  if (rc) return rc;
+  if (c->dtype == MPDATA_F64)
+    return mass_launch<double>(c, (const double*)psi, (const double*)g, out_dev);
+  return mass_launch<float>(c, (const float*)psi, (const float*)g, out_dev);
+}
+
+long long mpdata_launch_count(mpdata_ctx* c) { return c ? c->launches : -1; }
+
+int mpdata_profile(mpdata_ctx* c, int enable) {
+  if (!c) return MPDATA_EINVAL;
+  if (enable && !c->prof_ev) {
+    const int cap = 8192;
+    c->prof_ev = new (std::nothrow) cudaEvent_t[2 * cap];
+    c->prof_stage = new (std::nothrow) int[cap];
+    if (!c->prof_ev || !c->prof_stage) return MPDATA_ENOMEM;
+    for (int q = 0; q < 2 * cap; ++q) {
+      cudaError_t e = cudaEventCreate(&c->prof_ev[q]);
+      if (e != cudaSuccess) {
+        for (int r = 0; r < q; ++r) cudaEventDestroy(c->prof_ev[r]);
+        delete[] c->prof_ev;
+        c->prof_ev = nullptr;
+        return cuda_fail(c, e, "cudaEventCreate");
+      }
+    }
+    c->prof_cap = cap;
+  }
+  if (enable) c->prof_n = 0;
+  c->prof_on = enable != 0;
+  return MPDATA_OK;
+}
+
+int mpdata_profile_read(mpdata_ctx* c, int stage, double* ms, int* launches) {
+  if (!c || !ms || !launches || stage < 0 || stage >= MPDATA_NSTAGES) return MPDATA_EINVAL;
+  *ms = 0.0;
+  *launches = 0;
+  if (!c->prof_ev) return MPDATA_OK;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream synchronize");
+  for (int q = 0; q < c->prof_n; ++q) {
+    if (c->prof_stage[q] != stage) continue;
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, c->prof_ev[2 * q], c->prof_ev[2 * q + 1]);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventElapsedTime");
+    *ms += t;
+    ++*launches;
+  }
+  return MPDATA_OK;
+}
+
+void mpdata_destroy(mpdata_ctx* c) {
+  if (!c) return;
+  if (c->prof_ev) {
+    for (int q = 0; q < 2 * c->prof_cap; ++q) cudaEventDestroy(c->prof_ev[q]);
+    delete[] c->prof_ev;
+    delete[] c->prof_stage;
+  }
+  if (c->scratch) cudaFree(c->scratch);
+  if (c->hbuf) cudaFree(c->hbuf);
+  delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,226 @@
+// staged.cuh -- the unfused MPDATA step: one simple kernel per stage, one
+// thread per interior cell, every intermediate in device memory.
+//
+// This is the "without fusion" organisation of Table 2 (each stage re-reads
+// its inputs from main memory, as the separate Fortran subroutines of
+// Listing 8 do).  Each face flux is computed once, by the cell on its left
+// (the face's owner), and read by both neighbours, so the flux divergence
+// telescopes exactly and mass is conserved to the rounding of psi*G alone.
+#pragma once
+#include "grid.cuh"
+
+namespace mpd {
+namespace staged {
+
+struct Cell {
+  int i, j, k;
+  bool ok;
+};
+
+__device__ __forceinline__ Cell cell_of(const Geo& g) {
+  Cell c;
+  c.i = blockIdx.x * blockDim.x + threadIdx.x;
+  c.j = blockIdx.y * blockDim.y + threadIdx.y;
+  c.k = blockIdx.z;
+  c.ok = c.i < g.nx && c.j < g.ny;
+  return c;
+}
+
+// Vertical-face value with the closed bottom and top faces.
+template <class T>
+__device__ __forceinline__ T wface(const T* w, const Geo& g, int i, int j, int k) {
+  return (k < 0 || k >= g.nz - 1) ? T(0) : w[at(g, i, j, k)];
+}
+
+// Donor-cell fluxes through the three "+" faces of every cell.
+template <class T>
+__global__ void flux_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
+                            const T* __restrict__ cv, const T* __restrict__ cw,
+                            T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ fz) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  int64_t q = at(g, c.i, c.j, c.k);
+  T p = P[q];
+  fx[q] = donor(p, P[at(g, wrap_up(c.i, g.nx), c.j, c.k)], cu[q]);
+  fy[q] = donor(p, P[at(g, c.i, wrap_up(c.j, g.ny), c.k)], cv[q]);
+  fz[q] = (c.k < g.nz - 1) ? donor(p, P[q + g.pxy], cw[q]) : T(0);
+}
+
+// Flux divergence and advance (Listings 8/9): out = P - (1/G) sum dF.
+// P and out may be the same buffer (each thread reads and writes only its
+// own point), so neither is declared __restrict__.
+template <class T>
+__global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
+                               const T* __restrict__ fy, const T* __restrict__ fz,
+                               const T* __restrict__ G, T* out) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  int64_t q = at(g, c.i, c.j, c.k);
+  T fxm = fx[at(g, wrap_dn(c.i, g.nx), c.j, c.k)];
+  T fym = fy[at(g, c.i, wrap_dn(c.j, g.ny), c.k)];
+  T fzm = c.k > 0 ? fz[q - g.pxy] : T(0);
+  out[q] = P[q] - ((fx[q] - fxm) + (fy[q] - fym) + (fz[q] - fzm)) / G[q];
+}
+
+// Antidiffusive pseudo-velocities on the "+" faces of every cell
+// (Smolarkiewicz 1984; G-weighted form of Smolarkiewicz & Margolin 1998).
+template <class T>
+__global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
+                              const T* __restrict__ cv, const T* __restrict__ cw,
+                              const T* __restrict__ G, T* __restrict__ ut, T* __restrict__ vt,
+                              T* __restrict__ wt) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  const T eps = Eps<T>::v, half = T(0.5), quarter = T(0.25);
+  const int i = c.i, j = c.j, k = c.k;
+  const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
+  const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
+  const int kp = clampk(k + 1, g.nz), km = clampk(k - 1, g.nz);
+  auto p = [&](int a, int b, int d) { return P[at(g, a, b, d)]; };
+  const int64_t q = at(g, i, j, k);
+  const T pc = P[q];
+  {  // x face between (i) and (ip)
+    T U = cu[q];
+    T pr = p(ip, j, k);
+    T Gf = half * (G[q] + G[at(g, ip, j, k)]);
+    T A = (pr - pc) / (pr + pc + eps);
+    T a1 = p(ip, jp, k), a2 = p(i, jp, k), a3 = p(ip, jm, k), a4 = p(i, jm, k);
+    T By = half * (a1 + a2 - a3 - a4) / (a1 + a2 + a3 + a4 + eps);
+    T b1 = p(ip, j, kp), b2 = p(i, j, kp), b3 = p(ip, j, km), b4 = p(i, j, km);
+    T Bz = half * (b1 + b2 - b3 - b4) / (b1 + b2 + b3 + b4 + eps);
+    T Vb = quarter * (cv[q] + cv[at(g, ip, j, k)] + cv[at(g, i, jm, k)] + cv[at(g, ip, jm, k)]);
+    T Wb = quarter * (wface(cw, g, i, j, k) + wface(cw, g, ip, j, k) + wface(cw, g, i, j, k - 1) +
+                      wface(cw, g, ip, j, k - 1));
+    ut[q] = (fabs(U) - U * U / Gf) * A - U * (Vb * By + Wb * Bz) / Gf;
+  }
+  {  // y face between (j) and (jp)
+    T V = cv[q];
+    T pr = p(i, jp, k);
+    T Gf = half * (G[q] + G[at(g, i, jp, k)]);
+    T A = (pr - pc) / (pr + pc + eps);
+    T a1 = p(ip, jp, k), a2 = p(ip, j, k), a3 = p(im, jp, k), a4 = p(im, j, k);
+    T Bx = half * (a1 + a2 - a3 - a4) / (a1 + a2 + a3 + a4 + eps);
+    T b1 = p(i, jp, kp), b2 = p(i, j, kp), b3 = p(i, jp, km), b4 = p(i, j, km);
+    T Bz = half * (b1 + b2 - b3 - b4) / (b1 + b2 + b3 + b4 + eps);
+    T Ub = quarter * (cu[q] + cu[at(g, i, jp, k)] + cu[at(g, im, j, k)] + cu[at(g, im, jp, k)]);
+    T Wb = quarter * (wface(cw, g, i, j, k) + wface(cw, g, i, jp, k) + wface(cw, g, i, j, k - 1) +
+                      wface(cw, g, i, jp, k - 1));
+    vt[q] = (fabs(V) - V * V / Gf) * A - V * (Ub * Bx + Wb * Bz) / Gf;
+  }
+  if (k < g.nz - 1) {  // z face between (k) and (k+1); the top face is closed
+    T W = cw[q];
+    T pr = p(i, j, k + 1);
+    T Gf = half * (G[q] + G[q + g.pxy]);
+    T A = (pr - pc) / (pr + pc + eps);
+    T a1 = p(ip, j, k + 1), a2 = p(ip, j, k), a3 = p(im, j, k + 1), a4 = p(im, j, k);
+    T Bx = half * (a1 + a2 - a3 - a4) / (a1 + a2 + a3 + a4 + eps);
+    T b1 = p(i, jp, k + 1), b2 = p(i, jp, k), b3 = p(i, jm, k + 1), b4 = p(i, jm, k);
+    T By = half * (b1 + b2 - b3 - b4) / (b1 + b2 + b3 + b4 + eps);
+    T Ub = quarter * (cu[q] + cu[q + g.pxy] + cu[at(g, im, j, k)] + cu[at(g, im, j, k + 1)]);
+    T Vb = quarter * (cv[q] + cv[q + g.pxy] + cv[at(g, i, jm, k)] + cv[at(g, i, jm, k + 1)]);
+    wt[q] = (fabs(W) - W * W / Gf) * A - W * (Ub * Bx + Vb * By) / Gf;
+  } else {
+    wt[q] = T(0);
+  }
+}
+
+// Non-oscillatory limiter, first half: bounds over the 7-point stencil of
+// psi^n (P0) and psi^(m-1) (P), incoming/outgoing antidiffusive fluxes and
+// the scale factors beta-up, beta-down (Smolarkiewicz & Grabowski 1990).
+template <class T>
+__global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict__ P,
+                            const T* __restrict__ ut, const T* __restrict__ vt,
+                            const T* __restrict__ wt, const T* __restrict__ G,
+                            T* __restrict__ bu, T* __restrict__ bd) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  const T eps = Eps<T>::v, zero = T(0);
+  const int i = c.i, j = c.j, k = c.k;
+  const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
+  const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
+  const int kp = clampk(k + 1, g.nz), km = clampk(k - 1, g.nz);
+  const int64_t q = at(g, i, j, k);
+  const int64_t nb[6] = {at(g, im, j, k), at(g, ip, j, k), at(g, i, jm, k),
+                         at(g, i, jp, k), at(g, i, j, km), at(g, i, j, kp)};
+  T pc = P[q];
+  T hi = fmax(P0[q], pc), lo = fmin(P0[q], pc);
+  for (int s = 0; s < 6; ++s) {
+    T a = P0[nb[s]], b = P[nb[s]];
+    hi = fmax(hi, fmax(a, b));
+    lo = fmin(lo, fmin(a, b));
+  }
+  T fxp = donor(pc, P[nb[1]], ut[q]);
+  T fxm = donor(P[nb[0]], pc, ut[nb[0]]);
+  T fyp = donor(pc, P[nb[3]], vt[q]);
+  T fym = donor(P[nb[2]], pc, vt[nb[2]]);
+  T fzp = k < g.nz - 1 ? donor(pc, P[nb[5]], wt[q]) : zero;
+  T fzm = k > 0 ? donor(P[nb[4]], pc, wt[nb[4]]) : zero;
+  T in = (fmax(fxm, zero) - fmin(fxp, zero)) + (fmax(fym, zero) - fmin(fyp, zero)) +
+         (fmax(fzm, zero) - fmin(fzp, zero));
+  T out = (fmax(fxp, zero) - fmin(fxm, zero)) + (fmax(fyp, zero) - fmin(fym, zero)) +
+          (fmax(fzp, zero) - fmin(fzm, zero));
+  bu[q] = (hi - pc) * G[q] / (in + eps);
+  bd[q] = (pc - lo) * G[q] / (out + eps);
+}
+
+// Limited velocity on a face: min(1, bd_L, bu_R)[Ut]+ + min(1, bu_L, bd_R)[Ut]-.
+template <class T>
+__device__ __forceinline__ T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
+  T cpos = fmin(fmin(T(1), bdL), buR);
+  T cneg = fmin(fmin(T(1), buL), bdR);
+  return cpos * fmax(Ut, T(0)) + cneg * fmin(Ut, T(0));
+}
+
+// Second half: limited velocities on the "+" faces and their donor fluxes.
+// With ul != nullptr the limited velocities are kept for a further pass.
+template <class T>
+__global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ ut,
+                               const T* __restrict__ vt, const T* __restrict__ wt,
+                               const T* __restrict__ bu, const T* __restrict__ bd,
+                               T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ fz,
+                               T* __restrict__ ul, T* __restrict__ vl, T* __restrict__ wl) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  const int64_t q = at(g, c.i, c.j, c.k);
+  const int64_t qx = at(g, wrap_up(c.i, g.nx), c.j, c.k);
+  const int64_t qy = at(g, c.i, wrap_up(c.j, g.ny), c.k);
+  T pc = P[q], buc = bu[q], bdc = bd[q];
+  T lx = limit_face(ut[q], buc, bdc, bu[qx], bd[qx]);
+  T ly = limit_face(vt[q], buc, bdc, bu[qy], bd[qy]);
+  T lz = T(0);
+  if (c.k < g.nz - 1) lz = limit_face(wt[q], buc, bdc, bu[q + g.pxy], bd[q + g.pxy]);
+  fx[q] = donor(pc, P[qx], lx);
+  fy[q] = donor(pc, P[qy], ly);
+  fz[q] = c.k < g.nz - 1 ? donor(pc, P[q + g.pxy], lz) : T(0);
+  if (ul) { ul[q] = lx; vl[q] = ly; wl[q] = lz; }
+}
+
+}  // namespace staged
+
+// Halo fill of a padded field: periodic in i and j (corners included); in k
+// an edge copy (kind 0) or closed faces set to zero (kind 1, vertical-face
+// fields, which also zeroes the top face k = nz-1).
+template <class T>
+__global__ void halo_kernel(Geo g, T* __restrict__ f, int kind) {
+  const int64_t n = g.total;
+  const int64_t pyy = g.ny + 2 * (int64_t)g.h;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int ii = (int)(t % g.px) - g.h;
+    int jj = (int)((t / g.px) % pyy) - g.h;
+    int kk = (int)(t / g.pxy) - g.h;
+    bool inner = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz;
+    if (kind == 1) {
+      if (kk < 0 || kk >= g.nz - 1) { f[t] = T(0); continue; }
+      if (inner) continue;
+    } else if (inner) {
+      continue;
+    }
+    int is = ((ii % g.nx) + g.nx) % g.nx;
+    int js = ((jj % g.ny) + g.ny) % g.ny;
+    int ks = kk < 0 ? 0 : (kk >= g.nz ? g.nz - 1 : kk);
+    f[t] = f[at(g, is, js, ks)];
+  }
+}
+
+}  // namespace mpd

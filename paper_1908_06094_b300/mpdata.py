@@ -1,0 +1,97 @@
+"""torch-tensor front end of the C ABI: checks shapes/dtypes/devices and
+passes raw device pointers and the current CUDA stream.  No arithmetic."""
+from __future__ import annotations
+
+import torch
+
+from . import _capi as C
+
+_DT = {torch.float64: C.MPDATA_F64, torch.float32: C.MPDATA_F32}
+
+
+def padded_shape(nx: int, ny: int, nz: int, h: int):
+    return (nz + 2 * h, ny + 2 * h, nx + 2 * h)
+
+
+class MPDATA:
+    """One grid's MPDATA context (owns the library scratch of one step).
+
+    Fields are C-contiguous CUDA tensors of shape padded_shape(nx, ny, nz, h)
+    and this context's dtype; U, V, W are G-weighted Courant numbers on the
+    faces i+1/2, j+1/2, k+1/2.
+    """
+
+    def __init__(self, nx, ny, nz, halo=2, iord=2, nonoscillatory=True,
+                 dtype=torch.float64, device=None, variant=None):
+        if dtype not in _DT:
+            raise TypeError(f"dtype must be float64 or float32, got {dtype}")
+        self.nx, self.ny, self.nz, self.h = nx, ny, nz, halo
+        self.iord, self.nonosc, self.dtype = iord, int(bool(nonoscillatory)), dtype
+        self.device = torch.device(device if device is not None else "cuda")
+        with torch.cuda.device(self.device):
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+            self._ctx = C.mpdata_init(nx, ny, nz, halo, iord, self.nonosc, _DT[dtype],
+                                      C.MPDATA_K_ZEROFLUX, stream)
+        if variant is not None:
+            C.mpdata_set_variant(self._ctx, variant)
+        self.shape = padded_shape(nx, ny, nz, halo)
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            C.mpdata_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ptr(self, t: torch.Tensor, name: str) -> int:
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != self.dtype or tuple(t.shape) != self.shape or not t.is_contiguous():
+            raise ValueError(f"{name}: expected contiguous {self.dtype} tensor of shape "
+                             f"{self.shape}, got {t.dtype} {tuple(t.shape)}")
+        if t.device != self.device and not (self.device.index is None and t.device.type == "cuda"):
+            raise ValueError(f"{name} is on {t.device}, context on {self.device}")
+        return t.data_ptr()
+
+    def _sync_stream(self):
+        C.mpdata_set_stream(self._ctx, torch.cuda.current_stream(self.device).cuda_stream)
+
+    def set_variant(self, variant: int):
+        C.mpdata_set_variant(self._ctx, variant)
+
+    def step(self, psi, u, v, w, g, nsteps: int = 1):
+        """Advance psi in place by nsteps steps (asynchronous, current stream)."""
+        self._sync_stream()
+        C.mpdata_step(self._ctx, self._ptr(psi, "psi"), self._ptr(u, "u"), self._ptr(v, "v"),
+                      self._ptr(w, "w"), self._ptr(g, "g"), nsteps)
+        return psi
+
+    def fill_halo(self, f, kind: int = C.MPDATA_HALO_CELL):
+        self._sync_stream()
+        C.mpdata_fill_halo(self._ctx, self._ptr(f, "field"), kind)
+        return f
+
+    def mass(self, psi, g, out=None):
+        """sum psi*G over the interior as a 0-d float64 CUDA tensor (no sync)."""
+        self._sync_stream()
+        if out is None:
+            out = torch.empty((), dtype=torch.float64, device=psi.device)
+        C.mpdata_mass(self._ctx, self._ptr(psi, "psi"), self._ptr(g, "g"), out.data_ptr())
+        return out
+
+    def step_host(self, psi_h, u_h, v_h, w_h, g_h, nsteps: int = 1):
+        """HOST-buffer variant: tensors on the CPU (pinned for speed); psi_h
+        is overwritten with the result; returns after the stream finished."""
+        for name, t in (("psi", psi_h), ("u", u_h), ("v", v_h), ("w", w_h), ("g", g_h)):
+            if t.is_cuda or t.dtype != self.dtype or tuple(t.shape) != self.shape \
+                    or not t.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous CPU {self.dtype} tensor of "
+                                 f"shape {self.shape}")
+        self._sync_stream()
+        C.mpdata_step_host(self._ctx, psi_h.data_ptr(), u_h.data_ptr(), v_h.data_ptr(),
+                           w_h.data_ptr(), g_h.data_ptr(), nsteps)
+        return psi_h
