@@ -154,6 +154,32 @@ MPDATA_API int mpdata_profile(mpdata_ctx *c, int enable);
  * of timed launches of one stage.  Errors: EINVAL, ECUDA. */
 MPDATA_API int mpdata_profile_read(mpdata_ctx *c, int stage, double *ms, int *launches);
 
+/* Mass without a context and without allocating: the same deterministic
+ * sum over the interior of psi*G as mpdata_mass, for callers that cannot call
+ * cudaMalloc -- code running inside a global-mode stream capture (where
+ * allocation is an error), applications whose device memory is all handed
+ * out by their own pool or arena, and hosts that forbid allocation after
+ * start-up.  (mpdata_init allocates, so those callers cannot get a context.)
+ * The paper has no counterpart: this is a library-interface addition.
+ *   psi, g   padded DEVICE fields [nz+2h][ny+2h][nx+2h] of dtype, 16-byte
+ *            aligned, read at interior points only;
+ *   out_dev  DEVICE double that receives the sum (8-byte aligned);
+ *   cuda_stream  the stream the two kernels run on (NULL = legacy default).
+ * Scratch: a file-scope device array of MPDATA_MASS_NOALLOC_PARTIALS doubles
+ * (9472 bytes) that every GPU loading the library keeps until exit.  All
+ * calls on one device share it: two calls whose kernels overlap on that GPU
+ * (for example on two streams) race on it, so the caller must order them.
+ * Each call overwrites every partial before reading it, so nothing carries
+ * over from the previous call.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.
+ * Limits: ny*nz <= MPDATA_MASS_NOALLOC_MAX_ROWS and (nx+2h)(ny+2h) < 2^31,
+ * else MPDATA_ERANGE.  Errors: EINVAL, EALIGN, ERANGE, EDEVICE, ECUDA. */
+#define MPDATA_MASS_NOALLOC_PARTIALS 1184
+#define MPDATA_MASS_NOALLOC_MAX_ROWS 2147483647LL
+MPDATA_API int mpdata_mass_noalloc(const void *psi, const void *g, int nx, int ny, int nz,
+                                   int halo, int dtype, double *out_dev, void *cuda_stream);
+
 /* Destroy a context and free its scratch (NULL is ignored). */
 MPDATA_API void mpdata_destroy(mpdata_ctx *c);
 

@@ -51,6 +51,7 @@ SIGNATURES = {
     "mpdata_last_error_string": (ctypes.c_char_p, [_c]),
     "mpdata_version": (_i, []),
     "mpdata_launch_count": (ctypes.c_longlong, [_c]),
+    "mpdata_mass_noalloc": (_i, [_c, _c, _i, _i, _i, _i, _i, _c, _c]),
     "mpdata_profile": (_i, [_c, _i]),
     "mpdata_profile_read": (_i, [_c, _i, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int)]),
@@ -145,3 +146,9 @@ def mpdata_profile_read(ctx, stage: int):
     _check(lib.mpdata_profile_read(ctx, stage, ctypes.byref(ms), ctypes.byref(n)),
            "mpdata_profile_read", ctx)
     return ms.value, n.value
+
+
+def mpdata_mass_noalloc(psi, g, nx, ny, nz, halo, dtype, out_dev, cuda_stream=0):
+    """Context-free mass sum that allocates nothing (see include/mpdata.h)."""
+    _check(lib.mpdata_mass_noalloc(psi, g, nx, ny, nz, halo, dtype, out_dev, cuda_stream),
+           "mpdata_mass_noalloc")

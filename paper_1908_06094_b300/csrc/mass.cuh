@@ -42,7 +42,7 @@ mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
   if (threadIdx.x == 0) part[blockIdx.x] = b;
 }
 
-__global__ void __launch_bounds__(1024)
+static __global__ void __launch_bounds__(1024)
 mass_final_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
   __shared__ double sh[1024];
   double s = 0.0;
