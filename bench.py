@@ -295,7 +295,7 @@ def run_ours(args, wl_name):
                        "step": "one MPDATA step + FP64 mass reduction",
                        "l2": "no flush: the 5 input fields (%.0f MB) exceed the 126 MB L2"
                              % (5 * esize * padded[0].size / 1e6),
-                       "variant": "staged" if args.variant == 1 else "default",
+                       "variant": {0: "fused", 1: "staged", 2: "auto"}.get(args.variant, "auto"),
                        "parallelism": f"replicas x{ws}"},
             "hbm_roofline_frac_step": round(value / ws * step_bytes / npts / 1e9 / hbm, 4),
             "roofline": roof,
@@ -391,7 +391,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="latlon256_f64", choices=sorted(WORKLOADS))
-    ap.add_argument("--variant", type=int, default=None, help="0 fused, 1 staged")
+    ap.add_argument("--variant", type=int, default=None, help="0 fused, 1 staged, 2 auto (default)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e and CPU-baseline legs")

@@ -75,8 +75,11 @@ enum mpdata_halo_kind {
   MPDATA_HALO_WFACE = 1  /* W: periodic i-j, closed faces (zero) in k    */
 };
 enum mpdata_variant {
-  MPDATA_FUSED = 0,  /* default: fused kernels, intermediates on chip     */
-  MPDATA_STAGED = 1  /* one kernel per stage, intermediates in memory     */
+  MPDATA_FUSED = 0,  /* one kernel per step, intermediates on chip         */
+  MPDATA_STAGED = 1, /* one kernel per stage, intermediates in memory      */
+  MPDATA_AUTO = 2    /* default: the faster of the two for the dtype on the
+                        B300 (FP64: staged, since the fused kernel's halo
+                        recompute costs FP64-pipe work; FP32: fused)        */
 };
 
 /* Create a context for one grid.
@@ -96,15 +99,27 @@ MPDATA_API int mpdata_init(mpdata_ctx **out, int nx, int ny, int nz, int halo, i
 /* Change the stream later calls are issued on. Errors: EINVAL. */
 MPDATA_API int mpdata_set_stream(mpdata_ctx *c, void *cuda_stream);
 
-/* Choose the kernel organisation (mpdata_variant); both give the same
- * step to rounding.  Errors: EINVAL. */
+/* Choose the kernel organisation (mpdata_variant); all give the same step
+ * to rounding.  The fused kernel runs only when iord == 2 and nx, ny >= 2h;
+ * other contexts use the staged kernels whatever is chosen.
+ * Errors: EINVAL. */
 MPDATA_API int mpdata_set_variant(mpdata_ctx *c, int variant);
 
 /* Advance psi (in/out, device) by nsteps MPDATA steps with Courant fields
- * u, v, w and metric g (device, read-only).  nsteps >= 0.
+ * u, v, w and metric g (device, read-only).  nsteps >= 0.  With the fused
+ * kernels the steps alternate between psi and context scratch, and an odd
+ * nsteps ends with a device copy back into psi.
  * Errors: EINVAL (null pointer, nsteps < 0), EALIGN, ECUDA. */
 MPDATA_API int mpdata_step(mpdata_ctx *c, void *psi, const void *u, const void *v, const void *w,
                 const void *g, int nsteps);
+
+/* One step out of place: psi_out = step(psi_in), halo of psi_out filled;
+ * psi_in is not modified.  The two buffers must be distinct (a caller that
+ * double-buffers its state avoids the copy-back mpdata_step makes when the
+ * fused kernels run an odd number of steps).
+ * Errors: EINVAL (null pointer, psi_in == psi_out), EALIGN, ECUDA. */
+MPDATA_API int mpdata_step_out(mpdata_ctx *c, const void *psi_in, void *psi_out, const void *u,
+                               const void *v, const void *w, const void *g);
 
 /* The same from HOST buffers: copies psi, u, v, w, g (padded, HOST) to
  * context-owned device buffers, runs nsteps steps, copies psi back to the

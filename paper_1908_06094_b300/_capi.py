@@ -26,6 +26,7 @@ MPDATA_HALO_CELL = 0
 MPDATA_HALO_WFACE = 1
 MPDATA_FUSED = 0
 MPDATA_STAGED = 1
+MPDATA_AUTO = 2
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libmpdata_b300.so not built (expected at {LIB_PATH}); "
@@ -43,6 +44,7 @@ SIGNATURES = {
     "mpdata_set_stream": (_i, [_c, _c]),
     "mpdata_set_variant": (_i, [_c, _i]),
     "mpdata_step": (_i, [_c, _c, _c, _c, _c, _c, _i]),
+    "mpdata_step_out": (_i, [_c, _c, _c, _c, _c, _c, _c]),
     "mpdata_step_host": (_i, [_c, _c, _c, _c, _c, _c, _i]),
     "mpdata_fill_halo": (_i, [_c, _c, _i]),
     "mpdata_mass": (_i, [_c, _c, _c, _c]),
@@ -113,6 +115,10 @@ def mpdata_set_variant(ctx, variant):
 
 def mpdata_step(ctx, psi, u, v, w, g, nsteps):
     _check(lib.mpdata_step(ctx, psi, u, v, w, g, nsteps), "mpdata_step", ctx)
+
+
+def mpdata_step_out(ctx, psi_in, psi_out, u, v, w, g):
+    _check(lib.mpdata_step_out(ctx, psi_in, psi_out, u, v, w, g), "mpdata_step_out", ctx)
 
 
 def mpdata_step_host(ctx, psi_h, u_h, v_h, w_h, g_h, nsteps):

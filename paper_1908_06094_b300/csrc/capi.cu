@@ -11,6 +11,7 @@
 #include "grid.cuh"
 #include "mass.cuh"
 #include "staged.cuh"
+#include "fused.cuh"
 
 using mpd::Geo;
 
@@ -23,6 +24,8 @@ struct mpdata_ctx {
   void* scratch;
   void *psi1, *psi2, *fx, *fy, *fz, *ut, *vt, *wt, *bu, *bd, *ul, *vl, *wl;
   double* part;
+  // fused kernel launch shape (chosen in init)
+  int fused_ok, nchunks, kchunk;
   // device copies for the HOST-buffer call (allocated on its first use)
   void* hbuf;
   // instrumentation
@@ -82,15 +85,19 @@ int halo_launch(mpdata_ctx* c, T* f, int kind) {
 }
 
 // One MPDATA step, staged organisation (one kernel per stage).
+// psi_out may equal psi_in: psi_in is last read (by the limiter) before the
+// final advance writes psi_out.
 template <class T>
-int step_staged(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G) {
+int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T* V,
+                const T* W, const T* G) {
   using namespace mpd::staged;
   const Geo& g = c->g;
   const dim3 grid = cell_grid(g);
   cudaStream_t s = c->stream;
+  const T* psi = psi_in;
   T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
   // pass 1: donor cell
-  T* cur = c->iord == 1 ? psi : (T*)c->psi1;
+  T* cur = c->iord == 1 ? psi_out : (T*)c->psi1;
   MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
              flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
   MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
@@ -121,7 +128,7 @@ int step_staged(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const
                  flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, tset[0], tset[1], tset[2],
                                                              fx, fy, fz));
     }
-    T* dest = !more ? psi : (cur == (T*)c->psi1 ? (T*)c->psi2 : (T*)c->psi1);
+    T* dest = !more ? psi_out : (cur == (T*)c->psi1 ? (T*)c->psi2 : (T*)c->psi1);
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
                advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, fx, fy, fz, G, dest));
     MPD_CHECK_LAUNCH(c, "corrective pass");
@@ -132,14 +139,125 @@ int step_staged(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const
   return MPDATA_OK;
 }
 
+// Tile shapes of the fused kernel: TX x TY columns per CTA, NT threads.
+template <class T> struct FusedShape;
+// MINB: CTAs per SM the register budget is sized for (shared memory allows
+// 2 for FP64 and 4 for FP32 at these tiles).
+template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 16, NT = 256, MINB = 2; };
+template <> struct FusedShape<float> { static constexpr int TX = 32, TY = 16, NT = 256, MINB = 3; };
+
+template <class T, bool LIMIT>
+auto fused_kernel_ptr() {
+  using F = FusedShape<T>;
+  return mpd::fused::step_kernel<T, F::TX, F::TY, F::NT, F::MINB, LIMIT>;
+}
+
+template <class T>
+size_t fused_smem() {
+  using F = FusedShape<T>;
+  return mpd::fused::Layout<T, F::TX, F::TY>::bytes;
+}
+
+// Pick the k-chunking so that the grid covers the GPU about twice.
+template <class T>
+int fused_setup(mpdata_ctx* c) {
+  using F = FusedShape<T>;
+  const Geo& g = c->g;
+  c->fused_ok = 0;
+  if (c->iord != 2 || g.nx < 2 * g.h || g.ny < 2 * g.h) return MPDATA_OK;
+  const size_t bytes = fused_smem<T>();
+  auto k1 = fused_kernel_ptr<T, true>();
+  auto k0 = fused_kernel_ptr<T, false>();
+  if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+          cudaSuccess ||
+      cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return MPDATA_OK;  // not eligible on this device: the staged kernels run
+  }
+  int occ = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->nonosc ? k1 : k0, F::NT, bytes);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  cudaGetLastError();
+  if (occ < 1) return MPDATA_OK;
+  const long ctas = (long)((g.nx + F::TX - 1) / F::TX) * ((g.ny + F::TY - 1) / F::TY);
+  // Split k into chunks when there are too few column tiles to load every
+  // SM: an SM's time ~ (CTAs it runs) x (levels per chunk + the ~4 extra
+  // planes each chunk recomputes at its start); take the cheapest split.
+  long best_n = 1;
+  double best_cost = 1e300;
+  for (long n = 1; n <= g.nz; ++n) {
+    const long kc = (g.nz + n - 1) / n;
+    const long nn = (g.nz + kc - 1) / kc;
+    const long per_sm = (ctas * nn + sms - 1) / sms;
+    const double cost = (double)per_sm * (kc + 4);
+    if (cost < best_cost - 1e-9) { best_cost = cost; best_n = nn; }
+  }
+  c->nchunks = (int)best_n;
+  c->kchunk = (g.nz + c->nchunks - 1) / c->nchunks;
+  c->nchunks = (g.nz + c->kchunk - 1) / c->kchunk;
+  c->fused_ok = 1;
+  return MPDATA_OK;
+}
+
+template <class T>
+int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, const T* W,
+                 const T* G) {
+  using F = FusedShape<T>;
+  const Geo& g = c->g;
+  dim3 grid((g.nx + F::TX - 1) / F::TX, (g.ny + F::TY - 1) / F::TY, c->nchunks);
+  const size_t bytes = fused_smem<T>();
+  if (c->nonosc)
+    MPD_LAUNCH(c, MPDATA_STAGE_FUSED, (fused_kernel_ptr<T, true>())<<<grid, F::NT, bytes, c->stream>>>(
+                                          g, c->kchunk, in, U, V, W, G, out));
+  else
+    MPD_LAUNCH(c, MPDATA_STAGE_FUSED, (fused_kernel_ptr<T, false>())<<<grid, F::NT, bytes, c->stream>>>(
+                                          g, c->kchunk, in, U, V, W, G, out));
+  MPD_CHECK_LAUNCH(c, "fused step kernel");
+  return MPDATA_OK;
+}
+
+bool use_fused(const mpdata_ctx* c) {
+  if (!c->fused_ok) return false;
+  if (c->variant == MPDATA_AUTO) return c->dtype == MPDATA_F32;
+  return c->variant == MPDATA_FUSED;
+}
+
+// One step psi_in -> psi_out (distinct buffers), halo of psi_out filled.
+template <class T>
+int step_out(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, const T* W,
+             const T* G) {
+  if (use_fused(c)) return fused_launch<T>(c, in, out, U, V, W, G);
+  int rc = step_staged<T>(c, in, out, U, V, W, G);
+  if (rc) return rc;
+  return halo_launch<T>(c, out, MPDATA_HALO_CELL);
+}
+
 template <class T>
 int step_n(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G, int nsteps) {
   if (nsteps == 0) return MPDATA_OK;
-  for (int s = 0; s < nsteps; ++s) {
-    int rc = step_staged<T>(c, psi, U, V, W, G);
-    if (rc) return rc;
+  if (!use_fused(c)) {
+    for (int s = 0; s < nsteps; ++s) {
+      int rc = step_staged<T>(c, psi, psi, U, V, W, G);
+      if (rc) return rc;
+    }
+    return halo_launch<T>(c, psi, MPDATA_HALO_CELL);
   }
-  return halo_launch<T>(c, psi, MPDATA_HALO_CELL);
+  // the fused kernel cannot work in place: alternate with the scratch field
+  T* scratch = (T*)c->psi1;
+  const T* src = psi;
+  for (int s = 0; s < nsteps; ++s) {
+    T* dst = (src == psi) ? scratch : psi;
+    int rc = fused_launch<T>(c, src, dst, U, V, W, G);
+    if (rc) return rc;
+    src = dst;
+  }
+  if (src != psi) {
+    cudaError_t e = cudaMemcpyAsync(psi, src, (size_t)c->g.total * sizeof(T),
+                                    cudaMemcpyDeviceToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy-back");
+  }
+  return MPDATA_OK;
 }
 
 template <class T>
@@ -204,7 +322,7 @@ int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, in
   c->nonosc = nonosc;
   c->dtype = dtype;
   c->kbc = k_bc;
-  c->variant = MPDATA_STAGED;
+  c->variant = MPDATA_AUTO;
   c->device = dev;
   c->esize = dtype == MPDATA_F64 ? 8 : 4;
   c->stream = (cudaStream_t)stream;
@@ -221,6 +339,7 @@ int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, in
                       &c->bd, &c->psi2, &c->ul, &c->vl, &c->wl};
   for (int q = 0; q < nfields; ++q) *slots[q] = p + q * fbytes;
   c->part = (double*)(p + nfields * fbytes);
+  if (dtype == MPDATA_F64) fused_setup<double>(c); else fused_setup<float>(c);
   *out = c;
   return MPDATA_OK;
 }
@@ -232,8 +351,7 @@ int mpdata_set_stream(mpdata_ctx* c, void* stream) {
 }
 
 int mpdata_set_variant(mpdata_ctx* c, int variant) {
-  if (!c || (variant != MPDATA_STAGED && variant != MPDATA_FUSED)) return MPDATA_EINVAL;
-  if (variant == MPDATA_FUSED) return MPDATA_EINVAL;  // not available in this build
+  if (!c || variant < MPDATA_FUSED || variant > MPDATA_AUTO) return MPDATA_EINVAL;
   c->variant = variant;
   return MPDATA_OK;
 }
@@ -249,6 +367,20 @@ int mpdata_step(mpdata_ctx* c, void* psi, const void* u, const void* v, const vo
                           (const double*)w, (const double*)g, nsteps);
   return step_n<float>(c, (float*)psi, (const float*)u, (const float*)v, (const float*)w,
                        (const float*)g, nsteps);
+}
+
+int mpdata_step_out(mpdata_ctx* c, const void* psi_in, void* psi_out, const void* u,
+                    const void* v, const void* w, const void* g) {
+  if (!c) return MPDATA_EINVAL;
+  const void* f[6] = {psi_in, psi_out, u, v, w, g};
+  int rc = check_fields(f, 6);
+  if (rc) return rc;
+  if (psi_in == psi_out) return MPDATA_EINVAL;
+  if (c->dtype == MPDATA_F64)
+    return step_out<double>(c, (const double*)psi_in, (double*)psi_out, (const double*)u,
+                            (const double*)v, (const double*)w, (const double*)g);
+  return step_out<float>(c, (const float*)psi_in, (float*)psi_out, (const float*)u,
+                         (const float*)v, (const float*)w, (const float*)g);
 }
 
 int mpdata_step_host(mpdata_ctx* c, void* psi_h, const void* u_h, const void* v_h,

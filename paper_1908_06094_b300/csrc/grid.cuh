@@ -36,15 +36,107 @@ __device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i
 __device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 __device__ __forceinline__ int clampk(int k, int nz) { return k < 0 ? 0 : (k >= nz ? nz - 1 : k); }
 
-// Donor-cell (upwind) flux through a face: left value L, right value R,
-// face Courant number C (Listings 4/5).
-template <class T>
-__device__ __forceinline__ T donor(T L, T R, T C) {
-  return fmax(C, T(0)) * L + fmin(C, T(0)) * R;
-}
-
 template <class T> struct Eps;
 template <> struct Eps<double> { static constexpr double v = 1e-15; };
 template <> struct Eps<float> { static constexpr float v = 1e-15f; };
+
+// Explicitly rounded multiply and fused multiply-add: the compiler never
+// re-contracts these, so one formula evaluated at two places in the code (a
+// face flux seen from its left and from its right cell) gives the same bits.
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// Sign tests on the bit pattern (integer pipe): on the B300 the FP64 pipe
+// issues 2 lanes per SM per clock, so compares and min/max of doubles are
+// kept off it.  nonneg(x) is true for +0 and positive x.
+__device__ __forceinline__ bool nonneg(double x) { return __double2hiint(x) >= 0; }
+__device__ __forceinline__ bool nonneg(float x) { return __float_as_int(x) >= 0; }
+
+// [x]+ and [x]- of the donor-cell split.
+template <class T> __device__ __forceinline__ T pos(T x) { return nonneg(x) ? x : T(0); }
+template <class T> __device__ __forceinline__ T neg(T x) { return nonneg(x) ? T(0) : x; }
+__device__ __forceinline__ double absv(double x) {
+  return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ float absv(float x) { return fabsf(x); }
+
+// Donor-cell (upwind) flux through a face: left value L, right value R,
+// face Courant number C (Listings 4/5): max(C,0) L + min(C,0) R, which is
+// C*L for C >= 0 and C*R otherwise (one product, the same rounded value).
+template <class T>
+__device__ __forceinline__ T donor(T L, T R, T C) {
+  return mul_rn(C, nonneg(C) ? L : R);
+}
+
+// min/max.  FP32 uses the hardware min/max (integer-rate pipe).  FP64 maps
+// each double to an int64 key with the same order (sign-magnitude ->
+// two's complement: flip the magnitude bits of negatives) and compares keys.
+__device__ __forceinline__ long long okey(double x) {
+  long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double vmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
+__device__ __forceinline__ double vmin(double a, double b) { return okey(a) <= okey(b) ? a : b; }
+__device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+// min of non-negative values (limiter factors): raw bit patterns order them.
+__device__ __forceinline__ double nmin(double a, double b) {
+  return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
+}
+__device__ __forceinline__ float nmin(float a, float b) { return fminf(a, b); }
+
+// Reciprocal of a positive normal number.  FP32: the hardware approximation
+// (rcp.approx, about 1 ulp).  FP64: the hardware seed refined by two
+// Newton-Raphson steps r <- r + r (1 - b r), each doubling the correct bits
+// (seed ~2^-20 relative -> ~2^-40 -> full precision); a*rcp(b) is then
+// within ~2 ulp of a/b.  Used for every ratio of the scheme: A, B, beta,
+// 1/G and 1/G_face, whose denominators are >= epsilon > 0 or G > 0.
+__device__ __forceinline__ float rcp(float b) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+  return r;
+}
+__device__ __forceinline__ double rcp(double b) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+  r = fma(r, fma(-b, r, 1.0), r);
+  r = fma(r, fma(-b, r, 1.0), r);
+  return r;
+}
+
+// Limited velocity on a face (non-oscillatory option):
+// min(1, bd_L, bu_R) [Ut]+ + min(1, bu_L, bd_R) [Ut]-; the betas are >= 0,
+// and only one of the two parts is non-zero.
+template <class T>
+__device__ __forceinline__ T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
+  return nonneg(Ut) ? mul_rn(nmin(nmin(T(1), bdL), buR), Ut)
+                    : mul_rn(nmin(nmin(T(1), buL), bdR), Ut);
+}
+
+// Antidiffusive pseudo-velocity on one face from its ingredients:
+//   U       face Courant number;           gsum  G_L + G_R (G_face = gsum/2)
+//   pl, pr  psi1 left and right;           s1p, s1m  sums of the two psi1
+//           values one row/level above and below in the first cross direction
+//   s2p, s2m  the same in the second cross direction
+//   vsum, wsum  sums of the four cross-direction Courant numbers around the face
+// Ut = (|U| - U^2/Gf) A - U (Vbar B1 + Wbar B2)/Gf with A = (pr-pl)/(pr+pl+eps),
+// B = (1/2)(s+ - s-)/(s+ + s- + eps), Vbar = vsum/4 (Smolarkiewicz 1984,
+// G-weighted as in Smolarkiewicz & Margolin 1998).  The factors 1/2 and 1/4
+// are applied as one exact 1/8 scaling.
+template <class T>
+__device__ __forceinline__ T pseudo_velocity(T U, T gsum, T pl, T pr, T s1p, T s1m, T s2p,
+                                             T s2m, T vsum, T wsum) {
+  const T eps = Eps<T>::v;
+  const T rG = T(2) * rcp(gsum);                       // 1/Gf
+  const T A = (pr - pl) * rcp(pr + pl + eps);
+  const T B1 = (s1p - s1m) * rcp(s1p + s1m + eps);     // 2 B1
+  const T B2 = (s2p - s2m) * rcp(s2p + s2m + eps);     // 2 B2
+  const T q = U * rG;
+  const T diff = absv(U) - U * q;                      // |U| - U^2/Gf
+  const T cross = T(0.125) * (vsum * B1 + wsum * B2);  // Vbar B1 + Wbar B2
+  return diff * A - q * cross;
+}
 
 }  // namespace mpd

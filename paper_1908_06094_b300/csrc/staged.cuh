@@ -59,7 +59,7 @@ __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
   T fxm = fx[at(g, wrap_dn(c.i, g.nx), c.j, c.k)];
   T fym = fy[at(g, c.i, wrap_dn(c.j, g.ny), c.k)];
   T fzm = c.k > 0 ? fz[q - g.pxy] : T(0);
-  out[q] = P[q] - ((fx[q] - fxm) + (fy[q] - fym) + (fz[q] - fzm)) / G[q];
+  out[q] = P[q] - ((fx[q] - fxm) + (fy[q] - fym) + (fz[q] - fzm)) * rcp(G[q]);
 }
 
 // Antidiffusive pseudo-velocities on the "+" faces of every cell
@@ -79,46 +79,32 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
   auto p = [&](int a, int b, int d) { return P[at(g, a, b, d)]; };
   const int64_t q = at(g, i, j, k);
   const T pc = P[q];
+  (void)eps; (void)half; (void)quarter;
   {  // x face between (i) and (ip)
-    T U = cu[q];
-    T pr = p(ip, j, k);
-    T Gf = half * (G[q] + G[at(g, ip, j, k)]);
-    T A = (pr - pc) / (pr + pc + eps);
-    T a1 = p(ip, jp, k), a2 = p(i, jp, k), a3 = p(ip, jm, k), a4 = p(i, jm, k);
-    T By = half * (a1 + a2 - a3 - a4) / (a1 + a2 + a3 + a4 + eps);
-    T b1 = p(ip, j, kp), b2 = p(i, j, kp), b3 = p(ip, j, km), b4 = p(i, j, km);
-    T Bz = half * (b1 + b2 - b3 - b4) / (b1 + b2 + b3 + b4 + eps);
-    T Vb = quarter * (cv[q] + cv[at(g, ip, j, k)] + cv[at(g, i, jm, k)] + cv[at(g, ip, jm, k)]);
-    T Wb = quarter * (wface(cw, g, i, j, k) + wface(cw, g, ip, j, k) + wface(cw, g, i, j, k - 1) +
-                      wface(cw, g, ip, j, k - 1));
-    ut[q] = (fabs(U) - U * U / Gf) * A - U * (Vb * By + Wb * Bz) / Gf;
+    const T s1p = p(ip, jp, k) + p(i, jp, k), s1m = p(ip, jm, k) + p(i, jm, k);
+    const T s2p = p(ip, j, kp) + p(i, j, kp), s2m = p(ip, j, km) + p(i, j, km);
+    const T vs = cv[q] + cv[at(g, ip, j, k)] + cv[at(g, i, jm, k)] + cv[at(g, ip, jm, k)];
+    const T ws = wface(cw, g, i, j, k) + wface(cw, g, ip, j, k) + wface(cw, g, i, j, k - 1) +
+                 wface(cw, g, ip, j, k - 1);
+    ut[q] = pseudo_velocity(cu[q], G[q] + G[at(g, ip, j, k)], pc, p(ip, j, k), s1p, s1m, s2p,
+                            s2m, vs, ws);
   }
   {  // y face between (j) and (jp)
-    T V = cv[q];
-    T pr = p(i, jp, k);
-    T Gf = half * (G[q] + G[at(g, i, jp, k)]);
-    T A = (pr - pc) / (pr + pc + eps);
-    T a1 = p(ip, jp, k), a2 = p(ip, j, k), a3 = p(im, jp, k), a4 = p(im, j, k);
-    T Bx = half * (a1 + a2 - a3 - a4) / (a1 + a2 + a3 + a4 + eps);
-    T b1 = p(i, jp, kp), b2 = p(i, j, kp), b3 = p(i, jp, km), b4 = p(i, j, km);
-    T Bz = half * (b1 + b2 - b3 - b4) / (b1 + b2 + b3 + b4 + eps);
-    T Ub = quarter * (cu[q] + cu[at(g, i, jp, k)] + cu[at(g, im, j, k)] + cu[at(g, im, jp, k)]);
-    T Wb = quarter * (wface(cw, g, i, j, k) + wface(cw, g, i, jp, k) + wface(cw, g, i, j, k - 1) +
-                      wface(cw, g, i, jp, k - 1));
-    vt[q] = (fabs(V) - V * V / Gf) * A - V * (Ub * Bx + Wb * Bz) / Gf;
+    const T s1p = p(ip, jp, k) + p(ip, j, k), s1m = p(im, jp, k) + p(im, j, k);
+    const T s2p = p(i, jp, kp) + p(i, j, kp), s2m = p(i, jp, km) + p(i, j, km);
+    const T us = cu[q] + cu[at(g, i, jp, k)] + cu[at(g, im, j, k)] + cu[at(g, im, jp, k)];
+    const T ws = wface(cw, g, i, j, k) + wface(cw, g, i, jp, k) + wface(cw, g, i, j, k - 1) +
+                 wface(cw, g, i, jp, k - 1);
+    vt[q] = pseudo_velocity(cv[q], G[q] + G[at(g, i, jp, k)], pc, p(i, jp, k), s1p, s1m, s2p,
+                            s2m, us, ws);
   }
   if (k < g.nz - 1) {  // z face between (k) and (k+1); the top face is closed
-    T W = cw[q];
-    T pr = p(i, j, k + 1);
-    T Gf = half * (G[q] + G[q + g.pxy]);
-    T A = (pr - pc) / (pr + pc + eps);
-    T a1 = p(ip, j, k + 1), a2 = p(ip, j, k), a3 = p(im, j, k + 1), a4 = p(im, j, k);
-    T Bx = half * (a1 + a2 - a3 - a4) / (a1 + a2 + a3 + a4 + eps);
-    T b1 = p(i, jp, k + 1), b2 = p(i, jp, k), b3 = p(i, jm, k + 1), b4 = p(i, jm, k);
-    T By = half * (b1 + b2 - b3 - b4) / (b1 + b2 + b3 + b4 + eps);
-    T Ub = quarter * (cu[q] + cu[q + g.pxy] + cu[at(g, im, j, k)] + cu[at(g, im, j, k + 1)]);
-    T Vb = quarter * (cv[q] + cv[q + g.pxy] + cv[at(g, i, jm, k)] + cv[at(g, i, jm, k + 1)]);
-    wt[q] = (fabs(W) - W * W / Gf) * A - W * (Ub * Bx + Vb * By) / Gf;
+    const T s1p = p(ip, j, k + 1) + p(ip, j, k), s1m = p(im, j, k + 1) + p(im, j, k);
+    const T s2p = p(i, jp, k + 1) + p(i, jp, k), s2m = p(i, jm, k + 1) + p(i, jm, k);
+    const T us = cu[q] + cu[q + g.pxy] + cu[at(g, im, j, k)] + cu[at(g, im, j, k + 1)];
+    const T vs = cv[q] + cv[q + g.pxy] + cv[at(g, i, jm, k)] + cv[at(g, i, jm, k + 1)];
+    wt[q] = pseudo_velocity(cw[q], G[q] + G[q + g.pxy], pc, p(i, j, k + 1), s1p, s1m, s2p, s2m,
+                            us, vs);
   } else {
     wt[q] = T(0);
   }
@@ -143,11 +129,11 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
   const int64_t nb[6] = {at(g, im, j, k), at(g, ip, j, k), at(g, i, jm, k),
                          at(g, i, jp, k), at(g, i, j, km), at(g, i, j, kp)};
   T pc = P[q];
-  T hi = fmax(P0[q], pc), lo = fmin(P0[q], pc);
+  T hi = vmax(P0[q], pc), lo = vmin(P0[q], pc);
   for (int s = 0; s < 6; ++s) {
     T a = P0[nb[s]], b = P[nb[s]];
-    hi = fmax(hi, fmax(a, b));
-    lo = fmin(lo, fmin(a, b));
+    hi = vmax(hi, vmax(a, b));
+    lo = vmin(lo, vmin(a, b));
   }
   T fxp = donor(pc, P[nb[1]], ut[q]);
   T fxm = donor(P[nb[0]], pc, ut[nb[0]]);
@@ -155,20 +141,10 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
   T fym = donor(P[nb[2]], pc, vt[nb[2]]);
   T fzp = k < g.nz - 1 ? donor(pc, P[nb[5]], wt[q]) : zero;
   T fzm = k > 0 ? donor(P[nb[4]], pc, wt[nb[4]]) : zero;
-  T in = (fmax(fxm, zero) - fmin(fxp, zero)) + (fmax(fym, zero) - fmin(fyp, zero)) +
-         (fmax(fzm, zero) - fmin(fzp, zero));
-  T out = (fmax(fxp, zero) - fmin(fxm, zero)) + (fmax(fyp, zero) - fmin(fym, zero)) +
-          (fmax(fzp, zero) - fmin(fzm, zero));
-  bu[q] = (hi - pc) * G[q] / (in + eps);
-  bd[q] = (pc - lo) * G[q] / (out + eps);
-}
-
-// Limited velocity on a face: min(1, bd_L, bu_R)[Ut]+ + min(1, bu_L, bd_R)[Ut]-.
-template <class T>
-__device__ __forceinline__ T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
-  T cpos = fmin(fmin(T(1), bdL), buR);
-  T cneg = fmin(fmin(T(1), buL), bdR);
-  return cpos * fmax(Ut, T(0)) + cneg * fmin(Ut, T(0));
+  T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
+  T out = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
+  bu[q] = (hi - pc) * G[q] * rcp(in + eps);
+  bd[q] = (pc - lo) * G[q] * rcp(out + eps);
 }
 
 // Second half: limited velocities on the "+" faces and their donor fluxes.

@@ -70,6 +70,14 @@ class MPDATA:
                       self._ptr(w, "w"), self._ptr(g, "g"), nsteps)
         return psi
 
+    def step_out(self, psi_in, psi_out, u, v, w, g):
+        """One step psi_out = step(psi_in) (distinct tensors; current stream)."""
+        self._sync_stream()
+        C.mpdata_step_out(self._ctx, self._ptr(psi_in, "psi_in"), self._ptr(psi_out, "psi_out"),
+                          self._ptr(u, "u"), self._ptr(v, "v"), self._ptr(w, "w"),
+                          self._ptr(g, "g"))
+        return psi_out
+
     def fill_halo(self, f, kind: int = C.MPDATA_HALO_CELL):
         self._sync_stream()
         C.mpdata_fill_halo(self._ctx, self._ptr(f, "field"), kind)

@@ -48,14 +48,18 @@ def _device():
     build.build()
 
 
+VARIANTS = {"fused": 0, "staged": 1}
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("shape", SHAPES, ids=[f"{a}x{b}x{c}" for a, b, c in SHAPES])
 @pytest.mark.parametrize("iord,nonosc", SCHEMES)
-def test_f64_parity_small(shape, iord, nonosc):
+def test_f64_parity_small(shape, iord, nonosc, variant):
     nx, ny, nz = shape
     c = synth.random_case(nx, ny, nz, seed=nx * 1000 + ny * 10 + nz, cmax=0.3)
     for nsteps in (1, 3):
         ref = _oracle(c, iord, nonosc, nsteps)
-        got = run_library(c, torch.float64, iord, nonosc, nsteps)
+        got = run_library(c, torch.float64, iord, nonosc, nsteps, variant=VARIANTS[variant])
         assert rel_err(got, ref) <= F64_TOL * nsteps, (shape, nsteps)
         # the halo of the result is the periodic/edge-copy image of its interior
         inner = synth.interior(got, c.halo)
@@ -65,13 +69,14 @@ def test_f64_parity_small(shape, iord, nonosc):
         assert np.array_equal(got, ref_halo)
 
 
+@pytest.mark.parametrize("variant", list(VARIANTS))
 @pytest.mark.parametrize("shape", [(13, 11, 6), (37, 29, 9), (16, 16, 1)])
-@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 1), (3, 1)])
-def test_f32_against_f64_oracle(shape, iord, nonosc):
+@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1), (3, 1)])
+def test_f32_against_f64_oracle(shape, iord, nonosc, variant):
     nx, ny, nz = shape
     c = rounded_inputs(synth.random_case(nx, ny, nz, seed=99, cmax=0.3), torch.float32)
     ref = _oracle(c, iord, nonosc, 2)
-    got = run_library(c, torch.float32, iord, nonosc, 2)
+    got = run_library(c, torch.float32, iord, nonosc, 2, variant=VARIANTS[variant])
     assert rel_err(got, ref) <= 2 * F32_TOL
 
 
@@ -85,13 +90,55 @@ def test_rotating_cone_100_steps_f64():
 
 def test_latlon_256_full_field_f64():
     """The 3D FP64 configuration at full size (256x256x64, halo 2) in the
-    launch configuration the benchmark times: full-field comparison after 1
-    and 4 steps."""
+    launch configuration the benchmark times (fused kernel, k split into
+    chunks): full-field comparison after 1 and 4 steps, both variants."""
     c = synth.latlon_3d(256, 256, 64)
     for nsteps in (1, 4):
         ref = _oracle(c, 2, 1, nsteps)
-        got = run_library(c, torch.float64, 2, 1, nsteps)
-        assert rel_err(got, ref) <= F64_TOL * nsteps
+        for v in VARIANTS.values():
+            got = run_library(c, torch.float64, 2, 1, nsteps, variant=v)
+            assert rel_err(got, ref) <= F64_TOL * nsteps, (nsteps, v)
+
+
+@pytest.mark.parametrize("nz", [9, 40, 64])
+def test_fused_k_chunk_restart(nz):
+    """Few columns and many levels: the fused kernel splits k into chunks
+    that each rebuild their first planes' intermediates."""
+    c = synth.random_case(37, 20, nz, seed=nz, cmax=0.3)
+    ref = _oracle(c, 2, 1, 2)
+    got = run_library(c, torch.float64, 2, 1, 2, variant=0)
+    assert rel_err(got, ref) <= 2 * F64_TOL
+
+
+def test_out_of_place_step_equals_in_place():
+    from paper_1908_06094_b300 import MPDATA
+    c = synth.random_case(40, 36, 10, seed=77)
+    for dt in (torch.float64, torch.float32):
+        for variant in VARIANTS.values():
+            m = MPDATA(c.nx, c.ny, c.nz, halo=2, dtype=dt, variant=variant)
+            d = [to_dev(synth.pad(x, 2), dt) for x in (c.psi, c.u, c.v, c.w, c.g)]
+            psi_in = d[0].clone()
+            out = torch.full_like(d[0], float("nan"))
+            m.step_out(psi_in, out, *d[1:])
+            m.step(*d, nsteps=1)
+            assert torch.equal(out, d[0])
+            assert torch.equal(psi_in, to_dev(synth.pad(c.psi, 2), dt))  # input untouched
+            m.close()
+
+
+def test_fused_and_staged_agree_and_conserve():
+    from paper_1908_06094_b300 import MPDATA
+    c = synth.latlon_3d(64, 48, 12)
+    outs = []
+    for variant in VARIANTS.values():
+        m = MPDATA(c.nx, c.ny, c.nz, halo=2, dtype=torch.float64, variant=variant)
+        d = [to_dev(synth.pad(x, 2), torch.float64) for x in (c.psi, c.u, c.v, c.w, c.g)]
+        m0 = m.mass(d[0], d[4]).item()
+        m.step(*d, nsteps=7)
+        assert abs(m.mass(d[0], d[4]).item() - m0) <= 1e-14 * m0
+        outs.append(d[0].cpu().numpy())
+        m.close()
+    assert rel_err(outs[0], outs[1]) <= 7 * F64_TOL
 
 
 def test_latlon_512_f32_full_field():
