@@ -52,6 +52,7 @@ def _bind(path):
     lib.orc_mass.argtypes = [I, I, I, I, _D, _D]
     lib.orc_mass.restype = ctypes.c_double
     lib.orc_tlm.argtypes = [I, I, I, I, I, I, I] + [_D] * 11
+    lib.orc_adjoint.argtypes = [I, I, I, I, I, I, I] + [_D] * 9
     return lib
 
 
@@ -138,3 +139,18 @@ def tlm(psi, u, v, w, g, dpsi, du, dv, dw, h: int, iord: int = 2, nonosc: int = 
     dout = np.zeros_like(arrs[0])
     _load().orc_tlm(nx, ny, nz, h, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(out), _p(dout))
     return out, dout
+
+
+def adjoint(psi, u, v, w, g, psib, h: int, iord: int = 2, nonosc: int = 1, nsteps: int = 1):
+    """Reverse mode of nsteps steps.  psib: dJ/dpsi_T (padded, interior used).
+    Returns (dJ/dpsi_0, dJ/dU, dJ/dV, dJ/dW), padded with zero halos."""
+    nx, ny, nz = _dims(psi, h)
+    arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (psi, u, v, w, g)]
+    pb = np.array(psib, dtype=np.float64, order="C", copy=True)
+    ub, vb, wb = (np.zeros_like(arrs[0]) for _ in range(3))
+    _load().orc_adjoint(nx, ny, nz, h, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(pb),
+                        _p(ub), _p(vb), _p(wb))
+    inner = np.zeros_like(pb)
+    sl = (slice(h, h + nz), slice(h, h + ny), slice(h, h + nx))
+    inner[sl] = pb[sl]
+    return inner, ub, vb, wb

@@ -345,6 +345,300 @@ void mpdata_step(const Grid& g, int iord, int nonosc, const T* psi_in, const T* 
   for (long q = 0; q < n; ++q) psi_out[q] = P[q];
 }
 
+
+/* ========================================================= adjoint (reverse) */
+
+/* Reverse of fill_halo_periodic: every halo value was a copy of an interior
+   (or, in k, an edge-plane) value, so its adjoint is added to that source
+   and cleared; done in the reverse order of the forward fill. */
+void rev_halo_periodic(double* a, const Grid& g) {
+  for (int k = -g.h; k < g.nz + g.h; ++k) {
+    if (k >= 0 && k < g.nz) continue;
+    int ks = k < 0 ? 0 : g.nz - 1;
+    for (int j = -g.h; j < g.ny + g.h; ++j)
+      for (int i = -g.h; i < g.nx + g.h; ++i) {
+        a[g.at(i, j, ks)] += a[g.at(i, j, k)];
+        a[g.at(i, j, k)] = 0.0;
+      }
+  }
+  for (int k = 0; k < g.nz; ++k) {
+    for (int j = -g.h; j < g.ny + g.h; ++j)
+      if (j < 0 || j >= g.ny)
+        for (int i = -g.h; i < g.nx + g.h; ++i) {
+          a[g.at(i, wrap(j, g.ny), k)] += a[g.at(i, j, k)];
+          a[g.at(i, j, k)] = 0.0;
+        }
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = -g.h; i < g.nx + g.h; ++i)
+        if (i < 0 || i >= g.nx) {
+          a[g.at(wrap(i, g.nx), j, k)] += a[g.at(i, j, k)];
+          a[g.at(i, j, k)] = 0.0;
+        }
+  }
+}
+
+/* Reverse of fill_halo_wface: the closed faces were overwritten with zero,
+   so their adjoints are dropped; the rest is the periodic reverse. */
+void rev_halo_wface(double* a, const Grid& g) {
+  for (int k = -g.h; k < g.nz + g.h; ++k) {
+    if (k >= 0 && k < g.nz - 1) continue;
+    for (int j = -g.h; j < g.ny + g.h; ++j)
+      for (int i = -g.h; i < g.nx + g.h; ++i) a[g.at(i, j, k)] = 0.0;
+  }
+  rev_halo_periodic(a, g);
+}
+
+/* Reverse of F(L,R,C) = max(C,0) L + min(C,0) R with adjoint fb: the branch
+   rules of omax/omin (a tie at C = 0 takes C on both sides). */
+inline void rev_donor(double fb, double L, double R, double C, double* Lb, double* Rb,
+                      double* Cb) {
+  *Lb += fb * (C >= 0 ? C : 0.0);
+  *Rb += fb * (C <= 0 ? C : 0.0);
+  *Cb += fb * ((C >= 0 ? L : 0.0) + (C <= 0 ? R : 0.0));
+}
+
+/* Reverse of advance: out = P - (1/G) sum_d [F_+ - F_-], for the adjoint
+   ob of out at the interior points; accumulates into Pb and the velocity
+   adjoints (padded arrays, halo entries included). */
+void rev_advance(const Grid& g, const double* P, const double* u, const double* v,
+                 const double* w, const double* G, const double* ob, double* Pb, double* ub,
+                 double* vb, double* wb) {
+  const long D[3] = {1, g.px, g.px * g.py};
+  const double* vel[3] = {u, v, w};
+  double* velb[3] = {ub, vb, wb};
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        double a = ob[c];
+        Pb[c] += a;
+        double s = -a / G[c];
+        for (int d = 0; d < 3; ++d) {
+          rev_donor(s, P[c], P[c + D[d]], vel[d][c], &Pb[c], &Pb[c + D[d]], &velb[d][c]);
+          rev_donor(-s, P[c - D[d]], P[c], vel[d][c - D[d]], &Pb[c - D[d]], &Pb[c],
+                    &velb[d][c - D[d]]);
+        }
+      }
+}
+
+/* Reverse of the pseudo-velocity of one face.  L, R: the two cells;
+   Y1/Y2: the strides of the two cross directions; cv1, cv2 the Courant
+   fields of those directions, with their own "minus" strides M1, M2 (the
+   cross averages take the faces at L, R, L-M, R-M). */
+inline void rev_face_pseudo(double ub, const double* P, long L, long R, long Y1, long Y2,
+                            double U, double Gf, const double* c1, const double* c2, long M1,
+                            long M2, double* Pb, double* Ub, double* c1b, double* c2b) {
+  const double eps = EPS;
+  double n = P[R] - P[L], d = P[R] + P[L] + eps, A = n / d;
+  double n1 = 0.5 * (P[R + Y1] + P[L + Y1] - P[R - Y1] - P[L - Y1]);
+  double d1 = P[R + Y1] + P[L + Y1] + P[R - Y1] + P[L - Y1] + eps;
+  double B1 = n1 / d1;
+  double n2 = 0.5 * (P[R + Y2] + P[L + Y2] - P[R - Y2] - P[L - Y2]);
+  double d2 = P[R + Y2] + P[L + Y2] + P[R - Y2] + P[L - Y2] + eps;
+  double B2 = n2 / d2;
+  double C1 = 0.25 * (c1[L] + c1[R] + c1[L - M1] + c1[R - M1]);
+  double C2 = 0.25 * (c2[L] + c2[R] + c2[L - M2] + c2[R - M2]);
+  double Dd = oabs(U) - U * U / Gf;
+  double X = C1 * B1 + C2 * B2;
+  double sg = U > 0 ? 1.0 : (U < 0 ? -1.0 : 0.0);
+  *Ub += ub * (sg * A - 2.0 * U / Gf * A - X / Gf);
+  double Ab = ub * Dd;
+  double B1b = ub * (-U * C1 / Gf), B2b = ub * (-U * C2 / Gf);
+  double C1b = ub * (-U * B1 / Gf), C2b = ub * (-U * B2 / Gf);
+  Pb[R] += Ab * (1.0 - A) / d;
+  Pb[L] += Ab * (-1.0 - A) / d;
+  double wp = B1b * (0.5 - B1) / d1, wm = B1b * (-0.5 - B1) / d1;
+  Pb[R + Y1] += wp; Pb[L + Y1] += wp; Pb[R - Y1] += wm; Pb[L - Y1] += wm;
+  wp = B2b * (0.5 - B2) / d2; wm = B2b * (-0.5 - B2) / d2;
+  Pb[R + Y2] += wp; Pb[L + Y2] += wp; Pb[R - Y2] += wm; Pb[L - Y2] += wm;
+  c1b[L] += 0.25 * C1b; c1b[R] += 0.25 * C1b; c1b[L - M1] += 0.25 * C1b; c1b[R - M1] += 0.25 * C1b;
+  c2b[L] += 0.25 * C2b; c2b[R] += 0.25 * C2b; c2b[L - M2] += 0.25 * C2b; c2b[R - M2] += 0.25 * C2b;
+}
+
+void rev_pseudo(const Grid& g, const double* P, const double* u, const double* v, const double* w,
+                const double* G, const double* utb, const double* vtb, const double* wtb,
+                double* Pb, double* ub, double* vb, double* wb) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        rev_face_pseudo(utb[c], P, c, c + X, Y, Z, u[c], 0.5 * (G[c] + G[c + X]), v, w, Y, Z,
+                        Pb, &ub[c], vb, wb);
+        rev_face_pseudo(vtb[c], P, c, c + Y, X, Z, v[c], 0.5 * (G[c] + G[c + Y]), u, w, X, Z,
+                        Pb, &vb[c], ub, wb);
+        if (k < g.nz - 1)
+          rev_face_pseudo(wtb[c], P, c, c + Z, X, Y, w[c], 0.5 * (G[c] + G[c + Z]), u, v, X, Y,
+                          Pb, &wb[c], ub, vb);
+      }
+}
+
+/* Reverse of limit_face: routes the adjoint of the limited velocity to Ut and
+   to the betas that won the two min(1, ., .) folds (tie: the earlier one). */
+inline void rev_limit_face(double lb, double Ut, double buL, double bdL, double buR, double bdR,
+                           double* Utb, double* buLb, double* bdLb, double* buRb, double* bdRb) {
+  double m1 = (1.0 <= bdL) ? 1.0 : bdL;
+  bool p_is_bdL = !(1.0 <= bdL);
+  double cpos = (m1 <= buR) ? m1 : buR;
+  bool p_first = (m1 <= buR);
+  double n1 = (1.0 <= buL) ? 1.0 : buL;
+  bool n_is_buL = !(1.0 <= buL);
+  double cneg = (n1 <= bdR) ? n1 : bdR;
+  bool n_first = (n1 <= bdR);
+  *Utb += lb * ((Ut >= 0 ? cpos : 0.0) + (Ut <= 0 ? cneg : 0.0));
+  double cpb = lb * (Ut >= 0 ? Ut : 0.0), cnb = lb * (Ut <= 0 ? Ut : 0.0);
+  if (p_first) { if (p_is_bdL) *bdLb += cpb; } else { *buRb += cpb; }
+  if (n_first) { if (n_is_buL) *buLb += cnb; } else { *bdRb += cnb; }
+}
+
+void rev_limit(const Grid& g, const double* ut, const double* vt, const double* wt,
+               const double* bu, const double* bd, const double* ulb, const double* vlb,
+               const double* wlb, double* utb, double* vtb, double* wtb, double* bub,
+               double* bdb) {
+  const long D[3] = {1, g.px, g.px * g.py};
+  const double* vt3[3] = {ut, vt, wt};
+  const double* lb3[3] = {ulb, vlb, wlb};
+  double* tb3[3] = {utb, vtb, wtb};
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        for (int d = 0; d < 3; ++d) {
+          if (d == 2 && k == g.nz - 1) continue;  // closed top face: constant
+          long r = c + D[d];
+          rev_limit_face(lb3[d][c], vt3[d][c], bu[c], bd[c], bu[r], bd[r], &tb3[d][c], &bub[c],
+                         &bdb[c], &bub[r], &bdb[r]);
+        }
+      }
+}
+
+/* Reverse of limiter_betas for the adjoints bub, bdb of the betas. */
+void rev_beta(const Grid& g, const double* P0, const double* P, const double* ut,
+              const double* vt, const double* wt, const double* G, const double* bub,
+              const double* bdb, double* P0b, double* Pb, double* utb, double* vtb, double* wtb) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+  const long nb[6] = {-X, X, -Y, Y, -Z, Z};
+  const long D[3] = {X, Y, Z};
+  const double* vt3[3] = {ut, vt, wt};
+  double* tb3[3] = {utb, vtb, wtb};
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        // bounds, remembering which element won each fold (same order as forward)
+        double hi = P0[c], lo = P0[c];
+        double* hip = &P0b[c];
+        double* lop = &P0b[c];
+        if (!(hi >= P[c])) { hi = P[c]; hip = &Pb[c]; }
+        if (!(lo <= P[c])) { lo = P[c]; lop = &Pb[c]; }
+        for (int q = 0; q < 6; ++q) {
+          long n = c + nb[q];
+          if (!(hi >= P0[n])) { hi = P0[n]; hip = &P0b[n]; }
+          if (!(hi >= P[n])) { hi = P[n]; hip = &Pb[n]; }
+          if (!(lo <= P0[n])) { lo = P0[n]; lop = &P0b[n]; }
+          if (!(lo <= P[n])) { lo = P[n]; lop = &Pb[n]; }
+        }
+        double fp[3], fm[3];
+        for (int d = 0; d < 3; ++d) {
+          fp[d] = donor(P[c], P[c + D[d]], vt3[d][c]);
+          fm[d] = donor(P[c - D[d]], P[c], vt3[d][c - D[d]]);
+        }
+        double in = (omax(fm[0], 0.0) - omin(fp[0], 0.0)) + (omax(fm[1], 0.0) - omin(fp[1], 0.0)) +
+                    (omax(fm[2], 0.0) - omin(fp[2], 0.0));
+        double out = (omax(fp[0], 0.0) - omin(fm[0], 0.0)) + (omax(fp[1], 0.0) - omin(fm[1], 0.0)) +
+                     (omax(fp[2], 0.0) - omin(fm[2], 0.0));
+        double din = in + EPS, dout = out + EPS;
+        double bu = (hi - P[c]) * G[c] / din, bd = (P[c] - lo) * G[c] / dout;
+        double ab = bub[c], db = bdb[c];
+        *hip += ab * G[c] / din;
+        Pb[c] -= ab * G[c] / din;
+        double inb = -ab * bu / din;
+        Pb[c] += db * G[c] / dout;
+        *lop -= db * G[c] / dout;
+        double outb = -db * bd / dout;
+        for (int d = 0; d < 3; ++d) {
+          // top/bottom closed faces carry constant zero fluxes
+          bool has_p = !(d == 2 && k == g.nz - 1), has_m = !(d == 2 && k == 0);
+          double fpb = -inb * (fp[d] <= 0 ? 1.0 : 0.0) + outb * (fp[d] >= 0 ? 1.0 : 0.0);
+          double fmb = inb * (fm[d] >= 0 ? 1.0 : 0.0) - outb * (fm[d] <= 0 ? 1.0 : 0.0);
+          if (has_p) rev_donor(fpb, P[c], P[c + D[d]], vt3[d][c], &Pb[c], &Pb[c + D[d]], &tb3[d][c]);
+          if (has_m)
+            rev_donor(fmb, P[c - D[d]], P[c], vt3[d][c - D[d]], &Pb[c - D[d]], &Pb[c],
+                      &tb3[d][c - D[d]]);
+        }
+      }
+}
+
+/* One adjoint step: psib holds the adjoint of psi^(n+1) at interior points
+   on entry and that of psi^n on exit; ubar, vbar, wbar are incremented. */
+void adjoint_step(const Grid& g, int iord, int nonosc, const double* psi_in, const double* Uin,
+                  const double* Vin, const double* Win, const double* Gin, double* psib,
+                  double* ubar, double* vbar, double* wbar) {
+  const long n = g.size();
+  std::vector<double> P1(n), ut(n), vt(n), wt(n), mx(n), mn(n), bu(n), bd(n), ul(n), vl(n), wl(n);
+  std::vector<double> tmp(n);
+  Stages st{P1.data(), ut.data(), vt.data(), wt.data(), mx.data(), mn.data(), bu.data(),
+            bd.data(), ul.data(), vl.data(), wl.data()};
+  mpdata_step<double>(g, iord, nonosc, psi_in, Uin, Vin, Win, Gin, tmp.data(), &st);
+  std::vector<double> P0(n), U(n), V(n), W(n), G(n);
+  for (long q = 0; q < n; ++q) { P0[q] = psi_in[q]; U[q] = Uin[q]; V[q] = Vin[q]; W[q] = Win[q]; G[q] = Gin[q]; }
+  fill_halo_periodic(P0.data(), g);
+  fill_halo_periodic(U.data(), g);
+  fill_halo_periodic(V.data(), g);
+  fill_halo_periodic(G.data(), g);
+  fill_halo_wface(W.data(), g);
+  std::vector<double> P0b(n, 0.0), P1b(n, 0.0), Ub(n, 0.0), Vb(n, 0.0), Wb(n, 0.0);
+  std::vector<double> ob(n, 0.0);
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) ob[g.at(i, j, k)] = psib[g.at(i, j, k)];
+  if (iord == 1) {
+    rev_advance(g, P0.data(), U.data(), V.data(), W.data(), G.data(), ob.data(), P0b.data(),
+                Ub.data(), Vb.data(), Wb.data());
+  } else {
+    std::vector<double> utb(n, 0.0), vtb(n, 0.0), wtb(n, 0.0);
+    std::vector<double> ulb(n, 0.0), vlb(n, 0.0), wlb(n, 0.0), bub(n, 0.0), bdb(n, 0.0);
+    double* velb[3] = {nonosc ? ulb.data() : utb.data(), nonosc ? vlb.data() : vtb.data(),
+                       nonosc ? wlb.data() : wtb.data()};
+    const double* vel[3] = {nonosc ? ul.data() : ut.data(), nonosc ? vl.data() : vt.data(),
+                            nonosc ? wl.data() : wt.data()};
+    rev_advance(g, P1.data(), vel[0], vel[1], vel[2], G.data(), ob.data(), P1b.data(), velb[0],
+                velb[1], velb[2]);
+    rev_halo_periodic(velb[0], g);
+    rev_halo_periodic(velb[1], g);
+    rev_halo_wface(velb[2], g);
+    if (nonosc) {
+      rev_limit(g, ut.data(), vt.data(), wt.data(), bu.data(), bd.data(), ulb.data(), vlb.data(),
+                wlb.data(), utb.data(), vtb.data(), wtb.data(), bub.data(), bdb.data());
+      rev_halo_periodic(bub.data(), g);
+      rev_halo_periodic(bdb.data(), g);
+      rev_beta(g, P0.data(), P1.data(), ut.data(), vt.data(), wt.data(), G.data(), bub.data(),
+               bdb.data(), P0b.data(), P1b.data(), utb.data(), vtb.data(), wtb.data());
+      rev_halo_periodic(utb.data(), g);
+      rev_halo_periodic(vtb.data(), g);
+      rev_halo_wface(wtb.data(), g);
+    }
+    rev_pseudo(g, P1.data(), U.data(), V.data(), W.data(), G.data(), utb.data(), vtb.data(),
+               wtb.data(), P1b.data(), Ub.data(), Vb.data(), Wb.data());
+    rev_halo_periodic(P1b.data(), g);
+    rev_advance(g, P0.data(), U.data(), V.data(), W.data(), G.data(), P1b.data(), P0b.data(),
+                Ub.data(), Vb.data(), Wb.data());
+  }
+  rev_halo_periodic(P0b.data(), g);
+  rev_halo_periodic(Ub.data(), g);
+  rev_halo_periodic(Vb.data(), g);
+  rev_halo_wface(Wb.data(), g);
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        psib[c] = P0b[c];
+        ubar[c] += Ub[c];
+        vbar[c] += Vb[c];
+        wbar[c] += Wb[c];
+      }
+}
+
 }  // namespace
 
 /* =============================================================== C ABI */
@@ -427,6 +721,27 @@ void orc_tlm(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps, co
     p.swap(o);
   }
   for (long q = 0; q < n; ++q) { psi_out[q] = p[q].v; dpsi_out[q] = p[q].d; }
+}
+
+/* Adjoint of nsteps steps (iord 1 or 2): psib holds dJ/dpsi at step nsteps
+   (interior) on entry and dJ/dpsi at step 0 on exit; ubar, vbar, wbar are
+   incremented by dJ/dU, dJ/dV, dJ/dW.  The forward states are recomputed
+   from psi (all stored; the oracle is for small grids).  G is held fixed. */
+void orc_adjoint(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps,
+                 const double* psi, const double* U, const double* V, const double* W,
+                 const double* G, double* psib, double* ubar, double* vbar, double* wbar) {
+  Grid g(nx, ny, nz, h);
+  long n = g.size();
+  std::vector<std::vector<double>> states(nsteps > 0 ? nsteps : 1, std::vector<double>(n));
+  std::vector<double> cur(psi, psi + n);
+  for (int s = 0; s < nsteps; ++s) {
+    states[s] = cur;
+    std::vector<double> nxt(n);
+    mpdata_step<double>(g, iord, nonosc, cur.data(), U, V, W, G, nxt.data(), nullptr);
+    cur.swap(nxt);
+  }
+  for (int s = nsteps - 1; s >= 0; --s)
+    adjoint_step(g, iord, nonosc, states[s].data(), U, V, W, G, psib, ubar, vbar, wbar);
 }
 
 }  // extern "C"

@@ -47,17 +47,32 @@ MUTANTS = [
      "T cpos = omin(omin(one, bdL), buR);",
      "T cpos = omin(omin(one, buL), bdR);"),
     ("limiter bounds miss the upward neighbour",
-     "const long nb[6] = {-X, X, -Y, Y, -Z, Z};",
-     "const long nb[6] = {-X, -X, -Y, Y, -Z, Z};"),
+     "const long nb[6] = {-X, X, -Y, Y, -Z, Z};\n#pragma omp parallel for",
+     "const long nb[6] = {-X, -X, -Y, Y, -Z, Z};\n#pragma omp parallel for"),
     ("top face left open",
-     "if (k >= 0 && k < g.nz - 1) continue;",
-     "if (k >= 0 && k < g.nz) continue;"),
+     "  fill_halo_periodic(f, g);\n  for (int k = -g.h; k < g.nz + g.h; ++k) {\n    if (k >= 0 && k < g.nz - 1) continue;",
+     "  fill_halo_periodic(f, g);\n  for (int k = -g.h; k < g.nz + g.h; ++k) {\n    if (k >= 0 && k < g.nz) continue;"),
     ("advance forgets 1/G",
      "out[c] = P[c] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) / G[c];",
      "out[c] = P[c] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm));"),
     ("epsilon dropped",
      "const double EPS = 1e-15;",
      "const double EPS = 0.0;"),
+    ("adjoint drops the 1/4 of the cross average",
+     "c1b[L] += 0.25 * C1b; c1b[R] += 0.25 * C1b;",
+     "c1b[L] += C1b; c1b[R] += 0.25 * C1b;"),
+    ("adjoint routes the limiter factor to the wrong beta",
+     "if (p_first) { if (p_is_bdL) *bdLb += cpb; } else { *buRb += cpb; }",
+     "if (p_first) { if (p_is_bdL) *buRb += cpb; } else { *bdLb += cpb; }"),
+    ("adjoint skips folding the psi1 halo",
+     "    rev_halo_periodic(P1b.data(), g);\n    rev_advance(",
+     "    rev_advance("),
+    ("adjoint breaks bound ties the other way",
+     "if (!(hi >= P[c])) { hi = P[c]; hip = &Pb[c]; }",
+     "if (!(hi > P[c])) { hi = P[c]; hip = &Pb[c]; }"),
+    ("adjoint forgets d|U|/dU",
+     "*Ub += ub * (sg * A - 2.0 * U / Gf * A - X / Gf);",
+     "*Ub += ub * (-2.0 * U / Gf * A - X / Gf);"),
     ("y halo not wrapped",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, wrap(j, g.ny), k)];",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, j < 0 ? 0 : g.ny - 1, k)];"),
@@ -88,6 +103,9 @@ def _pin_battery():
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("x", -0.4),
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("y", 0.4),
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("z", -0.4),
+        lambda: pins.test_adjoint_dot_product_against_tlm(2, 1, 1),
+        lambda: pins.test_adjoint_dot_product_against_tlm(2, 0, 1),
+        pins.test_adjoint_dot_product_on_rotating_cone,
     ]
     failed = 0
     for chk in checks:

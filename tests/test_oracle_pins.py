@@ -372,3 +372,73 @@ def test_limiter_inactive_on_smooth_monotone_data(axis, c):
     unl = interior(oracle.run(*P, h=H, iord=2, nonosc=0), H)
     assert np.array_equal(lim[sl], unl[sl])
     assert not np.array_equal(unl, psi)
+
+
+# ---------------------------------------------------------------- adjoint --
+
+def _inner(a, b, h=H):
+    return float(np.sum(interior(a, h) * interior(b, h)))
+
+
+@pytest.mark.parametrize("iord,nonosc,nsteps", [(1, 0, 1), (2, 0, 1), (2, 1, 1), (2, 1, 3),
+                                                (2, 0, 3)])
+def test_adjoint_dot_product_against_tlm(iord, nonosc, nsteps):
+    """<L dx, dy> = <dx, L^T dy> with L the dual-number tangent-linear model
+    (an independent derivative of the forward code) and L^T the hand-written
+    reverse mode, to 1e-12 relative."""
+    c = synth.random_case(9, 8, 5, seed=41, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
+    rng = np.random.default_rng(42)
+    P = [pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    dx = [pad(rng.standard_normal(c.psi.shape), H) for _ in range(4)]
+    dy = pad(rng.standard_normal(c.psi.shape), H)
+    _, tl = oracle.tlm(*P, *dx, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps)
+    lhs = _inner(tl, dy)
+    pb, ub, vb, wb = oracle.adjoint(*P, dy, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps)
+    rhs = _inner(dx[0], pb) + _inner(dx[1], ub) + _inner(dx[2], vb) + _inner(dx[3], wb)
+    assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1e-30), (lhs, rhs)
+
+
+def test_adjoint_dot_product_on_rotating_cone():
+    """The same identity on the cone configuration: exact ties (flat
+    background, zero velocities outside the rotation radius) exercise the
+    branch rules shared by the tangent and the adjoint."""
+    c = synth.rotation_2d(24, radius_frac=0.4, cone_radius=4.0, cone_offset=5.0)
+    rng = np.random.default_rng(7)
+    P = [pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    dx = [pad(rng.standard_normal(c.psi.shape), H) for _ in range(4)]
+    dx[3][:] = 0.0
+    dy = pad(rng.standard_normal(c.psi.shape), H)
+    _, tl = oracle.tlm(*P, *dx, h=H, iord=2, nonosc=1, nsteps=4)
+    pb, ub, vb, wb = oracle.adjoint(*P, dy, h=H, iord=2, nonosc=1, nsteps=4)
+    lhs = _inner(tl, dy)
+    rhs = _inner(dx[0], pb) + _inner(dx[1], ub) + _inner(dx[2], vb)
+    assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """dJ/dx from the reverse mode against central differences of
+    J = sum (psi_T - psi_obs)^2 G, in random directions of psi_0 and of the
+    Courant fields (relative error <= 1e-6, h = 1e-6 |x|)."""
+    c = synth.random_case(8, 7, 4, seed=51, cmax=0.25, psi_lo=0.3, psi_hi=1.4)
+    rng = np.random.default_rng(52)
+    P = [pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    obs = P[0] + pad(0.05 * rng.standard_normal(c.psi.shape), H)
+
+    def J(p, u, v, w):
+        out = oracle.run(p, u, v, w, P[4], h=H, iord=2, nonosc=1, nsteps=3)
+        return float(np.sum(interior((out - obs) ** 2 * P[4], H)))
+
+    out = oracle.run(*P, h=H, iord=2, nonosc=1, nsteps=3)
+    dJ = 2.0 * (out - obs) * P[4]
+    pb, ub, vb, wb = oracle.adjoint(*P, dJ, h=H, iord=2, nonosc=1, nsteps=3)
+    grads = [pb, ub, vb, wb]
+    for trial in range(6):
+        d = [pad(rng.standard_normal(c.psi.shape), H) for _ in range(4)]
+        d[3][H + c.nz - 1] = 0.0
+        x = P[:4]
+        eps = 1e-6 * max(np.max(np.abs(interior(a, H))) for a in x)
+        jp = J(*(a + eps * b for a, b in zip(x, d)))
+        jm = J(*(a - eps * b for a, b in zip(x, d)))
+        fd = (jp - jm) / (2 * eps)
+        an = sum(_inner(gr, dd) for gr, dd in zip(grads, d))
+        assert abs(fd - an) <= 1e-6 * abs(an), (trial, fd, an)
