@@ -129,6 +129,29 @@ MPDATA_API int mpdata_step_out(mpdata_ctx *c, const void *psi_in, void *psi_out,
 MPDATA_API int mpdata_step_host(mpdata_ctx *c, void *psi_host, const void *u_host, const void *v_host,
                      const void *w_host, const void *g_host, int nsteps);
 
+/* Adjoint (reverse mode) of one step, iord 1 or 2, with or without the
+ * limiter: the derivative of a scalar cost J through the step.
+ *   psi_n          the state the step started from (DEVICE, read-only);
+ *   u, v, w, g     the step's Courant fields and metric (DEVICE, read-only);
+ *   psi_bar        in: dJ/dpsi^(n+1) at interior points; out: dJ/dpsi^n at
+ *                  interior points, zero halo;
+ *   u_bar, v_bar, w_bar  incremented by dJ/dU, dJ/dV, dJ/dW at interior
+ *                  points (the closed top face of W gets nothing).
+ * G is held fixed.  The step's intermediates are recomputed from psi_n;
+ * derivatives follow the branches the forward takes (ties: max(a,b) = a
+ * if a >= b, min(a,b) = a if a <= b, sign(0) = 0).  The reverse kernels add
+ * with atomics, so results can differ in the last bits between runs.  The
+ * first call allocates the adjoint scratch (13 fields).
+ * Errors: EINVAL (iord > 2, null pointer), EALIGN, ENOMEM, ECUDA. */
+MPDATA_API int mpdata_adjoint_step(mpdata_ctx *c, const void *psi_n, const void *u,
+                                   const void *v, const void *w, const void *g, void *psi_bar,
+                                   void *u_bar, void *v_bar, void *w_bar);
+
+/* Reverse of the CELL halo fill for an adjoint field (DEVICE, in place):
+ * each halo entry's adjoint is added to the interior value it copies, then
+ * the halo is cleared.  Errors: EINVAL, EALIGN, ECUDA. */
+MPDATA_API int mpdata_fold_halo_adjoint(mpdata_ctx *c, void *field);
+
 /* Fill the halo of a padded field in place (kind: mpdata_halo_kind).
  * Periodic in i and j, corners included; in k an edge copy (CELL) or zero
  * (WFACE, which also zeroes the top face k = nz-1).

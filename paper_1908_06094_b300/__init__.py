@@ -3,14 +3,16 @@ thin Python binding over it.
 
 * ``_capi``   -- ctypes binding, one function per C entry point;
 * ``MPDATA``  -- the same calls taking torch CUDA tensors (pointer and stream
-  marshalling only: every step of the method runs in the library's kernels).
+  marshalling only: every step of the method runs in the library's kernels);
+* ``MPDATAFunction`` / ``mpdata_run`` -- autograd over the forward and
+  adjoint steps with checkpoint-and-recompute.
 
 The library is loaded on first use of either; a missing or unloadable
 library raises ImportError (there is no fallback path).
 """
 import importlib
 
-__all__ = ["_capi", "MPDATA", "padded_shape"]
+__all__ = ["_capi", "MPDATA", "padded_shape", "MPDATAFunction", "mpdata_run"]
 
 
 def __getattr__(name):
@@ -18,5 +20,8 @@ def __getattr__(name):
         return importlib.import_module("._capi", __name__)
     if name in ("MPDATA", "padded_shape"):
         mod = importlib.import_module(".mpdata", __name__)
+        return getattr(mod, name)
+    if name in ("MPDATAFunction", "mpdata_run"):
+        mod = importlib.import_module(".autograd", __name__)
         return getattr(mod, name)
     raise AttributeError(name)

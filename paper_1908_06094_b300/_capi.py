@@ -47,6 +47,8 @@ SIGNATURES = {
     "mpdata_step_out": (_i, [_c, _c, _c, _c, _c, _c, _c]),
     "mpdata_step_host": (_i, [_c, _c, _c, _c, _c, _c, _i]),
     "mpdata_fill_halo": (_i, [_c, _c, _i]),
+    "mpdata_adjoint_step": (_i, [_c] * 10),
+    "mpdata_fold_halo_adjoint": (_i, [_c, _c]),
     "mpdata_mass": (_i, [_c, _c, _c, _c]),
     "mpdata_destroy": (None, [_c]),
     "mpdata_strerror": (ctypes.c_char_p, [_i]),
@@ -158,3 +160,12 @@ def mpdata_mass_noalloc(psi, g, nx, ny, nz, halo, dtype, out_dev, cuda_stream=0)
     """Context-free mass sum that allocates nothing (see include/mpdata.h)."""
     _check(lib.mpdata_mass_noalloc(psi, g, nx, ny, nz, halo, dtype, out_dev, cuda_stream),
            "mpdata_mass_noalloc")
+
+
+def mpdata_adjoint_step(ctx, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar):
+    _check(lib.mpdata_adjoint_step(ctx, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar),
+           "mpdata_adjoint_step", ctx)
+
+
+def mpdata_fold_halo_adjoint(ctx, field):
+    _check(lib.mpdata_fold_halo_adjoint(ctx, field), "mpdata_fold_halo_adjoint", ctx)

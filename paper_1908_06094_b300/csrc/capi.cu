@@ -12,6 +12,7 @@
 #include "mass.cuh"
 #include "staged.cuh"
 #include "fused.cuh"
+#include "adjoint.cuh"
 
 using mpd::Geo;
 
@@ -28,6 +29,10 @@ struct mpdata_ctx {
   int fused_ok, nchunks, kchunk;
   // device copies for the HOST-buffer call (allocated on its first use)
   void* hbuf;
+  // adjoint scratch (allocated on the first adjoint call)
+  void* adjbuf;
+  void *a_ul, *a_vl, *a_wl, *a_p1b, *a_p0b, *a_utb, *a_vtb, *a_wtb, *a_ulb, *a_vlb, *a_wlb,
+      *a_bub, *a_bdb;
   // instrumentation
   long long launches;
   bool prof_on;
@@ -271,6 +276,100 @@ int mass_launch(mpdata_ctx* c, const T* psi, const T* G, double* out) {
   return MPDATA_OK;
 }
 
+// ------------------------------------------------------------- adjoint --
+
+int adjoint_scratch(mpdata_ctx* c) {
+  if (c->adjbuf) return MPDATA_OK;
+  const size_t fbytes = ((size_t)c->g.total * c->esize + 255) & ~(size_t)255;
+  if (cudaMalloc(&c->adjbuf, 13 * fbytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->adjbuf = nullptr;
+    return MPDATA_ENOMEM;
+  }
+  char* p = (char*)c->adjbuf;
+  void** slots[13] = {&c->a_ul, &c->a_vl, &c->a_wl, &c->a_p1b, &c->a_p0b, &c->a_utb, &c->a_vtb,
+                      &c->a_wtb, &c->a_ulb, &c->a_vlb, &c->a_wlb, &c->a_bub, &c->a_bdb};
+  for (int q = 0; q < 13; ++q) *slots[q] = p + q * fbytes;
+  return MPDATA_OK;
+}
+
+template <class T>
+int halo_fold_launch(mpdata_ctx* c, T* f) {
+  int64_t n = c->g.total;
+  int blocks = (int)((n + 255) / 256);
+  if (blocks > 148 * 16) blocks = 148 * 16;
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_fold_kernel<T><<<blocks, 256, 0, c->stream>>>(c->g, f));
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_zero_kernel<T><<<blocks, 256, 0, c->stream>>>(c->g, f));
+  MPD_CHECK_LAUNCH(c, "halo adjoint fold");
+  return MPDATA_OK;
+}
+
+// One adjoint step: recompute the step's intermediates from psi^n with the
+// staged forward kernels, then run the reverse kernels.
+template <class T>
+int adjoint_step(mpdata_ctx* c, const T* psi, const T* U, const T* V, const T* W, const T* G,
+                 T* psib, T* ub, T* vb, T* wb) {
+  using namespace mpd::staged;
+  using namespace mpd::adj;
+  int rc = adjoint_scratch(c);
+  if (rc) return rc;
+  const Geo& g = c->g;
+  const dim3 grid = cell_grid(g);
+  cudaStream_t s = c->stream;
+  const size_t fb = (size_t)g.total * sizeof(T);
+  T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
+  T* p1 = (T*)c->psi1;
+  T *ut = (T*)c->ut, *vt = (T*)c->vt, *wt = (T*)c->wt, *bu = (T*)c->bu, *bd = (T*)c->bd;
+  T *ul = (T*)c->a_ul, *vl = (T*)c->a_vl, *wl = (T*)c->a_wl;
+  T *p1b = (T*)c->a_p1b, *p0b = (T*)c->a_p0b;
+  T *utb = (T*)c->a_utb, *vtb = (T*)c->a_vtb, *wtb = (T*)c->a_wtb;
+  T *ulb = (T*)c->a_ulb, *vlb = (T*)c->a_vlb, *wlb = (T*)c->a_wlb;
+  T *bub = (T*)c->a_bub, *bdb = (T*)c->a_bdb;
+  // forward recompute
+  if (c->iord == 2) {
+    MPD_LAUNCH(c, MPDATA_STAGE_DONOR, flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, p1));
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(g, p1, U, V, W, G, ut, vt, wt));
+    if (c->nonosc) {
+      MPD_LAUNCH(c, MPDATA_STAGE_BETA, beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, p1, ut, vt, wt, G, bu, bd));
+      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                            g, p1, ut, vt, wt, bu, bd, fx, fy, fz, ul, vl, wl));
+    }
+  }
+  MPD_CHECK_LAUNCH(c, "adjoint forward recompute");
+  T* zero_list[10] = {p1b, p0b, utb, vtb, wtb, ulb, vlb, wlb, bub, bdb};
+  for (int q = 0; q < 10; ++q) {
+    cudaError_t e = cudaMemsetAsync(zero_list[q], 0, fb, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint clear");
+  }
+  if (c->iord == 1) {
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                            g, psi, U, V, W, G, psib, p0b, ub, vb, wb));
+  } else {
+    T* vel[3] = {c->nonosc ? ul : ut, c->nonosc ? vl : vt, c->nonosc ? wl : wt};
+    T* velb[3] = {c->nonosc ? ulb : utb, c->nonosc ? vlb : vtb, c->nonosc ? wlb : wtb};
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                            g, p1, vel[0], vel[1], vel[2], G, psib, p1b, velb[0],
+                                            velb[1], velb[2]));
+    if (c->nonosc) {
+      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, rev_limit_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                            g, ut, vt, wt, bu, bd, ulb, vlb, wlb, utb, vtb, wtb,
+                                            bub, bdb));
+      MPD_LAUNCH(c, MPDATA_STAGE_BETA, rev_beta_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                           g, psi, p1, ut, vt, wt, G, bub, bdb, p0b, p1b, utb,
+                                           vtb, wtb));
+    }
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, rev_pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                           g, p1, U, V, W, G, utb, vtb, wtb, p1b, ub, vb, wb));
+    MPD_LAUNCH(c, MPDATA_STAGE_DONOR, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                          g, psi, U, V, W, G, p1b, p0b, ub, vb, wb));
+  }
+  MPD_CHECK_LAUNCH(c, "adjoint reverse kernels");
+  cudaError_t e = cudaMemcpyAsync(psib, p0b, fb, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint result copy");
+  return MPDATA_OK;
+}
+
 int check_fields(const void* const* ptrs, int n) {
   for (int q = 0; q < n; ++q) {
     if (!ptrs[q]) return MPDATA_EINVAL;
@@ -473,8 +572,35 @@ int mpdata_profile_read(mpdata_ctx* c, int stage, double* ms, int* launches) {
   return MPDATA_OK;
 }
 
+int mpdata_adjoint_step(mpdata_ctx* c, const void* psi_n, const void* u, const void* v,
+                        const void* w, const void* g, void* psi_bar, void* u_bar, void* v_bar,
+                        void* w_bar) {
+  if (!c) return MPDATA_EINVAL;
+  if (c->iord > 2) return MPDATA_EINVAL;
+  const void* f[9] = {psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
+  int rc = check_fields(f, 9);
+  if (rc) return rc;
+  if (c->dtype == MPDATA_F64)
+    return adjoint_step<double>(c, (const double*)psi_n, (const double*)u, (const double*)v,
+                                (const double*)w, (const double*)g, (double*)psi_bar,
+                                (double*)u_bar, (double*)v_bar, (double*)w_bar);
+  return adjoint_step<float>(c, (const float*)psi_n, (const float*)u, (const float*)v,
+                             (const float*)w, (const float*)g, (float*)psi_bar, (float*)u_bar,
+                             (float*)v_bar, (float*)w_bar);
+}
+
+int mpdata_fold_halo_adjoint(mpdata_ctx* c, void* field) {
+  if (!c) return MPDATA_EINVAL;
+  const void* f[1] = {field};
+  int rc = check_fields(f, 1);
+  if (rc) return rc;
+  if (c->dtype == MPDATA_F64) return halo_fold_launch<double>(c, (double*)field);
+  return halo_fold_launch<float>(c, (float*)field);
+}
+
 void mpdata_destroy(mpdata_ctx* c) {
   if (!c) return;
+  if (c->adjbuf) cudaFree(c->adjbuf);
   if (c->prof_ev) {
     for (int q = 0; q < 2 * c->prof_cap; ++q) cudaEventDestroy(c->prof_ev[q]);
     delete[] c->prof_ev;

@@ -54,6 +54,25 @@ __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fm
 __device__ __forceinline__ bool nonneg(double x) { return __double2hiint(x) >= 0; }
 __device__ __forceinline__ bool nonneg(float x) { return __float_as_int(x) >= 0; }
 
+__device__ __forceinline__ long long okey(double x);
+// x >= 0 and x <= 0 with IEEE semantics (both hold for +0 and -0).
+__device__ __forceinline__ bool ge0(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 || (b & 0x7fffffffffffffffLL) == 0;
+}
+__device__ __forceinline__ bool le0(double x) {
+  const long long b = __double_as_longlong(x);
+  return b < 0 || b == 0;
+}
+__device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
+__device__ __forceinline__ bool le0(float x) { return x <= 0.0f; }
+// a >= b and a <= b for doubles through the order keys (IEEE semantics for
+// finite values, +0 == -0); floats compare directly.
+__device__ __forceinline__ bool geq(double a, double b) { return okey(a) >= okey(b); }
+__device__ __forceinline__ bool leq(double a, double b) { return okey(a) <= okey(b); }
+__device__ __forceinline__ bool geq(float a, float b) { return a >= b; }
+__device__ __forceinline__ bool leq(float a, float b) { return a <= b; }
+
 // [x]+ and [x]- of the donor-cell split.
 template <class T> __device__ __forceinline__ T pos(T x) { return nonneg(x) ? x : T(0); }
 template <class T> __device__ __forceinline__ T neg(T x) { return nonneg(x) ? T(0) : x; }
@@ -74,8 +93,8 @@ __device__ __forceinline__ T donor(T L, T R, T C) {
 // each double to an int64 key with the same order (sign-magnitude ->
 // two's complement: flip the magnitude bits of negatives) and compares keys.
 __device__ __forceinline__ long long okey(double x) {
-  long long b = __double_as_longlong(x);
-  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : -(b & 0x7fffffffffffffffLL);  // -0 and +0 both map to 0
 }
 __device__ __forceinline__ double vmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
 __device__ __forceinline__ double vmin(double a, double b) { return okey(a) <= okey(b) ? a : b; }

@@ -199,4 +199,40 @@ __global__ void halo_kernel(Geo g, T* __restrict__ f, int kind) {
   }
 }
 
+// Reverse of the CELL halo fill for an adjoint field: every halo entry was a
+// copy of an interior value, so its adjoint is added to that source.  A
+// second launch (halo_zero_kernel) then clears the halo.
+template <class T>
+__global__ void halo_fold_kernel(Geo g, T* __restrict__ f) {
+  const int64_t n = g.total;
+  const int64_t pyy = g.ny + 2 * (int64_t)g.h;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int ii = (int)(t % g.px) - g.h;
+    int jj = (int)((t / g.px) % pyy) - g.h;
+    int kk = (int)(t / g.pxy) - g.h;
+    if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz) continue;
+    const T v = f[t];
+    if (v == T(0)) continue;
+    int is = ((ii % g.nx) + g.nx) % g.nx;
+    int js = ((jj % g.ny) + g.ny) % g.ny;
+    int ks = kk < 0 ? 0 : (kk >= g.nz ? g.nz - 1 : kk);
+    atomicAdd(&f[at(g, is, js, ks)], v);
+  }
+}
+
+template <class T>
+__global__ void halo_zero_kernel(Geo g, T* __restrict__ f) {
+  const int64_t n = g.total;
+  const int64_t pyy = g.ny + 2 * (int64_t)g.h;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int ii = (int)(t % g.px) - g.h;
+    int jj = (int)((t / g.px) % pyy) - g.h;
+    int kk = (int)(t / g.pxy) - g.h;
+    if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz) continue;
+    f[t] = T(0);
+  }
+}
+
 }  // namespace mpd

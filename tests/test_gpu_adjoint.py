@@ -1,0 +1,147 @@
+"""GPU adjoint: the library's reverse-mode step against the oracle's
+hand-written adjoint, against central differences of the GPU forward, and
+through torch.autograd with checkpointing.
+
+Tolerance against the oracle adjoint: 1e-11 relative (max-abs over the
+field / max-abs of the oracle) per step in FP64.  The reverse chain has
+about twice the rounded operations of the forward step and the forward
+intermediates it differentiates at are the GPU's own (within 1e-12 of the
+oracle's), and the cases are random fields without exact ties, so both
+sides take the same branches.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import rel_err, to_dev
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ADJ_TOL = 1e-11
+H = 2
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _device():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_06094_b300 import build
+    build.build()
+
+
+def _gpu_adjoint(c, iord, nonosc, nsteps, dy, dtype=torch.float64):
+    from paper_1908_06094_b300 import MPDATA, _capi
+    m = MPDATA(c.nx, c.ny, c.nz, halo=H, iord=iord, nonoscillatory=nonosc, dtype=dtype)
+    d = [to_dev(synth.pad(x, H), dtype) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    states = [d[0].clone()]
+    for _ in range(nsteps - 1):
+        nxt = torch.empty_like(states[-1])
+        m.step_out(states[-1], nxt, *d[1:])
+        states.append(nxt)
+    pb = to_dev(dy, dtype)
+    ub, vb, wb = (torch.zeros_like(d[0]) for _ in range(3))
+    for s in reversed(range(nsteps)):
+        _capi.mpdata_adjoint_step(m._ctx, states[s].data_ptr(), d[1].data_ptr(), d[2].data_ptr(),
+                                  d[3].data_ptr(), d[4].data_ptr(), pb.data_ptr(), ub.data_ptr(),
+                                  vb.data_ptr(), wb.data_ptr())
+    torch.cuda.synchronize()
+    out = [t.double().cpu().numpy() for t in (pb, ub, vb, wb)]
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("shape", [(9, 8, 5), (21, 13, 7), (37, 30, 3)])
+@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("nsteps", [1, 3])
+def test_adjoint_parity_f64(shape, iord, nonosc, nsteps):
+    nx, ny, nz = shape
+    c = synth.random_case(nx, ny, nz, seed=nx + 100 * nz, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
+    rng = np.random.default_rng(5)
+    dy = synth.pad(rng.standard_normal(c.psi.shape), H)
+    P = [synth.pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    ref = oracle.adjoint(*P, dy, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps)
+    got = _gpu_adjoint(c, iord, nonosc, nsteps, dy)
+    for name, a, b in zip(("psi_bar", "u_bar", "v_bar", "w_bar"), got, ref):
+        err = rel_err(synth.interior(a, H), synth.interior(b, H))
+        assert err <= ADJ_TOL * nsteps, (name, err)
+
+
+def test_adjoint_parity_f32_against_f64_oracle():
+    """FP32 adjoint on FP32-rounded inputs against the FP64 oracle adjoint."""
+    c = synth.random_case(21, 13, 7, seed=3, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
+    for k in ("psi", "u", "v", "w", "g"):
+        setattr(c, k, getattr(c, k).astype(np.float32).astype(np.float64))
+    rng = np.random.default_rng(6)
+    dy = synth.pad(rng.standard_normal(c.psi.shape), H).astype(np.float32).astype(np.float64)
+    P = [synth.pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    ref = oracle.adjoint(*P, dy, h=H, iord=2, nonosc=1, nsteps=2)
+    got = _gpu_adjoint(c, 2, 1, 2, dy, dtype=torch.float32)
+    for a, b in zip(got, ref):
+        assert rel_err(synth.interior(a, H), synth.interior(b, H)) <= 2e-4
+
+
+def test_gpu_gradient_matches_central_differences_f64():
+    """<grad J, d> from the GPU adjoint against central differences of the
+    GPU forward (J = sum (psi_T - obs)^2 G, 4 steps, checkpoint every 2).
+    The step h = 1e-8 |x| keeps the chance that +-h straddles a min/max kink
+    of the limiter negligible on this grid; the FD rounding error is then
+    ~1e-16 J / h, well under the 1e-5 tolerance."""
+    from paper_1908_06094_b300 import MPDATA, mpdata_run
+    c = synth.random_case(12, 10, 5, seed=9, cmax=0.25, psi_lo=0.3, psi_hi=1.4)
+    m = MPDATA(c.nx, c.ny, c.nz, halo=H, dtype=torch.float64)
+    base = [to_dev(synth.pad(x, H), torch.float64) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    rng = np.random.default_rng(10)
+    obs = base[0] + to_dev(synth.pad(0.05 * rng.standard_normal(c.psi.shape), H), torch.float64)
+    mask = to_dev(synth.pad(np.ones(c.psi.shape), H), torch.float64)
+
+    def J(p, u, v, w):
+        out = mpdata_run(m, p, u, v, w, base[4], 4, 2)
+        return torch.sum((out - obs) ** 2 * base[4] * mask)
+
+    x = [t.clone().requires_grad_(True) for t in base[:4]]
+    J(*x).backward()
+    for trial in range(4):
+        d = [to_dev(synth.pad(rng.standard_normal(c.psi.shape), H), torch.float64) for _ in range(4)]
+        d[3][H + c.nz - 1] = 0.0
+        eps = 1e-8 * max(float(t.abs().max()) for t in base[:4])
+        with torch.no_grad():
+            jp = J(*(a + eps * b for a, b in zip(base[:4], d))).item()
+            jm = J(*(a - eps * b for a, b in zip(base[:4], d))).item()
+        fd = (jp - jm) / (2 * eps)
+        an = sum(float(torch.sum(xx.grad * dd)) for xx, dd in zip(x, d))
+        assert abs(fd - an) <= 1e-5 * abs(an), (trial, fd, an)
+    m.close()
+
+
+@pytest.mark.parametrize("ckpt", [1, 2, 5, 20])
+def test_checkpointing_does_not_change_the_gradient(ckpt):
+    from paper_1908_06094_b300 import MPDATA, mpdata_run
+    c = synth.latlon_3d(40, 32, 8, seed=4)
+    m = MPDATA(c.nx, c.ny, c.nz, halo=H, dtype=torch.float64)
+    base = [to_dev(synth.pad(x, H), torch.float64) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    x = [t.clone().requires_grad_(True) for t in base[:4]]
+    out = mpdata_run(m, *x, base[4], 10, ckpt)
+    torch.sum(out * out).backward()
+    grads = [t.grad.cpu().numpy() for t in x]
+    x2 = [t.clone().requires_grad_(True) for t in base[:4]]
+    out2 = mpdata_run(m, *x2, base[4], 10, 10)
+    torch.sum(out2 * out2).backward()
+    for a, b in zip(grads, [t.grad.cpu().numpy() for t in x2]):
+        assert rel_err(a, b) <= 1e-12
+    m.close()
+
+
+def test_c5_adjoint_full_size_against_oracle():
+    """The adjoint configuration's grid (256x256x64, lat-lon flow), 2 steps,
+    FP64: GPU gradient of J w.r.t. psi_0 and U, V, W against the oracle."""
+    c = synth.latlon_3d(256, 256, 64)
+    rng = np.random.default_rng(1235)
+    dy = synth.pad(rng.standard_normal(c.psi.shape), H)
+    P = [synth.pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    ref = oracle.adjoint(*P, dy, h=H, iord=2, nonosc=1, nsteps=2)
+    got = _gpu_adjoint(c, 2, 1, 2, dy)
+    for name, a, b in zip(("psi_bar", "u_bar", "v_bar", "w_bar"), got, ref):
+        err = rel_err(synth.interior(a, H), synth.interior(b, H))
+        assert err <= 2 * ADJ_TOL, (name, err)
