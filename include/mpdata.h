@@ -165,6 +165,56 @@ MPDATA_API int mpdata_fill_halo(mpdata_ctx *c, void *field, int kind);
  * to *out_dev, a DEVICE double.  Errors: EINVAL, EALIGN, ECUDA. */
 MPDATA_API int mpdata_mass(mpdata_ctx *c, const void *psi, const void *g, double *out_dev);
 
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems in one persistent launch.
+ *
+ * Each domain has its own grid and Courant fields and ntracers tracers that
+ * share them.  One batch step advances every tracer of every domain by one
+ * MPDATA step (iord 2) from one tracer buffer into the other (ping-pong).
+ * Domains need nx, ny >= 2*halo and halo >= 2.  The work is split into items
+ * (domain, column tile, level chunk, tracer) that the CTAs of one persistent
+ * kernel take from an atomic counter; the tracers of one tile are
+ * consecutive items, so their shared U, V, W, G columns come from L2.
+ * ---------------------------------------------------------------------- */
+typedef struct mpdata_domain_desc {
+  int nx, ny, nz, halo;  /* grid of this domain                              */
+  int ntracers;          /* tracers sharing its Courant fields                */
+  void *psi_a, *psi_b;   /* DEVICE: ntracers padded fields each, consecutive  */
+                         /* (tracer stride = one padded field); distinct      */
+  const void *u, *v, *w, *g; /* DEVICE padded fields of the domain           */
+} mpdata_domain_desc;
+
+typedef struct mpdata_batch mpdata_batch; /* opaque */
+
+/* Create a batch from a HOST array of ndomains descriptors (copied; the
+ * buffers they point to stay owned by the caller).  Allocates the device
+ * descriptor table.  Errors: EINVAL, EALIGN, ERANGE, ENOMEM, EDEVICE, ECUDA. */
+MPDATA_API int mpdata_batch_init(mpdata_batch **out, const mpdata_domain_desc *domains,
+                                 int ndomains, int nonoscillatory, int dtype, void *cuda_stream);
+
+/* One step of every tracer: direction 0 reads psi_a and writes psi_b,
+ * direction 1 the reverse.  With use_graph = 1 the launch (counter reset +
+ * persistent kernel) is captured once per direction into a CUDA graph and
+ * replayed (needs a non-default stream).  Errors: EINVAL, ECUDA. */
+MPDATA_API int mpdata_batch_step(mpdata_batch *b, int direction, int use_graph);
+
+/* Tile shape (index into the compiled shapes: FP32 32x16, 64x8, 32x8,
+ * 64x16; FP64 32x16, 32x8, 64x8) and level-chunk length (0 = whole
+ * columns).  Setting waits for the stream and drops captured graphs. */
+MPDATA_API int mpdata_batch_set_config(mpdata_batch *b, int shape, int kchunk_levels);
+MPDATA_API int mpdata_batch_get_config(mpdata_batch *b, int *shape, int *kchunk_levels,
+                                       int *tile_x, int *tile_y, int *threads,
+                                       long long *items);
+
+/* Time every shape x chunk length (0, 32, 16, 8) over reps steps and keep
+ * the fastest; *best_ms gets its time per step.  It runs steps on the
+ * batch's buffers, so their contents change.  Errors: EINVAL, ECUDA. */
+MPDATA_API int mpdata_batch_autotune(mpdata_batch *b, int reps, double *best_ms);
+
+MPDATA_API long long mpdata_batch_launch_count(mpdata_batch *b);
+MPDATA_API const char *mpdata_batch_last_error_string(mpdata_batch *b);
+MPDATA_API void mpdata_batch_destroy(mpdata_batch *b);
+
 /* Instrumentation.  Stage ids of the kernels the library launches. */
 enum mpdata_stage {
   MPDATA_STAGE_HALO = 0,     /* halo fill of psi (a1)                        */

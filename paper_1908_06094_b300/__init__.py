@@ -4,6 +4,7 @@ thin Python binding over it.
 * ``_capi``   -- ctypes binding, one function per C entry point;
 * ``MPDATA``  -- the same calls taking torch CUDA tensors (pointer and stream
   marshalling only: every step of the method runs in the library's kernels);
+* ``MPDATABatch`` -- many domains x tracers in one persistent launch;
 * ``MPDATAFunction`` / ``mpdata_run`` -- autograd over the forward and
   adjoint steps with checkpoint-and-recompute.
 
@@ -12,7 +13,7 @@ library raises ImportError (there is no fallback path).
 """
 import importlib
 
-__all__ = ["_capi", "MPDATA", "padded_shape", "MPDATAFunction", "mpdata_run"]
+__all__ = ["_capi", "MPDATA", "padded_shape", "MPDATAFunction", "mpdata_run", "MPDATABatch"]
 
 
 def __getattr__(name):
@@ -21,6 +22,8 @@ def __getattr__(name):
     if name in ("MPDATA", "padded_shape"):
         mod = importlib.import_module(".mpdata", __name__)
         return getattr(mod, name)
+    if name == "MPDATABatch":
+        return importlib.import_module(".batch", __name__).MPDATABatch
     if name in ("MPDATAFunction", "mpdata_run"):
         mod = importlib.import_module(".autograd", __name__)
         return getattr(mod, name)

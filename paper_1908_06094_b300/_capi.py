@@ -38,6 +38,18 @@ _c = ctypes.c_void_p
 _i = ctypes.c_int
 _ctxpp = ctypes.POINTER(ctypes.c_void_p)
 
+class mpdata_domain_desc(ctypes.Structure):
+    """struct mpdata_domain_desc of include/mpdata.h."""
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("halo", ctypes.c_int), ("ntracers", ctypes.c_int),
+                ("psi_a", ctypes.c_void_p), ("psi_b", ctypes.c_void_p),
+                ("u", ctypes.c_void_p), ("v", ctypes.c_void_p), ("w", ctypes.c_void_p),
+                ("g", ctypes.c_void_p)]
+
+
+_dp = ctypes.POINTER(mpdata_domain_desc)
+_ip = ctypes.POINTER(ctypes.c_int)
+
 # symbol -> (restype, argtypes); the list is the ABI that include/mpdata.h declares
 SIGNATURES = {
     "mpdata_init": (_i, [_ctxpp, _i, _i, _i, _i, _i, _i, _i, _i, _c]),
@@ -55,6 +67,15 @@ SIGNATURES = {
     "mpdata_last_error_string": (ctypes.c_char_p, [_c]),
     "mpdata_version": (_i, []),
     "mpdata_launch_count": (ctypes.c_longlong, [_c]),
+    "mpdata_batch_init": (_i, [_ctxpp, _dp, _i, _i, _i, _c]),
+    "mpdata_batch_step": (_i, [_c, _i, _i]),
+    "mpdata_batch_set_config": (_i, [_c, _i, _i]),
+    "mpdata_batch_get_config": (_i, [_c, _ip, _ip, _ip, _ip, _ip,
+                                     ctypes.POINTER(ctypes.c_longlong)]),
+    "mpdata_batch_autotune": (_i, [_c, _i, ctypes.POINTER(ctypes.c_double)]),
+    "mpdata_batch_launch_count": (ctypes.c_longlong, [_c]),
+    "mpdata_batch_last_error_string": (ctypes.c_char_p, [_c]),
+    "mpdata_batch_destroy": (None, [_c]),
     "mpdata_mass_noalloc": (_i, [_c, _c, _i, _i, _i, _i, _i, _c, _c]),
     "mpdata_profile": (_i, [_c, _i]),
     "mpdata_profile_read": (_i, [_c, _i, ctypes.POINTER(ctypes.c_double),
@@ -169,3 +190,48 @@ def mpdata_adjoint_step(ctx, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar):
 
 def mpdata_fold_halo_adjoint(ctx, field):
     _check(lib.mpdata_fold_halo_adjoint(ctx, field), "mpdata_fold_halo_adjoint", ctx)
+
+
+def _bcheck(rc, where, b=None):
+    if rc != MPDATA_OK:
+        detail = lib.mpdata_batch_last_error_string(b).decode() if (b and rc == MPDATA_ECUDA) else ""
+        raise MPDATAError(rc, where, detail)
+
+
+def mpdata_batch_init(descs, nonoscillatory, dtype, cuda_stream=0):
+    arr = (mpdata_domain_desc * len(descs))(*descs)
+    out = ctypes.c_void_p()
+    _bcheck(lib.mpdata_batch_init(ctypes.byref(out), arr, len(descs), nonoscillatory, dtype,
+                                  cuda_stream), "mpdata_batch_init")
+    return out.value
+
+
+def mpdata_batch_step(b, direction, use_graph):
+    _bcheck(lib.mpdata_batch_step(b, direction, int(bool(use_graph))), "mpdata_batch_step", b)
+
+
+def mpdata_batch_set_config(b, shape, kchunk_levels):
+    _bcheck(lib.mpdata_batch_set_config(b, shape, kchunk_levels), "mpdata_batch_set_config", b)
+
+
+def mpdata_batch_get_config(b):
+    v = [ctypes.c_int() for _ in range(5)]
+    items = ctypes.c_longlong()
+    _bcheck(lib.mpdata_batch_get_config(b, *[ctypes.byref(x) for x in v], ctypes.byref(items)),
+            "mpdata_batch_get_config", b)
+    return dict(shape=v[0].value, kchunk=v[1].value, tile_x=v[2].value, tile_y=v[3].value,
+                threads=v[4].value, items=items.value)
+
+
+def mpdata_batch_autotune(b, reps):
+    ms = ctypes.c_double()
+    _bcheck(lib.mpdata_batch_autotune(b, reps, ctypes.byref(ms)), "mpdata_batch_autotune", b)
+    return ms.value
+
+
+def mpdata_batch_launch_count(b):
+    return lib.mpdata_batch_launch_count(b)
+
+
+def mpdata_batch_destroy(b):
+    lib.mpdata_batch_destroy(b)

@@ -46,20 +46,22 @@ struct Layout {
   static constexpr size_t bytes = NVAL * sizeof(T) + CN * sizeof(int);
 };
 
-template <class T, int TX, int TY, int NT, int MINB, bool LIMIT>
-__global__ void __launch_bounds__(NT, MINB)
-step_kernel(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
-            const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
-            T* __restrict__ out) {
+// One tile of the step: columns [i0, i0+TX) x [j0, j0+TY), levels [k0, k1),
+// psi^n P0 -> out.  Called by every thread of the CTA; smem_raw holds
+// Layout::bytes.  Starts with a barrier, so consecutive calls from one CTA
+// (the persistent batched kernel) may reuse the shared memory.
+template <class T, int TX, int TY, int NT, bool LIMIT>
+__device__ __forceinline__ void step_tile(const Geo& g, int i0, int j0, int k0, int k1,
+                                          const T* __restrict__ P0, const T* __restrict__ U,
+                                          const T* __restrict__ V, const T* __restrict__ W,
+                                          const T* __restrict__ G, T* __restrict__ out,
+                                          unsigned char* smem_raw) {
   using L = Layout<T, TX, TY>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
   T* sm = reinterpret_cast<T*>(smem_raw);
   int* col = reinterpret_cast<int*>(sm + L::NVAL);
   const int tid = threadIdx.x;
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const int nz = g.nz;
-  const int k0 = blockIdx.z * kchunk;
-  const int k1 = min(nz, k0 + kchunk);
+  __syncthreads();
   const T eps = Eps<T>::v, zero = T(0);
 
   // wrapped column offsets (j*px + i) of the tile + 3 ring
@@ -177,10 +179,9 @@ step_kernel(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U
         const T n1 = P0[pb + C(x - 1, y)], n2 = P0[pb + C(x + 1, y)];
         const T n3 = P0[pb + C(x, y - 1)], n4 = P0[pb + C(x, y + 1)];
         const T n5 = P0[plane(bm) + c], n6 = P0[plane(bp) + c];
-        T hi = vmax(vmax(vmax(pc, p0), vmax(n1, n2)), vmax(vmax(n3, n4), vmax(n5, n6)));
-        T lo = vmin(vmin(vmin(pc, p0), vmin(n1, n2)), vmin(vmin(n3, n4), vmin(n5, n6)));
-        hi = vmax(hi, vmax(vmax(vmax(pxm, pxp), vmax(pym, pyp)), vmax(pzm, pzp)));
-        lo = vmin(lo, vmin(vmin(vmin(pxm, pxp), vmin(pym, pyp)), vmin(pzm, pzp)));
+        const T vals[14] = {pc, p0, n1, n2, n3, n4, n5, n6, pxm, pxp, pym, pyp, pzm, pzp};
+        T hi, lo;
+        bounds(vals, hi, lo);
         const T fxp = donor(pc, pxp, ut[S(x, y)]);
         const T fxm = donor(pxm, pc, ut[S(x - 1, y)]);
         const T fyp = donor(pc, pyp, vt[S(x, y)]);
@@ -268,6 +269,17 @@ step_kernel(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U
     // no barrier needed here: the next iteration's stage A writes a psi1
     // slot this stage does not read, and every later stage is behind a barrier
   }
+}
+
+template <class T, int TX, int TY, int NT, int MINB, bool LIMIT>
+__global__ void __launch_bounds__(NT, MINB)
+step_kernel(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
+            const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
+            T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k0 = blockIdx.z * kchunk;
+  step_tile<T, TX, TY, NT, LIMIT>(g, blockIdx.x * TX, blockIdx.y * TY, k0, min(g.nz, k0 + kchunk),
+                                  P0, U, V, W, G, out, smem_raw);
 }
 
 }  // namespace fused

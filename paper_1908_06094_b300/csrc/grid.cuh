@@ -55,6 +55,7 @@ __device__ __forceinline__ bool nonneg(double x) { return __double2hiint(x) >= 0
 __device__ __forceinline__ bool nonneg(float x) { return __float_as_int(x) >= 0; }
 
 __device__ __forceinline__ long long okey(double x);
+__device__ __forceinline__ long long okey0(double x);
 // x >= 0 and x <= 0 with IEEE semantics (both hold for +0 and -0).
 __device__ __forceinline__ bool ge0(double x) {
   const long long b = __double_as_longlong(x);
@@ -68,8 +69,8 @@ __device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
 __device__ __forceinline__ bool le0(float x) { return x <= 0.0f; }
 // a >= b and a <= b for doubles through the order keys (IEEE semantics for
 // finite values, +0 == -0); floats compare directly.
-__device__ __forceinline__ bool geq(double a, double b) { return okey(a) >= okey(b); }
-__device__ __forceinline__ bool leq(double a, double b) { return okey(a) <= okey(b); }
+__device__ __forceinline__ bool geq(double a, double b) { return okey0(a) >= okey0(b); }
+__device__ __forceinline__ bool leq(double a, double b) { return okey0(a) <= okey0(b); }
 __device__ __forceinline__ bool geq(float a, float b) { return a >= b; }
 __device__ __forceinline__ bool leq(float a, float b) { return a <= b; }
 
@@ -94,12 +95,46 @@ __device__ __forceinline__ T donor(T L, T R, T C) {
 // two's complement: flip the magnitude bits of negatives) and compares keys.
 __device__ __forceinline__ long long okey(double x) {
   const long long b = __double_as_longlong(x);
-  return b >= 0 ? b : -(b & 0x7fffffffffffffffLL);  // -0 and +0 both map to 0
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);  // -0 sorts just below +0
+}
+// The same order with -0 and +0 equal (IEEE ties), for branch decisions
+// that must match IEEE comparisons exactly (the adjoint's tie rules).
+__device__ __forceinline__ long long okey0(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : -(b & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double kdecode(long long k) {
+  return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
 }
 __device__ __forceinline__ double vmax(double a, double b) { return okey(a) >= okey(b) ? a : b; }
 __device__ __forceinline__ double vmin(double a, double b) { return okey(a) <= okey(b) ? a : b; }
 __device__ __forceinline__ float vmax(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ float vmin(float a, float b) { return fminf(a, b); }
+// Largest and smallest of n values (the limiter bounds).  FP64 folds on the
+// order keys (one key per value, integer compares), FP32 on min/max.
+template <int N>
+__device__ __forceinline__ void bounds(const double (&v)[N], double& hi, double& lo) {
+  long long kh = okey(v[0]), kl = kh;
+#pragma unroll
+  for (int q = 1; q < N; ++q) {
+    const long long k = okey(v[q]);
+    kh = k > kh ? k : kh;
+    kl = k < kl ? k : kl;
+  }
+  hi = kdecode(kh);
+  lo = kdecode(kl);
+}
+template <int N>
+__device__ __forceinline__ void bounds(const float (&v)[N], float& hi, float& lo) {
+  hi = v[0];
+  lo = v[0];
+#pragma unroll
+  for (int q = 1; q < N; ++q) {
+    hi = fmaxf(hi, v[q]);
+    lo = fminf(lo, v[q]);
+  }
+}
+
 // min of non-negative values (limiter factors): raw bit patterns order them.
 __device__ __forceinline__ double nmin(double a, double b) {
   return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;

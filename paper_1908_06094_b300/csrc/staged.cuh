@@ -129,12 +129,10 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
   const int64_t nb[6] = {at(g, im, j, k), at(g, ip, j, k), at(g, i, jm, k),
                          at(g, i, jp, k), at(g, i, j, km), at(g, i, j, kp)};
   T pc = P[q];
-  T hi = vmax(P0[q], pc), lo = vmin(P0[q], pc);
-  for (int s = 0; s < 6; ++s) {
-    T a = P0[nb[s]], b = P[nb[s]];
-    hi = vmax(hi, vmax(a, b));
-    lo = vmin(lo, vmin(a, b));
-  }
+  const T vals[14] = {P0[q], pc, P0[nb[0]], P[nb[0]], P0[nb[1]], P[nb[1]], P0[nb[2]], P[nb[2]],
+                      P0[nb[3]], P[nb[3]], P0[nb[4]], P[nb[4]], P0[nb[5]], P[nb[5]]};
+  T hi, lo;
+  bounds(vals, hi, lo);
   T fxp = donor(pc, P[nb[1]], ut[q]);
   T fxm = donor(P[nb[0]], pc, ut[nb[0]]);
   T fyp = donor(pc, P[nb[3]], vt[q]);
