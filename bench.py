@@ -60,6 +60,28 @@ STAGE_WORDS = {
 }
 STEP_WORDS = 6
 
+# Algorithmic floating-point operations per interior point of each stage,
+# counted from the formulas (each +, -, *, / is one; min, max and |x| are
+# not counted).  Per face of the pseudo-velocity: G_face 2, A 4, each B 9,
+# each cross average 4, the combination 10 -> 42; three faces -> 126.
+STAGE_FLOPS = {
+    "donor": 9,      # three "+" face fluxes (2 mul + 1 add each)
+    "advance": 7,    # 5 adds, 1 division, 1 subtraction
+    "pseudo": 126,
+    "beta": 36,      # six fluxes (18), in/out sums (10), two betas (8)
+    "limit": 18,     # three limited velocities (9) and their fluxes (9)
+    "mass": 2,
+    "halo": 0,
+    "fused": 212,    # the whole step: 25 + 126 + 36 + 18 + 7
+    "fused_donor": 25,
+}
+STEP_FLOPS = 212
+
+# FP64 peak of the B300 from its unit count and clock: 2 FP64 FMA lanes per
+# SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained = 2) x 148 SMs x 2.032 GHz x 2 flops per FMA.
+FP64_PEAK_GFLOPS = 2 * 148 * 2.032 * 2
+
 
 def table2_accesses(nodes: int, edges: int, fused: bool) -> int:
     """Main-memory accesses per vertical plane for the MPDATA fluxes with the
@@ -272,16 +294,33 @@ def run_ours(args, wl_name):
         if dom:
             t, k = stage_ms[dom]
             per_launch_ms = t / k
-            bytes_launch = STAGE_WORDS[dom] * esize * npts
-            achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
             src = _source_hash()
             traffic = _traffic_from_profiles(dom, wl_name, src)
-            roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
-                    "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
-                    "traffic": traffic, "algorithmic_bytes": bytes_launch,
-                    "launch_ms": round(per_launch_ms, 5), "peak_source": peak_kind,
-                    "stage_share": {s: round(v[0] / sum(x[0] for x in stage_ms.values()), 4)
-                                    for s, v in stage_ms.items()}}
+            share = {s_: round(v[0] / sum(x[0] for x in stage_ms.values()), 4)
+                     for s_, v in stage_ms.items()}
+            if dt == torch.float64:
+                # FP64 on the B300 runs at 1/64 of FP32: these kernels are bound by
+                # the FP64 pipe, not by HBM
+                flops = STAGE_FLOPS[dom] * npts
+                achieved = flops / (per_launch_ms / 1e3) / 1e9
+                roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1),
+                        "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s (FP64)",
+                        "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
+                        "algorithmic_flops": flops,
+                        "hbm_frac": round(STAGE_WORDS[dom] * esize * npts /
+                                          (per_launch_ms / 1e3) / 1e9 / hbm, 4),
+                        "launch_ms": round(per_launch_ms, 5), "peak_source":
+                        "unit count x max clock (measured FMA probe: 1086)",
+                        "stage_share": share}
+            else:
+                bytes_launch = STAGE_WORDS[dom] * esize * npts
+                achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
+                roof = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                        "peak": hbm, "unit": "GB/s", "frac": round(achieved / hbm, 4),
+                        "traffic": traffic, "algorithmic_bytes": bytes_launch,
+                        "launch_ms": round(per_launch_ms, 5),
+                        "peak_source": peak_kind + " (MEASURED_PEAKS hbm_gbs)",
+                        "stage_share": share}
         step_bytes = STEP_WORDS * esize * npts
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -298,6 +337,8 @@ def run_ours(args, wl_name):
                        "variant": {0: "fused", 1: "staged", 2: "auto"}.get(args.variant, "auto"),
                        "parallelism": f"replicas x{ws}"},
             "hbm_roofline_frac_step": round(value / ws * step_bytes / npts / 1e9 / hbm, 4),
+            "fp64_alu_frac_step": (round(value / ws * STEP_FLOPS / 1e9 / FP64_PEAK_GFLOPS, 4)
+                                   if dt == torch.float64 else None),
             "roofline": roof,
             "gpu_launches": launches,
             "mass_drift_rel": abs(m1 - m0) / abs(m0) if m0 else None,
@@ -324,6 +365,7 @@ def run_ours(args, wl_name):
         out["adjoint"] = {"f64": measure_adjoint(dev, torch.float64),
                           "f32": measure_adjoint(dev, torch.float32)}
         out["batched"] = measure_batched(dev)
+        out["fp32"] = measure_config(dev, "latlon512_f32")
         out["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": ncores,
                                "kind": "oracle",
                                "sample": f"{cpu_steps} full steps of the same workload "
@@ -332,6 +374,58 @@ def run_ours(args, wl_name):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return out
+
+
+def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
+    """Another configuration measured the same way as the headline (device
+    resident inputs, CUDA events, per-stage event timing): value and the
+    roofline of its dominant kernel."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1908_06094_b300 import MPDATA, _capi
+    wl = WORKLOADS[wl_name]
+    dt = torch.float64 if wl["dtype"] == "f64" else torch.float32
+    h = wl["halo"]
+    c = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=1234)
+    padded = [synth.pad(x, h) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    d = [torch.from_numpy(x).to(dev, dt).contiguous() for x in padded]
+    m = MPDATA(wl["nx"], wl["ny"], wl["nz"], halo=h, dtype=dt, device=dev)
+    if variant is not None:
+        m.set_variant(variant)
+    npts = wl["nx"] * wl["ny"] * wl["nz"]
+    out_mass = torch.empty((), dtype=torch.float64, device=dev)
+    m0 = m.mass(d[0], d[4]).item()
+    for _ in range(warmup):
+        m.step(*d, nsteps=1)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    _capi.mpdata_profile(m._ctx, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        m.step(*d, nsteps=1)
+        m.mass(d[0], d[4], out=out_mass)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    st = {n: _capi.mpdata_profile_read(m._ctx, sid) for n, sid in _capi.STAGES.items()}
+    st = {n: v for n, v in st.items() if v[1]}
+    m1 = out_mass.item()
+    m.close()
+    hbm, _ = _peaks()
+    esize = 8 if dt == torch.float64 else 4
+    dom = max(st, key=lambda n: st[n][0])
+    per = st[dom][0] / st[dom][1]
+    gbs = STAGE_WORDS[dom] * esize * npts / (per / 1e3) / 1e9
+    value = npts * steps / (ms / 1e3)
+    return {"workload": f"latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']} {wl['dtype']}",
+            "value": value, "unit": UNIT, "ms_per_step": ms / steps, "dtype": wl["dtype"],
+            "hbm_roofline_frac_step": round(value * STEP_WORDS * esize / 1e9 / hbm, 4),
+            "mass_drift_rel_after_steps": abs(m1 - m0) / abs(m0),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                         "launch_ms": round(per, 5)}}
 
 
 def measure_adjoint(dev, dtype, nsteps=20, ckpt=5, reps=2):
