@@ -199,8 +199,9 @@ MPDATA_API int mpdata_batch_init(mpdata_batch **out, const mpdata_domain_desc *d
 MPDATA_API int mpdata_batch_step(mpdata_batch *b, int direction, int use_graph);
 
 /* Tile shape (index into the compiled shapes: FP32 32x16, 64x8, 32x8,
- * 64x16; FP64 32x16, 32x8, 64x8) and level-chunk length (0 = whole
- * columns).  Setting waits for the stream and drops captured graphs. */
+ * 16x16; FP64 32x8, 16x16, 16x8; one thread per column of the tile and a
+ * 2-cell ring) and level-chunk length (0 = whole columns).  Setting waits
+ * for the stream and drops captured graphs. */
 MPDATA_API int mpdata_batch_set_config(mpdata_batch *b, int shape, int kchunk_levels);
 MPDATA_API int mpdata_batch_get_config(mpdata_batch *b, int *shape, int *kchunk_levels,
                                        int *tile_x, int *tile_y, int *threads,

@@ -22,7 +22,7 @@
 #include <vector>
 
 #include "../../include/mpdata.h"
-#include "fused.cuh"
+#include "fused2.cuh"
 #include "grid.cuh"
 
 using mpd::Geo;
@@ -49,7 +49,7 @@ __device__ __forceinline__ int find_domain(const BDom* __restrict__ d, int nd, l
 }
 
 template <class T, int TX, int TY, int NT, int MINB, bool LIMIT>
-__global__ void __launch_bounds__(NT, MINB)
+__global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 batch_kernel(const BDom* __restrict__ dom, int nd, long long nitems, int* counter, int dir) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ long long s_item;
@@ -69,10 +69,10 @@ batch_kernel(const BDom* __restrict__ dom, int nd, long long nitems, int* counte
     const T* src = (const T*)(dir == 0 ? b.pa : (const void*)b.pb) + tr * b.tstride;
     T* dst = (T*)(dir == 0 ? b.pb : (void*)b.pa) + tr * b.tstride;
     const int k0 = ch * b.kchunk;
-    mpd::fused::step_tile<T, TX, TY, NT, LIMIT>(b.g, tx * TX, ty * TY, k0, min(b.g.nz, k0 + b.kchunk),
-                                                src, (const T*)b.u, (const T*)b.v, (const T*)b.w,
-                                                (const T*)b.gm, dst, smem_raw);
-    // step_tile begins with a barrier, so s_item is not rewritten before all
+    mpd::fused2::step_tile2<T, TX, TY, LIMIT>(b.g, tx * TX, ty * TY, k0, min(b.g.nz, k0 + b.kchunk),
+                                              src, (const T*)b.u, (const T*)b.v, (const T*)b.w,
+                                              (const T*)b.gm, dst, smem_raw);
+    // step_tile2 begins with a barrier, so s_item is not rewritten before all
     // threads have read it
   }
 }
@@ -81,20 +81,21 @@ batch_kernel(const BDom* __restrict__ dom, int nd, long long nitems, int* counte
 struct Shape {
   int tx, ty, nt;
 };
-constexpr Shape kShapes32[] = {{32, 16, 256}, {64, 8, 256}, {32, 8, 256}, {64, 16, 512}};
-constexpr Shape kShapes64[] = {{32, 16, 256}, {32, 8, 256}, {64, 8, 256}};
+// one thread per column of the tile + 2 ring: nt = (tx+4)(ty+4)
+constexpr Shape kShapes32[] = {{32, 16, 720}, {64, 8, 816}, {32, 8, 432}, {16, 16, 400}};
+constexpr Shape kShapes64[] = {{32, 8, 432}, {16, 16, 400}, {16, 8, 240}};
 constexpr int kNShapes32 = 4, kNShapes64 = 3;
 
 template <class T, int S> struct ShapeOf;
 #define MPD_SHAPE(TT, S, X, Y, N) \
   template <> struct ShapeOf<TT, S> { static constexpr int TX = X, TY = Y, NT = N; };
-MPD_SHAPE(float, 0, 32, 16, 256)
-MPD_SHAPE(float, 1, 64, 8, 256)
-MPD_SHAPE(float, 2, 32, 8, 256)
-MPD_SHAPE(float, 3, 64, 16, 512)
-MPD_SHAPE(double, 0, 32, 16, 256)
-MPD_SHAPE(double, 1, 32, 8, 256)
-MPD_SHAPE(double, 2, 64, 8, 256)
+MPD_SHAPE(float, 0, 32, 16, 720)
+MPD_SHAPE(float, 1, 64, 8, 816)
+MPD_SHAPE(float, 2, 32, 8, 432)
+MPD_SHAPE(float, 3, 16, 16, 400)
+MPD_SHAPE(double, 0, 32, 8, 432)
+MPD_SHAPE(double, 1, 16, 16, 400)
+MPD_SHAPE(double, 2, 16, 8, 240)
 #undef MPD_SHAPE
 
 }  // namespace
@@ -125,14 +126,14 @@ int bfail(mpdata_batch* b, cudaError_t e, const char* where) {
 template <class T, int S, bool LIMIT>
 const void* kernel_ptr() {
   using Sh = ShapeOf<T, S>;
-  constexpr int MINB = sizeof(T) == 8 ? 1 : 2;
+  constexpr int MINB = 1;
   return reinterpret_cast<const void*>(&batch_kernel<T, Sh::TX, Sh::TY, Sh::NT, MINB, LIMIT>);
 }
 
 template <class T, int S>
 size_t smem_of() {
   using Sh = ShapeOf<T, S>;
-  return mpd::fused::Layout<T, Sh::TX, Sh::TY>::bytes;
+  return mpd::fused2::Layout<T, Sh::TX, Sh::TY>::bytes;
 }
 
 template <class T>

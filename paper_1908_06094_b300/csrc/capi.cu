@@ -12,6 +12,7 @@
 #include "mass.cuh"
 #include "staged.cuh"
 #include "fused.cuh"
+#include "fused2.cuh"
 #include "adjoint.cuh"
 
 using mpd::Geo;
@@ -144,23 +145,28 @@ int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T*
   return MPDATA_OK;
 }
 
-// Tile shapes of the fused kernel: TX x TY columns per CTA, NT threads.
+// Tile shape of the fused kernel (one thread per column of the tile + 2
+// ring: (TX+4)(TY+4) threads); MINB: CTAs per SM the registers are sized for.
 template <class T> struct FusedShape;
-// MINB: CTAs per SM the register budget is sized for (shared memory allows
-// 2 for FP64 and 4 for FP32 at these tiles).
-template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 16, NT = 256, MINB = 2; };
-template <> struct FusedShape<float> { static constexpr int TX = 32, TY = 16, NT = 256, MINB = 3; };
+template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 8, MINB = 1; };
+template <> struct FusedShape<float> { static constexpr int TX = 32, TY = 16, MINB = 1; };
 
 template <class T, bool LIMIT>
 auto fused_kernel_ptr() {
   using F = FusedShape<T>;
-  return mpd::fused::step_kernel<T, F::TX, F::TY, F::NT, F::MINB, LIMIT>;
+  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT>;
 }
 
 template <class T>
 size_t fused_smem() {
   using F = FusedShape<T>;
-  return mpd::fused::Layout<T, F::TX, F::TY>::bytes;
+  return mpd::fused2::Layout<T, F::TX, F::TY>::bytes;
+}
+
+template <class T>
+constexpr int fused_threads() {
+  using F = FusedShape<T>;
+  return (F::TX + 4) * (F::TY + 4);
 }
 
 // Pick the k-chunking so that the grid covers the GPU about twice.
@@ -181,7 +187,7 @@ int fused_setup(mpdata_ctx* c) {
     return MPDATA_OK;  // not eligible on this device: the staged kernels run
   }
   int occ = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->nonosc ? k1 : k0, F::NT, bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->nonosc ? k1 : k0, fused_threads<T>(), bytes);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   cudaGetLastError();
   if (occ < 1) return MPDATA_OK;
@@ -213,11 +219,13 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
   dim3 grid((g.nx + F::TX - 1) / F::TX, (g.ny + F::TY - 1) / F::TY, c->nchunks);
   const size_t bytes = fused_smem<T>();
   if (c->nonosc)
-    MPD_LAUNCH(c, MPDATA_STAGE_FUSED, (fused_kernel_ptr<T, true>())<<<grid, F::NT, bytes, c->stream>>>(
-                                          g, c->kchunk, in, U, V, W, G, out));
+    MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+               (fused_kernel_ptr<T, true>())<<<grid, fused_threads<T>(), bytes, c->stream>>>(
+                   g, c->kchunk, in, U, V, W, G, out));
   else
-    MPD_LAUNCH(c, MPDATA_STAGE_FUSED, (fused_kernel_ptr<T, false>())<<<grid, F::NT, bytes, c->stream>>>(
-                                          g, c->kchunk, in, U, V, W, G, out));
+    MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+               (fused_kernel_ptr<T, false>())<<<grid, fused_threads<T>(), bytes, c->stream>>>(
+                   g, c->kchunk, in, U, V, W, G, out));
   MPD_CHECK_LAUNCH(c, "fused step kernel");
   return MPDATA_OK;
 }

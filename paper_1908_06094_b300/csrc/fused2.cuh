@@ -1,0 +1,309 @@
+// fused2.cuh -- the one-kernel MPDATA step (iord = 2) with one thread per
+// column.
+//
+// Same pipeline as fused.cuh (stages A..E on planes t+2, t+1, t+1, t, t),
+// organised so that almost every instruction is arithmetic:
+//   * the CTA has one thread per column of the tile + 2 ring, (TX+4)(TY+4)
+//     threads; a thread keeps its own column's values (psi^n, U, V, W, G,
+//     psi1, the pseudo-velocities, the betas, the vertical fluxes) in
+//     register queues as it marches up in k, so vertical neighbours cost
+//     nothing;
+//   * each plane of psi^n, U, V, W, G is read from device memory once per CTA
+//     (every thread loads its own column one plane ahead; threads 0..115
+//     also load the radius-3 ring that the donor pass of the outer cells
+//     needs) and published in shared memory, where horizontal neighbours are
+//     read at compile-time offsets from the thread's own slot;
+//   * the wrapped (periodic) column offsets are computed once per thread.
+// Intermediates that neighbours need (psi1, Ut, Vt, betas, x/y fluxes) go to
+// shared-memory rings; Wt and the vertical fluxes stay in registers.
+#pragma once
+#include "grid.cuh"
+
+namespace mpd {
+namespace fused2 {
+
+template <class T, int TX, int TY>
+struct Layout {
+  static constexpr int EX = TX + 4, EY = TY + 4, SN = EX * EY;  // radius-2 planes
+  static constexpr int RX = TX + 6, RY = TY + 6, RN = RX * RY;  // radius-3 planes
+  static constexpr int NT = SN;                                 // threads per CTA
+  static constexpr int NRING = RN - SN;                         // radius-3 ring cells
+  // offsets (in elements of T)
+  static constexpr int P0S = 0;             // psi^n, 2 planes, radius 3
+  static constexpr int US = P0S + 2 * RN;   // U, 2 planes, radius 3
+  static constexpr int VS = US + 2 * RN;    // V, 2 planes, radius 3
+  static constexpr int WS = VS + 2 * RN;    // W, 2 faces, radius 2
+  static constexpr int GS = WS + 2 * SN;    // G, 1 plane, radius 2
+  static constexpr int P1S = GS + SN;       // psi1, 4 planes
+  static constexpr int UTS = P1S + 4 * SN;  // Ut, 1 plane
+  static constexpr int VTS = UTS + SN;      // Vt, 1 plane
+  static constexpr int BUS = VTS + SN;      // beta-up, 2 planes
+  static constexpr int BDS = BUS + 2 * SN;  // beta-down, 2 planes
+  static constexpr int FXS = BDS + 2 * SN;  // x-face fluxes
+  static constexpr int FYS = FXS + SN;      // y-face fluxes
+  static constexpr int NVAL = FYS + SN;
+  static constexpr size_t bytes = (size_t)NVAL * sizeof(T);
+};
+
+template <class T, int TX, int TY, bool LIMIT>
+__device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
+                                           const T* __restrict__ P0, const T* __restrict__ U,
+                                           const T* __restrict__ V, const T* __restrict__ W,
+                                           const T* __restrict__ G, T* __restrict__ out,
+                                           unsigned char* smem_raw) {
+  using L = Layout<T, TX, TY>;
+  constexpr int EX = L::EX, RX = L::RX;
+  T* sm = reinterpret_cast<T*>(smem_raw);
+  const int tid = threadIdx.x;
+  const int nz = g.nz;
+  const T zero = T(0), eps = Eps<T>::v;
+
+  // own column: (x, y) in [-2, TX+1] x [-2, TY+1]
+  const int x = tid % EX - 2, y = tid / EX - 2;
+  const int s2 = tid;                         // radius-2 slot
+  const int s3 = (y + 3) * RX + (x + 3);      // radius-3 slot
+  auto wrapi = [&](int i) { return ((i % g.nx) + g.nx) % g.nx; };
+  auto wrapj = [&](int j) { return ((j % g.ny) + g.ny) % g.ny; };
+  const int64_t col = (int64_t)wrapj(j0 + y) * g.px + wrapi(i0 + x);
+  // radius-3 ring cell of this thread (threads < NRING)
+  const bool ringer = tid < L::NRING;
+  int r3 = 0;
+  int64_t rcol = 0;
+  if (ringer) {
+    int rx, ry, r = tid;
+    if (r < RX) { rx = r - 3; ry = -3; }
+    else if ((r -= RX) < RX) { rx = r - 3; ry = TY + 2; }
+    else if ((r -= RX) < L::EY) { rx = -3; ry = r - 2; }
+    else { r -= L::EY; rx = TX + 2; ry = r - 2; }
+    r3 = (ry + 3) * RX + (rx + 3);
+    rcol = (int64_t)wrapj(j0 + ry) * g.px + wrapi(i0 + rx);
+  }
+  const int64_t pxy = g.pxy;
+  auto clampk_ = [&](int k) { return k < 0 ? 0 : (k >= nz ? nz - 1 : k); };
+  // per-thread column pointers (plane 0); plane k is + k*pxy (warp-uniform)
+  const int64_t c0 = g.off0 + col, rc0 = g.off0 + rcol;
+  auto ld = [&](const T* f, int k, int64_t c) { return f[c + (int64_t)clampk_(k) * pxy]; };
+  // vertical face value with the closed bottom and top faces
+  auto ldw = [&](int k, int64_t c) { return (k < 0 || k >= nz - 1) ? zero : W[c + (int64_t)k * pxy]; };
+  // shared-memory views
+  T* p0s = sm + L::P0S;
+  T* us = sm + L::US;
+  T* vs = sm + L::VS;
+  T* ws = sm + L::WS;
+  T* gs = sm + L::GS;
+  T* p1s = sm + L::P1S;
+  T* uts = sm + L::UTS;
+  T* vts = sm + L::VTS;
+  T* fxs = sm + L::FXS;
+  T* fys = sm + L::FYS;
+  auto P1 = [&](int k, int o) -> T& { return p1s[(k & 3) * L::SN + s2 + o]; };
+
+  // Stages B, C and D are computed on every column, not only on the region
+  // the next stage reads (no divergent branches); the extra lanes read
+  // neighbouring shared slots that stay inside the shared allocation (the
+  // arrays are laid out so a radius-1 step off the plane lands in the
+  // neighbouring array) and their results are never read.
+  const bool inT = x >= 0 && x < TX && y >= 0 && y < TY;
+  const int gi = i0 + x, gj = j0 + y;
+  const bool writes = inT && gi < g.nx && gj < g.ny;
+
+  const int t0 = k0 - 5;
+  // register queues of the own column (values at planes t..t+3 / faces t..t+2)
+  T p0 = ld(P0, t0, c0), p1 = ld(P0, t0 + 1, c0), p2 = ld(P0, t0 + 2, c0);
+  T p3 = ld(P0, t0 + 3, c0), pn = ld(P0, t0 + 4, c0);
+  T u1 = ld(U, t0 + 1, c0), u2 = ld(U, t0 + 2, c0), un = ld(U, t0 + 3, c0);
+  T v1 = ld(V, t0 + 1, c0), v2 = ld(V, t0 + 2, c0), vn = ld(V, t0 + 3, c0);
+  T w0 = ldw(t0, c0), w1 = ldw(t0 + 1, c0), w2 = ldw(t0 + 2, c0), wn = ldw(t0 + 3, c0);
+  T g0 = ld(G, t0, c0), g1 = ld(G, t0 + 1, c0), g2 = ld(G, t0 + 2, c0), gn = ld(G, t0 + 3, c0);
+  T rp = zero, ru = zero, rv = zero;  // ring values of plane t+2
+  if (ringer) { rp = ld(P0, t0 + 2, rc0); ru = ld(U, t0 + 2, rc0); rv = ld(V, t0 + 2, rc0); }
+  T q0 = zero, q1 = zero, q2 = zero;     // psi1 at t, t+1, t+2
+  T utA = zero, vtA = zero, utB = zero, vtB = zero;  // Ut, Vt at t, t+1
+  T wtA = zero, wtB = zero;              // Wt at faces t+1/2, t+3/2
+  T buA = zero, bdA = zero, buB = zero, bdB = zero;  // betas at t, t+1
+  T fzA = zero, fzB = zero;              // vertical fluxes at faces t-1/2, t+1/2
+
+  __syncthreads();  // the shared memory may still be read by a previous tile
+  for (int t = t0; t < k1; ++t) {
+    // ---- publish plane t+2 of psi^n, U, V, face t+1 of W, plane t+1 of G --
+    {
+      const int a = t + 2;
+      p0s[(a & 1) * L::RN + s3] = p2;
+      us[(a & 1) * L::RN + s3] = u2;
+      vs[(a & 1) * L::RN + s3] = v2;
+      if (ringer) {
+        p0s[(a & 1) * L::RN + r3] = rp;
+        us[(a & 1) * L::RN + r3] = ru;
+        vs[(a & 1) * L::RN + r3] = rv;
+      }
+      ws[((t + 1) & 1) * L::SN + s2] = w1;
+      gs[s2] = g1;
+    }
+    // loads one plane ahead (used from the next iteration on); the plane
+    // offsets are the same for every thread
+    const int64_t o5 = (int64_t)clampk_(t + 5) * pxy, o4 = (int64_t)clampk_(t + 4) * pxy;
+    const int64_t o3 = (int64_t)clampk_(t + 3) * pxy;
+    const T pn_next = P0[c0 + o5];
+    const T un_next = U[c0 + o4], vn_next = V[c0 + o4], gn_next = G[c0 + o4];
+    const T wn_next = (t + 4 >= 0 && t + 4 < nz - 1) ? W[c0 + o4] : zero;  // closed faces
+    T rp_next = zero, ru_next = zero, rv_next = zero;
+    if (ringer) {
+      rp_next = P0[rc0 + o3];
+      ru_next = U[rc0 + o3];
+      rv_next = V[rc0 + o3];
+    }
+    __syncthreads();
+    // ---- A: psi1 on plane a = t+2 ---------------------------------------
+    const int a = t + 2;
+    if (a >= max(0, k0 - 3) && a <= min(nz - 1, k1 + 1)) {
+      const T* pa = p0s + (a & 1) * L::RN + s3;
+      const T* ua = us + (a & 1) * L::RN + s3;
+      const T* va = vs + (a & 1) * L::RN + s3;
+      const T fxp = donor(p2, pa[1], u2);
+      const T fxm = donor(pa[-1], p2, ua[-1]);
+      const T fyp = donor(p2, pa[RX], v2);
+      const T fym = donor(pa[-RX], p2, va[-RX]);
+      const T fzp = donor(p2, p3, w2);  // w2 = 0 on the top face
+      const T fzm = donor(p1, p2, w1);  // w1 = 0 on the bottom face
+      q2 = p2 - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) * rcp(g2);
+      P1(a, 0) = q2;
+    }
+    __syncthreads();
+    // ---- B: pseudo-velocities on plane b = t+1 ---------------------------
+    const int b = t + 1;
+    const bool runB = b >= max(0, k0 - 2) && b <= min(nz - 1, k1);
+    if (runB) {
+      const int bp = min(b + 1, nz - 1), bm = max(b - 1, 0);
+      const T qp = (bp == b) ? q1 : q2;  // own psi1 at the clamped b+1
+      const T qm = (bm == b) ? q1 : q0;  // own psi1 at the clamped b-1
+      const T* gb = gs + s2;
+      const T* vb = vs + (b & 1) * L::RN + s3;
+      const T* ub = us + (b & 1) * L::RN + s3;
+      const T* wb = ws + (b & 1) * L::SN + s2;
+      const T* wbm = ws + ((b - 1) & 1) * L::SN + s2;
+      {  // x face (used on x in [-2, TX], y in [-1, TY]; computed everywhere)
+        const T s1p = P1(b, EX + 1) + P1(b, EX), s1m = P1(b, -EX + 1) + P1(b, -EX);
+        const T s2p = P1(bp, 1) + qp, s2m = P1(bm, 1) + qm;
+        const T vsum = v1 + vb[1] + vb[-RX] + vb[-RX + 1];
+        const T wsum = w1 + wb[1] + w0 + wbm[1];
+        utB = pseudo_velocity(u1, g1 + gb[1], q1, P1(b, 1), s1p, s1m, s2p, s2m, vsum, wsum);
+        uts[s2] = utB;
+      }
+      {  // y face (used on x in [-1, TX], y in [-2, TY])
+        const T s1p = P1(b, EX + 1) + P1(b, 1), s1m = P1(b, EX - 1) + P1(b, -1);
+        const T s2p = P1(bp, EX) + qp, s2m = P1(bm, EX) + qm;
+        const T usum = u1 + ub[RX] + ub[-1] + ub[RX - 1];
+        const T wsum = w1 + wb[EX] + w0 + wbm[EX];
+        vtB = pseudo_velocity(v1, g1 + gb[EX], q1, P1(b, EX), s1p, s1m, s2p, s2m, usum, wsum);
+        vts[s2] = vtB;
+      }
+      {  // z face (used on x in [-1, TX], y in [-1, TY])
+        T res = zero;
+        if (b < nz - 1) {  // the top face is closed
+          const T* ub1 = us + ((b + 1) & 1) * L::RN + s3;
+          const T* vb1 = vs + ((b + 1) & 1) * L::RN + s3;
+          const T s1p = P1(b + 1, 1) + P1(b, 1), s1m = P1(b + 1, -1) + P1(b, -1);
+          const T s2p = P1(b + 1, EX) + P1(b, EX), s2m = P1(b + 1, -EX) + P1(b, -EX);
+          const T usum = u1 + u2 + ub[-1] + ub1[-1];
+          const T vsum = v1 + v2 + vb[-RX] + vb1[-RX];
+          res = pseudo_velocity(w1, g1 + g2, q1, q2, s1p, s1m, s2p, s2m, usum, vsum);
+        }
+        wtB = res;
+      }
+    }
+    __syncthreads();
+    // ---- C: limiter bounds and betas on plane b = t+1 --------------------
+    if (LIMIT && b >= max(0, k0 - 1) && b <= min(nz - 1, k1)) {  // used on tile + 1
+      const int bp = min(b + 1, nz - 1), bm = max(b - 1, 0);
+      const T qp = (bp == b) ? q1 : q2, qm = (bm == b) ? q1 : q0;
+      const T* pb = p0s + (b & 1) * L::RN + s3;
+      const T pxm = P1(b, -1), pxp = P1(b, 1), pym = P1(b, -EX), pyp = P1(b, EX);
+      const T vals[14] = {q1, p1, pb[-1], pb[1], pb[-RX], pb[RX], p0, p2,
+                          pxm, pxp, pym, pyp, qm, qp};
+      T hi, lo;
+      bounds(vals, hi, lo);
+      const T fxp = donor(q1, pxp, utB);
+      const T fxm = donor(pxm, q1, uts[s2 - 1]);
+      const T fyp = donor(q1, pyp, vtB);
+      const T fym = donor(pym, q1, vts[s2 - EX]);
+      const T fzp = donor(q1, qp, wtB);  // wtB = 0 on the top face
+      const T fzm = donor(qm, q1, wtA);  // wtA = 0 on the bottom face
+      const T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
+      const T ou = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
+      buB = (hi - q1) * g1 * rcp(in + eps);
+      bdB = (q1 - lo) * g1 * rcp(ou + eps);
+      sm[L::BUS + (b & 1) * L::SN + s2] = buB;
+      sm[L::BDS + (b & 1) * L::SN + s2] = bdB;
+    }
+    __syncthreads();
+    // ---- D: limited donor fluxes of plane t and face t+1/2 ---------------
+    if (t >= max(0, k0 - 1) && t <= k1 - 1) {
+      const T* bu0 = sm + L::BUS + (t & 1) * L::SN + s2;
+      const T* bd0 = sm + L::BDS + (t & 1) * L::SN + s2;
+      {  // used on x in [-1, TX-1], y in [0, TY-1]
+        T u = utA;
+        if (LIMIT) u = limit_face(u, buA, bdA, bu0[1], bd0[1]);
+        fxs[s2] = donor(q0, P1(t, 1), u);
+      }
+      {  // used on x in [0, TX-1], y in [-1, TY-1]
+        T v = vtA;
+        if (LIMIT) v = limit_face(v, buA, bdA, bu0[EX], bd0[EX]);
+        fys[s2] = donor(q0, P1(t, EX), v);
+      }
+      T f = zero;
+      if (t < nz - 1) {
+        T w = wtA;
+        if (LIMIT) w = limit_face(w, buA, bdA, buB, bdB);
+        f = donor(q0, q1, w);
+      }
+      fzB = f;
+    }
+    __syncthreads();
+    // ---- E: advance and write psi^(n+1) on plane t ------------------------
+    if (t >= k0 && writes) {
+      const T fzm = t > 0 ? fzA : zero;
+      const T r = q0 - ((fxs[s2] - fxs[s2 - 1]) + (fys[s2] - fys[s2 - EX]) + (fzB - fzm)) * rcp(g0);
+      const int ni = (gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0);
+      const int nj = (gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0);
+      const int klo = (t == 0) ? -g.h : t, khi = (t == nz - 1) ? nz - 1 + g.h : t;
+      for (int kk = klo; kk <= khi; ++kk) {
+        if (kk != t && kk >= 0 && kk < nz) continue;
+        const int64_t pk = g.off0 + (int64_t)kk * g.pxy;
+        for (int a2 = 0; a2 <= (ni != 0); ++a2) {
+          const int ii = gi + a2 * ni * g.nx;
+          for (int b2 = 0; b2 <= (nj != 0); ++b2) {
+            const int jj = gj + b2 * nj * g.ny;
+            out[pk + (int64_t)jj * g.px + ii] = r;
+          }
+        }
+      }
+    }
+    // ---- shift the queues ------------------------------------------------
+    p0 = p1; p1 = p2; p2 = p3; p3 = pn; pn = pn_next;
+    u1 = u2; u2 = un; un = un_next;
+    v1 = v2; v2 = vn; vn = vn_next;
+    w0 = w1; w1 = w2; w2 = wn; wn = wn_next;
+    g0 = g1; g1 = g2; g2 = gn; gn = gn_next;
+    rp = rp_next; ru = ru_next; rv = rv_next;
+    q0 = q1; q1 = q2;
+    utA = utB; vtA = vtB; wtA = wtB;
+    buA = buB; bdA = bdB;
+    fzA = fzB;
+    // The next iteration publishes into slots nobody reads after this point
+    // of the current one; its first barrier orders the rest.
+  }
+}
+
+template <class T, int TX, int TY, int MINB, bool LIMIT>
+__global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
+step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
+             const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
+             T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k0 = blockIdx.z * kchunk;
+  step_tile2<T, TX, TY, LIMIT>(g, blockIdx.x * TX, blockIdx.y * TY, k0, min(g.nz, k0 + kchunk),
+                               P0, U, V, W, G, out, smem_raw);
+}
+
+}  // namespace fused2
+}  // namespace mpd

@@ -74,9 +74,12 @@ __device__ __forceinline__ bool leq(double a, double b) { return okey0(a) <= oke
 __device__ __forceinline__ bool geq(float a, float b) { return a >= b; }
 __device__ __forceinline__ bool leq(float a, float b) { return a <= b; }
 
-// [x]+ and [x]- of the donor-cell split.
-template <class T> __device__ __forceinline__ T pos(T x) { return nonneg(x) ? x : T(0); }
-template <class T> __device__ __forceinline__ T neg(T x) { return nonneg(x) ? T(0) : x; }
+// [x]+ and [x]- of the donor-cell split (FP32: one min/max instruction; FP64:
+// a sign-bit select, off the FP64 pipe).
+__device__ __forceinline__ double pos(double x) { return nonneg(x) ? x : 0.0; }
+__device__ __forceinline__ double neg(double x) { return nonneg(x) ? 0.0 : x; }
+__device__ __forceinline__ float pos(float x) { return fmaxf(x, 0.0f); }
+__device__ __forceinline__ float neg(float x) { return fminf(x, 0.0f); }
 __device__ __forceinline__ double absv(double x) {
   return __longlong_as_double(__double_as_longlong(x) & 0x7fffffffffffffffLL);
 }
