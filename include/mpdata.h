@@ -137,15 +137,36 @@ MPDATA_API int mpdata_step_host(mpdata_ctx *c, void *psi_host, const void *u_hos
  *                  interior points, zero halo;
  *   u_bar, v_bar, w_bar  incremented by dJ/dU, dJ/dV, dJ/dW at interior
  *                  points (the closed top face of W gets nothing).
- * G is held fixed.  The step's intermediates are recomputed from psi_n;
- * derivatives follow the branches the forward takes (ties: max(a,b) = a
- * if a >= b, min(a,b) = a if a <= b, sign(0) = 0).  The reverse kernels add
- * with atomics, so results can differ in the last bits between runs.  The
- * first call allocates the adjoint scratch (13 fields).
+ * G is held fixed.  The step's intermediates are recomputed from psi_n
+ * (mpdata_adjoint_step_tape reuses a recorded tape instead); derivatives
+ * follow the branches the forward takes (ties: max(a,b) = a if a >= b,
+ * min(a,b) = a if a <= b, sign(0) = 0).  The pseudo-velocity reverse is a
+ * gather (no atomics); the other reverse kernels add with atomics, so
+ * results can differ in the last bits between runs.  The first call
+ * allocates the adjoint scratch (44 fields).
  * Errors: EINVAL (iord > 2, null pointer), EALIGN, ENOMEM, ECUDA. */
 MPDATA_API int mpdata_adjoint_step(mpdata_ctx *c, const void *psi_n, const void *u,
                                    const void *v, const void *w, const void *g, void *psi_bar,
                                    void *u_bar, void *v_bar, void *w_bar);
+
+/* Taped steps: the adjoint without forward recomputation.
+ * mpdata_tape_bytes gives the size of one step's tape (9 fields: psi1, the
+ * unlimited and limited pseudo-velocities, the two betas).
+ * mpdata_step_tape runs one forward step psi_in -> psi_out (distinct, halo
+ * filled) with the staged kernels and keeps its intermediates in the
+ * caller-owned DEVICE buffer tape (16-byte aligned).
+ * mpdata_adjoint_step_tape is mpdata_adjoint_step for a step whose tape
+ * was recorded from the same psi_n, u, v, w, g.
+ * Errors: EINVAL (iord > 2, null pointer, psi_in == psi_out), EALIGN,
+ * ENOMEM, ECUDA. */
+MPDATA_API int mpdata_tape_bytes(mpdata_ctx *c, size_t *bytes);
+MPDATA_API int mpdata_step_tape(mpdata_ctx *c, const void *psi_in, void *psi_out,
+                                const void *u, const void *v, const void *w, const void *g,
+                                void *tape);
+MPDATA_API int mpdata_adjoint_step_tape(mpdata_ctx *c, const void *tape, const void *psi_n,
+                                        const void *u, const void *v, const void *w,
+                                        const void *g, void *psi_bar, void *u_bar,
+                                        void *v_bar, void *w_bar);
 
 /* Reverse of the CELL halo fill for an adjoint field (DEVICE, in place):
  * each halo entry's adjoint is added to the interior value it copies, then

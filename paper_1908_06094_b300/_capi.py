@@ -61,6 +61,9 @@ SIGNATURES = {
     "mpdata_fill_halo": (_i, [_c, _c, _i]),
     "mpdata_adjoint_step": (_i, [_c] * 10),
     "mpdata_fold_halo_adjoint": (_i, [_c, _c]),
+    "mpdata_tape_bytes": (_i, [_c, ctypes.POINTER(ctypes.c_size_t)]),
+    "mpdata_step_tape": (_i, [_c] * 8),
+    "mpdata_adjoint_step_tape": (_i, [_c] * 11),
     "mpdata_mass": (_i, [_c, _c, _c, _c]),
     "mpdata_destroy": (None, [_c]),
     "mpdata_strerror": (ctypes.c_char_p, [_i]),
@@ -235,3 +238,18 @@ def mpdata_batch_launch_count(b):
 
 def mpdata_batch_destroy(b):
     lib.mpdata_batch_destroy(b)
+
+
+def mpdata_tape_bytes(ctx) -> int:
+    n = ctypes.c_size_t()
+    _check(lib.mpdata_tape_bytes(ctx, ctypes.byref(n)), "mpdata_tape_bytes", ctx)
+    return n.value
+
+
+def mpdata_step_tape(ctx, psi_in, psi_out, u, v, w, g, tape):
+    _check(lib.mpdata_step_tape(ctx, psi_in, psi_out, u, v, w, g, tape), "mpdata_step_tape", ctx)
+
+
+def mpdata_adjoint_step_tape(ctx, tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar):
+    _check(lib.mpdata_adjoint_step_tape(ctx, tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar,
+                                        w_bar), "mpdata_adjoint_step_tape", ctx)

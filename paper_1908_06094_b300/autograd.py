@@ -2,10 +2,11 @@
 and adjoint steps, with checkpoint-and-recompute.
 
 forward(psi0, U, V, W, G, nsteps) runs nsteps steps and keeps psi every
-``ckpt`` steps; backward walks the segments in reverse, recomputes each
-segment's states from its checkpoint (library forward steps), then applies
-the library's adjoint step to each state in reverse order.  Memory: about
-nsteps/ckpt + ckpt fields.  G is not differentiated.  Every step of both
+``ckpt`` steps; backward walks the segments in reverse, re-runs each
+segment once from its checkpoint with taped library steps (each keeping
+its intermediates), then applies the library's taped adjoint step to each
+step in reverse order.  Memory: nsteps/ckpt checkpoints plus ckpt states
+and tapes (9 fields each).  G is not differentiated.  Every step of both
 passes runs in the library's kernels; this module only orders the calls.
 """
 from __future__ import annotations
@@ -42,20 +43,26 @@ class MPDATAFunction(torch.autograd.Function):
         # the output's halo holds copies of interior values
         C.mpdata_fold_halo_adjoint(m._ctx, m._ptr(psib, "grad"))
         ub, vb, wb = torch.zeros_like(u), torch.zeros_like(v), torch.zeros_like(w)
+        nbytes = C.mpdata_tape_bytes(m._ctx)
         nseg = len(ckpts)
+        seglen = min(ckpt, nsteps)
+        tapes = [torch.empty(nbytes, dtype=torch.uint8, device=u.device) for _ in range(seglen)]
+        states = [torch.empty_like(ckpts[0]) for _ in range(seglen + 1)]
+        P = lambda t, name: m._ptr(t, name)  # noqa: E731
         for seg in reversed(range(nseg)):
             start = seg * ckpt
             end = min(start + ckpt, nsteps)
-            states = [ckpts[seg]]
-            for _ in range(start, end - 1):
-                nxt = torch.empty_like(states[-1])
-                m.step_out(states[-1], nxt, u, v, w, g)
-                states.append(nxt)
+            # record the segment once: its states and every step's tape
+            states[0].copy_(ckpts[seg])
+            for s in range(end - start):
+                C.mpdata_step_tape(m._ctx, P(states[s], "state"), P(states[s + 1], "state"),
+                                   P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
+                                   tapes[s].data_ptr())
             for s in reversed(range(end - start)):
-                C.mpdata_adjoint_step(m._ctx, m._ptr(states[s], "state"), m._ptr(u, "u"),
-                                      m._ptr(v, "v"), m._ptr(w, "w"), m._ptr(g, "g"),
-                                      m._ptr(psib, "psi_bar"), m._ptr(ub, "u_bar"),
-                                      m._ptr(vb, "v_bar"), m._ptr(wb, "w_bar"))
+                C.mpdata_adjoint_step_tape(m._ctx, tapes[s].data_ptr(), P(states[s], "state"),
+                                           P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
+                                           P(psib, "psi_bar"), P(ub, "u_bar"), P(vb, "v_bar"),
+                                           P(wb, "w_bar"))
         return psib, ub, vb, wb, None, None, None, None
 
 

@@ -2,14 +2,14 @@
 // without the limiter) on the GPU.
 //
 // The forward intermediates of the step (psi1, the pseudo-velocities, the
-// betas and the limited velocities) are recomputed by the staged forward
-// kernels from the checkpointed psi^n; the kernels here then run the forward
-// stages backwards, one thread per interior cell: each thread takes the
-// adjoint of what its cell computed (its update, its "+" face quantities,
-// its betas) and adds the contributions to every value that computation
-// read, with atomic adds (the neighbours it reads are read by other cells
-// too).  Periodic and clamped neighbours are addressed by wrapped indices,
-// so the reverse of the halo fill is implicit.
+// betas and the limited velocities) come from a tape recorded by the staged
+// forward kernels; the kernels here run the forward stages backwards, one
+// thread per interior cell.  The advance, limiter and beta reverses scatter:
+// each thread adds the adjoint of what its cell computed into every value
+// that computation read, with atomic adds.  The pseudo-velocity reverse, the
+// heaviest, is a gather in two passes without atomics (rev_pw, rev_pg).
+// Periodic and clamped neighbours are addressed by wrapped indices, so the
+// reverse of the halo fill is implicit.
 //
 // Derivatives follow the branch the forward took, with the tie rules
 // max(a,b) = a if a >= b, min(a,b) = a if a <= b, d|x| = sign(x) dx with
@@ -67,98 +67,6 @@ __global__ void rev_advance_kernel(Geo g, const T* __restrict__ P, const T* __re
   if (c.k < g.nz - 1) face(s, P[q], P[q + g.pxy], cw[q], true, q + g.pxy, &wb[q]);
   if (c.k > 0) face(-s, P[q - g.pxy], P[q], cw[q - g.pxy], false, q - g.pxy, &wb[q - g.pxy]);
   aadd(&Pb[q], own);
-}
-
-// Reverse of one face's pseudo-velocity.  L, R: the two cells; l1p/r1p and
-// l1m/r1m: the cells one step up/down the first cross direction (next to L
-// and R), the same for the second; k1*: the cross Courant field of the first
-// cross direction at the four faces of its average, k2* of the second
-// (a negative index marks a closed vertical face, which is constant).
-template <class T>
-__device__ __forceinline__ void rev_face(T ub, const T* P, int64_t L, int64_t R, int64_t l1p,
-                                         int64_t r1p, int64_t l1m, int64_t r1m, int64_t l2p,
-                                         int64_t r2p, int64_t l2m, int64_t r2m, T U, T Gf,
-                                         const T* c1, const int64_t* k1, const T* c2,
-                                         const int64_t* k2, T* Pb, T* Ub, T* c1b, T* c2b) {
-  const T eps = Eps<T>::v;
-  const T rd = rcp(P[R] + P[L] + eps);
-  const T A = (P[R] - P[L]) * rd;
-  const T n1 = T(0.5) * (P[r1p] + P[l1p] - P[r1m] - P[l1m]);
-  const T rd1 = rcp(P[r1p] + P[l1p] + P[r1m] + P[l1m] + eps);
-  const T B1 = n1 * rd1;
-  const T n2 = T(0.5) * (P[r2p] + P[l2p] - P[r2m] - P[l2m]);
-  const T rd2 = rcp(P[r2p] + P[l2p] + P[r2m] + P[l2m] + eps);
-  const T B2 = n2 * rd2;
-  T C1 = T(0), C2 = T(0);
-  for (int q = 0; q < 4; ++q) {
-    if (k1[q] >= 0) C1 += c1[k1[q]];
-    if (k2[q] >= 0) C2 += c2[k2[q]];
-  }
-  C1 *= T(0.25);
-  C2 *= T(0.25);
-  const T rG = rcp(Gf);
-  const T Dd = absv(U) - U * U * rG;
-  const T X = C1 * B1 + C2 * B2;
-  const T sg = (ge0(U) && le0(U)) ? T(0) : (nonneg(U) ? T(1) : T(-1));  // sign(0) = 0
-  aadd(Ub, ub * (sg * A - T(2) * U * rG * A - X * rG));
-  const T Ab = ub * Dd;
-  const T B1b = ub * (-U * C1 * rG), B2b = ub * (-U * C2 * rG);
-  const T C1b = T(0.25) * ub * (-U * B1 * rG), C2b = T(0.25) * ub * (-U * B2 * rG);
-  aadd(&Pb[R], Ab * (T(1) - A) * rd);
-  aadd(&Pb[L], Ab * (T(-1) - A) * rd);
-  T wp = B1b * (T(0.5) - B1) * rd1, wm = B1b * (T(-0.5) - B1) * rd1;
-  aadd(&Pb[r1p], wp); aadd(&Pb[l1p], wp); aadd(&Pb[r1m], wm); aadd(&Pb[l1m], wm);
-  wp = B2b * (T(0.5) - B2) * rd2;
-  wm = B2b * (T(-0.5) - B2) * rd2;
-  aadd(&Pb[r2p], wp); aadd(&Pb[l2p], wp); aadd(&Pb[r2m], wm); aadd(&Pb[l2m], wm);
-  for (int q = 0; q < 4; ++q) {
-    if (k1[q] >= 0) aadd(&c1b[k1[q]], C1b);
-    if (k2[q] >= 0) aadd(&c2b[k2[q]], C2b);
-  }
-}
-
-template <class T>
-__global__ void rev_pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
-                                  const T* __restrict__ cv, const T* __restrict__ cw,
-                                  const T* __restrict__ G, const T* __restrict__ utb,
-                                  const T* __restrict__ vtb, const T* __restrict__ wtb, T* Pb,
-                                  T* ub, T* vb, T* wb) {
-  Cell c = cell_of(g);
-  if (!c.ok) return;
-  const int i = c.i, j = c.j, k = c.k;
-  const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
-  const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
-  const int kp = clampk(k + 1, g.nz), km = clampk(k - 1, g.nz);
-  auto A_ = [&](int a, int b, int d) { return at(g, a, b, d); };
-  // a vertical face index, or -1 when the face is closed
-  auto wf = [&](int a, int b, int d) -> int64_t {
-    return (d < 0 || d >= g.nz - 1) ? -1 : at(g, a, b, d);
-  };
-  const int64_t q = A_(i, j, k);
-  {  // x face (i+1/2): cross directions y (V) and z (W)
-    const int64_t R = A_(ip, j, k);
-    const int64_t k1[4] = {q, R, A_(i, jm, k), A_(ip, jm, k)};
-    const int64_t k2[4] = {wf(i, j, k), wf(ip, j, k), wf(i, j, k - 1), wf(ip, j, k - 1)};
-    rev_face(utb[q], P, q, R, A_(i, jp, k), A_(ip, jp, k), A_(i, jm, k), A_(ip, jm, k),
-             A_(i, j, kp), A_(ip, j, kp), A_(i, j, km), A_(ip, j, km), cu[q],
-             T(0.5) * (G[q] + G[R]), cv, k1, cw, k2, Pb, &ub[q], vb, wb);
-  }
-  {  // y face (j+1/2): cross directions x (U) and z (W)
-    const int64_t R = A_(i, jp, k);
-    const int64_t k1[4] = {q, R, A_(im, j, k), A_(im, jp, k)};
-    const int64_t k2[4] = {wf(i, j, k), wf(i, jp, k), wf(i, j, k - 1), wf(i, jp, k - 1)};
-    rev_face(vtb[q], P, q, R, A_(ip, j, k), A_(ip, jp, k), A_(im, j, k), A_(im, jp, k),
-             A_(i, j, kp), A_(i, jp, kp), A_(i, j, km), A_(i, jp, km), cv[q],
-             T(0.5) * (G[q] + G[R]), cu, k1, cw, k2, Pb, &vb[q], ub, wb);
-  }
-  if (k < g.nz - 1) {  // z face (k+1/2): cross directions x (U) and y (V)
-    const int64_t R = q + g.pxy;
-    const int64_t k1[4] = {q, R, A_(im, j, k), A_(im, j, k + 1)};
-    const int64_t k2[4] = {q, R, A_(i, jm, k), A_(i, jm, k + 1)};
-    rev_face(wtb[q], P, q, R, A_(ip, j, k), A_(ip, j, k + 1), A_(im, j, k), A_(im, j, k + 1),
-             A_(i, jp, k), A_(i, jp, k + 1), A_(i, jm, k), A_(i, jm, k + 1), cw[q],
-             T(0.5) * (G[q] + G[R]), cu, k1, cv, k2, Pb, &wb[q], ub, vb);
-  }
 }
 
 // Reverse of the limited velocity of a face (see the tie rules above).
@@ -270,6 +178,149 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
       const int64_t l = nb[2 * d];
       rev_donor(fmb, P[l], P[q], vel[d][l], &Pb[l], &Pb[q], &velb[d][l]);
     }
+  }
+}
+
+
+// ---------------------------------------------------------------------------
+// Pseudo-velocity reverse in gather form (no atomics).
+//
+// Pass 1 (rev_pw_kernel), per cell and its three "+" faces f, from the
+// adjoint ub_f of the pseudo-velocity: adds dJ/dU_f (own face) and stores
+// eight weights per face, the adjoint routed to each stencil point:
+//   wl, wr    to psi1 at L and R through A,
+//   w1p, w1m  to the two psi1 values on each side of the first cross
+//             direction (B1), w2p, w2m the same for B2,
+//   c1, c2    to each of the four Courant faces of the two cross averages.
+// Pass 2 (rev_pg_kernel), per cell q: gathers every weight whose stencil
+// point is q (about thirty faces) into dJ/dpsi1_q, and the cross weights
+// of the eight faces whose averages contain each of q's three Courant
+// faces.  The clamped k neighbours of the boundary levels gather the
+// weights of the faces whose clamped index lands on them.
+enum { kWL = 0, kWR, kW1P, kW1M, kW2P, kW2M, kC1, kC2, kNW };
+
+template <class T>
+__global__ void rev_pw_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
+                              const T* __restrict__ cv, const T* __restrict__ cw,
+                              const T* __restrict__ G, const T* __restrict__ utb,
+                              const T* __restrict__ vtb, const T* __restrict__ wtb,
+                              T* __restrict__ wts, T* ub, T* vb, T* wb) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  const T eps = Eps<T>::v;
+  const int i = c.i, j = c.j, k = c.k;
+  const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
+  const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
+  const int kp = clampk(k + 1, g.nz), km = clampk(k - 1, g.nz);
+  auto A_ = [&](int a, int b, int d) { return at(g, a, b, d); };
+  auto wfv = [&](int a, int b, int d) -> T {
+    return (d < 0 || d >= g.nz - 1) ? T(0) : cw[at(g, a, b, d)];
+  };
+  const int64_t q = A_(i, j, k);
+  const int64_t F = g.total;  // one weight field
+  // fam: 0 x, 1 y, 2 z; fields [fam][kNW]
+  auto put = [&](int fam, int w, T v) { wts[((int64_t)fam * kNW + w) * F + q] = v; };
+  auto face = [&](int fam, T ubv, T U, T Gf, T pl, T pr, T s1pv, T s1mv, T s2pv, T s2mv,
+                  T C1sum, T C2sum, T* Ub) {
+    const T rd = rcp(pr + pl + eps);
+    const T A = (pr - pl) * rd;
+    const T rd1 = rcp(s1pv + s1mv + eps), rd2 = rcp(s2pv + s2mv + eps);
+    const T B1 = T(0.5) * (s1pv - s1mv) * rd1, B2 = T(0.5) * (s2pv - s2mv) * rd2;
+    const T C1 = T(0.25) * C1sum, C2 = T(0.25) * C2sum;
+    const T rG = rcp(Gf);
+    const T Dd = absv(U) - U * U * rG;
+    const T X = C1 * B1 + C2 * B2;
+    const T sg = (ge0(U) && le0(U)) ? T(0) : (nonneg(U) ? T(1) : T(-1));
+    *Ub += ubv * (sg * A - T(2) * U * rG * A - X * rG);
+    const T Ab = ubv * Dd;
+    const T B1b = ubv * (-U * C1 * rG), B2b = ubv * (-U * C2 * rG);
+    put(fam, kWL, Ab * (T(-1) - A) * rd);
+    put(fam, kWR, Ab * (T(1) - A) * rd);
+    put(fam, kW1P, B1b * (T(0.5) - B1) * rd1);
+    put(fam, kW1M, B1b * (T(-0.5) - B1) * rd1);
+    put(fam, kW2P, B2b * (T(0.5) - B2) * rd2);
+    put(fam, kW2M, B2b * (T(-0.5) - B2) * rd2);
+    put(fam, kC1, T(0.25) * ubv * (-U * B1 * rG));
+    put(fam, kC2, T(0.25) * ubv * (-U * B2 * rG));
+  };
+  auto p = [&](int a, int b, int d) { return P[A_(a, b, d)]; };
+  {  // x face: cross directions y (V) and z (W)
+    const int64_t R = A_(ip, j, k);
+    face(0, utb[q], cu[q], T(0.5) * (G[q] + G[R]), p(i, j, k), p(ip, j, k),
+         p(ip, jp, k) + p(i, jp, k), p(ip, jm, k) + p(i, jm, k),
+         p(ip, j, kp) + p(i, j, kp), p(ip, j, km) + p(i, j, km),
+         cv[q] + cv[R] + cv[A_(i, jm, k)] + cv[A_(ip, jm, k)],
+         wfv(i, j, k) + wfv(ip, j, k) + wfv(i, j, k - 1) + wfv(ip, j, k - 1), &ub[q]);
+  }
+  {  // y face: cross directions x (U) and z (W)
+    const int64_t R = A_(i, jp, k);
+    face(1, vtb[q], cv[q], T(0.5) * (G[q] + G[R]), p(i, j, k), p(i, jp, k),
+         p(ip, jp, k) + p(ip, j, k), p(im, jp, k) + p(im, j, k),
+         p(i, jp, kp) + p(i, j, kp), p(i, jp, km) + p(i, j, km),
+         cu[q] + cu[R] + cu[A_(im, j, k)] + cu[A_(im, jp, k)],
+         wfv(i, j, k) + wfv(i, jp, k) + wfv(i, j, k - 1) + wfv(i, jp, k - 1), &vb[q]);
+  }
+  if (k < g.nz - 1) {  // z face: cross directions x (U) and y (V)
+    const int64_t R = q + g.pxy;
+    face(2, wtb[q], cw[q], T(0.5) * (G[q] + G[R]), p(i, j, k), p(i, j, k + 1),
+         p(ip, j, k + 1) + p(ip, j, k), p(im, j, k + 1) + p(im, j, k),
+         p(i, jp, k + 1) + p(i, jp, k), p(i, jm, k + 1) + p(i, jm, k),
+         cu[q] + cu[R] + cu[A_(im, j, k)] + cu[A_(im, j, k + 1)],
+         cv[q] + cv[R] + cv[A_(i, jm, k)] + cv[A_(i, jm, k + 1)], &wb[q]);
+  } else {
+    for (int w = 0; w < kNW; ++w) put(2, w, T(0));
+  }
+}
+
+template <class T>
+__global__ void rev_pg_kernel(Geo g, const T* __restrict__ wts, T* Pb, T* ub, T* vb, T* wb) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  const int i = c.i, j = c.j, k = c.k, nz = g.nz;
+  const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
+  const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
+  const int64_t F = g.total;
+  auto W = [&](int fam, int w, int a, int b, int d) -> T {
+    return wts[((int64_t)fam * kNW + w) * F + at(g, a, b, d)];
+  };
+  T s = T(0);
+  // x faces: A, B1 (y), B2 (z, clamped)
+  s += W(0, kWL, i, j, k) + W(0, kWR, im, j, k);
+  s += W(0, kW1P, i, jm, k) + W(0, kW1P, im, jm, k) + W(0, kW1M, i, jp, k) + W(0, kW1M, im, jp, k);
+  // y faces: A, B1 (x), B2 (z, clamped)
+  s += W(1, kWL, i, j, k) + W(1, kWR, i, jm, k);
+  s += W(1, kW1P, im, j, k) + W(1, kW1P, im, jm, k) + W(1, kW1M, ip, j, k) + W(1, kW1M, ip, jm, k);
+  // clamped z neighbours of the x and y faces: q is the "+z" point of the
+  // faces at level kf with clamp(kf+1) == k, the "-z" point where clamp(kf-1) == k
+  auto zgather = [&](int kf, int w) {
+    s += W(0, w, i, j, kf) + W(0, w, im, j, kf) + W(1, w, i, j, kf) + W(1, w, i, jm, kf);
+  };
+  if (k >= 1) zgather(k - 1, kW2P);
+  if (k == nz - 1) zgather(k, kW2P);
+  if (k + 1 <= nz - 1) zgather(k + 1, kW2M);
+  if (k == 0) zgather(k, kW2M);
+  // z faces (levels kf in [0, nz-2]; the top level holds zeros)
+  s += W(2, kWL, i, j, k);
+  if (k >= 1) s += W(2, kWR, i, j, k - 1);
+  s += W(2, kW1P, im, j, k) + W(2, kW1M, ip, j, k) + W(2, kW2P, i, jm, k) + W(2, kW2M, i, jp, k);
+  if (k >= 1)
+    s += W(2, kW1P, im, j, k - 1) + W(2, kW1M, ip, j, k - 1) + W(2, kW2P, i, jm, k - 1) +
+         W(2, kW2M, i, jp, k - 1);
+  const int64_t q = at(g, i, j, k);
+  Pb[q] += s;
+  // cross averages: U (face i+1/2) in y faces and z faces, V in x and z, W in x and y
+  T su = W(1, kC1, i, j, k) + W(1, kC1, i, jm, k) + W(1, kC1, ip, j, k) + W(1, kC1, ip, jm, k);
+  su += W(2, kC1, i, j, k) + W(2, kC1, ip, j, k);
+  if (k >= 1) su += W(2, kC1, i, j, k - 1) + W(2, kC1, ip, j, k - 1);
+  ub[q] += su;
+  T sv = W(0, kC1, i, j, k) + W(0, kC1, im, j, k) + W(0, kC1, i, jp, k) + W(0, kC1, im, jp, k);
+  sv += W(2, kC2, i, j, k) + W(2, kC2, i, jp, k);
+  if (k >= 1) sv += W(2, kC2, i, j, k - 1) + W(2, kC2, i, jp, k - 1);
+  vb[q] += sv;
+  if (k <= nz - 2) {  // open vertical face
+    T sw = W(0, kC2, i, j, k) + W(0, kC2, im, j, k) + W(0, kC2, i, j, k + 1) + W(0, kC2, im, j, k + 1);
+    sw += W(1, kC2, i, j, k) + W(1, kC2, i, jm, k) + W(1, kC2, i, j, k + 1) + W(1, kC2, i, jm, k + 1);
+    wb[q] += sw;
   }
 }
 

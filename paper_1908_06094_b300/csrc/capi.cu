@@ -32,8 +32,7 @@ struct mpdata_ctx {
   void* hbuf;
   // adjoint scratch (allocated on the first adjoint call)
   void* adjbuf;
-  void *a_ul, *a_vl, *a_wl, *a_p1b, *a_p0b, *a_utb, *a_vtb, *a_wtb, *a_ulb, *a_vlb, *a_wlb,
-      *a_bub, *a_bdb;
+  void* a_out;  // the recomputed psi^(n+1) of mpdata_adjoint_step
   // instrumentation
   long long launches;
   bool prof_on;
@@ -286,19 +285,37 @@ int mass_launch(mpdata_ctx* c, const T* psi, const T* G, double* out) {
 
 // ------------------------------------------------------------- adjoint --
 
+constexpr int kTapeFields = 9;   // psi1, Ut, Vt, Wt, beta-up, beta-down, Ul, Vl, Wl
+constexpr int kAdjFields = 10 + 24 + kTapeFields + 1;  // adjoints, weights, tape, psi^(n+1)
+
+size_t field_pad(const mpdata_ctx* c) {
+  return ((size_t)c->g.total * c->esize + 255) & ~(size_t)255;
+}
+
 int adjoint_scratch(mpdata_ctx* c) {
   if (c->adjbuf) return MPDATA_OK;
-  const size_t fbytes = ((size_t)c->g.total * c->esize + 255) & ~(size_t)255;
-  if (cudaMalloc(&c->adjbuf, 13 * fbytes) != cudaSuccess) {
+  if (cudaMalloc(&c->adjbuf, kAdjFields * field_pad(c)) != cudaSuccess) {
     cudaGetLastError();
     c->adjbuf = nullptr;
     return MPDATA_ENOMEM;
   }
-  char* p = (char*)c->adjbuf;
-  void** slots[13] = {&c->a_ul, &c->a_vl, &c->a_wl, &c->a_p1b, &c->a_p0b, &c->a_utb, &c->a_vtb,
-                      &c->a_wtb, &c->a_ulb, &c->a_vlb, &c->a_wlb, &c->a_bub, &c->a_bdb};
-  for (int q = 0; q < 13; ++q) *slots[q] = p + q * fbytes;
+  c->a_out = (char*)c->adjbuf + (size_t)(kAdjFields - 1) * field_pad(c);
   return MPDATA_OK;
+}
+
+template <class T>
+struct Tape {
+  T *p1, *ut, *vt, *wt, *bu, *bd, *ul, *vl, *wl;
+};
+
+template <class T>
+Tape<T> tape_view(const mpdata_ctx* c, void* base) {
+  char* p = (char*)base;
+  const size_t f = field_pad(c);
+  Tape<T> t;
+  T** slots[kTapeFields] = {&t.p1, &t.ut, &t.vt, &t.wt, &t.bu, &t.bd, &t.ul, &t.vl, &t.wl};
+  for (int q = 0; q < kTapeFields; ++q) *slots[q] = (T*)(p + q * f);
+  return t;
 }
 
 template <class T>
@@ -312,39 +329,53 @@ int halo_fold_launch(mpdata_ctx* c, T* f) {
   return MPDATA_OK;
 }
 
-// One adjoint step: recompute the step's intermediates from psi^n with the
-// staged forward kernels, then run the reverse kernels.
+// One staged forward step psi_in -> psi_out that keeps its intermediates in
+// the tape (iord 1 or 2).
 template <class T>
-int adjoint_step(mpdata_ctx* c, const T* psi, const T* U, const T* V, const T* W, const T* G,
-                 T* psib, T* ub, T* vb, T* wb) {
+int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const T* W,
+              const T* G, Tape<T> tp) {
   using namespace mpd::staged;
+  const Geo& g = c->g;
+  const dim3 grid = cell_grid(g);
+  cudaStream_t s = c->stream;
+  T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
+  MPD_LAUNCH(c, MPDATA_STAGE_DONOR, flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
+  if (c->iord == 1) {
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, out));
+  } else {
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, tp.p1));
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, U, V, W, G, tp.ut, tp.vt, tp.wt));
+    if (c->nonosc) {
+      MPD_LAUNCH(c, MPDATA_STAGE_BETA, beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd));
+      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                            g, tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, fx, fy, fz, tp.ul, tp.vl, tp.wl));
+    } else {
+      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt, fx, fy, fz));
+    }
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, fx, fy, fz, G, out));
+  }
+  MPD_CHECK_LAUNCH(c, "taped forward step");
+  return halo_launch<T>(c, out, MPDATA_HALO_CELL);
+}
+
+// The reverse kernels of one step, from its tape.
+template <class T>
+int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V, const T* W,
+                 const T* G, T* psib, T* ub, T* vb, T* wb) {
   using namespace mpd::adj;
   int rc = adjoint_scratch(c);
   if (rc) return rc;
   const Geo& g = c->g;
   const dim3 grid = cell_grid(g);
   cudaStream_t s = c->stream;
+  const size_t f = field_pad(c);
+  char* base = (char*)c->adjbuf;
+  T *p1b = (T*)(base + 0 * f), *p0b = (T*)(base + 1 * f);
+  T *utb = (T*)(base + 2 * f), *vtb = (T*)(base + 3 * f), *wtb = (T*)(base + 4 * f);
+  T *ulb = (T*)(base + 5 * f), *vlb = (T*)(base + 6 * f), *wlb = (T*)(base + 7 * f);
+  T *bub = (T*)(base + 8 * f), *bdb = (T*)(base + 9 * f);
+  T* wts = (T*)(base + 10 * f);  // 24 weight fields, g.total apart
   const size_t fb = (size_t)g.total * sizeof(T);
-  T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
-  T* p1 = (T*)c->psi1;
-  T *ut = (T*)c->ut, *vt = (T*)c->vt, *wt = (T*)c->wt, *bu = (T*)c->bu, *bd = (T*)c->bd;
-  T *ul = (T*)c->a_ul, *vl = (T*)c->a_vl, *wl = (T*)c->a_wl;
-  T *p1b = (T*)c->a_p1b, *p0b = (T*)c->a_p0b;
-  T *utb = (T*)c->a_utb, *vtb = (T*)c->a_vtb, *wtb = (T*)c->a_wtb;
-  T *ulb = (T*)c->a_ulb, *vlb = (T*)c->a_vlb, *wlb = (T*)c->a_wlb;
-  T *bub = (T*)c->a_bub, *bdb = (T*)c->a_bdb;
-  // forward recompute
-  if (c->iord == 2) {
-    MPD_LAUNCH(c, MPDATA_STAGE_DONOR, flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
-    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, p1));
-    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(g, p1, U, V, W, G, ut, vt, wt));
-    if (c->nonosc) {
-      MPD_LAUNCH(c, MPDATA_STAGE_BETA, beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, p1, ut, vt, wt, G, bu, bd));
-      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                            g, p1, ut, vt, wt, bu, bd, fx, fy, fz, ul, vl, wl));
-    }
-  }
-  MPD_CHECK_LAUNCH(c, "adjoint forward recompute");
   T* zero_list[10] = {p1b, p0b, utb, vtb, wtb, ulb, vlb, wlb, bub, bdb};
   for (int q = 0; q < 10; ++q) {
     cudaError_t e = cudaMemsetAsync(zero_list[q], 0, fb, s);
@@ -354,21 +385,23 @@ int adjoint_step(mpdata_ctx* c, const T* psi, const T* U, const T* V, const T* W
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
                                             g, psi, U, V, W, G, psib, p0b, ub, vb, wb));
   } else {
-    T* vel[3] = {c->nonosc ? ul : ut, c->nonosc ? vl : vt, c->nonosc ? wl : wt};
+    T* vel[3] = {c->nonosc ? tp.ul : tp.ut, c->nonosc ? tp.vl : tp.vt, c->nonosc ? tp.wl : tp.wt};
     T* velb[3] = {c->nonosc ? ulb : utb, c->nonosc ? vlb : vtb, c->nonosc ? wlb : wtb};
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                            g, p1, vel[0], vel[1], vel[2], G, psib, p1b, velb[0],
+                                            g, tp.p1, vel[0], vel[1], vel[2], G, psib, p1b, velb[0],
                                             velb[1], velb[2]));
     if (c->nonosc) {
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, rev_limit_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                            g, ut, vt, wt, bu, bd, ulb, vlb, wlb, utb, vtb, wtb,
-                                            bub, bdb));
+                                            g, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, ulb, vlb, wlb,
+                                            utb, vtb, wtb, bub, bdb));
       MPD_LAUNCH(c, MPDATA_STAGE_BETA, rev_beta_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                           g, psi, p1, ut, vt, wt, G, bub, bdb, p0b, p1b, utb,
-                                           vtb, wtb));
+                                           g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, bub, bdb, p0b,
+                                           p1b, utb, vtb, wtb));
     }
-    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, rev_pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                           g, p1, U, V, W, G, utb, vtb, wtb, p1b, ub, vb, wb));
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, rev_pw_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                           g, tp.p1, U, V, W, G, utb, vtb, wtb, wts, ub, vb, wb));
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                           g, wts, p1b, ub, vb, wb));
     MPD_LAUNCH(c, MPDATA_STAGE_DONOR, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
                                           g, psi, U, V, W, G, p1b, p0b, ub, vb, wb));
   }
@@ -376,6 +409,19 @@ int adjoint_step(mpdata_ctx* c, const T* psi, const T* U, const T* V, const T* W
   cudaError_t e = cudaMemcpyAsync(psib, p0b, fb, cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "adjoint result copy");
   return MPDATA_OK;
+}
+
+// One adjoint step with its own forward recompute (into the internal tape).
+template <class T>
+int adjoint_step(mpdata_ctx* c, const T* psi, const T* U, const T* V, const T* W, const T* G,
+                 T* psib, T* ub, T* vb, T* wb) {
+  int rc = adjoint_scratch(c);
+  if (rc) return rc;
+  Tape<T> tp = tape_view<T>(c, (char*)c->adjbuf + (size_t)(10 + 24) * field_pad(c));
+  // the recomputed psi^(n+1) goes to the context's second psi scratch
+  T* out = (T*)c->a_out;
+  if ((rc = step_tape<T>(c, psi, out, U, V, W, G, tp))) return rc;
+  return adjoint_tape<T>(c, tp, psi, U, V, W, G, psib, ub, vb, wb);
 }
 
 int check_fields(const void* const* ptrs, int n) {
@@ -595,6 +641,45 @@ int mpdata_adjoint_step(mpdata_ctx* c, const void* psi_n, const void* u, const v
   return adjoint_step<float>(c, (const float*)psi_n, (const float*)u, (const float*)v,
                              (const float*)w, (const float*)g, (float*)psi_bar, (float*)u_bar,
                              (float*)v_bar, (float*)w_bar);
+}
+
+int mpdata_tape_bytes(mpdata_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return MPDATA_EINVAL;
+  *bytes = kTapeFields * field_pad(c);
+  return MPDATA_OK;
+}
+
+int mpdata_step_tape(mpdata_ctx* c, const void* psi_in, void* psi_out, const void* u,
+                     const void* v, const void* w, const void* g, void* tape) {
+  if (!c || c->iord > 2) return MPDATA_EINVAL;
+  const void* f[7] = {psi_in, psi_out, u, v, w, g, tape};
+  int rc = check_fields(f, 7);
+  if (rc) return rc;
+  if (psi_in == psi_out) return MPDATA_EINVAL;
+  if (c->dtype == MPDATA_F64)
+    return step_tape<double>(c, (const double*)psi_in, (double*)psi_out, (const double*)u,
+                             (const double*)v, (const double*)w, (const double*)g,
+                             tape_view<double>(c, tape));
+  return step_tape<float>(c, (const float*)psi_in, (float*)psi_out, (const float*)u,
+                          (const float*)v, (const float*)w, (const float*)g,
+                          tape_view<float>(c, tape));
+}
+
+int mpdata_adjoint_step_tape(mpdata_ctx* c, const void* tape, const void* psi_n, const void* u,
+                             const void* v, const void* w, const void* g, void* psi_bar,
+                             void* u_bar, void* v_bar, void* w_bar) {
+  if (!c || c->iord > 2) return MPDATA_EINVAL;
+  const void* f[10] = {tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
+  int rc = check_fields(f, 10);
+  if (rc) return rc;
+  if (c->dtype == MPDATA_F64)
+    return adjoint_tape<double>(c, tape_view<double>(c, (void*)tape), (const double*)psi_n,
+                                (const double*)u, (const double*)v, (const double*)w,
+                                (const double*)g, (double*)psi_bar, (double*)u_bar,
+                                (double*)v_bar, (double*)w_bar);
+  return adjoint_tape<float>(c, tape_view<float>(c, (void*)tape), (const float*)psi_n,
+                             (const float*)u, (const float*)v, (const float*)w, (const float*)g,
+                             (float*)psi_bar, (float*)u_bar, (float*)v_bar, (float*)w_bar);
 }
 
 int mpdata_fold_halo_adjoint(mpdata_ctx* c, void* field) {

@@ -70,10 +70,26 @@ mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
   __shared__ double sh[MASS_THREADS];
   const int rows = g.ny * g.nz;
   typename MassAcc<T>::type acc;
-  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
-    const int j = r % g.ny, k = r / g.ny;
-    const int64_t base = at(g, 0, j, k);
-    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) acc.add(psi[base + i], G[base + i]);
+  // R rows at a time: all their loads are issued before the (fixed-order)
+  // accumulation, so each thread keeps 2R loads in flight
+  constexpr int R = 4;
+  for (int r0 = blockIdx.x; r0 < rows; r0 += R * gridDim.x) {
+    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+      T a[R], b[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const int r = r0 + q * gridDim.x;
+        a[q] = b[q] = T(0);
+        if (r < rows) {
+          const int64_t base = at(g, 0, r % g.ny, r / g.ny);
+          a[q] = psi[base + i];
+          b[q] = G[base + i];
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < R; ++q)
+        if (r0 + q * gridDim.x < rows) acc.add(a[q], b[q]);
+    }
   }
   acc.flush();
   double b = block_fold(acc.s, sh);

@@ -145,3 +145,42 @@ def test_c5_adjoint_full_size_against_oracle():
     for name, a, b in zip(("psi_bar", "u_bar", "v_bar", "w_bar"), got, ref):
         err = rel_err(synth.interior(a, H), synth.interior(b, H))
         assert err <= 2 * ADJ_TOL, (name, err)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_taped_adjoint_equals_recomputing_adjoint(dtype):
+    """mpdata_adjoint_step_tape on a tape recorded by mpdata_step_tape gives
+    the same adjoint as mpdata_adjoint_step (which records its own tape)."""
+    from paper_1908_06094_b300 import MPDATA, _capi
+    c = synth.random_case(33, 20, 7, seed=17, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
+    m = MPDATA(c.nx, c.ny, c.nz, halo=H, dtype=dtype)
+    d = [to_dev(synth.pad(x, H), dtype) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    rng = np.random.default_rng(3)
+    dy = to_dev(synth.pad(rng.standard_normal(c.psi.shape), H), dtype)
+    tape = torch.empty(_capi.mpdata_tape_bytes(m._ctx), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(d[0])
+    _capi.mpdata_step_tape(m._ctx, d[0].data_ptr(), out.data_ptr(), *[t.data_ptr() for t in d[1:]],
+                           tape.data_ptr())
+    res = []
+    for taped in (True, False):
+        pb = dy.clone()
+        bars = [torch.zeros_like(d[0]) for _ in range(3)]
+        if taped:
+            _capi.mpdata_adjoint_step_tape(m._ctx, tape.data_ptr(), d[0].data_ptr(),
+                                           *[t.data_ptr() for t in d[1:]], pb.data_ptr(),
+                                           *[t.data_ptr() for t in bars])
+        else:
+            _capi.mpdata_adjoint_step(m._ctx, d[0].data_ptr(), *[t.data_ptr() for t in d[1:]],
+                                      pb.data_ptr(), *[t.data_ptr() for t in bars])
+        torch.cuda.synchronize()
+        res.append([pb.double().cpu().numpy()] + [t.double().cpu().numpy() for t in bars])
+    tol = 1e-13 if dtype == torch.float64 else 1e-5
+    for a, b in zip(*res):
+        assert rel_err(a, b) <= tol
+    # the taped step's output equals the ordinary step's
+    ref = torch.empty_like(d[0])
+    m.set_variant(1)
+    m.step_out(d[0], ref, *d[1:])
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    m.close()
