@@ -6,11 +6,13 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <type_traits>
 
 #include "../../include/mpdata.h"
 #include "grid.cuh"
 #include "mass.cuh"
 #include "staged.cuh"
+#include "pseudo64.cuh"
 #include "fused.cuh"
 #include "fused2.cuh"
 #include "adjoint.cuh"
@@ -89,6 +91,26 @@ int halo_launch(mpdata_ctx* c, T* f, int kind) {
   return MPDATA_OK;
 }
 
+// The pseudo-velocity stage: FP64 on the k-marching common-denominator
+// kernel (bound by FP64 instruction count), FP32 on the cell-parallel one.
+template <class T>
+void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W, const T* G,
+                   T* ut, T* vt, T* wt) {
+  const Geo& g = c->g;
+  if constexpr (std::is_same<T, double>::value) {
+    namespace M = mpd::march;
+    const dim3 grid((g.nx + M::TX - 1) / M::TX, (g.ny + M::TY - 1) / M::TY,
+                    (g.nz + M::KC - 1) / M::KC);
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+               M::pseudo_march_kernel<<<grid, dim3(M::TX, M::TY), 0, c->stream>>>(
+                   g, P, U, V, W, G, ut, vt, wt, M::KC));
+  } else {
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+               mpd::staged::pseudo_kernel<T><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
+                   g, P, U, V, W, G, ut, vt, wt));
+  }
+}
+
 // One MPDATA step, staged organisation (one kernel per stage).
 // psi_out may equal psi_in: psi_in is last read (by the limiter) before the
 // final advance writes psi_out.
@@ -116,9 +138,7 @@ int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T*
     T** tset = (cu == setA[0]) ? setB : setA;  // unlimited pseudo-velocities
     T** lset = (tset == setA) ? setB : setA;   // limited ones (next pass's input)
     const bool more = m < c->iord;
-    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-               pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, cu, cv, cw, G, tset[0],
-                                                             tset[1], tset[2]));
+    pseudo_launch<T>(c, cur, cu, cv, cw, G, tset[0], tset[1], tset[2]);
     if (c->nonosc) {
       MPD_LAUNCH(c, MPDATA_STAGE_BETA,
                  beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, cur, tset[0], tset[1],
@@ -344,7 +364,7 @@ int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, out));
   } else {
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, tp.p1));
-    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, pseudo_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, U, V, W, G, tp.ut, tp.vt, tp.wt));
+    pseudo_launch<T>(c, tp.p1, U, V, W, G, tp.ut, tp.vt, tp.wt);
     if (c->nonosc) {
       MPD_LAUNCH(c, MPDATA_STAGE_BETA, beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd));
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(

@@ -2,7 +2,7 @@
 //
 // Two levels with a fixed shape: MASS_BLOCKS blocks each own the interior
 // rows (j,k) r = b, b + MASS_BLOCKS, ...; a thread owns the points
-// i = t, t + 256, ... of each of its block's rows, accumulating them in that
+// i = t, t + 256, ... of each of its block's rows, accumulating them in a
 // fixed order (see MassAcc); the block folds its 256 partials in a fixed
 // tree.  One
 // more block folds the MASS_BLOCKS partials the same way.  The result does
@@ -30,20 +30,24 @@ __device__ __forceinline__ double block_fold(double v, double* sh) {
 // multiply-add per point.  FP32: the FP64 pipe of the B300 issues 2 lanes
 // per SM per clock, so the products are formed exactly as float pairs
 // (hi = a*b, lo = fma(a, b, -hi)) and summed in a float-float accumulator
-// (Knuth's two-sum on the high parts) over runs of at most 16 points, whose
-// total goes into the FP64 sum: the run's error is below 16 * 2^-48 of the
-// run's magnitude, far under the FP64 rounding of the final sum.
+// (Knuth's two-sum on the high parts) over one group of at most
+// MassAcc<float>::R points, whose total then goes into the FP64 sum: the
+// group's error is below R * 2^-48 of its magnitude, far under the FP64
+// rounding of the final sum.  The flush is unconditional code after each
+// group, so the FP64 work is two conversions and two adds per R points.
 struct MassAcc64 {
+  static constexpr int R = 4;
   double s = 0.0;
   __device__ __forceinline__ void add(double a, double b) { s = fma(a, b, s); }
   __device__ __forceinline__ void flush() {}
 };
 struct MassAcc32 {
+  static constexpr int R = 16;
   double s = 0.0;
   float hi = 0.f, lo = 0.f;
-  int n = 0;
   // every operation explicitly rounded: a contraction of hi + a*b into one
-  // fma would break the exactness the two-sum relies on
+  // fma would break the exactness the two-sum relies on.  A padded point
+  // (a = b = 0) leaves hi and lo unchanged.
   __device__ __forceinline__ void add(float a, float b) {
     const float p = __fmul_rn(a, b), e = __fmaf_rn(a, b, -p);  // p + e == a*b exactly
     const float t = __fadd_rn(hi, p);                          // two-sum of hi and p
@@ -51,47 +55,50 @@ struct MassAcc32 {
     const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bv)), __fsub_rn(p, bv));
     hi = t;
     lo = __fadd_rn(lo, __fadd_rn(err, e));
-    if (++n == 16) flush();
   }
   __device__ __forceinline__ void flush() {
     s += (double)hi + (double)lo;
     hi = lo = 0.f;
-    n = 0;
   }
 };
 template <class T> struct MassAcc;
 template <> struct MassAcc<double> { using type = MassAcc64; };
 template <> struct MassAcc<float> { using type = MassAcc32; };
 
+// A block takes the interior rows r0 + q*gridDim.x (q < R) of each group in
+// turn; the row bases are computed once per group and all 2R loads of a
+// point column are issued before its (fixed-order) accumulation.  Rows past
+// the end read as zeros, which add exactly nothing.
 template <class T>
 __global__ void __launch_bounds__(MASS_THREADS)
 mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
                     double* __restrict__ part) {
   __shared__ double sh[MASS_THREADS];
+  using Acc = typename MassAcc<T>::type;
+  constexpr int R = Acc::R;
   const int rows = g.ny * g.nz;
-  typename MassAcc<T>::type acc;
-  // R rows at a time: all their loads are issued before the (fixed-order)
-  // accumulation, so each thread keeps 2R loads in flight
-  constexpr int R = 4;
+  Acc acc;
   for (int r0 = blockIdx.x; r0 < rows; r0 += R * gridDim.x) {
+    int64_t base[R];
+    bool ok[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int r = r0 + q * gridDim.x;
+      ok[q] = r < rows;
+      base[q] = ok[q] ? at(g, 0, r % g.ny, r / g.ny) : 0;
+    }
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
       T a[R], b[R];
 #pragma unroll
       for (int q = 0; q < R; ++q) {
-        const int r = r0 + q * gridDim.x;
-        a[q] = b[q] = T(0);
-        if (r < rows) {
-          const int64_t base = at(g, 0, r % g.ny, r / g.ny);
-          a[q] = psi[base + i];
-          b[q] = G[base + i];
-        }
+        a[q] = ok[q] ? psi[base[q] + i] : T(0);
+        b[q] = ok[q] ? G[base[q] + i] : T(0);
       }
 #pragma unroll
-      for (int q = 0; q < R; ++q)
-        if (r0 + q * gridDim.x < rows) acc.add(a[q], b[q]);
+      for (int q = 0; q < R; ++q) acc.add(a[q], b[q]);
+      acc.flush();
     }
   }
-  acc.flush();
   double b = block_fold(acc.s, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
 }

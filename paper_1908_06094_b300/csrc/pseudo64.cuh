@@ -1,0 +1,208 @@
+// pseudo64.cuh -- FP64 antidiffusive pseudo-velocities, the corrective-pass
+// stage of the MPDATA sequence of Listing 8 (velocity formula of
+// Smolarkiewicz 1984, G-weighted as in Smolarkiewicz & Margolin 1998),
+// organised for the B300's FP64 pipe.
+//
+// The B300 issues FP64 arithmetic at 2 lanes per SM per clock, so this
+// stage, the costliest of the step, is bound by its count of FP64
+// instructions, not by memory.  Two changes against the cell-parallel form
+// (one thread computes the three faces of its cell from scratch, about 140
+// FP64 instructions per cell) bring it to about 90:
+//
+//  1. Each face needs four ratios -- A, two B's and 1/G_face -- and the four
+//     divisions (a reciprocal seed plus a refinement each) dominate.  They
+//     are put over one common denominator:
+//        Ut = [4(|U| Gs - 2U^2) N_A D_1 D_2 - U D_A (S1 N_1 D_2 + S2 N_2 D_1)]
+//             / (4 Gs D_A D_1 D_2)
+//     with Gs = G_L + G_R, N_A/D_A = A, N_1/D_1 = 2B_1, N_2/D_2 = 2B_2 and
+//     S1, S2 the sums of the four cross-direction Courant numbers; in exact
+//     arithmetic this is the same rational function as the per-ratio form.
+//     The denominators are >= epsilon for non-negative psi, so the product
+//     stays in the normal range (it would overflow only for |psi| ~ 1e90).
+//  2. Every psi pair sum S (psi_L + psi_R across a face) is used by five
+//     faces (as D_A of its own face and as one of the four B sums of the
+//     faces beside it), and every pair of Courant numbers by two.  A CTA
+//     owns a TX x TY column tile and marches k: each thread forms the pair
+//     sums of its own cell once per plane, keeps the ones its own faces need
+//     at k-1, k, k+1 in registers, and publishes the ones its neighbours
+//     need (i +- 1, j +- 1) in shared memory; a few warps fill the one-cell
+//     ring around the tile.  Threads past a ragged domain edge take the
+//     periodic image of their cell, so they supply exactly the ring values
+//     the edge cells need.
+#pragma once
+#include "grid.cuh"
+
+namespace mpd {
+namespace march {
+
+constexpr int TX = 32, TY = 8, KC = 8;
+
+// 4x exactly, by raising the exponent: x is a sum of two metric factors G,
+// positive and normal, far from the top of the range.
+__device__ __forceinline__ double times4(double x) {
+  return __hiloint2double(__double2hiint(x) + (2 << 20), __double2loint(x));
+}
+
+// One face from its ingredients (see the header comment); DA = S_own + eps,
+// N1 = S(+1) - S(-1), D1 = S(+1) + S(-1) + eps in the first cross
+// direction, N2, D2 in the second, s1, s2 the cross Courant sums.
+__device__ __forceinline__ double face(double U, double gsum, double pl, double pr, double DA,
+                                       double N1, double D1, double N2, double D2, double s1,
+                                       double s2) {
+  const double g4 = times4(gsum);
+  const double NA = pr - pl;
+  const double t1 = fma(U * -8.0, U, fabs(U) * g4);  // 4 (|U| Gs - 2 U^2)
+  const double D12 = D1 * D2;
+  const double inner = fma(s1 * N1, D2, (s2 * N2) * D1);
+  const double num = fma(-(U * DA), inner, D12 * (t1 * NA));
+  const double den = (g4 * DA) * D12;
+  return num * rcp(den);
+}
+
+// One plane of published sums; row index r+1 holds tile row r (r = -1 ..
+// TY), column index c+1 tile column c (c = -1 .. TX).
+struct Plane {
+  double sx[TY + 2][TX], ex[TY + 2][TX];      // S_x = psi(i) + psi(i+1), S_x + eps
+  double sy[TY][TX + 2], ey[TY][TX + 2];      // S_y = psi(j) + psi(j+1), S_y + eps
+  double sz[TY + 2][TX + 2], ez[TY + 2][TX + 2];  // S_z = psi(k) + psi(k+1), + eps
+  double pvx[TY + 1][TX], pvz[TY + 1][TX];    // V(i)+V(i+1); V(k)+V(k+1)  rows -1 .. TY-1
+  double puy[TY][TX + 1], puz[TY][TX + 1];    // U(j)+U(j+1); U(k)+U(k+1)  cols -1 .. TX-1
+};
+
+// Grid: (ceil(nx/TX), ceil(ny/TY), ceil(nz/kc)); block (TX, TY).  Writes the
+// unlimited pseudo-velocities ut, vt, wt of every interior cell of its tile
+// and k range (wt = 0 on the closed top face).
+__global__ void __launch_bounds__(TX * TY, 2)
+pseudo_march_kernel(Geo g, const double* __restrict__ P, const double* __restrict__ cu,
+                    const double* __restrict__ cv, const double* __restrict__ cw,
+                    const double* __restrict__ G, double* __restrict__ ut,
+                    double* __restrict__ vt, double* __restrict__ wt, int kc) {
+  __shared__ Plane sm[2];
+  const double eps = Eps<double>::v;
+  const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const bool own = i0 + tx < g.nx && j0 + ty < g.ny;
+  const int i = (i0 + tx) % g.nx, j = (j0 + ty) % g.ny;
+  const int64_t o = at(g, i, j, 0), oi = at(g, wrap_up(i, g.nx), j, 0);
+  const int64_t oj = at(g, i, wrap_up(j, g.ny), 0);
+
+  // ring task: rows j0-1 and j0+TY (threads 0 .. 2TX-1), columns i0-1 and
+  // i0+TX (the next 2TY threads)
+  int rkind = 0, rs = 0, rc = 0;
+  int64_t ro = 0, rn = 0;
+  if (t < 2 * TX) {
+    rkind = 1;
+    rc = t % TX;
+    const bool up = t >= TX;
+    const int ri = (i0 + rc) % g.nx;
+    const int rj = up ? (j0 + TY) % g.ny : (j0 + g.ny - 1) % g.ny;
+    rs = up ? TY + 1 : 0;
+    ro = at(g, ri, rj, 0);
+    rn = at(g, wrap_up(ri, g.nx), rj, 0);
+  } else if (t < 2 * TX + 2 * TY) {
+    rkind = 2;
+    rs = (t - 2 * TX) % TY;
+    const bool up = t >= 2 * TX + TY;
+    const int rj = (j0 + rs) % g.ny;
+    const int ri = up ? (i0 + TX) % g.nx : (i0 + g.nx - 1) % g.nx;
+    rc = up ? TX + 1 : 0;
+    ro = at(g, ri, rj, 0);
+    rn = at(g, ri, wrap_up(rj, g.ny), 0);
+  }
+
+  const int64_t pxy = g.pxy;
+  const int k0 = blockIdx.z * kc, k1 = min(k0 + kc, g.nz);
+  // register queues: psi and pair sums at k (and k-1), W pairs at k-1/2
+  double pc = P[o + k0 * pxy], pi = P[oi + k0 * pxy], pj = P[oj + k0 * pxy];
+  double sx = pc + pi, exx = sx + eps, sy = pc + pj, eyy = sy + eps;
+  const int64_t ob = (k0 > 0 ? k0 - 1 : 0) * pxy;
+  double sxm = P[o + ob] + P[oi + ob], sym = P[o + ob] + P[oj + ob];
+  double pwxm = 0.0, pwym = 0.0;
+  if (k0 > 0) {
+    pwxm = cw[o + ob] + cw[oi + ob];
+    pwym = cw[o + ob] + cw[oj + ob];
+  }
+
+  for (int k = k0; k < k1; ++k) {
+    const int64_t ok = k * pxy;
+    const bool top = k == g.nz - 1;
+    const int64_t on = top ? ok : ok + pxy;  // k+1, clamped (edge copy of psi)
+    const double pcn = P[o + on], pin = P[oi + on], pjn = P[oj + on];
+    const double sxn = pcn + pin, exn = sxn + eps, syn = pcn + pjn, eyn = syn + eps;
+    const double uc = cu[o + ok], vc = cv[o + ok], wc = cw[o + ok];
+    const double pvx = vc + cv[oi + ok], puy = uc + cu[oj + ok];
+    double sz = 0.0, ez = 0.0, puz = 0.0, pvz = 0.0, pwx = 0.0, pwy = 0.0;
+    if (!top) {  // the face k+1/2 is open
+      sz = pc + pcn;
+      ez = sz + eps;
+      puz = uc + cu[o + on];
+      pvz = vc + cv[o + on];
+      pwx = wc + cw[oi + ok];
+      pwy = wc + cw[oj + ok];
+    }
+    Plane& s = sm[k & 1];
+    s.sx[ty + 1][tx] = sx;
+    s.ex[ty + 1][tx] = exx;
+    s.sy[ty][tx + 1] = sy;
+    s.ey[ty][tx + 1] = eyy;
+    s.sz[ty + 1][tx + 1] = sz;
+    s.ez[ty + 1][tx + 1] = ez;
+    s.pvx[ty + 1][tx] = pvx;
+    s.pvz[ty + 1][tx] = pvz;
+    s.puy[ty][tx + 1] = puy;
+    s.puz[ty][tx + 1] = puz;
+    if (rkind == 1) {  // row ring: S_x, S_z (+eps above), V pairs below
+      const double a = P[ro + ok];
+      const double rsx = a + P[rn + ok];
+      const double rsz = top ? 0.0 : a + P[ro + on];
+      s.sx[rs][rc] = rsx;
+      s.sz[rs][rc + 1] = rsz;
+      if (rs == 0) {
+        const double v0 = cv[ro + ok];
+        s.pvx[0][rc] = v0 + cv[rn + ok];
+        s.pvz[0][rc] = top ? 0.0 : v0 + cv[ro + on];
+      } else {
+        s.ex[rs][rc] = rsx + eps;
+        s.ez[rs][rc + 1] = rsz + eps;
+      }
+    } else if (rkind == 2) {  // column ring: S_y, S_z (+eps right), U pairs left
+      const double a = P[ro + ok];
+      const double rsy = a + P[rn + ok];
+      const double rsz = top ? 0.0 : a + P[ro + on];
+      s.sy[rs][rc] = rsy;
+      s.sz[rs + 1][rc] = rsz;
+      if (rc == 0) {
+        const double u0 = cu[ro + ok];
+        s.puy[rs][0] = u0 + cu[rn + ok];
+        s.puz[rs][0] = top ? 0.0 : u0 + cu[ro + on];
+      } else {
+        s.ey[rs][rc] = rsy + eps;
+        s.ez[rs + 1][rc] = rsz + eps;
+      }
+    }
+    __syncthreads();
+    if (own) {
+      ut[o + ok] = face(uc, G[o + ok] + G[oi + ok], pc, pi, exx,
+                        s.sx[ty + 2][tx] - s.sx[ty][tx], s.ex[ty + 2][tx] + s.sx[ty][tx],
+                        sxn - sxm, exn + sxm, s.pvx[ty + 1][tx] + s.pvx[ty][tx], pwx + pwxm);
+      vt[o + ok] = face(vc, G[o + ok] + G[oj + ok], pc, pj, eyy,
+                        s.sy[ty][tx + 2] - s.sy[ty][tx], s.ey[ty][tx + 2] + s.sy[ty][tx],
+                        syn - sym, eyn + sym, s.puy[ty][tx + 1] + s.puy[ty][tx], pwy + pwym);
+      wt[o + ok] = top ? 0.0
+                       : face(wc, G[o + ok] + G[o + on], pc, pcn, ez,
+                              s.sz[ty + 1][tx + 2] - s.sz[ty + 1][tx],
+                              s.ez[ty + 1][tx + 2] + s.sz[ty + 1][tx],
+                              s.sz[ty + 2][tx + 1] - s.sz[ty][tx + 1],
+                              s.ez[ty + 2][tx + 1] + s.sz[ty][tx + 1],
+                              s.puz[ty][tx + 1] + s.puz[ty][tx],
+                              s.pvz[ty + 1][tx] + s.pvz[ty][tx]);
+    }
+    sxm = sx; sx = sxn; exx = exn;
+    sym = sy; sy = syn; eyy = eyn;
+    pwxm = pwx; pwym = pwy;
+    pc = pcn; pi = pin; pj = pjn;
+  }
+}
+
+}  // namespace march
+}  // namespace mpd
