@@ -150,8 +150,9 @@ MPDATA_API int mpdata_adjoint_step(mpdata_ctx *c, const void *psi_n, const void 
                                    void *u_bar, void *v_bar, void *w_bar);
 
 /* Taped steps: the adjoint without forward recomputation.
- * mpdata_tape_bytes gives the size of one step's tape (9 fields: psi1, the
- * unlimited and limited pseudo-velocities, the two betas).
+ * mpdata_tape_bytes gives the size of one step's tape (11 fields: psi1, the
+ * unlimited and limited pseudo-velocities, the two betas and the two
+ * reciprocals 1/(in+eps), 1/(out+eps) of the limiter's flux sums).
  * mpdata_step_tape runs one forward step psi_in -> psi_out (distinct, halo
  * filled) with the staged kernels and keeps its intermediates in the
  * caller-owned DEVICE buffer tape (16-byte aligned).

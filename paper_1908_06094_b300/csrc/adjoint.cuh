@@ -4,7 +4,8 @@
 // The forward intermediates of the step (psi1, the pseudo-velocities, the
 // betas and the limited velocities) come from a tape recorded by the staged
 // forward kernels; the kernels here run the forward stages backwards, one
-// thread per interior cell.  The advance, limiter and beta reverses scatter:
+// thread per interior cell (the pseudo-velocity weights: k-marching tiles).
+// The advance, limiter and beta reverses scatter:
 // each thread adds the adjoint of what its cell computed into every value
 // that computation read, with atomic adds.  The pseudo-velocity reverse, the
 // heaviest, is a gather in two passes without atomics (rev_pw, rev_pg).
@@ -19,6 +20,7 @@
 #pragma once
 #include "grid.cuh"
 #include "staged.cuh"
+#include "march.cuh"
 
 namespace mpd {
 namespace adj {
@@ -27,15 +29,6 @@ using staged::Cell;
 using staged::cell_of;
 
 template <class T> __device__ __forceinline__ void aadd(T* p, T v) { atomicAdd(p, v); }
-
-// Reverse of F(L,R,C) = max(C,0) L + min(C,0) R for the adjoint fb.
-template <class T>
-__device__ __forceinline__ void rev_donor(T fb, T L, T R, T C, T* Lb, T* Rb, T* Cb) {
-  const bool ge = ge0(C), le = le0(C);
-  aadd(Lb, fb * (ge ? C : T(0)));
-  aadd(Rb, fb * (le ? C : T(0)));
-  aadd(Cb, fb * ((ge ? L : T(0)) + (le ? R : T(0))));
-}
 
 // Reverse of out = P - (1/G) sum_d [F(P_c, P_c+d, C_c) - F(P_c-d, P_c, C_c-d)]
 // for the adjoint ob of out.
@@ -53,12 +46,18 @@ __global__ void rev_advance_kernel(Geo g, const T* __restrict__ P, const T* __re
   const int64_t yp = at(g, c.i, wrap_up(c.j, g.ny), c.k), ym = at(g, c.i, wrap_dn(c.j, g.ny), c.k);
   // the own cell's share of all six face terms is added once
   T own = a;
+  // dF/dL = [C]+-indicator * C, dF/dR likewise, dF/dC = L or R: only the
+  // upwind value has a non-zero partial (both are 0 * fb when C == 0)
   auto face = [&](T fb, T L, T R, T C, bool own_is_left, int64_t other, T* Cb) {
     const bool ge = ge0(C), le = le0(C);
-    const T dl = fb * (ge ? C : T(0)), dr = fb * (le ? C : T(0));
-    if (own_is_left) { own += dl; aadd(&Pb[other], dr); }
-    else { own += dr; aadd(&Pb[other], dl); }
-    aadd(Cb, fb * ((ge ? L : T(0)) + (le ? R : T(0))));
+    if (ge && le) {
+      aadd(Cb, fb * (L + R));
+      return;
+    }
+    const T d = fb * C;
+    if (ge == own_is_left) own += d;
+    else aadd(&Pb[other], d);
+    aadd(Cb, fb * (ge ? L : R));
   };
   face(s, P[q], P[xp], cu[q], true, xp, &ub[q]);
   face(-s, P[xm], P[q], cu[xm], false, xm, &ub[xm]);
@@ -118,17 +117,29 @@ __global__ void rev_limit_kernel(Geo g, const T* __restrict__ ut, const T* __res
   }
 }
 
+// Reverse of the beta stage from the tape (beta-up/down and the
+// reciprocals ri = 1/(in+eps), ro = 1/(out+eps) of the forward):
+//   beta_up = (hi - psi) G ri,  beta_dn = (psi - lo) G ro,
+// in = sum of incoming antidiffusive fluxes, out = outgoing.  A cell whose
+// two beta adjoints are zero (its betas never won the limiter's min)
+// contributes exactly nothing and returns at once.  The adjoint of a face
+// flux F from this cell's in/out is outb (F > 0) or -inb (F < 0) on its
+// "+" faces, inb or -outb on its "-" faces, and both (outb - inb) when F is
+// zero; it then goes to the upwind psi1 value and the face's velocity.
 template <class T>
 __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict__ P,
                                 const T* __restrict__ ut, const T* __restrict__ vt,
                                 const T* __restrict__ wt, const T* __restrict__ G,
+                                const T* __restrict__ bu, const T* __restrict__ bd,
+                                const T* __restrict__ rin, const T* __restrict__ rout,
                                 const T* __restrict__ bub, const T* __restrict__ bdb, T* P0b,
                                 T* Pb, T* utb, T* vtb, T* wtb) {
   Cell c = cell_of(g);
   if (!c.ok) return;
-  const T eps = Eps<T>::v;
   const int i = c.i, j = c.j, k = c.k;
   const int64_t q = at(g, i, j, k);
+  const T ab = bub[q], db = bdb[q];
+  if (ge0(ab) && le0(ab) && ge0(db) && le0(db)) return;
   const int64_t nb[6] = {at(g, wrap_dn(i, g.nx), j, k), at(g, wrap_up(i, g.nx), j, k),
                          at(g, i, wrap_dn(j, g.ny), k), at(g, i, wrap_up(j, g.ny), k),
                          at(g, i, j, clampk(k - 1, g.nz)), at(g, i, j, clampk(k + 1, g.nz))};
@@ -144,48 +155,49 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
     if (!leq(lo, P0[n])) { lo = P0[n]; lop = &P0b[n]; }
     if (!leq(lo, P[n])) { lo = P[n]; lop = &Pb[n]; }
   }
+  const T gc = G[q], ri = rin[q], ro = rout[q];
+  const T x = ab * gc * ri, y = db * gc * ro;  // d beta_up/d hi, -d beta_dn/d lo
+  aadd(hip, x);
+  aadd(lop, -y);
+  aadd(&Pb[q], y - x);
+  const T inb = -ab * bu[q] * ri, outb = -db * bd[q] * ro;
+  const T dio = outb - inb;
+  const T pc = P[q];
   const T* vel[3] = {ut, vt, wt};
   T* velb[3] = {utb, vtb, wtb};
-  T fp[3], fm[3];
-  bool hp[3], hm[3];
-  for (int d = 0; d < 3; ++d) {
-    hp[d] = !(d == 2 && k == g.nz - 1);
-    hm[d] = !(d == 2 && k == 0);
-    fp[d] = hp[d] ? donor(P[q], P[nb[2 * d + 1]], vel[d][q]) : T(0);
-    fm[d] = hm[d] ? donor(P[nb[2 * d]], P[q], vel[d][nb[2 * d]]) : T(0);
-  }
-  T in = T(0), out = T(0);
-  for (int d = 0; d < 3; ++d) {
-    in += (ge0(fm[d]) ? fm[d] : T(0)) - (le0(fp[d]) ? fp[d] : T(0));
-    out += (ge0(fp[d]) ? fp[d] : T(0)) - (le0(fm[d]) ? fm[d] : T(0));
-  }
-  const T gc = G[q];
-  const T rin = rcp(in + eps), rout = rcp(out + eps);
-  const T bu = (hi - P[q]) * gc * rin, bd = (P[q] - lo) * gc * rout;
-  const T ab = bub[q], db = bdb[q];
-  aadd(hip, ab * gc * rin);
-  aadd(lop, -db * gc * rout);
-  aadd(&Pb[q], -ab * gc * rin + db * gc * rout);
-  const T inb = -ab * bu * rin, outb = -db * bd * rout;
-  for (int d = 0; d < 3; ++d) {
-    const T fpb = (le0(fp[d]) ? -inb : T(0)) + (ge0(fp[d]) ? outb : T(0));
-    const T fmb = (ge0(fm[d]) ? inb : T(0)) - (le0(fm[d]) ? outb : T(0));
-    if (hp[d]) {
-      const int64_t r = nb[2 * d + 1];
-      rev_donor(fpb, P[q], P[r], vel[d][q], &Pb[q], &Pb[r], &velb[d][q]);
+  // reverse of F = donor(L, R, C) for the adjoint fb: only the upwind value
+  // has a non-zero partial (both are 0 * fb when C == 0)
+  auto rdonor = [&](T fb, T L, T R, T C, T* Lb, T* Rb, T* Cb) {
+    const bool ge = ge0(C), le = le0(C);
+    if (ge && le) {
+      aadd(Cb, fb * (L + R));
+      return;
     }
-    if (hm[d]) {
+    aadd(ge ? Lb : Rb, fb * C);
+    aadd(Cb, fb * (ge ? L : R));
+  };
+  for (int d = 0; d < 3; ++d) {
+    if (!(d == 2 && k == g.nz - 1)) {
+      const int64_t r = nb[2 * d + 1];
+      const T C = vel[d][q], pr = P[r];
+      const T fp = donor(pc, pr, C);
+      const T fpb = ge0(fp) ? (le0(fp) ? dio : outb) : -inb;
+      rdonor(fpb, pc, pr, C, &Pb[q], &Pb[r], &velb[d][q]);
+    }
+    if (!(d == 2 && k == 0)) {
       const int64_t l = nb[2 * d];
-      rev_donor(fmb, P[l], P[q], vel[d][l], &Pb[l], &Pb[q], &velb[d][l]);
+      const T C = vel[d][l], pl = P[l];
+      const T fm = donor(pl, pc, C);
+      const T fmb = ge0(fm) ? (le0(fm) ? -dio : inb) : -outb;
+      rdonor(fmb, pl, pc, C, &Pb[l], &Pb[q], &velb[d][l]);
     }
   }
 }
 
-
 // ---------------------------------------------------------------------------
 // Pseudo-velocity reverse in gather form (no atomics).
 //
-// Pass 1 (rev_pw_kernel), per cell and its three "+" faces f, from the
+// Pass 1 (RevPseudo), per cell and its three "+" faces f, from the
 // adjoint ub_f of the pseudo-velocity: adds dJ/dU_f (own face) and stores
 // eight weights per face, the adjoint routed to each stencil point:
 //   wl, wr    to psi1 at L and R through A,
@@ -199,78 +211,57 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
 // weights of the faces whose clamped index lands on them.
 enum { kWL = 0, kWR, kW1P, kW1M, kW2P, kW2M, kC1, kC2, kNW };
 
+// sign(U) with sign(0) = 0
 template <class T>
-__global__ void rev_pw_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
-                              const T* __restrict__ cv, const T* __restrict__ cw,
-                              const T* __restrict__ G, const T* __restrict__ utb,
-                              const T* __restrict__ vtb, const T* __restrict__ wtb,
-                              T* __restrict__ wts, T* ub, T* vb, T* wb) {
-  Cell c = cell_of(g);
-  if (!c.ok) return;
-  const T eps = Eps<T>::v;
-  const int i = c.i, j = c.j, k = c.k;
-  const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
-  const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
-  const int kp = clampk(k + 1, g.nz), km = clampk(k - 1, g.nz);
-  auto A_ = [&](int a, int b, int d) { return at(g, a, b, d); };
-  auto wfv = [&](int a, int b, int d) -> T {
-    return (d < 0 || d >= g.nz - 1) ? T(0) : cw[at(g, a, b, d)];
-  };
-  const int64_t q = A_(i, j, k);
-  const int64_t F = g.total;  // one weight field
-  // fam: 0 x, 1 y, 2 z; fields [fam][kNW]
-  auto put = [&](int fam, int w, T v) { wts[((int64_t)fam * kNW + w) * F + q] = v; };
-  auto face = [&](int fam, T ubv, T U, T Gf, T pl, T pr, T s1pv, T s1mv, T s2pv, T s2mv,
-                  T C1sum, T C2sum, T* Ub) {
-    const T rd = rcp(pr + pl + eps);
-    const T A = (pr - pl) * rd;
-    const T rd1 = rcp(s1pv + s1mv + eps), rd2 = rcp(s2pv + s2mv + eps);
-    const T B1 = T(0.5) * (s1pv - s1mv) * rd1, B2 = T(0.5) * (s2pv - s2mv) * rd2;
-    const T C1 = T(0.25) * C1sum, C2 = T(0.25) * C2sum;
-    const T rG = rcp(Gf);
-    const T Dd = absv(U) - U * U * rG;
-    const T X = C1 * B1 + C2 * B2;
-    const T sg = (ge0(U) && le0(U)) ? T(0) : (nonneg(U) ? T(1) : T(-1));
-    *Ub += ubv * (sg * A - T(2) * U * rG * A - X * rG);
-    const T Ab = ubv * Dd;
-    const T B1b = ubv * (-U * C1 * rG), B2b = ubv * (-U * C2 * rG);
-    put(fam, kWL, Ab * (T(-1) - A) * rd);
-    put(fam, kWR, Ab * (T(1) - A) * rd);
-    put(fam, kW1P, B1b * (T(0.5) - B1) * rd1);
-    put(fam, kW1M, B1b * (T(-0.5) - B1) * rd1);
-    put(fam, kW2P, B2b * (T(0.5) - B2) * rd2);
-    put(fam, kW2M, B2b * (T(-0.5) - B2) * rd2);
-    put(fam, kC1, T(0.25) * ubv * (-U * B1 * rG));
-    put(fam, kC2, T(0.25) * ubv * (-U * B2 * rG));
-  };
-  auto p = [&](int a, int b, int d) { return P[A_(a, b, d)]; };
-  {  // x face: cross directions y (V) and z (W)
-    const int64_t R = A_(ip, j, k);
-    face(0, utb[q], cu[q], T(0.5) * (G[q] + G[R]), p(i, j, k), p(ip, j, k),
-         p(ip, jp, k) + p(i, jp, k), p(ip, jm, k) + p(i, jm, k),
-         p(ip, j, kp) + p(i, j, kp), p(ip, j, km) + p(i, j, km),
-         cv[q] + cv[R] + cv[A_(i, jm, k)] + cv[A_(ip, jm, k)],
-         wfv(i, j, k) + wfv(ip, j, k) + wfv(i, j, k - 1) + wfv(ip, j, k - 1), &ub[q]);
-  }
-  {  // y face: cross directions x (U) and z (W)
-    const int64_t R = A_(i, jp, k);
-    face(1, vtb[q], cv[q], T(0.5) * (G[q] + G[R]), p(i, j, k), p(i, jp, k),
-         p(ip, jp, k) + p(ip, j, k), p(im, jp, k) + p(im, j, k),
-         p(i, jp, kp) + p(i, j, kp), p(i, jp, km) + p(i, j, km),
-         cu[q] + cu[R] + cu[A_(im, j, k)] + cu[A_(im, jp, k)],
-         wfv(i, j, k) + wfv(i, jp, k) + wfv(i, j, k - 1) + wfv(i, jp, k - 1), &vb[q]);
-  }
-  if (k < g.nz - 1) {  // z face: cross directions x (U) and y (V)
-    const int64_t R = q + g.pxy;
-    face(2, wtb[q], cw[q], T(0.5) * (G[q] + G[R]), p(i, j, k), p(i, j, k + 1),
-         p(ip, j, k + 1) + p(ip, j, k), p(im, j, k + 1) + p(im, j, k),
-         p(i, jp, k + 1) + p(i, jp, k), p(i, jm, k + 1) + p(i, jm, k),
-         cu[q] + cu[R] + cu[A_(im, j, k)] + cu[A_(im, j, k + 1)],
-         cv[q] + cv[R] + cv[A_(i, jm, k)] + cv[A_(i, jm, k + 1)], &wb[q]);
-  } else {
-    for (int w = 0; w < kNW; ++w) put(2, w, T(0));
-  }
+__device__ __forceinline__ T sgn0(T U) {
+  return (ge0(U) && le0(U)) ? T(0) : (nonneg(U) ? T(1) : T(-1));
 }
+
+// Pass 1 as the face operation of march::march_kernel, which supplies each
+// face's ingredients from pair sums shared across the tile.  With
+// B1' = N1/D1 = 2 B1, B2' = 2 B2, qh = U/(G_L+G_R) (so U/G_face = 2 qh) and
+// X8 = s1 B1' + s2 B2' (8x the cross term Vbar B1 + Wbar B2):
+//   dUt/dU = A (sign U - 4 qh) - X8 rG2 / 4 with rG2 = 1/(G_L+G_R);
+//   wl, wr = -(ub Dd/DA) (1 + A), (ub Dd/DA) (1 - A), Dd = |U| - U^2/G_face;
+//   w1p, w1m = t1 (1 - B1'), -t1 (1 + B1') with t1 = m4 s1 / D1,
+//            m4 = -ub qh / 4 (w2p, w2m the same with s2, D2, B2');
+//   c1, c2 = m4 B1', m4 B2'.
+template <class T>
+struct RevPseudo {
+  const T *utb, *vtb, *wtb;
+  T* wts;
+  int64_t F;  // one weight field
+  T *ub, *vb, *wb;
+  __device__ __forceinline__ void put(int fam, int w, int64_t q, T v) const {
+    wts[((int64_t)fam * kNW + w) * F + q] = v;
+  }
+  __device__ __forceinline__ void face(int fam, int64_t q, const march::FaceIn<T>& f) const {
+    const T ubv = (fam == 0 ? utb : fam == 1 ? vtb : wtb)[q];
+    const T rd = rcp(f.DA), rd1 = rcp(f.D1), rd2 = rcp(f.D2), rG2 = rcp(f.gsum);
+    const T A = (f.pr - f.pl) * rd, B1 = f.N1 * rd1, B2 = f.N2 * rd2;
+    const T qh = f.U * rG2;
+    const T Dd = fma_rn(f.U * T(-2), qh, absv(f.U));
+    const T X8 = fma_rn(f.s2, B2, f.s1 * B1);
+    const T dU = fma_rn(X8 * rG2, T(-0.25), A * fma_rn(qh, T(-4), sgn0(f.U)));
+    T* Ub = fam == 0 ? ub : fam == 1 ? vb : wb;
+    Ub[q] = fma_rn(ubv, dU, Ub[q]);
+    const T Abr = ubv * Dd * rd;
+    put(fam, kWL, q, fma_rn(-Abr, A, -Abr));
+    put(fam, kWR, q, fma_rn(-Abr, A, Abr));
+    const T m4 = ubv * qh * T(-0.25);
+    const T t1 = m4 * f.s1 * rd1, t2 = m4 * f.s2 * rd2;
+    put(fam, kW1P, q, fma_rn(-t1, B1, t1));
+    put(fam, kW1M, q, fma_rn(-t1, B1, -t1));
+    put(fam, kW2P, q, fma_rn(-t2, B2, t2));
+    put(fam, kW2M, q, fma_rn(-t2, B2, -t2));
+    put(fam, kC1, q, m4 * B1);
+    put(fam, kC2, q, m4 * B2);
+  }
+  __device__ __forceinline__ void closed(int64_t q) const {
+#pragma unroll
+    for (int w = 0; w < kNW; ++w) put(2, w, q, T(0));
+  }
+};
 
 template <class T>
 __global__ void rev_pg_kernel(Geo g, const T* __restrict__ wts, T* Pb, T* ub, T* vb, T* wb) {

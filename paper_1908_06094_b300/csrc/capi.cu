@@ -12,7 +12,7 @@
 #include "grid.cuh"
 #include "mass.cuh"
 #include "staged.cuh"
-#include "pseudo64.cuh"
+#include "march.cuh"
 #include "fused.cuh"
 #include "fused2.cuh"
 #include "adjoint.cuh"
@@ -99,11 +99,10 @@ void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W
   const Geo& g = c->g;
   if constexpr (std::is_same<T, double>::value) {
     namespace M = mpd::march;
-    const dim3 grid((g.nx + M::TX - 1) / M::TX, (g.ny + M::TY - 1) / M::TY,
-                    (g.nz + M::KC - 1) / M::KC);
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-               M::pseudo_march_kernel<<<grid, dim3(M::TX, M::TY), 0, c->stream>>>(
-                   g, P, U, V, W, G, ut, vt, wt, M::KC));
+               (M::march_kernel<double, M::PseudoMerged><<<M::march_grid(g), dim3(M::TX, M::TY),
+                                                           0, c->stream>>>(
+                   g, P, U, V, W, G, M::PseudoMerged{ut, vt, wt}, M::KC)));
   } else {
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                mpd::staged::pseudo_kernel<T><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
@@ -142,7 +141,8 @@ int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T*
     if (c->nonosc) {
       MPD_LAUNCH(c, MPDATA_STAGE_BETA,
                  beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, cur, tset[0], tset[1],
-                                                             tset[2], G, (T*)c->bu, (T*)c->bd));
+                                                             tset[2], G, (T*)c->bu, (T*)c->bd,
+                                                             nullptr, nullptr));
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
                  limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
                      g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
@@ -305,7 +305,8 @@ int mass_launch(mpdata_ctx* c, const T* psi, const T* G, double* out) {
 
 // ------------------------------------------------------------- adjoint --
 
-constexpr int kTapeFields = 9;   // psi1, Ut, Vt, Wt, beta-up, beta-down, Ul, Vl, Wl
+// psi1, Ut, Vt, Wt, beta-up, beta-down, 1/(in+eps), 1/(out+eps), Ul, Vl, Wl
+constexpr int kTapeFields = 11;
 constexpr int kAdjFields = 10 + 24 + kTapeFields + 1;  // adjoints, weights, tape, psi^(n+1)
 
 size_t field_pad(const mpdata_ctx* c) {
@@ -325,7 +326,7 @@ int adjoint_scratch(mpdata_ctx* c) {
 
 template <class T>
 struct Tape {
-  T *p1, *ut, *vt, *wt, *bu, *bd, *ul, *vl, *wl;
+  T *p1, *ut, *vt, *wt, *bu, *bd, *ri, *ro, *ul, *vl, *wl;
 };
 
 template <class T>
@@ -333,7 +334,8 @@ Tape<T> tape_view(const mpdata_ctx* c, void* base) {
   char* p = (char*)base;
   const size_t f = field_pad(c);
   Tape<T> t;
-  T** slots[kTapeFields] = {&t.p1, &t.ut, &t.vt, &t.wt, &t.bu, &t.bd, &t.ul, &t.vl, &t.wl};
+  T** slots[kTapeFields] = {&t.p1, &t.ut, &t.vt, &t.wt, &t.bu, &t.bd,
+                            &t.ri, &t.ro, &t.ul, &t.vl, &t.wl};
   for (int q = 0; q < kTapeFields; ++q) *slots[q] = (T*)(p + q * f);
   return t;
 }
@@ -366,7 +368,7 @@ int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, tp.p1));
     pseudo_launch<T>(c, tp.p1, U, V, W, G, tp.ut, tp.vt, tp.wt);
     if (c->nonosc) {
-      MPD_LAUNCH(c, MPDATA_STAGE_BETA, beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd));
+      MPD_LAUNCH(c, MPDATA_STAGE_BETA, beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd, tp.ri, tp.ro));
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
                                             g, tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, fx, fy, fz, tp.ul, tp.vl, tp.wl));
     } else {
@@ -415,11 +417,16 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
                                             g, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, ulb, vlb, wlb,
                                             utb, vtb, wtb, bub, bdb));
       MPD_LAUNCH(c, MPDATA_STAGE_BETA, rev_beta_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                           g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, bub, bdb, p0b,
-                                           p1b, utb, vtb, wtb));
+                                           g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd,
+                                           tp.ri, tp.ro, bub, bdb, p0b, p1b, utb, vtb, wtb));
     }
-    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, rev_pw_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                           g, tp.p1, U, V, W, G, utb, vtb, wtb, wts, ub, vb, wb));
+    {
+      namespace M = mpd::march;
+      const RevPseudo<T> op{utb, vtb, wtb, wts, g.total, ub, vb, wb};
+      MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+                 (M::march_kernel<T, RevPseudo<T>><<<M::march_grid(g), dim3(M::TX, M::TY), 0, s>>>(
+                     g, tp.p1, U, V, W, G, op, M::KC)));
+    }
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(
                                            g, wts, p1b, ub, vb, wb));
     MPD_LAUNCH(c, MPDATA_STAGE_DONOR, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(

@@ -54,15 +54,24 @@ __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fm
 __device__ __forceinline__ bool nonneg(double x) { return __double2hiint(x) >= 0; }
 __device__ __forceinline__ bool nonneg(float x) { return __float_as_int(x) >= 0; }
 
+// The bit pattern of a double through an opaque move, so that integer tests
+// on it stay integer: a plain bit cast lets the compiler turn a test such as
+// (bits & 0x7fff...) == 0 back into an FP64 compare.
+__device__ __forceinline__ long long dbits(double x) {
+  long long b;
+  asm("mov.b64 %0, %1;" : "=l"(b) : "d"(x));
+  return b;
+}
+
 __device__ __forceinline__ long long okey(double x);
 __device__ __forceinline__ long long okey0(double x);
 // x >= 0 and x <= 0 with IEEE semantics (both hold for +0 and -0).
 __device__ __forceinline__ bool ge0(double x) {
-  const long long b = __double_as_longlong(x);
+  const long long b = dbits(x);
   return b >= 0 || (b & 0x7fffffffffffffffLL) == 0;
 }
 __device__ __forceinline__ bool le0(double x) {
-  const long long b = __double_as_longlong(x);
+  const long long b = dbits(x);
   return b < 0 || b == 0;
 }
 __device__ __forceinline__ bool ge0(float x) { return x >= 0.0f; }
@@ -97,13 +106,13 @@ __device__ __forceinline__ T donor(T L, T R, T C) {
 // each double to an int64 key with the same order (sign-magnitude ->
 // two's complement: flip the magnitude bits of negatives) and compares keys.
 __device__ __forceinline__ long long okey(double x) {
-  const long long b = __double_as_longlong(x);
+  const long long b = dbits(x);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);  // -0 sorts just below +0
 }
 // The same order with -0 and +0 equal (IEEE ties), for branch decisions
 // that must match IEEE comparisons exactly (the adjoint's tie rules).
 __device__ __forceinline__ long long okey0(double x) {
-  const long long b = __double_as_longlong(x);
+  const long long b = dbits(x);
   return b >= 0 ? b : -(b & 0x7fffffffffffffffLL);
 }
 __device__ __forceinline__ double kdecode(long long k) {
@@ -140,7 +149,7 @@ __device__ __forceinline__ void bounds(const float (&v)[N], float& hi, float& lo
 
 // min of non-negative values (limiter factors): raw bit patterns order them.
 __device__ __forceinline__ double nmin(double a, double b) {
-  return __double_as_longlong(a) <= __double_as_longlong(b) ? a : b;
+  return dbits(a) <= dbits(b) ? a : b;
 }
 __device__ __forceinline__ float nmin(float a, float b) { return fminf(a, b); }
 

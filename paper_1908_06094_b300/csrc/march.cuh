@@ -1,13 +1,15 @@
-// pseudo64.cuh -- FP64 antidiffusive pseudo-velocities, the corrective-pass
+// march.cuh -- the antidiffusive pseudo-velocity faces, the corrective-pass
 // stage of the MPDATA sequence of Listing 8 (velocity formula of
 // Smolarkiewicz 1984, G-weighted as in Smolarkiewicz & Margolin 1998),
-// organised for the B300's FP64 pipe.
+// organised for the B300's FP64 pipe: a k-marching tile kernel that hands
+// every face's ingredients to an operation (the forward velocity here, the
+// reverse-mode weights in adjoint.cuh).
 //
 // The B300 issues FP64 arithmetic at 2 lanes per SM per clock, so this
 // stage, the costliest of the step, is bound by its count of FP64
 // instructions, not by memory.  Two changes against the cell-parallel form
 // (one thread computes the three faces of its cell from scratch, about 140
-// FP64 instructions per cell) bring it to about 90:
+// FP64 instructions per cell) bring the FP64 forward to about 90:
 //
 //  1. Each face needs four ratios -- A, two B's and 1/G_face -- and the four
 //     divisions (a reciprocal seed plus a refinement each) dominate.  They
@@ -43,42 +45,58 @@ __device__ __forceinline__ double times4(double x) {
   return __hiloint2double(__double2hiint(x) + (2 << 20), __double2loint(x));
 }
 
-// One face from its ingredients (see the header comment); DA = S_own + eps,
-// N1 = S(+1) - S(-1), D1 = S(+1) + S(-1) + eps in the first cross
-// direction, N2, D2 in the second, s1, s2 the cross Courant sums.
-__device__ __forceinline__ double face(double U, double gsum, double pl, double pr, double DA,
-                                       double N1, double D1, double N2, double D2, double s1,
-                                       double s2) {
-  const double g4 = times4(gsum);
-  const double NA = pr - pl;
-  const double t1 = fma(U * -8.0, U, fabs(U) * g4);  // 4 (|U| Gs - 2 U^2)
-  const double D12 = D1 * D2;
-  const double inner = fma(s1 * N1, D2, (s2 * N2) * D1);
-  const double num = fma(-(U * DA), inner, D12 * (t1 * NA));
-  const double den = (g4 * DA) * D12;
-  return num * rcp(den);
-}
+// The ingredients of one face: U its Courant number, gsum = G_L + G_R,
+// pl, pr psi1 left and right, DA = S_own + eps, N1 = S(+1) - S(-1) and
+// D1 = S(+1) + S(-1) + eps in the first cross direction, N2, D2 in the
+// second, s1, s2 the sums of the four cross-direction Courant numbers
+// (first, second).  N1/D1 = 2 B1 and N2/D2 = 2 B2.
+template <class T>
+struct FaceIn {
+  T U, gsum, pl, pr, DA, N1, D1, N2, D2, s1, s2;
+};
+
+// Forward, FP64: the common-denominator form (see the header comment).
+struct PseudoMerged {
+  double *ut, *vt, *wt;
+  __device__ __forceinline__ void face(int fam, int64_t q, const FaceIn<double>& f) const {
+    const double g4 = times4(f.gsum);
+    const double NA = f.pr - f.pl;
+    const double t1 = fma(f.U * -8.0, f.U, fabs(f.U) * g4);  // 4 (|U| Gs - 2 U^2)
+    const double D12 = f.D1 * f.D2;
+    const double inner = fma(f.s1 * f.N1, f.D2, (f.s2 * f.N2) * f.D1);
+    const double num = fma(-(f.U * f.DA), inner, D12 * (t1 * NA));
+    const double den = (g4 * f.DA) * D12;
+    (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = num * rcp(den);
+  }
+  __device__ __forceinline__ void closed(int64_t q) const { wt[q] = 0.0; }
+};
 
 // One plane of published sums; row index r+1 holds tile row r (r = -1 ..
 // TY), column index c+1 tile column c (c = -1 .. TX).
+template <class T>
 struct Plane {
-  double sx[TY + 2][TX], ex[TY + 2][TX];      // S_x = psi(i) + psi(i+1), S_x + eps
-  double sy[TY][TX + 2], ey[TY][TX + 2];      // S_y = psi(j) + psi(j+1), S_y + eps
-  double sz[TY + 2][TX + 2], ez[TY + 2][TX + 2];  // S_z = psi(k) + psi(k+1), + eps
-  double pvx[TY + 1][TX], pvz[TY + 1][TX];    // V(i)+V(i+1); V(k)+V(k+1)  rows -1 .. TY-1
-  double puy[TY][TX + 1], puz[TY][TX + 1];    // U(j)+U(j+1); U(k)+U(k+1)  cols -1 .. TX-1
+  T sx[TY + 2][TX], ex[TY + 2][TX];          // S_x = psi(i) + psi(i+1), S_x + eps
+  T sy[TY][TX + 2], ey[TY][TX + 2];          // S_y = psi(j) + psi(j+1), S_y + eps
+  T sz[TY + 2][TX + 2], ez[TY + 2][TX + 2];  // S_z = psi(k) + psi(k+1), + eps
+  T pvx[TY + 1][TX], pvz[TY + 1][TX];        // V(i)+V(i+1); V(k)+V(k+1)  rows -1 .. TY-1
+  T puy[TY][TX + 1], puz[TY][TX + 1];        // U(j)+U(j+1); U(k)+U(k+1)  cols -1 .. TX-1
 };
 
-// Grid: (ceil(nx/TX), ceil(ny/TY), ceil(nz/kc)); block (TX, TY).  Writes the
-// unlimited pseudo-velocities ut, vt, wt of every interior cell of its tile
-// and k range (wt = 0 on the closed top face).
-__global__ void __launch_bounds__(TX * TY, 2)
-pseudo_march_kernel(Geo g, const double* __restrict__ P, const double* __restrict__ cu,
-                    const double* __restrict__ cv, const double* __restrict__ cw,
-                    const double* __restrict__ G, double* __restrict__ ut,
-                    double* __restrict__ vt, double* __restrict__ wt, int kc) {
-  __shared__ Plane sm[2];
-  const double eps = Eps<double>::v;
+// CTAs per SM the registers are sized for.
+template <class T> struct MarchMinB { static constexpr int v = 2; };
+template <> struct MarchMinB<float> { static constexpr int v = 3; };
+
+// Grid: (ceil(nx/TX), ceil(ny/TY), ceil(nz/kc)); block (TX, TY).  Calls
+// op.face(fam, q, ingredients) for the x (fam 0), y (1) and z (2) "+"
+// faces of every interior cell q of its tile and k range, and op.closed(q)
+// for the closed top face.
+template <class T, class Op>
+__global__ void __launch_bounds__(TX * TY, MarchMinB<T>::v)
+march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
+             const T* __restrict__ cv, const T* __restrict__ cw, const T* __restrict__ G, Op op,
+             int kc) {
+  __shared__ Plane<T> sm[2];
+  const T eps = Eps<T>::v, zero = T(0);
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
   const bool own = i0 + tx < g.nx && j0 + ty < g.ny;
@@ -113,11 +131,11 @@ pseudo_march_kernel(Geo g, const double* __restrict__ P, const double* __restric
   const int64_t pxy = g.pxy;
   const int k0 = blockIdx.z * kc, k1 = min(k0 + kc, g.nz);
   // register queues: psi and pair sums at k (and k-1), W pairs at k-1/2
-  double pc = P[o + k0 * pxy], pi = P[oi + k0 * pxy], pj = P[oj + k0 * pxy];
-  double sx = pc + pi, exx = sx + eps, sy = pc + pj, eyy = sy + eps;
+  T pc = P[o + k0 * pxy], pi = P[oi + k0 * pxy], pj = P[oj + k0 * pxy];
+  T sx = pc + pi, exx = sx + eps, sy = pc + pj, eyy = sy + eps;
   const int64_t ob = (k0 > 0 ? k0 - 1 : 0) * pxy;
-  double sxm = P[o + ob] + P[oi + ob], sym = P[o + ob] + P[oj + ob];
-  double pwxm = 0.0, pwym = 0.0;
+  T sxm = P[o + ob] + P[oi + ob], sym = P[o + ob] + P[oj + ob];
+  T pwxm = zero, pwym = zero;
   if (k0 > 0) {
     pwxm = cw[o + ob] + cw[oi + ob];
     pwym = cw[o + ob] + cw[oj + ob];
@@ -127,11 +145,11 @@ pseudo_march_kernel(Geo g, const double* __restrict__ P, const double* __restric
     const int64_t ok = k * pxy;
     const bool top = k == g.nz - 1;
     const int64_t on = top ? ok : ok + pxy;  // k+1, clamped (edge copy of psi)
-    const double pcn = P[o + on], pin = P[oi + on], pjn = P[oj + on];
-    const double sxn = pcn + pin, exn = sxn + eps, syn = pcn + pjn, eyn = syn + eps;
-    const double uc = cu[o + ok], vc = cv[o + ok], wc = cw[o + ok];
-    const double pvx = vc + cv[oi + ok], puy = uc + cu[oj + ok];
-    double sz = 0.0, ez = 0.0, puz = 0.0, pvz = 0.0, pwx = 0.0, pwy = 0.0;
+    const T pcn = P[o + on], pin = P[oi + on], pjn = P[oj + on];
+    const T sxn = pcn + pin, exn = sxn + eps, syn = pcn + pjn, eyn = syn + eps;
+    const T uc = cu[o + ok], vc = cv[o + ok], wc = cw[o + ok];
+    const T pvx = vc + cv[oi + ok], puy = uc + cu[oj + ok];
+    T sz = zero, ez = zero, puz = zero, pvz = zero, pwx = zero, pwy = zero;
     if (!top) {  // the face k+1/2 is open
       sz = pc + pcn;
       ez = sz + eps;
@@ -140,7 +158,7 @@ pseudo_march_kernel(Geo g, const double* __restrict__ P, const double* __restric
       pwx = wc + cw[oi + ok];
       pwy = wc + cw[oj + ok];
     }
-    Plane& s = sm[k & 1];
+    Plane<T>& s = sm[k & 1];
     s.sx[ty + 1][tx] = sx;
     s.ex[ty + 1][tx] = exx;
     s.sy[ty][tx + 1] = sy;
@@ -152,29 +170,29 @@ pseudo_march_kernel(Geo g, const double* __restrict__ P, const double* __restric
     s.puy[ty][tx + 1] = puy;
     s.puz[ty][tx + 1] = puz;
     if (rkind == 1) {  // row ring: S_x, S_z (+eps above), V pairs below
-      const double a = P[ro + ok];
-      const double rsx = a + P[rn + ok];
-      const double rsz = top ? 0.0 : a + P[ro + on];
+      const T a = P[ro + ok];
+      const T rsx = a + P[rn + ok];
+      const T rsz = top ? zero : a + P[ro + on];
       s.sx[rs][rc] = rsx;
       s.sz[rs][rc + 1] = rsz;
       if (rs == 0) {
-        const double v0 = cv[ro + ok];
+        const T v0 = cv[ro + ok];
         s.pvx[0][rc] = v0 + cv[rn + ok];
-        s.pvz[0][rc] = top ? 0.0 : v0 + cv[ro + on];
+        s.pvz[0][rc] = top ? zero : v0 + cv[ro + on];
       } else {
         s.ex[rs][rc] = rsx + eps;
         s.ez[rs][rc + 1] = rsz + eps;
       }
     } else if (rkind == 2) {  // column ring: S_y, S_z (+eps right), U pairs left
-      const double a = P[ro + ok];
-      const double rsy = a + P[rn + ok];
-      const double rsz = top ? 0.0 : a + P[ro + on];
+      const T a = P[ro + ok];
+      const T rsy = a + P[rn + ok];
+      const T rsz = top ? zero : a + P[ro + on];
       s.sy[rs][rc] = rsy;
       s.sz[rs + 1][rc] = rsz;
       if (rc == 0) {
-        const double u0 = cu[ro + ok];
+        const T u0 = cu[ro + ok];
         s.puy[rs][0] = u0 + cu[rn + ok];
-        s.puz[rs][0] = top ? 0.0 : u0 + cu[ro + on];
+        s.puz[rs][0] = top ? zero : u0 + cu[ro + on];
       } else {
         s.ey[rs][rc] = rsy + eps;
         s.ez[rs + 1][rc] = rsz + eps;
@@ -182,26 +200,37 @@ pseudo_march_kernel(Geo g, const double* __restrict__ P, const double* __restric
     }
     __syncthreads();
     if (own) {
-      ut[o + ok] = face(uc, G[o + ok] + G[oi + ok], pc, pi, exx,
-                        s.sx[ty + 2][tx] - s.sx[ty][tx], s.ex[ty + 2][tx] + s.sx[ty][tx],
-                        sxn - sxm, exn + sxm, s.pvx[ty + 1][tx] + s.pvx[ty][tx], pwx + pwxm);
-      vt[o + ok] = face(vc, G[o + ok] + G[oj + ok], pc, pj, eyy,
-                        s.sy[ty][tx + 2] - s.sy[ty][tx], s.ey[ty][tx + 2] + s.sy[ty][tx],
-                        syn - sym, eyn + sym, s.puy[ty][tx + 1] + s.puy[ty][tx], pwy + pwym);
-      wt[o + ok] = top ? 0.0
-                       : face(wc, G[o + ok] + G[o + on], pc, pcn, ez,
-                              s.sz[ty + 1][tx + 2] - s.sz[ty + 1][tx],
-                              s.ez[ty + 1][tx + 2] + s.sz[ty + 1][tx],
-                              s.sz[ty + 2][tx + 1] - s.sz[ty][tx + 1],
-                              s.ez[ty + 2][tx + 1] + s.sz[ty][tx + 1],
-                              s.puz[ty][tx + 1] + s.puz[ty][tx],
-                              s.pvz[ty + 1][tx] + s.pvz[ty][tx]);
+      const int64_t q = o + ok;
+      op.face(0, q,
+              FaceIn<T>{uc, G[q] + G[oi + ok], pc, pi, exx, s.sx[ty + 2][tx] - s.sx[ty][tx],
+                        s.ex[ty + 2][tx] + s.sx[ty][tx], sxn - sxm, exn + sxm,
+                        s.pvx[ty + 1][tx] + s.pvx[ty][tx], pwx + pwxm});
+      op.face(1, q,
+              FaceIn<T>{vc, G[q] + G[oj + ok], pc, pj, eyy, s.sy[ty][tx + 2] - s.sy[ty][tx],
+                        s.ey[ty][tx + 2] + s.sy[ty][tx], syn - sym, eyn + sym,
+                        s.puy[ty][tx + 1] + s.puy[ty][tx], pwy + pwym});
+      if (top) {
+        op.closed(q);
+      } else {
+        op.face(2, q,
+                FaceIn<T>{wc, G[q] + G[o + on], pc, pcn, ez,
+                          s.sz[ty + 1][tx + 2] - s.sz[ty + 1][tx],
+                          s.ez[ty + 1][tx + 2] + s.sz[ty + 1][tx],
+                          s.sz[ty + 2][tx + 1] - s.sz[ty][tx + 1],
+                          s.ez[ty + 2][tx + 1] + s.sz[ty][tx + 1],
+                          s.puz[ty][tx + 1] + s.puz[ty][tx], s.pvz[ty + 1][tx] + s.pvz[ty][tx]});
+      }
     }
     sxm = sx; sx = sxn; exx = exn;
     sym = sy; sy = syn; eyy = eyn;
     pwxm = pwx; pwym = pwy;
     pc = pcn; pi = pin; pj = pjn;
   }
+}
+
+// Launch geometry of march_kernel.
+inline dim3 march_grid(const Geo& g) {
+  return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + KC - 1) / KC);
 }
 
 }  // namespace march

@@ -113,11 +113,14 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
 // Non-oscillatory limiter, first half: bounds over the 7-point stencil of
 // psi^n (P0) and psi^(m-1) (P), incoming/outgoing antidiffusive fluxes and
 // the scale factors beta-up, beta-down (Smolarkiewicz & Grabowski 1990).
+// With rin != nullptr the reciprocals 1/(in+eps) and 1/(out+eps) are kept
+// too (the adjoint's tape).
 template <class T>
 __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict__ P,
                             const T* __restrict__ ut, const T* __restrict__ vt,
                             const T* __restrict__ wt, const T* __restrict__ G,
-                            T* __restrict__ bu, T* __restrict__ bd) {
+                            T* __restrict__ bu, T* __restrict__ bd, T* __restrict__ rin,
+                            T* __restrict__ rout) {
   Cell c = cell_of(g);
   if (!c.ok) return;
   const T eps = Eps<T>::v, zero = T(0);
@@ -141,8 +144,13 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
   T fzm = k > 0 ? donor(P[nb[4]], pc, wt[nb[4]]) : zero;
   T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
   T out = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
-  bu[q] = (hi - pc) * G[q] * rcp(in + eps);
-  bd[q] = (pc - lo) * G[q] * rcp(out + eps);
+  const T ri = rcp(in + eps), ro = rcp(out + eps);
+  bu[q] = (hi - pc) * G[q] * ri;
+  bd[q] = (pc - lo) * G[q] * ro;
+  if (rin) {
+    rin[q] = ri;
+    rout[q] = ro;
+  }
 }
 
 // Second half: limited velocities on the "+" faces and their donor fluxes.
