@@ -197,7 +197,7 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
 // ---------------------------------------------------------------------------
 // Pseudo-velocity reverse in gather form (no atomics).
 //
-// Pass 1 (RevPseudo), per cell and its three "+" faces f, from the
+// Pass 1 (RevPseudo: face_weights), per cell and its three "+" faces f, from the
 // adjoint ub_f of the pseudo-velocity: adds dJ/dU_f (own face) and stores
 // eight weights per face, the adjoint routed to each stencil point:
 //   wl, wr    to psi1 at L and R through A,
@@ -226,40 +226,238 @@ __device__ __forceinline__ T sgn0(T U) {
 //   w1p, w1m = t1 (1 - B1'), -t1 (1 + B1') with t1 = m4 s1 / D1,
 //            m4 = -ub qh / 4 (w2p, w2m the same with s2, D2, B2');
 //   c1, c2 = m4 B1', m4 B2'.
+// The eight weights and the direct adjoint ub * dUt/dU of one face (see
+// above), for the face adjoint ub.
+template <class T>
+struct FaceW {
+  T wl, wr, w1p, w1m, w2p, w2m, c1, c2, du;
+};
+
+template <class T>
+__device__ __forceinline__ FaceW<T> face_weights(const march::FaceIn<T>& f, T ubv) {
+  const T rd = rcp(f.DA), rd1 = rcp(f.D1), rd2 = rcp(f.D2), rG2 = rcp(f.gsum);
+  const T A = (f.pr - f.pl) * rd, B1 = f.N1 * rd1, B2 = f.N2 * rd2;
+  const T qh = f.U * rG2;
+  const T Dd = fma_rn(f.U * T(-2), qh, absv(f.U));
+  const T X8 = fma_rn(f.s2, B2, f.s1 * B1);
+  const T dU = fma_rn(X8 * rG2, T(-0.25), A * fma_rn(qh, T(-4), sgn0(f.U)));
+  const T Abr = ubv * Dd * rd;
+  const T m4 = ubv * qh * T(-0.25);
+  const T t1 = m4 * f.s1 * rd1, t2 = m4 * f.s2 * rd2;
+  return FaceW<T>{fma_rn(-Abr, A, -Abr), fma_rn(-Abr, A, Abr), fma_rn(-t1, B1, t1),
+                  fma_rn(-t1, B1, -t1),  fma_rn(-t2, B2, t2),  fma_rn(-t2, B2, -t2),
+                  m4 * B1,               m4 * B2,              ubv * dU};
+}
+
+// Pass 1 as the cell operation of march::march_kernel (FP64): stores the
+// weights for the gather pass and adds the direct adjoint to ub, vb, wb.
 template <class T>
 struct RevPseudo {
+  using Acc = march::NoAcc;
+  static constexpr bool kAccum = false;
   const T *utb, *vtb, *wtb;
   T* wts;
   int64_t F;  // one weight field
   T *ub, *vb, *wb;
-  __device__ __forceinline__ void put(int fam, int w, int64_t q, T v) const {
-    wts[((int64_t)fam * kNW + w) * F + q] = v;
+  struct Load {
+    T x, y, z;  // the face adjoints of the cell's three "+" faces
+  };
+  __device__ __forceinline__ Load load(int64_t q) const { return {utb[q], vtb[q], wtb[q]}; }
+  __device__ __forceinline__ void store(int fam, int64_t q, const FaceW<T>& w) const {
+    T* b = wts + (int64_t)fam * kNW * F + q;
+    b[kWL * F] = w.wl;
+    b[kWR * F] = w.wr;
+    b[kW1P * F] = w.w1p;
+    b[kW1M * F] = w.w1m;
+    b[kW2P * F] = w.w2p;
+    b[kW2M * F] = w.w2m;
+    b[kC1 * F] = w.c1;
+    b[kC2 * F] = w.c2;
   }
-  __device__ __forceinline__ void face(int fam, int64_t q, const march::FaceIn<T>& f) const {
-    const T ubv = (fam == 0 ? utb : fam == 1 ? vtb : wtb)[q];
-    const T rd = rcp(f.DA), rd1 = rcp(f.D1), rd2 = rcp(f.D2), rG2 = rcp(f.gsum);
-    const T A = (f.pr - f.pl) * rd, B1 = f.N1 * rd1, B2 = f.N2 * rd2;
-    const T qh = f.U * rG2;
-    const T Dd = fma_rn(f.U * T(-2), qh, absv(f.U));
-    const T X8 = fma_rn(f.s2, B2, f.s1 * B1);
-    const T dU = fma_rn(X8 * rG2, T(-0.25), A * fma_rn(qh, T(-4), sgn0(f.U)));
-    T* Ub = fam == 0 ? ub : fam == 1 ? vb : wb;
-    Ub[q] = fma_rn(ubv, dU, Ub[q]);
-    const T Abr = ubv * Dd * rd;
-    put(fam, kWL, q, fma_rn(-Abr, A, -Abr));
-    put(fam, kWR, q, fma_rn(-Abr, A, Abr));
-    const T m4 = ubv * qh * T(-0.25);
-    const T t1 = m4 * f.s1 * rd1, t2 = m4 * f.s2 * rd2;
-    put(fam, kW1P, q, fma_rn(-t1, B1, t1));
-    put(fam, kW1M, q, fma_rn(-t1, B1, -t1));
-    put(fam, kW2P, q, fma_rn(-t2, B2, t2));
-    put(fam, kW2M, q, fma_rn(-t2, B2, -t2));
-    put(fam, kC1, q, m4 * B1);
-    put(fam, kC2, q, m4 * B2);
+  __device__ __forceinline__ void cell(int64_t q, const march::FaceIn<T>& fx,
+                                      const march::FaceIn<T>& fy, const march::FaceIn<T>& fz,
+                                      bool top, march::CellAt, Load l, Acc&) const {
+    const FaceW<T> x = face_weights(fx, l.x);
+    store(0, q, x);
+    ub[q] += x.du;
+    const FaceW<T> y = face_weights(fy, l.y);
+    store(1, q, y);
+    vb[q] += y.du;
+    if (top) {
+      store(2, q, FaceW<T>{});
+    } else {
+      const FaceW<T> z = face_weights(fz, l.z);
+      store(2, q, z);
+      wb[q] += z.du;
+    }
   }
-  __device__ __forceinline__ void closed(int64_t q) const {
+};
+
+// The pseudo-velocity reverse in one pass (FP32): each cell adds its three
+// faces' weights into shared accumulators of psi1-bar, U-, V- and W-bar,
+// the contributions of one cell to one point summed first (34 targets per
+// cell).  Every warp (one tile row) owns a private strip of each
+// accumulator -- the rows above, at and below its own, the tile's columns
+// plus the ring -- so for any one target offset its lanes write distinct
+// words: plain read-add-write, a __syncwarp between offsets, no atomics.
+// Levels: psi1-bar k-1, k, k+1 (a ring of three), U-, V-bar k, k+1 and
+// W-bar k-1, k (rings of two).  A level is complete once no later cell of
+// the CTA reaches it; its (up to three) strips are then summed in warp
+// order and added to the global field with fire-and-forget atomic adds
+// (the ring and the chunk's end levels are shared with other CTAs, and a
+// reduction never waits for the old value, unlike a plain add).
+template <class T>
+struct RevPseudoAcc {
+  static constexpr int TY = march::TY, C = march::TX + 2, R = TY + 2;
+  static constexpr int kStrip = TY * 3 * C;  // words of one accumulator level
+  struct Acc {
+    T p[3 * kStrip], u[2 * kStrip], v[2 * kStrip], w[2 * kStrip];
+  };
+  static constexpr bool kAccum = true;
+  static constexpr int kWords = 9 * kStrip;
+  static constexpr int kPos = (R * C + march::TX * march::TY - 1) / (march::TX * march::TY);
+  const T *utb, *vtb, *wtb;
+  T *pb, *ub, *vb, *wb;
+  struct Load {
+    T x, y, z;
+  };
+  // The flush positions of one thread: shared row r, column c (tile row
+  // r-1, column c-1) and the in-plane offset of their (wrapped) global point.
+  struct Pos {
+    int r, c;
+    int64_t off;
+  };
+  Pos pos[kPos];
+  __device__ __forceinline__ Load load(int64_t q) const { return {utb[q], vtb[q], wtb[q]}; }
+  __device__ __forceinline__ void zero(Acc& a, int t) {
+    T* f = a.p;
+    for (int q = t; q < kWords; q += march::TX * march::TY) f[q] = T(0);
+  }
+  __device__ __forceinline__ void setup(const Geo& g, int i0, int j0, int t) {
 #pragma unroll
-    for (int w = 0; w < kNW; ++w) put(2, w, q, T(0));
+    for (int m = 0; m < kPos; ++m) {
+      const int e = t + m * march::TX * march::TY;
+      Pos& P = pos[m];
+      P.r = e / C;
+      P.c = e % C;
+      const int ti = P.c - 1, tj = P.r - 1;
+      P.off = e < R * C ? at(g, (i0 + ti + g.nx) % g.nx, (j0 + tj + g.ny) % g.ny, 0) : 0;
+    }
+  }
+  // v into the strip word at row offset sr (0 below, 1 own, 2 above) and
+  // column offset dc from the cell, its base b = &strip[ty][0][c]
+  template <int SR, int DC>
+  __device__ __forceinline__ static void add(T* b, T v) {
+    b[SR * C + DC] += v;
+    __syncwarp();
+  }
+  __device__ __forceinline__ void cell(int64_t q, const march::FaceIn<T>& fx,
+                                      const march::FaceIn<T>& fy, const march::FaceIn<T>& fz,
+                                      bool top, march::CellAt at, Load l, Acc& a) const {
+    const T own = at.own ? T(1) : T(0);  // lanes past a ragged edge add zeros
+    const FaceW<T> x = face_weights(fx, own * l.x);
+    const FaceW<T> y = face_weights(fy, own * l.y);
+    const FaceW<T> z = top ? FaceW<T>{} : face_weights(fz, own * l.z);
+    const int k = at.k, cb = (at.r - 1) * 3 * C + at.c;
+    const int s3 = k % 3, s2 = k & 1;
+    T* p0 = a.p + s3 * kStrip + cb;
+    T* pq = a.p + (top ? s3 : (s3 == 2 ? 0 : s3 + 1)) * kStrip + cb;  // "+z" level, clamped
+    T* pm = a.p + (k > 0 ? (s3 == 0 ? 2 : s3 - 1) : s3) * kStrip + cb;  // "-z" level, clamped
+    // psi1-bar, same level
+    add<1, 0>(p0, x.wl + y.wl + z.wl);
+    add<1, 1>(p0, x.wr + y.w1p + z.w1p);
+    add<2, 0>(p0, x.w1p + y.wr + z.w2p);
+    add<2, 1>(p0, x.w1p + y.w1p);
+    add<0, 0>(p0, x.w1m + z.w2m);
+    add<0, 1>(p0, x.w1m);
+    add<2, -1>(p0, y.w1m);
+    add<1, -1>(p0, y.w1m + z.w1m);
+    // the level above (z faces; the x, y faces' +z points)
+    add<1, 0>(pq, x.w2p + y.w2p + z.wr);
+    add<1, 1>(pq, x.w2p + z.w1p);
+    add<2, 0>(pq, y.w2p + z.w2p);
+    if (!top) {
+      add<1, -1>(pq, z.w1m);
+      add<0, 0>(pq, z.w2m);
+    }
+    // the level below (the x, y faces' -z points, clamped at the bottom)
+    add<1, 0>(pm, x.w2m + y.w2m);
+    add<1, 1>(pm, x.w2m);
+    add<2, 0>(pm, y.w2m);
+    // U-bar and V-bar at k: own face terms and the cross averages
+    T* u0 = a.u + s2 * kStrip + cb;
+    T* v0 = a.v + s2 * kStrip + cb;
+    add<1, 0>(u0, x.du + y.c1 + z.c1);
+    add<2, 0>(u0, y.c1);
+    add<1, -1>(u0, y.c1 + z.c1);
+    add<2, -1>(u0, y.c1);
+    add<1, 0>(v0, y.du + x.c1 + z.c2);
+    add<1, 1>(v0, x.c1);
+    add<0, 0>(v0, x.c1 + z.c2);
+    add<0, 1>(v0, x.c1);
+    if (!top) {
+      T* u1 = a.u + (s2 ^ 1) * kStrip + cb;
+      T* v1 = a.v + (s2 ^ 1) * kStrip + cb;
+      add<1, 0>(u1, z.c1);
+      add<1, -1>(u1, z.c1);
+      add<1, 0>(v1, z.c2);
+      add<0, 0>(v1, z.c2);
+      T* w0 = a.w + s2 * kStrip + cb;  // W-bar at the open face k+1/2
+      add<1, 0>(w0, z.du + x.c2 + y.c2);
+      add<1, 1>(w0, x.c2);
+      add<2, 0>(w0, y.c2);
+    }
+    if (k > 0) {  // W-bar at the open face k-1/2
+      T* wm = a.w + (s2 ^ 1) * kStrip + cb;
+      add<1, 0>(wm, x.c2 + y.c2);
+      add<1, 1>(wm, x.c2);
+      add<2, 0>(wm, y.c2);
+    }
+  }
+  // Sum the strips of one accumulator level (base f) into dst at level kf
+  // and clear them.
+  __device__ __forceinline__ void flush_one(T* f, T* dst, int kf, const Geo& g) const {
+    const int64_t ok = (int64_t)kf * g.pxy;
+#pragma unroll
+    for (int m = 0; m < kPos; ++m) {
+      const Pos& P = pos[m];
+      if (P.r >= R) continue;
+      T v = T(0);
+      // warps w = r-2 .. r (within the tile) hold the point in strip row r-w
+#pragma unroll
+      for (int d = 2; d >= 0; --d) {
+        const int w = P.r - d;
+        if (w >= 0 && w < TY) {
+          T* x = f + (w * 3 + d) * C + P.c;
+          v += *x;
+          *x = T(0);
+        }
+      }
+      if (ge0(v) && le0(v)) continue;
+      atomicAdd(dst + P.off + ok, v);
+    }
+  }
+  // After the cells of level k (and a barrier): psi1-bar and W-bar level k-1
+  // and U-, V-bar level k are complete.  After the last level k1-1 (after),
+  // psi1-bar k1-1, k1, U-, V-bar k1 and W-bar k1-1 remain.
+  __device__ __forceinline__ void flush(Acc& a, int k, bool after, const Geo& g, int i0,
+                                       int j0, int k0, int k1, int t) const {
+    if (!after) {
+      if (k > 0) {
+        flush_one(a.p + ((k - 1) % 3) * kStrip, pb, k - 1, g);
+        flush_one(a.w + ((k - 1) & 1) * kStrip, wb, k - 1, g);
+      }
+      flush_one(a.u + (k & 1) * kStrip, ub, k, g);
+      flush_one(a.v + (k & 1) * kStrip, vb, k, g);
+    } else {
+      flush_one(a.p + ((k1 - 1) % 3) * kStrip, pb, k1 - 1, g);
+      flush_one(a.w + ((k1 - 1) & 1) * kStrip, wb, k1 - 1, g);
+      if (k1 < g.nz) {
+        flush_one(a.p + (k1 % 3) * kStrip, pb, k1, g);
+        flush_one(a.u + (k1 & 1) * kStrip, ub, k1, g);
+        flush_one(a.v + (k1 & 1) * kStrip, vb, k1, g);
+      }
+    }
   }
 };
 

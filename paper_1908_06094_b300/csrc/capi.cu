@@ -422,13 +422,24 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
     }
     {
       namespace M = mpd::march;
-      const RevPseudo<T> op{utb, vtb, wtb, wts, g.total, ub, vb, wb};
-      MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-                 (M::march_kernel<T, RevPseudo<T>><<<M::march_grid(g), dim3(M::TX, M::TY), 0, s>>>(
-                     g, tp.p1, U, V, W, G, op, M::KC)));
+      if constexpr (std::is_same<T, float>::value) {
+        // one pass, shared accumulators; a k chunk's first and last levels are
+        // flushed by two CTAs, so longer chunks move less
+        constexpr int kc = 16;
+        const RevPseudoAcc<T> op{utb, vtb, wtb, p1b, ub, vb, wb};
+        MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+                   (M::march_kernel<T, RevPseudoAcc<T>><<<M::march_grid(g, kc),
+                                                          dim3(M::TX, M::TY), 0, s>>>(
+                       g, tp.p1, U, V, W, G, op, kc)));
+      } else {
+        const RevPseudo<T> op{utb, vtb, wtb, wts, g.total, ub, vb, wb};
+        MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+                   (M::march_kernel<T, RevPseudo<T>><<<M::march_grid(g), dim3(M::TX, M::TY),
+                                                        0, s>>>(g, tp.p1, U, V, W, G, op, M::KC)));
+        MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+                   rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, p1b, ub, vb, wb));
+      }
     }
-    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO, rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                           g, wts, p1b, ub, vb, wb));
     MPD_LAUNCH(c, MPDATA_STAGE_DONOR, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
                                           g, psi, U, V, W, G, p1b, p0b, ub, vb, wb));
   }

@@ -55,8 +55,22 @@ struct FaceIn {
   T U, gsum, pl, pr, DA, N1, D1, N2, D2, s1, s2;
 };
 
+// Where the calling thread's cell sits: shared-memory row r = ty+1 and
+// column c = tx+1 of the tile-plus-ring planes, its level k.
+struct CellAt {
+  int r, c, k;
+  bool own;  // an interior cell (false: the periodic image past a ragged edge)
+};
+
+// Ops without shared accumulators.
+struct NoAcc {};
+
 // Forward, FP64: the common-denominator form (see the header comment).
 struct PseudoMerged {
+  using Acc = NoAcc;
+  struct Load {};
+  static constexpr bool kAccum = false;
+  __device__ __forceinline__ Load load(int64_t) const { return {}; }
   double *ut, *vt, *wt;
   __device__ __forceinline__ void face(int fam, int64_t q, const FaceIn<double>& f) const {
     const double g4 = times4(f.gsum);
@@ -68,7 +82,14 @@ struct PseudoMerged {
     const double den = (g4 * f.DA) * D12;
     (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = num * rcp(den);
   }
-  __device__ __forceinline__ void closed(int64_t q) const { wt[q] = 0.0; }
+  __device__ __forceinline__ void cell(int64_t q, const FaceIn<double>& fx,
+                                      const FaceIn<double>& fy, const FaceIn<double>& fz,
+                                      bool top, CellAt, Load, Acc&) const {
+    face(0, q, fx);
+    face(1, q, fy);
+    if (top) wt[q] = 0.0;
+    else face(2, q, fz);
+  }
 };
 
 // One plane of published sums; row index r+1 holds tile row r (r = -1 ..
@@ -84,18 +105,27 @@ struct Plane {
 
 // CTAs per SM the registers are sized for.
 template <class T> struct MarchMinB { static constexpr int v = 2; };
-template <> struct MarchMinB<float> { static constexpr int v = 3; };
+template <> struct MarchMinB<float> { static constexpr int v = 2; };
 
 // Grid: (ceil(nx/TX), ceil(ny/TY), ceil(nz/kc)); block (TX, TY).  Calls
-// op.face(fam, q, ingredients) for the x (fam 0), y (1) and z (2) "+"
-// faces of every interior cell q of its tile and k range, and op.closed(q)
-// for the closed top face.
+// op.cell(q, x, y, z, top, at, l, acc) with the ingredients of the x, y and
+// z "+" faces of every interior cell q of its tile and k range, l = op.load(q)
+// the op's own reads for the cell (top: the z
+// face is the closed top face and its ingredients are meaningless).  An op
+// with kAccum also owns shared accumulators (Op::Acc); it is called for
+// every thread of the tile (at.own false past a ragged edge), and after the
+// cells of level k and a barrier op.flush(acc, k, false, ...) writes out
+// the accumulator levels no later cell of the CTA touches, after the last
+// level op.flush(acc, k1-1, true, ...) the rest.
 template <class T, class Op>
 __global__ void __launch_bounds__(TX * TY, MarchMinB<T>::v)
 march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
              const T* __restrict__ cv, const T* __restrict__ cw, const T* __restrict__ G, Op op,
              int kc) {
-  __shared__ Plane<T> sm[2];
+  // op is a per-thread copy: accumulating ops keep their flush positions in it
+  // accumulating ops order the plane's reuse by their own barrier: one copy
+  __shared__ Plane<T> sm[Op::kAccum ? 1 : 2];
+  __shared__ typename Op::Acc acc;
   const T eps = Eps<T>::v, zero = T(0);
   const int tx = threadIdx.x, ty = threadIdx.y, t = ty * TX + tx;
   const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
@@ -130,6 +160,10 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
 
   const int64_t pxy = g.pxy;
   const int k0 = blockIdx.z * kc, k1 = min(k0 + kc, g.nz);
+  if constexpr (Op::kAccum) {
+    op.zero(acc, t);  // ordered by the first barrier
+    op.setup(g, i0, j0, t);
+  }
   // register queues: psi and pair sums at k (and k-1), W pairs at k-1/2
   T pc = P[o + k0 * pxy], pi = P[oi + k0 * pxy], pj = P[oj + k0 * pxy];
   T sx = pc + pi, exx = sx + eps, sy = pc + pj, eyy = sy + eps;
@@ -140,25 +174,58 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
     pwxm = cw[o + ob] + cw[oi + ob];
     pwym = cw[o + ob] + cw[oj + ob];
   }
+  // Everything level k reads from memory (n: level k+1, clamped).  FP32
+  // loads it one level ahead, so its latency overlaps the level before;
+  // FP64, bound by its arithmetic, loads it on arrival (fewer registers).
+  struct In {
+    T pcn, pin, pjn, uc, vc, wc, cvi, cuj, cwi, cwj, cun, cvn, gc, gi, gj, gn;
+    T ra, rb, rcn, rv0, rv1, rvn;  // ring task: psi at k (two points), k+1; Courant
+    typename Op::Load ol;
+  };
+  const T* rvel = rkind == 1 ? cv : cu;
+  auto load = [&](int k) {
+    const int64_t ok = k * pxy, on = (k == g.nz - 1 ? k : k + 1) * pxy;
+    In v;
+    v.pcn = P[o + on]; v.pin = P[oi + on]; v.pjn = P[oj + on];
+    v.uc = cu[o + ok]; v.vc = cv[o + ok]; v.wc = cw[o + ok];
+    v.cvi = cv[oi + ok]; v.cuj = cu[oj + ok]; v.cwi = cw[oi + ok]; v.cwj = cw[oj + ok];
+    v.cun = cu[o + on]; v.cvn = cv[o + on];
+    v.gc = G[o + ok]; v.gi = G[oi + ok]; v.gj = G[oj + ok]; v.gn = G[o + on];
+    if (rkind) {
+      v.ra = P[ro + ok]; v.rb = P[rn + ok]; v.rcn = P[ro + on];
+      v.rv0 = rvel[ro + ok]; v.rv1 = rvel[rn + ok]; v.rvn = rvel[ro + on];
+    }
+    v.ol = op.load(o + ok);
+    return v;
+  };
+  constexpr bool kAhead = sizeof(T) == 4;
+  In nx_;
+  if constexpr (kAhead) nx_ = load(k0);
 
   for (int k = k0; k < k1; ++k) {
     const int64_t ok = k * pxy;
     const bool top = k == g.nz - 1;
-    const int64_t on = top ? ok : ok + pxy;  // k+1, clamped (edge copy of psi)
-    const T pcn = P[o + on], pin = P[oi + on], pjn = P[oj + on];
+    In in;
+    if constexpr (kAhead) {
+      in = nx_;
+      nx_ = load(k + 1 < k1 ? k + 1 : k);
+    } else {
+      in = load(k);
+    }
+    const T pcn = in.pcn, pin = in.pin, pjn = in.pjn;
     const T sxn = pcn + pin, exn = sxn + eps, syn = pcn + pjn, eyn = syn + eps;
-    const T uc = cu[o + ok], vc = cv[o + ok], wc = cw[o + ok];
-    const T pvx = vc + cv[oi + ok], puy = uc + cu[oj + ok];
+    const T uc = in.uc, vc = in.vc, wc = in.wc;
+    const T pvx = vc + in.cvi, puy = uc + in.cuj;
     T sz = zero, ez = zero, puz = zero, pvz = zero, pwx = zero, pwy = zero;
     if (!top) {  // the face k+1/2 is open
       sz = pc + pcn;
       ez = sz + eps;
-      puz = uc + cu[o + on];
-      pvz = vc + cv[o + on];
-      pwx = wc + cw[oi + ok];
-      pwy = wc + cw[oj + ok];
+      puz = uc + in.cun;
+      pvz = vc + in.cvn;
+      pwx = wc + in.cwi;
+      pwy = wc + in.cwj;
     }
-    Plane<T>& s = sm[k & 1];
+    Plane<T>& s = sm[Op::kAccum ? 0 : (k & 1)];
     s.sx[ty + 1][tx] = sx;
     s.ex[ty + 1][tx] = exx;
     s.sy[ty][tx + 1] = sy;
@@ -170,67 +237,63 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
     s.puy[ty][tx + 1] = puy;
     s.puz[ty][tx + 1] = puz;
     if (rkind == 1) {  // row ring: S_x, S_z (+eps above), V pairs below
-      const T a = P[ro + ok];
-      const T rsx = a + P[rn + ok];
-      const T rsz = top ? zero : a + P[ro + on];
+      const T rsx = in.ra + in.rb;
+      const T rsz = top ? zero : in.ra + in.rcn;
       s.sx[rs][rc] = rsx;
       s.sz[rs][rc + 1] = rsz;
       if (rs == 0) {
-        const T v0 = cv[ro + ok];
-        s.pvx[0][rc] = v0 + cv[rn + ok];
-        s.pvz[0][rc] = top ? zero : v0 + cv[ro + on];
+        s.pvx[0][rc] = in.rv0 + in.rv1;
+        s.pvz[0][rc] = top ? zero : in.rv0 + in.rvn;
       } else {
         s.ex[rs][rc] = rsx + eps;
         s.ez[rs][rc + 1] = rsz + eps;
       }
     } else if (rkind == 2) {  // column ring: S_y, S_z (+eps right), U pairs left
-      const T a = P[ro + ok];
-      const T rsy = a + P[rn + ok];
-      const T rsz = top ? zero : a + P[ro + on];
+      const T rsy = in.ra + in.rb;
+      const T rsz = top ? zero : in.ra + in.rcn;
       s.sy[rs][rc] = rsy;
       s.sz[rs + 1][rc] = rsz;
       if (rc == 0) {
-        const T u0 = cu[ro + ok];
-        s.puy[rs][0] = u0 + cu[rn + ok];
-        s.puz[rs][0] = top ? zero : u0 + cu[ro + on];
+        s.puy[rs][0] = in.rv0 + in.rv1;
+        s.puz[rs][0] = top ? zero : in.rv0 + in.rvn;
       } else {
         s.ey[rs][rc] = rsy + eps;
         s.ez[rs + 1][rc] = rsz + eps;
       }
     }
     __syncthreads();
-    if (own) {
+    if (own || Op::kAccum) {  // accumulating ops run whole warps (zero weights past the edge)
       const int64_t q = o + ok;
-      op.face(0, q,
-              FaceIn<T>{uc, G[q] + G[oi + ok], pc, pi, exx, s.sx[ty + 2][tx] - s.sx[ty][tx],
+      op.cell(q,
+              FaceIn<T>{uc, in.gc + in.gi, pc, pi, exx, s.sx[ty + 2][tx] - s.sx[ty][tx],
                         s.ex[ty + 2][tx] + s.sx[ty][tx], sxn - sxm, exn + sxm,
-                        s.pvx[ty + 1][tx] + s.pvx[ty][tx], pwx + pwxm});
-      op.face(1, q,
-              FaceIn<T>{vc, G[q] + G[oj + ok], pc, pj, eyy, s.sy[ty][tx + 2] - s.sy[ty][tx],
+                        s.pvx[ty + 1][tx] + s.pvx[ty][tx], pwx + pwxm},
+              FaceIn<T>{vc, in.gc + in.gj, pc, pj, eyy, s.sy[ty][tx + 2] - s.sy[ty][tx],
                         s.ey[ty][tx + 2] + s.sy[ty][tx], syn - sym, eyn + sym,
-                        s.puy[ty][tx + 1] + s.puy[ty][tx], pwy + pwym});
-      if (top) {
-        op.closed(q);
-      } else {
-        op.face(2, q,
-                FaceIn<T>{wc, G[q] + G[o + on], pc, pcn, ez,
-                          s.sz[ty + 1][tx + 2] - s.sz[ty + 1][tx],
-                          s.ez[ty + 1][tx + 2] + s.sz[ty + 1][tx],
-                          s.sz[ty + 2][tx + 1] - s.sz[ty][tx + 1],
-                          s.ez[ty + 2][tx + 1] + s.sz[ty][tx + 1],
-                          s.puz[ty][tx + 1] + s.puz[ty][tx], s.pvz[ty + 1][tx] + s.pvz[ty][tx]});
-      }
+                        s.puy[ty][tx + 1] + s.puy[ty][tx], pwy + pwym},
+              FaceIn<T>{wc, in.gc + in.gn, pc, pcn, ez,
+                        s.sz[ty + 1][tx + 2] - s.sz[ty + 1][tx],
+                        s.ez[ty + 1][tx + 2] + s.sz[ty + 1][tx],
+                        s.sz[ty + 2][tx + 1] - s.sz[ty][tx + 1],
+                        s.ez[ty + 2][tx + 1] + s.sz[ty][tx + 1],
+                        s.puz[ty][tx + 1] + s.puz[ty][tx], s.pvz[ty + 1][tx] + s.pvz[ty][tx]},
+              top, CellAt{ty + 1, tx + 1, k, own}, in.ol, acc);
+    }
+    if constexpr (Op::kAccum) {
+      __syncthreads();
+      op.flush(acc, k, false, g, i0, j0, k0, k1, t);
     }
     sxm = sx; sx = sxn; exx = exn;
     sym = sy; sy = syn; eyy = eyn;
     pwxm = pwx; pwym = pwy;
     pc = pcn; pi = pin; pj = pjn;
   }
+  if constexpr (Op::kAccum) op.flush(acc, k1 - 1, true, g, i0, j0, k0, k1, t);
 }
 
 // Launch geometry of march_kernel.
-inline dim3 march_grid(const Geo& g) {
-  return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + KC - 1) / KC);
+inline dim3 march_grid(const Geo& g, int kc = KC) {
+  return dim3((g.nx + TX - 1) / TX, (g.ny + TY - 1) / TY, (g.nz + kc - 1) / kc);
 }
 
 }  // namespace march
