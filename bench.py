@@ -55,7 +55,7 @@ STAGE_WORDS = {
     "limit": 9,      # psi1, Ut, Vt, Wt, beta x2 -> fx, fy, fz
     "mass": 2,       # psi, G
     "halo": 0,
-    "fused": 7,      # psi^n, psi1, U, V, W, G -> psi^(n+1)
+    "fused": 6,      # psi^n, U, V, W, G -> psi^(n+1) (+ its halo images, a perimeter)
     "fused_donor": 6,  # psi^n, U, V, W, G -> psi1
 }
 STEP_WORDS = 6
@@ -165,10 +165,19 @@ def _dist():
     return ws, rank, local
 
 
-def _source_hash():
+# The sources a stage's dominant kernel is built and launched from: a DRAM
+# figure taken with ncu stays valid while these files are unchanged.
+STAGE_SOURCES = {
+    "pseudo": ("march.cuh", "grid.cuh"),                # FP64 k-marching pseudo-velocity
+    "fused": ("fused2.cuh", "grid.cuh", "capi.cu"),     # FP32 fused step (+ its chunking)
+}
+
+
+def _source_hash(stage=None):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1908_06094_b300", "csrc")
-    for fn in sorted(os.listdir(csrc)):
+    files = STAGE_SOURCES.get(stage) or sorted(os.listdir(csrc))
+    for fn in files:
         with open(os.path.join(csrc, fn), "rb") as f:
             h.update(fn.encode())
             h.update(f.read())
@@ -294,7 +303,7 @@ def run_ours(args, wl_name):
         if dom:
             t, k = stage_ms[dom]
             per_launch_ms = t / k
-            src = _source_hash()
+            src = _source_hash(dom)
             traffic = _traffic_from_profiles(dom, wl_name, src)
             share = {s_: round(v[0] / sum(x[0] for x in stage_ms.values()), 4)
                      for s_, v in stage_ms.items()}

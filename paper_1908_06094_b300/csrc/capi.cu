@@ -13,7 +13,6 @@
 #include "mass.cuh"
 #include "staged.cuh"
 #include "march.cuh"
-#include "fused.cuh"
 #include "fused2.cuh"
 #include "adjoint.cuh"
 

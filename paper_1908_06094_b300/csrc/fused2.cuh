@@ -1,8 +1,10 @@
 // fused2.cuh -- the one-kernel MPDATA step (iord = 2) with one thread per
 // column.
 //
-// Same pipeline as fused.cuh (stages A..E on planes t+2, t+1, t+1, t, t),
-// organised so that almost every instruction is arithmetic:
+// Per level t of the march, five stages run on planes t+2, t+1, t+1, t, t:
+// A psi1 (donor pass), B pseudo-velocities, C limiter bounds and betas,
+// D limited face fluxes, E advance and halo images.  They are organised so
+// that almost every instruction is arithmetic:
 //   * the CTA has one thread per column of the tile + 2 ring, (TX+4)(TY+4)
 //     threads; a thread keeps its own column's values (psi^n, U, V, W, G,
 //     psi1, the pseudo-velocities, the betas, the vertical fluxes) in
