@@ -3,12 +3,15 @@
 //
 // The forward intermediates of the step (psi1, the pseudo-velocities, the
 // betas and the limited velocities) come from a tape recorded by the staged
-// forward kernels; the kernels here run the forward stages backwards, one
-// thread per interior cell (the pseudo-velocity weights: k-marching tiles).
-// The advance, limiter and beta reverses scatter:
-// each thread adds the adjoint of what its cell computed into every value
-// that computation read, with atomic adds.  The pseudo-velocity reverse, the
-// heaviest, is a gather in two passes without atomics (rev_pw, rev_pg).
+// forward kernels; the kernels here run the forward stages backwards:
+//   * the two advance reverses gather per cell, without atomics, and store
+//     their outputs (no zeroing);
+//   * the limiter and beta reverses run one thread per cell and scatter the
+//     adjoints of the bounds and fluxes with atomic adds;
+//   * the pseudo-velocity reverse, the heaviest, runs on the k-marching
+//     tile scaffold of march.cuh: FP64 stores per-face weights and gathers
+//     them in a second pass (RevPseudo, rev_pg_kernel), FP32 accumulates
+//     them in shared memory in one pass (RevPseudoAcc).
 // Periodic and clamped neighbours are addressed by wrapped indices, so the
 // reverse of the halo fill is implicit.
 //
@@ -30,42 +33,67 @@ using staged::cell_of;
 
 template <class T> __device__ __forceinline__ void aadd(T* p, T v) { atomicAdd(p, v); }
 
-// Reverse of out = P - (1/G) sum_d [F(P_c, P_c+d, C_c) - F(P_c-d, P_c, C_c-d)]
-// for the adjoint ob of out.
-template <class T>
-__global__ void rev_advance_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
-                                   const T* __restrict__ cv, const T* __restrict__ cw,
-                                   const T* __restrict__ G, const T* __restrict__ ob,
-                                   T* Pb, T* ub, T* vb, T* wb) {
+// Reverse of the advance out = P - (1/G) sum_d [F(P_c, P_c+d, C_c) -
+// F(P_c-d, P_c, C_c-d)] for the adjoint ob of out.
+// It runs in gather form, without atomics.  With s = ob/G, the
+// adjoint of the flux through face f = (L, R) is Fb = s_R - s_L; cell q
+// takes the upwind partial Fb*C of each of its six faces where it is the
+// upwind value (C > 0 on its "+" faces, C < 0 on its "-" faces; both
+// partials vanish at C = 0), and the velocity adjoint Fb*(upwind value)
+// (L + R at C = 0) of its own three "+" faces.  ADD_P / ADD_C: accumulate
+// into Pb / the velocity adjoints, else store (the field's first writer).
+// S: s comes precomputed in sf (FP64, where six neighbour reciprocals would
+// cost 24 FP64 instructions), else it is formed from ob and G.
+template <class T, bool ADD_P, bool ADD_C, bool S>
+__global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
+                                          const T* __restrict__ cu, const T* __restrict__ cv,
+                                          const T* __restrict__ cw, const T* __restrict__ G,
+                                          const T* __restrict__ ob, const T* __restrict__ sf,
+                                          T* __restrict__ Pb, T* __restrict__ ub,
+                                          T* __restrict__ vb, T* __restrict__ wb) {
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
-  const T a = ob[q];
-  const T s = -a * rcp(G[q]);
+  auto s_at = [&](int64_t n) { return S ? sf[n] : ob[n] * rcp(G[n]); };
+  const T sq = s_at(q), pc = P[q];
+  T acc = ob[q];
+  // "+" face to neighbour n with Courant number C (q is its left value)
+  auto plus = [&](int64_t n, T C, T* Cb) {
+    const T Fb = s_at(n) - sq;
+    const bool ge = ge0(C), le = le0(C);
+    T cb;
+    if (ge && le) {
+      cb = Fb * (pc + P[n]);
+    } else {
+      if (ge) acc += Fb * C;
+      cb = Fb * (ge ? pc : P[n]);
+    }
+    *Cb = ADD_C ? *Cb + cb : cb;
+  };
+  // "-" face from neighbour n (q is its right value)
+  auto minus = [&](int64_t n, T C) {
+    if (!ge0(C)) acc += (sq - s_at(n)) * C;
+  };
   const int64_t xp = at(g, wrap_up(c.i, g.nx), c.j, c.k), xm = at(g, wrap_dn(c.i, g.nx), c.j, c.k);
   const int64_t yp = at(g, c.i, wrap_up(c.j, g.ny), c.k), ym = at(g, c.i, wrap_dn(c.j, g.ny), c.k);
-  // the own cell's share of all six face terms is added once
-  T own = a;
-  // dF/dL = [C]+-indicator * C, dF/dR likewise, dF/dC = L or R: only the
-  // upwind value has a non-zero partial (both are 0 * fb when C == 0)
-  auto face = [&](T fb, T L, T R, T C, bool own_is_left, int64_t other, T* Cb) {
-    const bool ge = ge0(C), le = le0(C);
-    if (ge && le) {
-      aadd(Cb, fb * (L + R));
-      return;
-    }
-    const T d = fb * C;
-    if (ge == own_is_left) own += d;
-    else aadd(&Pb[other], d);
-    aadd(Cb, fb * (ge ? L : R));
-  };
-  face(s, P[q], P[xp], cu[q], true, xp, &ub[q]);
-  face(-s, P[xm], P[q], cu[xm], false, xm, &ub[xm]);
-  face(s, P[q], P[yp], cv[q], true, yp, &vb[q]);
-  face(-s, P[ym], P[q], cv[ym], false, ym, &vb[ym]);
-  if (c.k < g.nz - 1) face(s, P[q], P[q + g.pxy], cw[q], true, q + g.pxy, &wb[q]);
-  if (c.k > 0) face(-s, P[q - g.pxy], P[q], cw[q - g.pxy], false, q - g.pxy, &wb[q - g.pxy]);
-  aadd(&Pb[q], own);
+  plus(xp, cu[q], &ub[q]);
+  minus(xm, cu[xm]);
+  plus(yp, cv[q], &vb[q]);
+  minus(ym, cv[ym]);
+  if (c.k < g.nz - 1) plus(q + g.pxy, cw[q], &wb[q]);
+  else if (!ADD_C) wb[q] = T(0);  // closed top face
+  if (c.k > 0) minus(q - g.pxy, cw[q - g.pxy]);
+  Pb[q] = ADD_P ? Pb[q] + acc : acc;
+}
+
+// s = ob/G per interior cell (the FP64 input of the gather form).
+template <class T>
+__global__ void rev_scale_kernel(Geo g, const T* __restrict__ ob, const T* __restrict__ G,
+                                 T* __restrict__ sf) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  const int64_t q = at(g, c.i, c.j, c.k);
+  sf[q] = ob[q] * rcp(G[q]);
 }
 
 // Reverse of the limited velocity of a face (see the tie rules above).
@@ -81,7 +109,7 @@ __device__ __forceinline__ void rev_limit_face(T lb, T Ut, T buL, T bdL, T buR, 
   const bool n_first = leq(n1, bdR);
   const T cneg = n_first ? n1 : bdR;
   const bool ge = ge0(Ut), le = le0(Ut);
-  aadd(Utb, lb * ((ge ? cpos : T(0)) + (le ? cneg : T(0))));
+  *Utb = lb * ((ge ? cpos : T(0)) + (le ? cneg : T(0)));  // the face's first writer
   const T cpb = lb * (ge ? Ut : T(0)), cnb = lb * (le ? Ut : T(0));
   if (p_first) {
     if (p_is_bdL) aadd(bdLb, cpb);
@@ -114,6 +142,8 @@ __global__ void rev_limit_kernel(Geo g, const T* __restrict__ ut, const T* __res
     const int64_t zp = q + g.pxy;
     rev_limit_face(wlb[q], wt[q], bu[q], bd[q], bu[zp], bd[zp], &wtb[q], &bub[q], &bdb[q],
                    &bub[zp], &bdb[zp]);
+  } else {
+    wtb[q] = T(0);  // closed top face
   }
 }
 
@@ -197,7 +227,7 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
 // ---------------------------------------------------------------------------
 // Pseudo-velocity reverse in gather form (no atomics).
 //
-// Pass 1 (RevPseudo: face_weights), per cell and its three "+" faces f, from the
+// Pass 1 (face_weights, RevPseudo), per cell and its three "+" faces f, from the
 // adjoint ub_f of the pseudo-velocity: adds dJ/dU_f (own face) and stores
 // eight weights per face, the adjoint routed to each stencil point:
 //   wl, wr    to psi1 at L and R through A,

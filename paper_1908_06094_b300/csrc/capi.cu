@@ -397,20 +397,41 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
   T *bub = (T*)(base + 8 * f), *bdb = (T*)(base + 9 * f);
   T* wts = (T*)(base + 10 * f);  // 24 weight fields, g.total apart
   const size_t fb = (size_t)g.total * sizeof(T);
-  T* zero_list[10] = {p1b, p0b, utb, vtb, wtb, ulb, vlb, wlb, bub, bdb};
-  for (int q = 0; q < 10; ++q) {
-    cudaError_t e = cudaMemsetAsync(zero_list[q], 0, fb, s);
-    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint clear");
+  // The gather-form advance reverses store their outputs; only the fields
+  // that atomic scatters reach first need clearing: p0b (beta-bound
+  // adjoints, then the donor reverse adds) and the beta adjoints.
+  if (c->iord >= 2) {
+    T* zero_list[3] = {p0b, bub, bdb};
+    for (int q = 0; q < (c->nonosc ? 3 : 1); ++q) {
+      cudaError_t e = cudaMemsetAsync(zero_list[q], 0, fb, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "adjoint clear");
+    }
   }
+  // gather-form advance reverse: FP32 forms s = ob/G on the fly, FP64 reads
+  // it from a pre-pass (wts is free while the advance reverses run)
+  constexpr bool kPreS = std::is_same<T, double>::value;
+  T* sf = wts;
+  auto adv = [&](int stage, const T* P, const T* cu_, const T* cv_, const T* cw_, const T* ob,
+                 T* Pb, T* Cu, T* Cv, T* Cw, bool add_p, bool add_c) {
+    if (kPreS)
+      MPD_LAUNCH(c, stage, rev_scale_kernel<T><<<grid, kCellBlock, 0, s>>>(g, ob, G, sf));
+    if (!add_p && !add_c)
+      MPD_LAUNCH(c, stage, (rev_advance_gather_kernel<T, false, false, kPreS><<<grid, kCellBlock, 0, s>>>(
+                               g, P, cu_, cv_, cw_, G, ob, sf, Pb, Cu, Cv, Cw)));
+    else if (!add_p)
+      MPD_LAUNCH(c, stage, (rev_advance_gather_kernel<T, false, true, kPreS><<<grid, kCellBlock, 0, s>>>(
+                               g, P, cu_, cv_, cw_, G, ob, sf, Pb, Cu, Cv, Cw)));
+    else
+      MPD_LAUNCH(c, stage, (rev_advance_gather_kernel<T, true, true, kPreS><<<grid, kCellBlock, 0, s>>>(
+                               g, P, cu_, cv_, cw_, G, ob, sf, Pb, Cu, Cv, Cw)));
+  };
   if (c->iord == 1) {
-    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                            g, psi, U, V, W, G, psib, p0b, ub, vb, wb));
+    adv(MPDATA_STAGE_ADVANCE, psi, U, V, W, psib, p0b, ub, vb, wb, false, true);
   } else {
     T* vel[3] = {c->nonosc ? tp.ul : tp.ut, c->nonosc ? tp.vl : tp.vt, c->nonosc ? tp.wl : tp.wt};
     T* velb[3] = {c->nonosc ? ulb : utb, c->nonosc ? vlb : vtb, c->nonosc ? wlb : wtb};
-    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                            g, tp.p1, vel[0], vel[1], vel[2], G, psib, p1b, velb[0],
-                                            velb[1], velb[2]));
+    adv(MPDATA_STAGE_ADVANCE, tp.p1, vel[0], vel[1], vel[2], psib, p1b, velb[0], velb[1],
+        velb[2], false, false);
     if (c->nonosc) {
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, rev_limit_kernel<T><<<grid, kCellBlock, 0, s>>>(
                                             g, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, ulb, vlb, wlb,
@@ -439,8 +460,7 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
                    rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, p1b, ub, vb, wb));
       }
     }
-    MPD_LAUNCH(c, MPDATA_STAGE_DONOR, rev_advance_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                          g, psi, U, V, W, G, p1b, p0b, ub, vb, wb));
+    adv(MPDATA_STAGE_DONOR, psi, U, V, W, p1b, p0b, ub, vb, wb, true, true);
   }
   MPD_CHECK_LAUNCH(c, "adjoint reverse kernels");
   cudaError_t e = cudaMemcpyAsync(psib, p0b, fb, cudaMemcpyDeviceToDevice, s);
