@@ -169,10 +169,10 @@ template <class T> struct FusedShape;
 template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 8, MINB = 1; };
 template <> struct FusedShape<float> { static constexpr int TX = 32, TY = 16, MINB = 1; };
 
-template <class T, bool LIMIT>
+template <class T, bool LIMIT, bool TAPE = false>
 auto fused_kernel_ptr() {
   using F = FusedShape<T>;
-  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT>;
+  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, TAPE>;
 }
 
 template <class T>
@@ -197,10 +197,13 @@ int fused_setup(mpdata_ctx* c) {
   const size_t bytes = fused_smem<T>();
   auto k1 = fused_kernel_ptr<T, true>();
   auto k0 = fused_kernel_ptr<T, false>();
-  if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-          cudaSuccess ||
-      cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-          cudaSuccess) {
+  auto kt1 = fused_kernel_ptr<T, true, true>();
+  auto kt0 = fused_kernel_ptr<T, false, true>();
+  const int ib = (int)bytes;
+  if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess ||
+      cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess ||
+      cudaFuncSetAttribute(kt1, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess ||
+      cudaFuncSetAttribute(kt0, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess) {
     cudaGetLastError();
     return MPDATA_OK;  // not eligible on this device: the staged kernels run
   }
@@ -229,21 +232,28 @@ int fused_setup(mpdata_ctx* c) {
   return MPDATA_OK;
 }
 
+// One fused step; with tape != nullptr it also writes the step's
+// intermediates of every interior cell (a taped step).
 template <class T>
 int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, const T* W,
-                 const T* G) {
+                 const T* G, const mpd::fused2::TapeOut<T>* tape = nullptr) {
   using F = FusedShape<T>;
   const Geo& g = c->g;
   dim3 grid((g.nx + F::TX - 1) / F::TX, (g.ny + F::TY - 1) / F::TY, c->nchunks);
   const size_t bytes = fused_smem<T>();
-  if (c->nonosc)
+  const mpd::fused2::TapeOut<T> tp = tape ? *tape : mpd::fused2::TapeOut<T>{};
+  auto go = [&](auto kern) {
     MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
-               (fused_kernel_ptr<T, true>())<<<grid, fused_threads<T>(), bytes, c->stream>>>(
-                   g, c->kchunk, in, U, V, W, G, out));
-  else
-    MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
-               (fused_kernel_ptr<T, false>())<<<grid, fused_threads<T>(), bytes, c->stream>>>(
-                   g, c->kchunk, in, U, V, W, G, out));
+               kern<<<grid, fused_threads<T>(), bytes, c->stream>>>(g, c->kchunk, in, U, V, W, G,
+                                                                   out, tp));
+  };
+  if (tape) {
+    if (c->nonosc) go(fused_kernel_ptr<T, true, true>());
+    else go(fused_kernel_ptr<T, false, true>());
+  } else {
+    if (c->nonosc) go(fused_kernel_ptr<T, true>());
+    else go(fused_kernel_ptr<T, false>());
+  }
   MPD_CHECK_LAUNCH(c, "fused step kernel");
   return MPDATA_OK;
 }
@@ -350,12 +360,18 @@ int halo_fold_launch(mpdata_ctx* c, T* f) {
   return MPDATA_OK;
 }
 
-// One staged forward step psi_in -> psi_out that keeps its intermediates in
-// the tape (iord 1 or 2).
+// One forward step psi_in -> psi_out that keeps its intermediates in the
+// tape (iord 1 or 2): the fused kernel where the plain step would run it,
+// else the staged kernels.
 template <class T>
 int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const T* W,
               const T* G, Tape<T> tp) {
   using namespace mpd::staged;
+  if (use_fused(c)) {  // the fused step writes the tape and the output's halo itself
+    const mpd::fused2::TapeOut<T> to{tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd,
+                                     tp.ri, tp.ro, tp.ul, tp.vl, tp.wl};
+    return fused_launch<T>(c, psi, out, U, V, W, G, &to);
+  }
   const Geo& g = c->g;
   const dim3 grid = cell_grid(g);
   cudaStream_t s = c->stream;

@@ -47,12 +47,20 @@ struct Layout {
   static constexpr size_t bytes = (size_t)NVAL * sizeof(T);
 };
 
-template <class T, int TX, int TY, bool LIMIT>
+// Where a taped step also writes the intermediates of its own cells (the
+// adjoint's tape): psi1, Ut, Vt, Wt, beta-up, beta-down, 1/(in+eps),
+// 1/(out+eps) and the limited Ul, Vl, Wl, all padded fields like psi.
+template <class T>
+struct TapeOut {
+  T *p1, *ut, *vt, *wt, *bu, *bd, *ri, *ro, *ul, *vl, *wl;
+};
+
+template <class T, int TX, int TY, bool LIMIT, bool TAPE = false>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
                                            const T* __restrict__ P0, const T* __restrict__ U,
                                            const T* __restrict__ V, const T* __restrict__ W,
                                            const T* __restrict__ G, T* __restrict__ out,
-                                           unsigned char* smem_raw) {
+                                           unsigned char* smem_raw, TapeOut<T> tape = {}) {
   using L = Layout<T, TX, TY>;
   constexpr int EX = L::EX, RX = L::RX;
   T* sm = reinterpret_cast<T*>(smem_raw);
@@ -123,6 +131,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   T utA = zero, vtA = zero, utB = zero, vtB = zero;  // Ut, Vt at t, t+1
   T wtA = zero, wtB = zero;              // Wt at faces t+1/2, t+3/2
   T buA = zero, bdA = zero, buB = zero, bdB = zero;  // betas at t, t+1
+  T riA = zero, roA = zero, riB = zero, roB = zero;  // their 1/(in+eps), 1/(out+eps) (tape)
   T fzA = zero, fzB = zero;              // vertical fluxes at faces t-1/2, t+1/2
 
   __syncthreads();  // the shared memory may still be read by a previous tile
@@ -232,8 +241,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T fzm = donor(qm, q1, wtA);  // wtA = 0 on the bottom face
       const T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
       const T ou = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
-      buB = (hi - q1) * g1 * rcp(in + eps);
-      bdB = (q1 - lo) * g1 * rcp(ou + eps);
+      const T ri = rcp(in + eps), ro = rcp(ou + eps);
+      buB = (hi - q1) * g1 * ri;
+      bdB = (q1 - lo) * g1 * ro;
+      if (TAPE) { riB = ri; roB = ro; }
       sm[L::BUS + (b & 1) * L::SN + s2] = buB;
       sm[L::BDS + (b & 1) * L::SN + s2] = bdB;
     }
@@ -242,23 +253,35 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     if (t >= max(0, k0 - 1) && t <= k1 - 1) {
       const T* bu0 = sm + L::BUS + (t & 1) * L::SN + s2;
       const T* bd0 = sm + L::BDS + (t & 1) * L::SN + s2;
-      {  // used on x in [-1, TX-1], y in [0, TY-1]
-        T u = utA;
-        if (LIMIT) u = limit_face(u, buA, bdA, bu0[1], bd0[1]);
-        fxs[s2] = donor(q0, P1(t, 1), u);
-      }
-      {  // used on x in [0, TX-1], y in [-1, TY-1]
-        T v = vtA;
-        if (LIMIT) v = limit_face(v, buA, bdA, bu0[EX], bd0[EX]);
-        fys[s2] = donor(q0, P1(t, EX), v);
-      }
-      T f = zero;
+      T u = utA;  // used on x in [-1, TX-1], y in [0, TY-1]
+      if (LIMIT) u = limit_face(u, buA, bdA, bu0[1], bd0[1]);
+      fxs[s2] = donor(q0, P1(t, 1), u);
+      T v = vtA;  // used on x in [0, TX-1], y in [-1, TY-1]
+      if (LIMIT) v = limit_face(v, buA, bdA, bu0[EX], bd0[EX]);
+      fys[s2] = donor(q0, P1(t, EX), v);
+      T f = zero, w = zero;
       if (t < nz - 1) {
-        T w = wtA;
+        w = wtA;
         if (LIMIT) w = limit_face(w, buA, bdA, buB, bdB);
         f = donor(q0, q1, w);
       }
       fzB = f;
+      if (TAPE && t >= k0 && writes) {
+        const int64_t q = c0 + (int64_t)t * pxy;
+        tape.p1[q] = q0;
+        tape.ut[q] = utA;
+        tape.vt[q] = vtA;
+        tape.wt[q] = wtA;  // 0 on the top face
+        if (LIMIT) {
+          tape.bu[q] = buA;
+          tape.bd[q] = bdA;
+          tape.ri[q] = riA;
+          tape.ro[q] = roA;
+          tape.ul[q] = u;
+          tape.vl[q] = v;
+          tape.wl[q] = w;
+        }
+      }
     }
     __syncthreads();
     // ---- E: advance and write psi^(n+1) on plane t ------------------------
@@ -290,21 +313,23 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     q0 = q1; q1 = q2;
     utA = utB; vtA = vtB; wtA = wtB;
     buA = buB; bdA = bdB;
+    if (TAPE) { riA = riB; roA = roB; }
     fzA = fzB;
     // The next iteration publishes into slots nobody reads after this point
     // of the current one; its first barrier orders the rest.
   }
 }
 
-template <class T, int TX, int TY, int MINB, bool LIMIT>
+template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false>
 __global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
              const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
-             T* __restrict__ out) {
+             T* __restrict__ out, TapeOut<T> tape) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k0 = blockIdx.z * kchunk;
-  step_tile2<T, TX, TY, LIMIT>(g, blockIdx.x * TX, blockIdx.y * TY, k0, min(g.nz, k0 + kchunk),
-                               P0, U, V, W, G, out, smem_raw);
+  step_tile2<T, TX, TY, LIMIT, TAPE>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
+                                     min(g.nz, k0 + kchunk), P0, U, V, W, G, out, smem_raw,
+                                     tape);
 }
 
 }  // namespace fused2

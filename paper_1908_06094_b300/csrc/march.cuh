@@ -103,9 +103,11 @@ struct Plane {
   T puy[TY][TX + 1], puz[TY][TX + 1];        // U(j)+U(j+1); U(k)+U(k+1)  cols -1 .. TX-1
 };
 
-// CTAs per SM the registers are sized for.
-template <class T> struct MarchMinB { static constexpr int v = 2; };
-template <> struct MarchMinB<float> { static constexpr int v = 2; };
+// CTAs per SM the registers are sized for.  (Loading each level one level
+// ahead, which costs ~20 registers, was measured slower for the FP32
+// reverse than the third CTA per SM it displaces: 178 vs 161 µs.)
+template <class T, class Op> struct MarchMinB { static constexpr int v = 2; };
+template <class Op> struct MarchMinB<float, Op> { static constexpr int v = 3; };
 
 // Grid: (ceil(nx/TX), ceil(ny/TY), ceil(nz/kc)); block (TX, TY).  Calls
 // op.cell(q, x, y, z, top, at, l, acc) with the ingredients of the x, y and
@@ -118,7 +120,7 @@ template <> struct MarchMinB<float> { static constexpr int v = 2; };
 // the accumulator levels no later cell of the CTA touches, after the last
 // level op.flush(acc, k1-1, true, ...) the rest.
 template <class T, class Op>
-__global__ void __launch_bounds__(TX * TY, MarchMinB<T>::v)
+__global__ void __launch_bounds__(TX * TY, MarchMinB<T, Op>::v)
 march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
              const T* __restrict__ cv, const T* __restrict__ cw, const T* __restrict__ G, Op op,
              int kc) {
@@ -174,9 +176,7 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
     pwxm = cw[o + ob] + cw[oi + ob];
     pwym = cw[o + ob] + cw[oj + ob];
   }
-  // Everything level k reads from memory (n: level k+1, clamped).  FP32
-  // loads it one level ahead, so its latency overlaps the level before;
-  // FP64, bound by its arithmetic, loads it on arrival (fewer registers).
+  // Everything level k reads from memory (n: level k+1, clamped).
   struct In {
     T pcn, pin, pjn, uc, vc, wc, cvi, cuj, cwi, cwj, cun, cvn, gc, gi, gj, gn;
     T ra, rb, rcn, rv0, rv1, rvn;  // ring task: psi at k (two points), k+1; Courant
@@ -198,20 +198,10 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
     v.ol = op.load(o + ok);
     return v;
   };
-  constexpr bool kAhead = sizeof(T) == 4;
-  In nx_;
-  if constexpr (kAhead) nx_ = load(k0);
-
   for (int k = k0; k < k1; ++k) {
     const int64_t ok = k * pxy;
     const bool top = k == g.nz - 1;
-    In in;
-    if constexpr (kAhead) {
-      in = nx_;
-      nx_ = load(k + 1 < k1 ? k + 1 : k);
-    } else {
-      in = load(k);
-    }
+    const In in = load(k);
     const T pcn = in.pcn, pin = in.pin, pjn = in.pjn;
     const T sxn = pcn + pin, exn = sxn + eps, syn = pcn + pjn, eyn = syn + eps;
     const T uc = in.uc, vc = in.vc, wc = in.wc;
