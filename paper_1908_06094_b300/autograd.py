@@ -5,9 +5,12 @@ forward(psi0, U, V, W, G, nsteps) runs nsteps steps and keeps psi every
 ``ckpt`` steps; backward walks the segments in reverse, re-runs each
 segment once from its checkpoint with taped library steps (each keeping
 its intermediates), then applies the library's taped adjoint step to each
-step in reverse order.  Memory: nsteps/ckpt checkpoints plus ckpt states
-and tapes (9 fields each).  G is not differentiated.  Every step of both
-passes runs in the library's kernels; this module only orders the calls.
+step in reverse order.  The last segment, which backward needs first, is
+taped already by the forward pass (when a gradient is wanted), so it is
+never re-run -- the segment schedule of checkpoint_sequential.  Memory:
+nsteps/ckpt checkpoints plus ckpt states and tapes (11 fields each).  G is
+not differentiated.  Every step of both passes runs in the library's
+kernels; this module only orders the calls.
 """
 from __future__ import annotations
 
@@ -25,14 +28,31 @@ class MPDATAFunction(torch.autograd.Function):
         ckpts = [psi0.detach().contiguous().clone()]
         cur = ckpts[0].clone()
         nxt = torch.empty_like(cur)
+        # the last segment [last, nsteps) is run taped when backward will follow
+        taped = nsteps > 0 and any(ctx.needs_input_grad[:4])
+        last = ((nsteps - 1) // ckpt) * ckpt if nsteps > 0 else 0
+        tapes, states = _buffers(model, u, ckpts[0], min(ckpt, nsteps)) if taped else ([], [])
+        P = lambda t, name: model._ptr(t, name)  # noqa: E731
         for s in range(nsteps):
-            model.step_out(cur, nxt, u, v, w, g)
-            cur, nxt = nxt, cur
+            if taped and s >= last:
+                i = s - last
+                if i == 0:
+                    states[0].copy_(cur)
+                model._sync_stream()
+                C.mpdata_step_tape(model._ctx, P(states[i], "state"), P(states[i + 1], "state"),
+                                   P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
+                                   tapes[i].data_ptr())
+                cur = states[i + 1]
+            else:
+                model.step_out(cur, nxt, u, v, w, g)
+                cur, nxt = nxt, cur
             if (s + 1) % ckpt == 0 and s + 1 < nsteps:
                 ckpts.append(cur.clone())
         ctx.model, ctx.nsteps, ctx.ckpt = model, nsteps, ckpt
+        ctx.tapes, ctx.states, ctx.taped = tapes, states, taped
         ctx.save_for_backward(u, v, w, g, *ckpts)
-        return cur
+        # states are reused by backward for the other segments: return a copy
+        return cur.clone() if taped else cur
 
     @staticmethod
     def backward(ctx, grad_out):
@@ -43,27 +63,38 @@ class MPDATAFunction(torch.autograd.Function):
         # the output's halo holds copies of interior values
         C.mpdata_fold_halo_adjoint(m._ctx, m._ptr(psib, "grad"))
         ub, vb, wb = torch.zeros_like(u), torch.zeros_like(v), torch.zeros_like(w)
-        nbytes = C.mpdata_tape_bytes(m._ctx)
         nseg = len(ckpts)
-        seglen = min(ckpt, nsteps)
-        tapes = [torch.empty(nbytes, dtype=torch.uint8, device=u.device) for _ in range(seglen)]
-        states = [torch.empty_like(ckpts[0]) for _ in range(seglen + 1)]
+        if ctx.taped:
+            tapes, states = ctx.tapes, ctx.states
+        else:
+            tapes, states = _buffers(m, u, ckpts[0], min(ckpt, nsteps))
         P = lambda t, name: m._ptr(t, name)  # noqa: E731
         for seg in reversed(range(nseg)):
             start = seg * ckpt
             end = min(start + ckpt, nsteps)
-            # record the segment once: its states and every step's tape
-            states[0].copy_(ckpts[seg])
-            for s in range(end - start):
-                C.mpdata_step_tape(m._ctx, P(states[s], "state"), P(states[s + 1], "state"),
-                                   P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
-                                   tapes[s].data_ptr())
+            if not (seg == nseg - 1 and ctx.taped):  # the forward pass taped the last one
+                # record the segment once: its states and every step's tape
+                states[0].copy_(ckpts[seg])
+                for s in range(end - start):
+                    C.mpdata_step_tape(m._ctx, P(states[s], "state"), P(states[s + 1], "state"),
+                                       P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
+                                       tapes[s].data_ptr())
             for s in reversed(range(end - start)):
                 C.mpdata_adjoint_step_tape(m._ctx, tapes[s].data_ptr(), P(states[s], "state"),
                                            P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
                                            P(psib, "psi_bar"), P(ub, "u_bar"), P(vb, "v_bar"),
                                            P(wb, "w_bar"))
+        ctx.tapes = ctx.states = None
         return psib, ub, vb, wb, None, None, None, None
+
+
+def _buffers(model: MPDATA, like_field, like_state, seglen: int):
+    """Tapes and states of one segment of seglen steps."""
+    nbytes = C.mpdata_tape_bytes(model._ctx)
+    tapes = [torch.empty(nbytes, dtype=torch.uint8, device=like_field.device)
+             for _ in range(seglen)]
+    states = [torch.empty_like(like_state) for _ in range(seglen + 1)]
+    return tapes, states
 
 
 def mpdata_run(model: MPDATA, psi0, u, v, w, g, nsteps: int, ckpt: int = 5):

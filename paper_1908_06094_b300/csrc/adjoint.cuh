@@ -6,8 +6,9 @@
 // forward kernels; the kernels here run the forward stages backwards:
 //   * the two advance reverses gather per cell, without atomics, and store
 //     their outputs (no zeroing);
-//   * the limiter and beta reverses run one thread per cell and scatter the
-//     adjoints of the bounds and fluxes with atomic adds;
+//   * the limiter reverse runs inside the second advance reverse, on each
+//     limited-velocity adjoint it produces; it and the beta reverse scatter
+//     the adjoints of the betas, bounds and fluxes with atomic adds;
 //   * the pseudo-velocity reverse, the heaviest, runs on the k-marching
 //     tile scaffold of march.cuh: FP64 stores per-face weights and gathers
 //     them in a second pass (RevPseudo, rev_pg_kernel), FP32 accumulates
@@ -32,59 +33,6 @@ using staged::Cell;
 using staged::cell_of;
 
 template <class T> __device__ __forceinline__ void aadd(T* p, T v) { atomicAdd(p, v); }
-
-// Reverse of the advance out = P - (1/G) sum_d [F(P_c, P_c+d, C_c) -
-// F(P_c-d, P_c, C_c-d)] for the adjoint ob of out.
-// It runs in gather form, without atomics.  With s = ob/G, the
-// adjoint of the flux through face f = (L, R) is Fb = s_R - s_L; cell q
-// takes the upwind partial Fb*C of each of its six faces where it is the
-// upwind value (C > 0 on its "+" faces, C < 0 on its "-" faces; both
-// partials vanish at C = 0), and the velocity adjoint Fb*(upwind value)
-// (L + R at C = 0) of its own three "+" faces.  ADD_P / ADD_C: accumulate
-// into Pb / the velocity adjoints, else store (the field's first writer).
-// S: s comes precomputed in sf (FP64, where six neighbour reciprocals would
-// cost 24 FP64 instructions), else it is formed from ob and G.
-template <class T, bool ADD_P, bool ADD_C, bool S>
-__global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
-                                          const T* __restrict__ cu, const T* __restrict__ cv,
-                                          const T* __restrict__ cw, const T* __restrict__ G,
-                                          const T* __restrict__ ob, const T* __restrict__ sf,
-                                          T* __restrict__ Pb, T* __restrict__ ub,
-                                          T* __restrict__ vb, T* __restrict__ wb) {
-  Cell c = cell_of(g);
-  if (!c.ok) return;
-  const int64_t q = at(g, c.i, c.j, c.k);
-  auto s_at = [&](int64_t n) { return S ? sf[n] : ob[n] * rcp(G[n]); };
-  const T sq = s_at(q), pc = P[q];
-  T acc = ob[q];
-  // "+" face to neighbour n with Courant number C (q is its left value)
-  auto plus = [&](int64_t n, T C, T* Cb) {
-    const T Fb = s_at(n) - sq;
-    const bool ge = ge0(C), le = le0(C);
-    T cb;
-    if (ge && le) {
-      cb = Fb * (pc + P[n]);
-    } else {
-      if (ge) acc += Fb * C;
-      cb = Fb * (ge ? pc : P[n]);
-    }
-    *Cb = ADD_C ? *Cb + cb : cb;
-  };
-  // "-" face from neighbour n (q is its right value)
-  auto minus = [&](int64_t n, T C) {
-    if (!ge0(C)) acc += (sq - s_at(n)) * C;
-  };
-  const int64_t xp = at(g, wrap_up(c.i, g.nx), c.j, c.k), xm = at(g, wrap_dn(c.i, g.nx), c.j, c.k);
-  const int64_t yp = at(g, c.i, wrap_up(c.j, g.ny), c.k), ym = at(g, c.i, wrap_dn(c.j, g.ny), c.k);
-  plus(xp, cu[q], &ub[q]);
-  minus(xm, cu[xm]);
-  plus(yp, cv[q], &vb[q]);
-  minus(ym, cv[ym]);
-  if (c.k < g.nz - 1) plus(q + g.pxy, cw[q], &wb[q]);
-  else if (!ADD_C) wb[q] = T(0);  // closed top face
-  if (c.k > 0) minus(q - g.pxy, cw[q - g.pxy]);
-  Pb[q] = ADD_P ? Pb[q] + acc : acc;
-}
 
 // s = ob/G per interior cell (the FP64 input of the gather form).
 template <class T>
@@ -123,29 +71,88 @@ __device__ __forceinline__ void rev_limit_face(T lb, T Ut, T buL, T bdL, T buR, 
   }
 }
 
-template <class T>
-__global__ void rev_limit_kernel(Geo g, const T* __restrict__ ut, const T* __restrict__ vt,
-                                 const T* __restrict__ wt, const T* __restrict__ bu,
-                                 const T* __restrict__ bd, const T* __restrict__ ulb,
-                                 const T* __restrict__ vlb, const T* __restrict__ wlb, T* utb,
-                                 T* vtb, T* wtb, T* bub, T* bdb) {
+// Reverse of the advance out = P - (1/G) sum_d [F(P_c, P_c+d, C_c) -
+// F(P_c-d, P_c, C_c-d)] for the adjoint ob of out.
+// It runs in gather form, without atomics.  With s = ob/G, the adjoint of
+// the flux through face f = (L, R) is Fb = s_R - s_L; cell q takes the
+// upwind partial Fb*C of each of its six faces where it is the upwind value
+// (C > 0 on its "+" faces, C < 0 on its "-" faces; both partials vanish at
+// C = 0), and hands the velocity adjoint Fb*(upwind value) (L + R at
+// C = 0) of each of its own three "+" faces to out(fam, q, n, cb) (n the
+// face's right cell), and its closed top face to out.closed(q).  ADD_P:
+// accumulate into Pb, else store (the field's first writer).  S: s comes
+// precomputed in sf (FP64, where six neighbour reciprocals would cost 24
+// FP64 instructions), else it is formed from ob and G.
+template <class T, bool ADD_P, bool S, class Out>
+__global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
+                                          const T* __restrict__ cu, const T* __restrict__ cv,
+                                          const T* __restrict__ cw, const T* __restrict__ G,
+                                          const T* __restrict__ ob, const T* __restrict__ sf,
+                                          T* __restrict__ Pb, Out out) {
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
-  const int64_t xp = at(g, wrap_up(c.i, g.nx), c.j, c.k);
-  const int64_t yp = at(g, c.i, wrap_up(c.j, g.ny), c.k);
-  rev_limit_face(ulb[q], ut[q], bu[q], bd[q], bu[xp], bd[xp], &utb[q], &bub[q], &bdb[q],
-                 &bub[xp], &bdb[xp]);
-  rev_limit_face(vlb[q], vt[q], bu[q], bd[q], bu[yp], bd[yp], &vtb[q], &bub[q], &bdb[q],
-                 &bub[yp], &bdb[yp]);
-  if (c.k < g.nz - 1) {
-    const int64_t zp = q + g.pxy;
-    rev_limit_face(wlb[q], wt[q], bu[q], bd[q], bu[zp], bd[zp], &wtb[q], &bub[q], &bdb[q],
-                   &bub[zp], &bdb[zp]);
-  } else {
-    wtb[q] = T(0);  // closed top face
-  }
+  auto s_at = [&](int64_t n) { return S ? sf[n] : ob[n] * rcp(G[n]); };
+  const T sq = s_at(q), pc = P[q];
+  T acc = ob[q];
+  // "+" face to neighbour n with Courant number C (q is its left value)
+  auto plus = [&](int fam, int64_t n, T C) {
+    const T Fb = s_at(n) - sq;
+    const bool ge = ge0(C), le = le0(C);
+    T cb;
+    if (ge && le) {
+      cb = Fb * (pc + P[n]);
+    } else {
+      if (ge) acc += Fb * C;
+      cb = Fb * (ge ? pc : P[n]);
+    }
+    out(fam, q, n, cb);
+  };
+  // "-" face from neighbour n (q is its right value)
+  auto minus = [&](int64_t n, T C) {
+    if (!ge0(C)) acc += (sq - s_at(n)) * C;
+  };
+  const int64_t xp = at(g, wrap_up(c.i, g.nx), c.j, c.k), xm = at(g, wrap_dn(c.i, g.nx), c.j, c.k);
+  const int64_t yp = at(g, c.i, wrap_up(c.j, g.ny), c.k), ym = at(g, c.i, wrap_dn(c.j, g.ny), c.k);
+  plus(0, xp, cu[q]);
+  minus(xm, cu[xm]);
+  plus(1, yp, cv[q]);
+  minus(ym, cv[ym]);
+  if (c.k < g.nz - 1) plus(2, q + g.pxy, cw[q]);
+  else out.closed(q);
+  if (c.k > 0) minus(q - g.pxy, cw[q - g.pxy]);
+  Pb[q] = ADD_P ? Pb[q] + acc : acc;
 }
+
+// Velocity adjoints of the advance reverse into fields: added (ADD) or
+// stored (the fields' first writer; the closed top face gets 0).
+template <class T, bool ADD>
+struct VelOut {
+  T *ub, *vb, *wb;
+  __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t, T cb) const {
+    T* f = fam == 0 ? ub : fam == 1 ? vb : wb;
+    f[q] = ADD ? f[q] + cb : cb;
+  }
+  __device__ __forceinline__ void closed(int64_t q) const {
+    if (!ADD) wb[q] = T(0);
+  }
+};
+
+// The limiter's reverse applied to each limited-velocity adjoint as the
+// advance reverse produces it (the limiter reverse is its only reader):
+// stores the unlimited-velocity adjoints and scatters the beta adjoints.
+template <class T>
+struct LimitOut {
+  const T *ut, *vt, *wt, *bu, *bd;
+  T *utb, *vtb, *wtb, *bub, *bdb;
+  __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t n, T lb) const {
+    const T* U = fam == 0 ? ut : fam == 1 ? vt : wt;
+    T* Ub = fam == 0 ? utb : fam == 1 ? vtb : wtb;
+    rev_limit_face(lb, U[q], bu[q], bd[q], bu[n], bd[n], &Ub[q], &bub[q], &bdb[q], &bub[n],
+                   &bdb[n]);
+  }
+  __device__ __forceinline__ void closed(int64_t q) const { wtb[q] = T(0); }
+};
 
 // Reverse of the beta stage from the tape (beta-up/down and the
 // reciprocals ri = 1/(in+eps), ro = 1/(out+eps) of the forward):

@@ -29,6 +29,8 @@ struct mpdata_ctx {
   double* part;
   // fused kernel launch shape (chosen in init)
   int fused_ok, nchunks, kchunk;
+  // level-chunk lengths of the k-marching kernels (0: not chosen yet)
+  int kc_fwd, kc_rev;
   // device copies for the HOST-buffer call (allocated on its first use)
   void* hbuf;
   // adjoint scratch (allocated on the first adjoint call)
@@ -90,6 +92,35 @@ int halo_launch(mpdata_ctx* c, T* f, int kind) {
   return MPDATA_OK;
 }
 
+// Level-chunk length of a k-marching kernel; a CTA costs about (its levels
+// + 2 start-up levels).  A kernel bound by the SM's FP64 pipe shares it
+// among the CTAs resident on an SM, so its time goes as (CTAs per SM) x
+// (levels + 2); a latency-bound one runs its resident CTAs side by side, so
+// its time goes as (waves of resident CTAs) x (levels + 2).  Take the
+// cheapest length.  (For the FP32 pseudo-velocity reverse on 256x256x64 the
+// wave model ranks the measured chunk lengths 13 < 8 < 11, 22 < 16 < 32.)
+template <class K>
+int march_chunk(mpdata_ctx* c, K kernel, bool pipe_bound) {
+  namespace M = mpd::march;
+  const Geo& g = c->g;
+  int occ = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, M::TX * M::TY, 0);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  cudaGetLastError();
+  if (occ < 1 || sms < 1) return M::KC;
+  const long tiles = (long)((g.nx + M::TX - 1) / M::TX) * ((g.ny + M::TY - 1) / M::TY);
+  const long slots = pipe_bound ? sms : (long)occ * sms;
+  int best = g.nz;
+  double best_cost = 1e300;
+  for (int kc = 1; kc <= g.nz; ++kc) {
+    const long n = (g.nz + kc - 1) / kc;
+    const long waves = (tiles * n + slots - 1) / slots;
+    const double cost = (double)waves * (kc + 2);
+    if (cost < best_cost - 1e-9) { best_cost = cost; best = kc; }
+  }
+  return best;
+}
+
 // The pseudo-velocity stage: FP64 on the k-marching common-denominator
 // kernel (bound by FP64 instruction count), FP32 on the cell-parallel one.
 template <class T>
@@ -98,10 +129,11 @@ void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W
   const Geo& g = c->g;
   if constexpr (std::is_same<T, double>::value) {
     namespace M = mpd::march;
+    auto kern = M::march_kernel<double, M::PseudoMerged>;
+    if (!c->kc_fwd) c->kc_fwd = march_chunk(c, kern, true);
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-               (M::march_kernel<double, M::PseudoMerged><<<M::march_grid(g), dim3(M::TX, M::TY),
-                                                           0, c->stream>>>(
-                   g, P, U, V, W, G, M::PseudoMerged{ut, vt, wt}, M::KC)));
+               kern<<<M::march_grid(g, c->kc_fwd), dim3(M::TX, M::TY), 0, c->stream>>>(
+                   g, P, U, V, W, G, M::PseudoMerged{ut, vt, wt}, c->kc_fwd));
   } else {
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                mpd::staged::pseudo_kernel<T><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
@@ -409,7 +441,7 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
   char* base = (char*)c->adjbuf;
   T *p1b = (T*)(base + 0 * f), *p0b = (T*)(base + 1 * f);
   T *utb = (T*)(base + 2 * f), *vtb = (T*)(base + 3 * f), *wtb = (T*)(base + 4 * f);
-  T *ulb = (T*)(base + 5 * f), *vlb = (T*)(base + 6 * f), *wlb = (T*)(base + 7 * f);
+  // fields 5..7 are unused (the limited-velocity adjoints live in registers)
   T *bub = (T*)(base + 8 * f), *bdb = (T*)(base + 9 * f);
   T* wts = (T*)(base + 10 * f);  // 24 weight fields, g.total apart
   const size_t fb = (size_t)g.total * sizeof(T);
@@ -428,30 +460,27 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
   constexpr bool kPreS = std::is_same<T, double>::value;
   T* sf = wts;
   auto adv = [&](int stage, const T* P, const T* cu_, const T* cv_, const T* cw_, const T* ob,
-                 T* Pb, T* Cu, T* Cv, T* Cw, bool add_p, bool add_c) {
+                 T* Pb, auto out, auto add_p) {
+    constexpr bool kAddP = decltype(add_p)::value;
     if (kPreS)
       MPD_LAUNCH(c, stage, rev_scale_kernel<T><<<grid, kCellBlock, 0, s>>>(g, ob, G, sf));
-    if (!add_p && !add_c)
-      MPD_LAUNCH(c, stage, (rev_advance_gather_kernel<T, false, false, kPreS><<<grid, kCellBlock, 0, s>>>(
-                               g, P, cu_, cv_, cw_, G, ob, sf, Pb, Cu, Cv, Cw)));
-    else if (!add_p)
-      MPD_LAUNCH(c, stage, (rev_advance_gather_kernel<T, false, true, kPreS><<<grid, kCellBlock, 0, s>>>(
-                               g, P, cu_, cv_, cw_, G, ob, sf, Pb, Cu, Cv, Cw)));
-    else
-      MPD_LAUNCH(c, stage, (rev_advance_gather_kernel<T, true, true, kPreS><<<grid, kCellBlock, 0, s>>>(
-                               g, P, cu_, cv_, cw_, G, ob, sf, Pb, Cu, Cv, Cw)));
+    MPD_LAUNCH(c, stage,
+               (rev_advance_gather_kernel<T, kAddP, kPreS, decltype(out)>
+                <<<grid, kCellBlock, 0, s>>>(g, P, cu_, cv_, cw_, G, ob, sf, Pb, out)));
   };
+  using Store = std::false_type;
+  using Add = std::true_type;
   if (c->iord == 1) {
-    adv(MPDATA_STAGE_ADVANCE, psi, U, V, W, psib, p0b, ub, vb, wb, false, true);
+    adv(MPDATA_STAGE_ADVANCE, psi, U, V, W, psib, p0b, VelOut<T, true>{ub, vb, wb}, Store{});
   } else {
-    T* vel[3] = {c->nonosc ? tp.ul : tp.ut, c->nonosc ? tp.vl : tp.vt, c->nonosc ? tp.wl : tp.wt};
-    T* velb[3] = {c->nonosc ? ulb : utb, c->nonosc ? vlb : vtb, c->nonosc ? wlb : wtb};
-    adv(MPDATA_STAGE_ADVANCE, tp.p1, vel[0], vel[1], vel[2], psib, p1b, velb[0], velb[1],
-        velb[2], false, false);
+    if (c->nonosc) {  // the limiter reverse rides on the final advance reverse
+      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ul, tp.vl, tp.wl, psib, p1b,
+          LimitOut<T>{tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, utb, vtb, wtb, bub, bdb}, Store{});
+    } else {
+      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ut, tp.vt, tp.wt, psib, p1b,
+          VelOut<T, false>{utb, vtb, wtb}, Store{});
+    }
     if (c->nonosc) {
-      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, rev_limit_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                            g, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, ulb, vlb, wlb,
-                                            utb, vtb, wtb, bub, bdb));
       MPD_LAUNCH(c, MPDATA_STAGE_BETA, rev_beta_kernel<T><<<grid, kCellBlock, 0, s>>>(
                                            g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd,
                                            tp.ri, tp.ro, bub, bdb, p0b, p1b, utb, vtb, wtb));
@@ -459,24 +488,25 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
     {
       namespace M = mpd::march;
       if constexpr (std::is_same<T, float>::value) {
-        // one pass, shared accumulators; a k chunk's first and last levels are
-        // flushed by two CTAs, so longer chunks move less
-        constexpr int kc = 16;
+        // one pass, shared accumulators
+        auto kern = M::march_kernel<T, RevPseudoAcc<T>>;
+        if (!c->kc_rev) c->kc_rev = march_chunk(c, kern, false);
         const RevPseudoAcc<T> op{utb, vtb, wtb, p1b, ub, vb, wb};
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-                   (M::march_kernel<T, RevPseudoAcc<T>><<<M::march_grid(g, kc),
-                                                          dim3(M::TX, M::TY), 0, s>>>(
-                       g, tp.p1, U, V, W, G, op, kc)));
+                   kern<<<M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s>>>(
+                       g, tp.p1, U, V, W, G, op, c->kc_rev));
       } else {
+        auto kern = M::march_kernel<T, RevPseudo<T>>;
+        if (!c->kc_rev) c->kc_rev = march_chunk(c, kern, true);
         const RevPseudo<T> op{utb, vtb, wtb, wts, g.total, ub, vb, wb};
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-                   (M::march_kernel<T, RevPseudo<T>><<<M::march_grid(g), dim3(M::TX, M::TY),
-                                                        0, s>>>(g, tp.p1, U, V, W, G, op, M::KC)));
+                   kern<<<M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s>>>(
+                       g, tp.p1, U, V, W, G, op, c->kc_rev));
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                    rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, p1b, ub, vb, wb));
       }
     }
-    adv(MPDATA_STAGE_DONOR, psi, U, V, W, p1b, p0b, ub, vb, wb, true, true);
+    adv(MPDATA_STAGE_DONOR, psi, U, V, W, p1b, p0b, VelOut<T, true>{ub, vb, wb}, Add{});
   }
   MPD_CHECK_LAUNCH(c, "adjoint reverse kernels");
   cudaError_t e = cudaMemcpyAsync(psib, p0b, fb, cudaMemcpyDeviceToDevice, s);
