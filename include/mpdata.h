@@ -140,10 +140,11 @@ MPDATA_API int mpdata_step_host(mpdata_ctx *c, void *psi_host, const void *u_hos
  * G is held fixed.  The step's intermediates are recomputed from psi_n
  * (mpdata_adjoint_step_tape reuses a recorded tape instead); derivatives
  * follow the branches the forward takes (ties: max(a,b) = a if a >= b,
- * min(a,b) = a if a <= b, sign(0) = 0).  The pseudo-velocity reverse is a
- * gather (no atomics); the other reverse kernels add with atomics, so
- * results can differ in the last bits between runs.  The first call
- * allocates the adjoint scratch (44 fields).
+ * min(a,b) = a if a <= b, sign(0) = 0).  The advance reverses gather
+ * without atomics; the limiter and beta reverses, and the FP32
+ * pseudo-velocity reverse, add with atomics, so results can differ in the
+ * last bits between runs.  The first call allocates the adjoint scratch
+ * (46 fields).
  * Errors: EINVAL (iord > 2, null pointer), EALIGN, ENOMEM, ECUDA. */
 MPDATA_API int mpdata_adjoint_step(mpdata_ctx *c, const void *psi_n, const void *u,
                                    const void *v, const void *w, const void *g, void *psi_bar,
@@ -154,7 +155,8 @@ MPDATA_API int mpdata_adjoint_step(mpdata_ctx *c, const void *psi_n, const void 
  * unlimited and limited pseudo-velocities, the two betas and the two
  * reciprocals 1/(in+eps), 1/(out+eps) of the limiter's flux sums).
  * mpdata_step_tape runs one forward step psi_in -> psi_out (distinct, halo
- * filled) with the staged kernels and keeps its intermediates in the
+ * filled) -- with the fused kernel where mpdata_step would run it, else the
+ * staged kernels -- and keeps its intermediates (interior points) in the
  * caller-owned DEVICE buffer tape (16-byte aligned).
  * mpdata_adjoint_step_tape is mpdata_adjoint_step for a step whose tape
  * was recorded from the same psi_n, u, v, w, g.

@@ -80,7 +80,8 @@ __device__ __forceinline__ void rev_limit_face(T lb, T Ut, T buL, T bdL, T buR, 
 // C = 0), and hands the velocity adjoint Fb*(upwind value) (L + R at
 // C = 0) of each of its own three "+" faces to out(fam, q, n, cb) (n the
 // face's right cell), and its closed top face to out.closed(q).  ADD_P:
-// accumulate into Pb, else store (the field's first writer).  S: s comes
+// Pb = Pin + the gathered sum (Pin may be Pb), else Pb = the sum (the
+// field's first writer).  Pb must not alias ob.  S: s comes
 // precomputed in sf (FP64, where six neighbour reciprocals would cost 24
 // FP64 instructions), else it is formed from ob and G.
 template <class T, bool ADD_P, bool S, class Out>
@@ -88,7 +89,7 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
                                           const T* __restrict__ cu, const T* __restrict__ cv,
                                           const T* __restrict__ cw, const T* __restrict__ G,
                                           const T* __restrict__ ob, const T* __restrict__ sf,
-                                          T* __restrict__ Pb, Out out) {
+                                          const T* Pin, T* Pb, Out out) {
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
@@ -121,7 +122,7 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
   if (c.k < g.nz - 1) plus(2, q + g.pxy, cw[q]);
   else out.closed(q);
   if (c.k > 0) minus(q - g.pxy, cw[q - g.pxy]);
-  Pb[q] = ADD_P ? Pb[q] + acc : acc;
+  Pb[q] = ADD_P ? Pin[q] + acc : acc;
 }
 
 // Velocity adjoints of the advance reverse into fields: added (ADD) or

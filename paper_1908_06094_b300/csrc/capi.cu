@@ -82,12 +82,18 @@ bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 dim3 cell_grid(const Geo& g) { return dim3((g.nx + 31) / 32, (g.ny + 7) / 8, g.nz); }
 const dim3 kCellBlock(32, 8, 1);
 
+// Grid of the halo kernels: one thread per halo cell (with the interior
+// top level of a WFACE fill).
+dim3 halo_grid(const Geo& g) {
+  const int64_t plane = g.px * (int64_t)(g.ny + 2 * g.h);
+  const int64_t n = (2 * g.h + 1) * plane + (int64_t)g.nz * 2 * g.h * (g.px + g.ny);
+  return dim3((unsigned)((n + 255) / 256));
+}
+
 template <class T>
 int halo_launch(mpdata_ctx* c, T* f, int kind) {
-  int64_t n = c->g.total;
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > 148 * 16) blocks = 148 * 16;
-  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_kernel<T><<<blocks, 256, 0, c->stream>>>(c->g, f, kind));
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO,
+             mpd::halo_kernel<T><<<halo_grid(c->g), 256, 0, c->stream>>>(c->g, f, kind));
   MPD_CHECK_LAUNCH(c, "halo_kernel");
   return MPDATA_OK;
 }
@@ -383,11 +389,9 @@ Tape<T> tape_view(const mpdata_ctx* c, void* base) {
 
 template <class T>
 int halo_fold_launch(mpdata_ctx* c, T* f) {
-  int64_t n = c->g.total;
-  int blocks = (int)((n + 255) / 256);
-  if (blocks > 148 * 16) blocks = 148 * 16;
-  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_fold_kernel<T><<<blocks, 256, 0, c->stream>>>(c->g, f));
-  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_zero_kernel<T><<<blocks, 256, 0, c->stream>>>(c->g, f));
+  const dim3 hg = halo_grid(c->g);
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_fold_kernel<T><<<hg, 256, 0, c->stream>>>(c->g, f));
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_zero_kernel<T><<<hg, 256, 0, c->stream>>>(c->g, f));
   MPD_CHECK_LAUNCH(c, "halo adjoint fold");
   return MPDATA_OK;
 }
@@ -460,24 +464,25 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
   constexpr bool kPreS = std::is_same<T, double>::value;
   T* sf = wts;
   auto adv = [&](int stage, const T* P, const T* cu_, const T* cv_, const T* cw_, const T* ob,
-                 T* Pb, auto out, auto add_p) {
+                 const T* Pin, T* Pb, auto out, auto add_p) {
     constexpr bool kAddP = decltype(add_p)::value;
     if (kPreS)
       MPD_LAUNCH(c, stage, rev_scale_kernel<T><<<grid, kCellBlock, 0, s>>>(g, ob, G, sf));
     MPD_LAUNCH(c, stage,
                (rev_advance_gather_kernel<T, kAddP, kPreS, decltype(out)>
-                <<<grid, kCellBlock, 0, s>>>(g, P, cu_, cv_, cw_, G, ob, sf, Pb, out)));
+                <<<grid, kCellBlock, 0, s>>>(g, P, cu_, cv_, cw_, G, ob, sf, Pin, Pb, out)));
   };
   using Store = std::false_type;
   using Add = std::true_type;
   if (c->iord == 1) {
-    adv(MPDATA_STAGE_ADVANCE, psi, U, V, W, psib, p0b, VelOut<T, true>{ub, vb, wb}, Store{});
+    adv(MPDATA_STAGE_ADVANCE, psi, U, V, W, psib, nullptr, p0b, VelOut<T, true>{ub, vb, wb},
+        Store{});
   } else {
     if (c->nonosc) {  // the limiter reverse rides on the final advance reverse
-      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ul, tp.vl, tp.wl, psib, p1b,
+      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ul, tp.vl, tp.wl, psib, nullptr, p1b,
           LimitOut<T>{tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, utb, vtb, wtb, bub, bdb}, Store{});
     } else {
-      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ut, tp.vt, tp.wt, psib, p1b,
+      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ut, tp.vt, tp.wt, psib, nullptr, p1b,
           VelOut<T, false>{utb, vtb, wtb}, Store{});
     }
     if (c->nonosc) {
@@ -506,11 +511,17 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
                    rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, p1b, ub, vb, wb));
       }
     }
-    adv(MPDATA_STAGE_DONOR, psi, U, V, W, p1b, p0b, VelOut<T, true>{ub, vb, wb}, Add{});
+    // psib (read last by the final advance reverse) takes the result directly
+    adv(MPDATA_STAGE_DONOR, psi, U, V, W, p1b, p0b, psib, VelOut<T, true>{ub, vb, wb}, Add{});
+  }
+  if (c->iord == 1) {  // there the reverse read psib while writing p0b
+    cudaError_t e = cudaMemcpyAsync(psib, p0b, fb, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(c, e, "adjoint result copy");
+  } else {  // psib's interior holds the result; its halo is cleared
+    MPD_LAUNCH(c, MPDATA_STAGE_HALO,
+               mpd::halo_zero_kernel<T><<<halo_grid(g), 256, 0, s>>>(g, psib));
   }
   MPD_CHECK_LAUNCH(c, "adjoint reverse kernels");
-  cudaError_t e = cudaMemcpyAsync(psib, p0b, fb, cudaMemcpyDeviceToDevice, s);
-  if (e != cudaSuccess) return cuda_fail(c, e, "adjoint result copy");
   return MPDATA_OK;
 }
 

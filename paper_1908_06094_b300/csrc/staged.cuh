@@ -179,66 +179,93 @@ __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restri
 
 }  // namespace staged
 
-// Halo fill of a padded field: periodic in i and j (corners included); in k
-// an edge copy (kind 0) or closed faces set to zero (kind 1, vertical-face
-// fields, which also zeroes the top face k = nz-1).
+// Halo kernels.  They visit halo cells only, one thread per cell of a 1D
+// enumeration (halo_count cells): first the levels that are all halo -- the
+// h levels below and above the interior, and with `top` the interior top
+// level too -- px * (ny+2h) cells each, then for every other interior level
+// its h-deep bands of rows below and above (2h * px cells) and of columns
+// left and right (2h * ny cells).
+struct HaloCell {
+  int ii, jj, kk;
+  bool whole;  // on an all-halo level
+};
+__device__ __forceinline__ int64_t halo_count(const Geo& g, bool top) {
+  const int64_t plane = g.px * (int64_t)(g.ny + 2 * g.h);
+  const int64_t band = 2 * (int64_t)g.h * (g.px + g.ny);
+  return (2 * g.h + top) * plane + (g.nz - top) * band;
+}
+__device__ __forceinline__ HaloCell halo_cell(const Geo& g, bool top, int64_t t) {
+  const int h = g.h, px = (int)g.px;
+  const int64_t plane = g.px * (int64_t)(g.ny + 2 * h);
+  const int64_t nwhole = (2 * h + top) * plane;
+  HaloCell c;
+  if (t < nwhole) {
+    const int w = (int)(t / plane), e = (int)(t % plane);
+    c.kk = w < h ? w - h : g.nz - top + (w - h);
+    c.ii = e % px - h;
+    c.jj = e / px - h;
+    c.whole = true;
+    return c;
+  }
+  const int64_t band = 2 * (int64_t)h * (g.px + g.ny);
+  const int64_t t2 = t - nwhole;
+  const int e = (int)(t2 % band);
+  c.kk = (int)(t2 / band);
+  c.whole = false;
+  const int nrow = 2 * h * px;
+  if (e < nrow) {
+    const int r = e / px;
+    c.ii = e % px - h;
+    c.jj = r < h ? r - h : g.ny + (r - h);
+  } else {
+    const int e2 = e - nrow, ci = e2 % (2 * h);
+    c.jj = e2 / (2 * h);
+    c.ii = ci < h ? ci - h : g.nx + (ci - h);
+  }
+  return c;
+}
+__device__ __forceinline__ int64_t padded_at(const Geo& g, const HaloCell& c) {
+  return g.off0 + (int64_t)c.kk * g.pxy + (int64_t)c.jj * g.px + c.ii;
+}
+// the interior value a halo cell copies (periodic in i, j; edge copy in k)
+__device__ __forceinline__ int64_t halo_source(const Geo& g, const HaloCell& c) {
+  const int is = ((c.ii % g.nx) + g.nx) % g.nx;
+  const int js = ((c.jj % g.ny) + g.ny) % g.ny;
+  const int ks = c.kk < 0 ? 0 : (c.kk >= g.nz ? g.nz - 1 : c.kk);
+  return at(g, is, js, ks);
+}
+
+// Fill: CELL (kind 0) periodic images in i and j, edge copy in k; WFACE
+// (kind 1) the same, except that the faces k < 0 and k >= nz-1 (the closed
+// bottom and top faces, interior included) are 0.
 template <class T>
 __global__ void halo_kernel(Geo g, T* __restrict__ f, int kind) {
-  const int64_t n = g.total;
-  const int64_t pyy = g.ny + 2 * (int64_t)g.h;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int ii = (int)(t % g.px) - g.h;
-    int jj = (int)((t / g.px) % pyy) - g.h;
-    int kk = (int)(t / g.pxy) - g.h;
-    bool inner = ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz;
-    if (kind == 1) {
-      if (kk < 0 || kk >= g.nz - 1) { f[t] = T(0); continue; }
-      if (inner) continue;
-    } else if (inner) {
-      continue;
-    }
-    int is = ((ii % g.nx) + g.nx) % g.nx;
-    int js = ((jj % g.ny) + g.ny) % g.ny;
-    int ks = kk < 0 ? 0 : (kk >= g.nz ? g.nz - 1 : kk);
-    f[t] = f[at(g, is, js, ks)];
-  }
+  const bool top = kind == 1;
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= halo_count(g, top)) return;
+  const HaloCell c = halo_cell(g, top, t);
+  const bool closed = kind == 1 && (c.kk < 0 || c.kk >= g.nz - 1);
+  f[padded_at(g, c)] = closed ? T(0) : f[halo_source(g, c)];
 }
 
 // Reverse of the CELL halo fill for an adjoint field: every halo entry was a
-// copy of an interior value, so its adjoint is added to that source.  A
-// second launch (halo_zero_kernel) then clears the halo.
+// copy of one interior value, so its adjoint is added to that value (atomic:
+// several halo entries copy the same corner values); a second launch
+// (halo_zero_kernel) then clears the halo.
 template <class T>
 __global__ void halo_fold_kernel(Geo g, T* __restrict__ f) {
-  const int64_t n = g.total;
-  const int64_t pyy = g.ny + 2 * (int64_t)g.h;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int ii = (int)(t % g.px) - g.h;
-    int jj = (int)((t / g.px) % pyy) - g.h;
-    int kk = (int)(t / g.pxy) - g.h;
-    if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz) continue;
-    const T v = f[t];
-    if (v == T(0)) continue;
-    int is = ((ii % g.nx) + g.nx) % g.nx;
-    int js = ((jj % g.ny) + g.ny) % g.ny;
-    int ks = kk < 0 ? 0 : (kk >= g.nz ? g.nz - 1 : kk);
-    atomicAdd(&f[at(g, is, js, ks)], v);
-  }
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= halo_count(g, false)) return;
+  const HaloCell c = halo_cell(g, false, t);
+  const T v = f[padded_at(g, c)];
+  if (v != T(0)) atomicAdd(&f[halo_source(g, c)], v);
 }
 
 template <class T>
 __global__ void halo_zero_kernel(Geo g, T* __restrict__ f) {
-  const int64_t n = g.total;
-  const int64_t pyy = g.ny + 2 * (int64_t)g.h;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    int ii = (int)(t % g.px) - g.h;
-    int jj = (int)((t / g.px) % pyy) - g.h;
-    int kk = (int)(t / g.pxy) - g.h;
-    if (ii >= 0 && ii < g.nx && jj >= 0 && jj < g.ny && kk >= 0 && kk < g.nz) continue;
-    f[t] = T(0);
-  }
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= halo_count(g, false)) return;
+  f[padded_at(g, halo_cell(g, false, t))] = T(0);
 }
 
 }  // namespace mpd
