@@ -58,16 +58,18 @@ __device__ __forceinline__ void rev_limit_face(T lb, T Ut, T buL, T bdL, T buR, 
   const T cneg = n_first ? n1 : bdR;
   const bool ge = ge0(Ut), le = le0(Ut);
   *Utb = lb * ((ge ? cpos : T(0)) + (le ? cneg : T(0)));  // the face's first writer
-  const T cpb = lb * (ge ? Ut : T(0)), cnb = lb * (le ? Ut : T(0));
-  if (p_first) {
-    if (p_is_bdL) aadd(bdLb, cpb);
+  // d/d(beta) of c * [Ut]+ (or [Ut]-) is lb * Ut on the branch Ut's sign
+  // takes, and exactly zero on the other one or when Ut or lb is zero: only
+  // non-zero adjoints are added
+  if (ge && le) return;
+  const T cb = lb * Ut;
+  if (ge0(cb) && le0(cb)) return;
+  if (ge) {
+    if (!p_first) aadd(buRb, cb);
+    else if (p_is_bdL) aadd(bdLb, cb);
   } else {
-    aadd(buRb, cpb);
-  }
-  if (n_first) {
-    if (n_is_buL) aadd(buLb, cnb);
-  } else {
-    aadd(bdRb, cnb);
+    if (!n_first) aadd(bdRb, cb);
+    else if (n_is_buL) aadd(buLb, cb);
   }
 }
 
