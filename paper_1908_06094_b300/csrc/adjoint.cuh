@@ -82,8 +82,9 @@ __device__ __forceinline__ void rev_limit_face(T lb, T Ut, T buL, T bdL, T buR, 
 // C = 0), and hands the velocity adjoint Fb*(upwind value) (L + R at
 // C = 0) of each of its own three "+" faces to out(fam, q, n, cb) (n the
 // face's right cell), and its closed top face to out.closed(q).  ADD_P:
-// Pb = Pin + the gathered sum (Pin may be Pb), else Pb = the sum (the
-// field's first writer).  Pb must not alias ob.  S: s comes
+// Pb = Pin + the gathered sum and Pin is cleared (its only reader; Pin and
+// Pb distinct), else Pb = the sum (the field's first writer).  Pb must not
+// alias ob.  S: s comes
 // precomputed in sf (FP64, where six neighbour reciprocals would cost 24
 // FP64 instructions), else it is formed from ob and G.
 template <class T, bool ADD_P, bool S, class Out>
@@ -91,7 +92,7 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
                                           const T* __restrict__ cu, const T* __restrict__ cv,
                                           const T* __restrict__ cw, const T* __restrict__ G,
                                           const T* __restrict__ ob, const T* __restrict__ sf,
-                                          const T* Pin, T* Pb, Out out) {
+                                          T* Pin, T* Pb, Out out) {
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
@@ -124,7 +125,12 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
   if (c.k < g.nz - 1) plus(2, q + g.pxy, cw[q]);
   else out.closed(q);
   if (c.k > 0) minus(q - g.pxy, cw[q - g.pxy]);
-  Pb[q] = ADD_P ? Pin[q] + acc : acc;
+  if (ADD_P) {
+    Pb[q] = Pin[q] + acc;
+    Pin[q] = T(0);
+  } else {
+    Pb[q] = acc;
+  }
 }
 
 // Velocity adjoints of the advance reverse into fields: added (ADD) or
@@ -172,7 +178,7 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
                                 const T* __restrict__ wt, const T* __restrict__ G,
                                 const T* __restrict__ bu, const T* __restrict__ bd,
                                 const T* __restrict__ rin, const T* __restrict__ rout,
-                                const T* __restrict__ bub, const T* __restrict__ bdb, T* P0b,
+                                T* __restrict__ bub, T* __restrict__ bdb, T* P0b,
                                 T* Pb, T* utb, T* vtb, T* wtb) {
   Cell c = cell_of(g);
   if (!c.ok) return;
@@ -180,6 +186,7 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
   const int64_t q = at(g, i, j, k);
   const T ab = bub[q], db = bdb[q];
   if (ge0(ab) && le0(ab) && ge0(db) && le0(db)) return;
+  bub[q] = bdb[q] = T(0);  // the only reader: leave them zero for the next step
   const int64_t nb[6] = {at(g, wrap_dn(i, g.nx), j, k), at(g, wrap_up(i, g.nx), j, k),
                          at(g, i, wrap_dn(j, g.ny), k), at(g, i, wrap_up(j, g.ny), k),
                          at(g, i, j, clampk(k - 1, g.nz)), at(g, i, j, clampk(k + 1, g.nz))};

@@ -31,6 +31,9 @@ struct mpdata_ctx {
   int fused_ok, nchunks, kchunk;
   // level-chunk lengths of the k-marching kernels (0: not chosen yet)
   int kc_fwd, kc_rev;
+  // the adjoint's accumulators (psi^n-bar, beta adjoints) are known to be
+  // zero: every reverse step leaves them so (its readers clear them)
+  bool adj_zero;
   // device copies for the HOST-buffer call (allocated on its first use)
   void* hbuf;
   // adjoint scratch (allocated on the first adjoint call)
@@ -450,21 +453,24 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
   T* wts = (T*)(base + 10 * f);  // 24 weight fields, g.total apart
   const size_t fb = (size_t)g.total * sizeof(T);
   // The gather-form advance reverses store their outputs; only the fields
-  // that atomic scatters reach first need clearing: p0b (beta-bound
-  // adjoints, then the donor reverse adds) and the beta adjoints.
-  if (c->iord >= 2) {
+  // that atomic scatters reach first must start at zero: p0b (beta-bound
+  // adjoints, then the donor reverse adds) and the beta adjoints.  Their
+  // only readers (the donor reverse, the beta reverse) clear them again, so
+  // they are cleared here only on the first step or after a failed one.
+  if (c->iord >= 2 && !c->adj_zero) {
     T* zero_list[3] = {p0b, bub, bdb};
-    for (int q = 0; q < (c->nonosc ? 3 : 1); ++q) {
+    for (int q = 0; q < 3; ++q) {
       cudaError_t e = cudaMemsetAsync(zero_list[q], 0, fb, s);
       if (e != cudaSuccess) return cuda_fail(c, e, "adjoint clear");
     }
   }
+  c->adj_zero = false;
   // gather-form advance reverse: FP32 forms s = ob/G on the fly, FP64 reads
   // it from a pre-pass (wts is free while the advance reverses run)
   constexpr bool kPreS = std::is_same<T, double>::value;
   T* sf = wts;
   auto adv = [&](int stage, const T* P, const T* cu_, const T* cv_, const T* cw_, const T* ob,
-                 const T* Pin, T* Pb, auto out, auto add_p) {
+                 T* Pin, T* Pb, auto out, auto add_p) {
     constexpr bool kAddP = decltype(add_p)::value;
     if (kPreS)
       MPD_LAUNCH(c, stage, rev_scale_kernel<T><<<grid, kCellBlock, 0, s>>>(g, ob, G, sf));
@@ -511,7 +517,8 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
                    rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, p1b, ub, vb, wb));
       }
     }
-    // psib (read last by the final advance reverse) takes the result directly
+    // psib (read last by the final advance reverse) takes the result
+    // directly; p0b is cleared as it is read
     adv(MPDATA_STAGE_DONOR, psi, U, V, W, p1b, p0b, psib, VelOut<T, true>{ub, vb, wb}, Add{});
   }
   if (c->iord == 1) {  // there the reverse read psib while writing p0b
@@ -522,6 +529,7 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
                mpd::halo_zero_kernel<T><<<halo_grid(g), 256, 0, s>>>(g, psib));
   }
   MPD_CHECK_LAUNCH(c, "adjoint reverse kernels");
+  c->adj_zero = true;
   return MPDATA_OK;
 }
 
