@@ -153,7 +153,8 @@ MPDATA_API int mpdata_adjoint_step(mpdata_ctx *c, const void *psi_n, const void 
 /* Taped steps: the adjoint without forward recomputation.
  * mpdata_tape_bytes gives the size of one step's tape (11 fields: psi1, the
  * unlimited and limited pseudo-velocities, the two betas and the two
- * reciprocals 1/(in+eps), 1/(out+eps) of the limiter's flux sums).
+ * reciprocals 1/(in+eps), 1/(out+eps) of the limiter's flux sums, which
+ * FP32 contexts leave unused).
  * mpdata_step_tape runs one forward step psi_in -> psi_out (distinct, halo
  * filled) -- with the fused kernel where mpdata_step would run it, else the
  * staged kernels -- and keeps its intermediates (interior points) in the

@@ -163,7 +163,7 @@ struct LimitOut {
   __device__ __forceinline__ void closed(int64_t q) const { wtb[q] = T(0); }
 };
 
-// Reverse of the beta stage from the tape (beta-up/down and the
+// Reverse of the beta stage from the tape (beta-up/down, and in FP64 the
 // reciprocals ri = 1/(in+eps), ro = 1/(out+eps) of the forward):
 //   beta_up = (hi - psi) G ri,  beta_dn = (psi - lo) G ro,
 // in = sum of incoming antidiffusive fluxes, out = outgoing.  A cell whose
@@ -202,16 +202,42 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
     if (!leq(lo, P0[n])) { lo = P0[n]; lop = &P0b[n]; }
     if (!leq(lo, P[n])) { lo = P[n]; lop = &Pb[n]; }
   }
-  const T gc = G[q], ri = rin[q], ro = rout[q];
+  const T pc = P[q];
+  const T* vel[3] = {ut, vt, wt};
+  T* velb[3] = {utb, vtb, wtb};
+  // the six face fluxes (0 through the closed bottom and top faces)
+  bool hp[3], hm[3];
+  T Cp[3], Cm[3], Pr[3], Pl[3], fp[3], fm[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    hp[d] = !(d == 2 && k == g.nz - 1);
+    hm[d] = !(d == 2 && k == 0);
+    Cp[d] = hp[d] ? vel[d][q] : T(0);
+    Pr[d] = P[nb[2 * d + 1]];
+    fp[d] = donor(pc, Pr[d], Cp[d]);
+    Cm[d] = hm[d] ? vel[d][nb[2 * d]] : T(0);
+    Pl[d] = P[nb[2 * d]];
+    fm[d] = donor(Pl[d], pc, Cm[d]);
+  }
+  T ri, ro;
+  if constexpr (sizeof(T) == 4) {
+    // FP32 re-forms 1/(in+eps), 1/(out+eps) from the fluxes, as the forward
+    // did (the same sums in the same order), instead of taping them
+    const T in = (pos(fm[0]) - neg(fp[0])) + (pos(fm[1]) - neg(fp[1])) + (pos(fm[2]) - neg(fp[2]));
+    const T ou = (pos(fp[0]) - neg(fm[0])) + (pos(fp[1]) - neg(fm[1])) + (pos(fp[2]) - neg(fm[2]));
+    ri = rcp(in + Eps<T>::v);
+    ro = rcp(ou + Eps<T>::v);
+  } else {
+    ri = rin[q];
+    ro = rout[q];
+  }
+  const T gc = G[q];
   const T x = ab * gc * ri, y = db * gc * ro;  // d beta_up/d hi, -d beta_dn/d lo
   aadd(hip, x);
   aadd(lop, -y);
   aadd(&Pb[q], y - x);
   const T inb = -ab * bu[q] * ri, outb = -db * bd[q] * ro;
   const T dio = outb - inb;
-  const T pc = P[q];
-  const T* vel[3] = {ut, vt, wt};
-  T* velb[3] = {utb, vtb, wtb};
   // reverse of F = donor(L, R, C) for the adjoint fb: only the upwind value
   // has a non-zero partial (both are 0 * fb when C == 0)
   auto rdonor = [&](T fb, T L, T R, T C, T* Lb, T* Rb, T* Cb) {
@@ -223,20 +249,17 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
     aadd(ge ? Lb : Rb, fb * C);
     aadd(Cb, fb * (ge ? L : R));
   };
+#pragma unroll
   for (int d = 0; d < 3; ++d) {
-    if (!(d == 2 && k == g.nz - 1)) {
+    if (hp[d]) {
       const int64_t r = nb[2 * d + 1];
-      const T C = vel[d][q], pr = P[r];
-      const T fp = donor(pc, pr, C);
-      const T fpb = ge0(fp) ? (le0(fp) ? dio : outb) : -inb;
-      rdonor(fpb, pc, pr, C, &Pb[q], &Pb[r], &velb[d][q]);
+      const T fpb = ge0(fp[d]) ? (le0(fp[d]) ? dio : outb) : -inb;
+      rdonor(fpb, pc, Pr[d], Cp[d], &Pb[q], &Pb[r], &velb[d][q]);
     }
-    if (!(d == 2 && k == 0)) {
+    if (hm[d]) {
       const int64_t l = nb[2 * d];
-      const T C = vel[d][l], pl = P[l];
-      const T fm = donor(pl, pc, C);
-      const T fmb = ge0(fm) ? (le0(fm) ? -dio : inb) : -outb;
-      rdonor(fmb, pl, pc, C, &Pb[l], &Pb[q], &velb[d][l]);
+      const T fmb = ge0(fm[d]) ? (le0(fm[d]) ? -dio : inb) : -outb;
+      rdonor(fmb, Pl[d], pc, Cm[d], &Pb[l], &Pb[q], &velb[d][l]);
     }
   }
 }

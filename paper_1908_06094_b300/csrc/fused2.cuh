@@ -48,11 +48,12 @@ struct Layout {
 };
 
 // Where a taped step also writes the intermediates of its own cells (the
-// adjoint's tape): psi1, Ut, Vt, Wt, beta-up, beta-down, 1/(in+eps),
-// 1/(out+eps) and the limited Ul, Vl, Wl, all padded fields like psi.
+// adjoint's tape): psi1, Ut, Vt, Wt, beta-up, beta-down and the limited Ul,
+// Vl, Wl, all padded fields like psi.  (The FP32 beta reverse re-forms the
+// reciprocals 1/(in+eps), 1/(out+eps) that the staged FP64 tape keeps.)
 template <class T>
 struct TapeOut {
-  T *p1, *ut, *vt, *wt, *bu, *bd, *ri, *ro, *ul, *vl, *wl;
+  T *p1, *ut, *vt, *wt, *bu, *bd, *ul, *vl, *wl;
 };
 
 template <class T, int TX, int TY, bool LIMIT, bool TAPE = false>
@@ -131,7 +132,6 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   T utA = zero, vtA = zero, utB = zero, vtB = zero;  // Ut, Vt at t, t+1
   T wtA = zero, wtB = zero;              // Wt at faces t+1/2, t+3/2
   T buA = zero, bdA = zero, buB = zero, bdB = zero;  // betas at t, t+1
-  T riA = zero, roA = zero, riB = zero, roB = zero;  // their 1/(in+eps), 1/(out+eps) (tape)
   T fzA = zero, fzB = zero;              // vertical fluxes at faces t-1/2, t+1/2
 
   __syncthreads();  // the shared memory may still be read by a previous tile
@@ -241,10 +241,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T fzm = donor(qm, q1, wtA);  // wtA = 0 on the bottom face
       const T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
       const T ou = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
-      const T ri = rcp(in + eps), ro = rcp(ou + eps);
-      buB = (hi - q1) * g1 * ri;
-      bdB = (q1 - lo) * g1 * ro;
-      if (TAPE) { riB = ri; roB = ro; }
+      buB = (hi - q1) * g1 * rcp(in + eps);
+      bdB = (q1 - lo) * g1 * rcp(ou + eps);
       sm[L::BUS + (b & 1) * L::SN + s2] = buB;
       sm[L::BDS + (b & 1) * L::SN + s2] = bdB;
     }
@@ -275,8 +273,6 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         if (LIMIT) {
           tape.bu[q] = buA;
           tape.bd[q] = bdA;
-          tape.ri[q] = riA;
-          tape.ro[q] = roA;
           tape.ul[q] = u;
           tape.vl[q] = v;
           tape.wl[q] = w;
@@ -313,7 +309,6 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     q0 = q1; q1 = q2;
     utA = utB; vtA = vtB; wtA = wtB;
     buA = buB; bdA = bdB;
-    if (TAPE) { riA = riB; roA = roB; }
     fzA = fzB;
     // The next iteration publishes into slots nobody reads after this point
     // of the current one; its first barrier orders the rest.
