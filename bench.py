@@ -566,6 +566,28 @@ def run_reference(args, wl_name):
                     "d2h_bytes_per_step": 0}}
 
 
+def adjoint_probe(dtype_name: str):
+    """The adjoint configuration's grid (256x256x64 lat-lon flow) through the
+    public autograd path, twice: 4 steps with checkpoints every 2, then
+    backward of sum(out^2).  Sized for a profiler's launch list."""
+    import torch
+    import synth
+    from paper_1908_06094_b300 import MPDATA, mpdata_run
+    dt = torch.float64 if dtype_name == "f64" else torch.float32
+    c = synth.latlon_3d(256, 256, 64, seed=1234)
+    h = 2
+    d = [torch.from_numpy(synth.pad(x, h)).to("cuda", dt).contiguous()
+         for x in (c.psi, c.u, c.v, c.w, c.g)]
+    m = MPDATA(c.nx, c.ny, c.nz, halo=h, dtype=dt)
+    for _ in range(2):
+        x = [t.clone().requires_grad_(True) for t in d[:4]]
+        out = mpdata_run(m, *x, d[4], 4, 2)
+        torch.sum(out * out).backward()
+    torch.cuda.synchronize()
+    m.close()
+    print("adjoint probe ok", flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -577,7 +599,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e and CPU-baseline legs")
+    ap.add_argument("--adjoint-probe", choices=["f64", "f32"], default=None,
+                    help="run a short adjoint workload for a profiler's launch list and exit")
     args = ap.parse_args()
+    if args.adjoint_probe:
+        adjoint_probe(args.adjoint_probe)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     out = run_reference(args, args.workload) if args.impl == "reference" else \
