@@ -407,8 +407,8 @@ int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const
               const T* G, Tape<T> tp) {
   using namespace mpd::staged;
   if (use_fused(c)) {  // the fused step writes the tape and the output's halo itself
-    const mpd::fused2::TapeOut<T> to{tp.p1, tp.ut, tp.vt, tp.wt, tp.bu,
-                                     tp.bd, tp.ul, tp.vl, tp.wl};
+    const mpd::fused2::TapeOut<T> to{tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd,
+                                     tp.ri, tp.ro, tp.ul, tp.vl, tp.wl};
     return fused_launch<T>(c, psi, out, U, V, W, G, &to);
   }
   const Geo& g = c->g;

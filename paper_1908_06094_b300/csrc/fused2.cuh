@@ -48,13 +48,15 @@ struct Layout {
 };
 
 // Where a taped step also writes the intermediates of its own cells (the
-// adjoint's tape): psi1, Ut, Vt, Wt, beta-up, beta-down and the limited Ul,
-// Vl, Wl, all padded fields like psi.  (The FP32 beta reverse re-forms the
-// reciprocals 1/(in+eps), 1/(out+eps) that the staged FP64 tape keeps.)
+// adjoint's tape): psi1, Ut, Vt, Wt, beta-up, beta-down, the limited Ul, Vl,
+// Wl and, in FP64 only, the reciprocals 1/(in+eps), 1/(out+eps) (the FP32
+// beta reverse re-forms them), all padded fields like psi.
 template <class T>
 struct TapeOut {
-  T *p1, *ut, *vt, *wt, *bu, *bd, *ul, *vl, *wl;
+  T *p1, *ut, *vt, *wt, *bu, *bd, *ri, *ro, *ul, *vl, *wl;
 };
+// whether the tape keeps the limiter's reciprocals
+template <class T> struct TapesReciprocals { static constexpr bool v = sizeof(T) == 8; };
 
 template <class T, int TX, int TY, bool LIMIT, bool TAPE = false>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
@@ -132,6 +134,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   T utA = zero, vtA = zero, utB = zero, vtB = zero;  // Ut, Vt at t, t+1
   T wtA = zero, wtB = zero;              // Wt at faces t+1/2, t+3/2
   T buA = zero, bdA = zero, buB = zero, bdB = zero;  // betas at t, t+1
+  constexpr bool kTapeR = TAPE && TapesReciprocals<T>::v;
+  T riA = zero, roA = zero, riB = zero, roB = zero;  // their 1/(in+eps), 1/(out+eps) (FP64 tape)
   T fzA = zero, fzB = zero;              // vertical fluxes at faces t-1/2, t+1/2
 
   __syncthreads();  // the shared memory may still be read by a previous tile
@@ -241,8 +245,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T fzm = donor(qm, q1, wtA);  // wtA = 0 on the bottom face
       const T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
       const T ou = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
-      buB = (hi - q1) * g1 * rcp(in + eps);
-      bdB = (q1 - lo) * g1 * rcp(ou + eps);
+      const T ri = rcp(in + eps), ro = rcp(ou + eps);
+      buB = (hi - q1) * g1 * ri;
+      bdB = (q1 - lo) * g1 * ro;
+      if (kTapeR) { riB = ri; roB = ro; }
       sm[L::BUS + (b & 1) * L::SN + s2] = buB;
       sm[L::BDS + (b & 1) * L::SN + s2] = bdB;
     }
@@ -273,6 +279,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         if (LIMIT) {
           tape.bu[q] = buA;
           tape.bd[q] = bdA;
+          if (kTapeR) {
+            tape.ri[q] = riA;
+            tape.ro[q] = roA;
+          }
           tape.ul[q] = u;
           tape.vl[q] = v;
           tape.wl[q] = w;
@@ -309,6 +319,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     q0 = q1; q1 = q2;
     utA = utB; vtA = vtB; wtA = wtB;
     buA = buB; bdA = bdB;
+    if (kTapeR) { riA = riB; roA = roB; }
     fzA = fzB;
     // The next iteration publishes into slots nobody reads after this point
     // of the current one; its first barrier orders the rest.

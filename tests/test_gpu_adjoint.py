@@ -31,9 +31,15 @@ def _device():
     build.build()
 
 
-def _gpu_adjoint(c, iord, nonosc, nsteps, dy, dtype=torch.float64):
+VARIANTS = {"fused": 0, "staged": 1, "auto": 2}
+
+
+def _gpu_adjoint(c, iord, nonosc, nsteps, dy, dtype=torch.float64, variant="auto"):
+    """The adjoint of nsteps steps through the C ABI.  variant chooses the
+    kernels of the forward and taped steps (fused / staged / auto)."""
     from paper_1908_06094_b300 import MPDATA, _capi
     m = MPDATA(c.nx, c.ny, c.nz, halo=H, iord=iord, nonoscillatory=nonosc, dtype=dtype)
+    m.set_variant(VARIANTS[variant])
     d = [to_dev(synth.pad(x, H), dtype) for x in (c.psi, c.u, c.v, c.w, c.g)]
     states = [d[0].clone()]
     for _ in range(nsteps - 1):
@@ -55,29 +61,38 @@ def _gpu_adjoint(c, iord, nonosc, nsteps, dy, dtype=torch.float64):
 @pytest.mark.parametrize("shape", [(9, 8, 5), (21, 13, 7), (37, 30, 3)])
 @pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1)])
 @pytest.mark.parametrize("nsteps", [1, 3])
-def test_adjoint_parity_f64(shape, iord, nonosc, nsteps):
+@pytest.mark.parametrize("variant", ["staged", "fused"])
+def test_adjoint_parity_f64(shape, iord, nonosc, nsteps, variant):
+    """FP64 adjoint against the oracle's, with the taped forward on the staged
+    kernels (the FP64 default) and on the fused kernel."""
     nx, ny, nz = shape
     c = synth.random_case(nx, ny, nz, seed=nx + 100 * nz, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
     rng = np.random.default_rng(5)
     dy = synth.pad(rng.standard_normal(c.psi.shape), H)
     P = [synth.pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
     ref = oracle.adjoint(*P, dy, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps)
-    got = _gpu_adjoint(c, iord, nonosc, nsteps, dy)
+    got = _gpu_adjoint(c, iord, nonosc, nsteps, dy, variant=variant)
     for name, a, b in zip(("psi_bar", "u_bar", "v_bar", "w_bar"), got, ref):
         err = rel_err(synth.interior(a, H), synth.interior(b, H))
         assert err <= ADJ_TOL * nsteps, (name, err)
 
 
-def test_adjoint_parity_f32_against_f64_oracle():
-    """FP32 adjoint on FP32-rounded inputs against the FP64 oracle adjoint."""
-    c = synth.random_case(21, 13, 7, seed=3, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
+@pytest.mark.parametrize("shape", [(9, 8, 5), (21, 13, 7), (40, 35, 6)])
+@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("variant", ["fused", "staged"])
+def test_adjoint_parity_f32_against_f64_oracle(shape, iord, nonosc, variant):
+    """FP32 adjoint on FP32-rounded inputs against the FP64 oracle adjoint,
+    with the taped forward on the fused kernel (the FP32 default) and on the
+    staged kernels; tiles are ragged in i and j."""
+    nx, ny, nz = shape
+    c = synth.random_case(nx, ny, nz, seed=3 + nx, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
     for k in ("psi", "u", "v", "w", "g"):
         setattr(c, k, getattr(c, k).astype(np.float32).astype(np.float64))
     rng = np.random.default_rng(6)
     dy = synth.pad(rng.standard_normal(c.psi.shape), H).astype(np.float32).astype(np.float64)
     P = [synth.pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
-    ref = oracle.adjoint(*P, dy, h=H, iord=2, nonosc=1, nsteps=2)
-    got = _gpu_adjoint(c, 2, 1, 2, dy, dtype=torch.float32)
+    ref = oracle.adjoint(*P, dy, h=H, iord=iord, nonosc=nonosc, nsteps=2)
+    got = _gpu_adjoint(c, iord, nonosc, 2, dy, dtype=torch.float32, variant=variant)
     for a, b in zip(got, ref):
         assert rel_err(synth.interior(a, H), synth.interior(b, H)) <= 2e-4
 
