@@ -58,7 +58,7 @@ struct TapeOut {
 // whether the tape keeps the limiter's reciprocals
 template <class T> struct TapesReciprocals { static constexpr bool v = sizeof(T) == 8; };
 
-template <class T, int TX, int TY, bool LIMIT, bool TAPE = false>
+template <class T, int TX, int TY, bool LIMIT, bool TAPE = false, int UNROLL = 1>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
                                            const T* __restrict__ P0, const T* __restrict__ U,
                                            const T* __restrict__ V, const T* __restrict__ W,
@@ -120,7 +120,16 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   const int gi = i0 + x, gj = j0 + y;
   const bool writes = inT && gi < g.nx && gj < g.ny;
 
-  const int t0 = k0 - 5;
+  // The march starts 5 levels below the chunk (stages A..E are 5 levels
+  // deep).  With UNROLL = 2 or 4 the start is rounded down to a multiple of
+  // UNROLL and the levels run in groups of UNROLL, so the ring slot indices
+  // (t & 1, t & 3) are constants of each unrolled copy; the extra levels at
+  // the start are skipped by the stage guards.  Measured on the B300: the
+  // single-domain kernel is fastest at 1 (1.10 ms, against 1.19 at 4 and
+  // 1.29 at 2 on 512x512x128), the batch, with its many short chunks, at 4
+  // (2.65e10 against 2.44e10 tracer-updates/s).
+  static_assert(UNROLL == 1 || UNROLL == 2 || UNROLL == 4, "UNROLL: 1, 2 or 4");
+  const int t0 = (k0 - 5) & ~(UNROLL - 1);
   // register queues of the own column (values at planes t..t+3 / faces t..t+2)
   T p0 = ld(P0, t0, c0), p1 = ld(P0, t0 + 1, c0), p2 = ld(P0, t0 + 2, c0);
   T p3 = ld(P0, t0 + 3, c0), pn = ld(P0, t0 + 4, c0);
@@ -139,7 +148,11 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   T fzA = zero, fzB = zero;              // vertical fluxes at faces t-1/2, t+1/2
 
   __syncthreads();  // the shared memory may still be read by a previous tile
-  for (int t = t0; t < k1; ++t) {
+  for (int tg = t0; tg < k1; tg += UNROLL) {
+#pragma unroll
+  for (int u = 0; u < UNROLL; ++u) {
+    const int t = tg + u;
+    if (t >= k1) break;  // uniform over the CTA
     // ---- publish plane t+2 of psi^n, U, V, face t+1 of W, plane t+1 of G --
     {
       const int a = t + 2;
@@ -323,6 +336,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     fzA = fzB;
     // The next iteration publishes into slots nobody reads after this point
     // of the current one; its first barrier orders the rest.
+  }
   }
 }
 
