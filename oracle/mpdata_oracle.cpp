@@ -575,11 +575,8 @@ void adjoint_step(const Grid& g, int iord, int nonosc, const double* psi_in, con
                   const double* Vin, const double* Win, const double* Gin, double* psib,
                   double* ubar, double* vbar, double* wbar) {
   const long n = g.size();
-  std::vector<double> P1(n), ut(n), vt(n), wt(n), mx(n), mn(n), bu(n), bd(n), ul(n), vl(n), wl(n);
-  std::vector<double> tmp(n);
-  Stages st{P1.data(), ut.data(), vt.data(), wt.data(), mx.data(), mn.data(), bu.data(),
-            bd.data(), ul.data(), vl.data(), wl.data()};
-  mpdata_step<double>(g, iord, nonosc, psi_in, Uin, Vin, Win, Gin, tmp.data(), &st);
+  // forward, keeping the input state and the intermediates of every
+  // corrective pass m = 2..iord (pass m at index m-2)
   std::vector<double> P0(n), U(n), V(n), W(n), G(n);
   for (long q = 0; q < n; ++q) { P0[q] = psi_in[q]; U[q] = Uin[q]; V[q] = Vin[q]; W[q] = Win[q]; G[q] = Gin[q]; }
   fill_halo_periodic(P0.data(), g);
@@ -587,43 +584,100 @@ void adjoint_step(const Grid& g, int iord, int nonosc, const double* psi_in, con
   fill_halo_periodic(V.data(), g);
   fill_halo_periodic(G.data(), g);
   fill_halo_wface(W.data(), g);
-  std::vector<double> P0b(n, 0.0), P1b(n, 0.0), Ub(n, 0.0), Vb(n, 0.0), Wb(n, 0.0);
+  struct Pass {
+    std::vector<double> P, ut, vt, wt, bu, bd, ul, vl, wl;  // P: the pass's input state
+  };
+  std::vector<Pass> pass(iord >= 2 ? iord - 1 : 0);
+  std::vector<double> cur(n), nxt(n);
+  advance(g, P0.data(), U.data(), V.data(), W.data(), G.data(), cur.data());
+  fill_halo_periodic(cur.data(), g);
+  const double *cu = U.data(), *cv = V.data(), *cw = W.data();
+  for (int m = 2; m <= iord; ++m) {
+    Pass& p = pass[m - 2];
+    p.P = cur;
+    for (auto* f : {&p.ut, &p.vt, &p.wt, &p.bu, &p.bd, &p.ul, &p.vl, &p.wl}) f->assign(n, 0.0);
+    pseudo_velocity(g, p.P.data(), cu, cv, cw, G.data(), p.ut.data(), p.vt.data(), p.wt.data());
+    fill_halo_periodic(p.ut.data(), g);
+    fill_halo_periodic(p.vt.data(), g);
+    fill_halo_wface(p.wt.data(), g);
+    if (nonosc) {
+      std::vector<double> mx(n), mn(n);
+      limiter_betas(g, P0.data(), p.P.data(), p.ut.data(), p.vt.data(), p.wt.data(), G.data(),
+                    mx.data(), mn.data(), p.bu.data(), p.bd.data());
+      limit_velocities(g, p.ut.data(), p.vt.data(), p.wt.data(), p.bu.data(), p.bd.data(),
+                       p.ul.data(), p.vl.data(), p.wl.data());
+    } else {
+      p.ul = p.ut;
+      p.vl = p.vt;
+      p.wl = p.wt;
+    }
+    fill_halo_periodic(p.ul.data(), g);
+    fill_halo_periodic(p.vl.data(), g);
+    fill_halo_wface(p.wl.data(), g);
+    advance(g, p.P.data(), p.ul.data(), p.vl.data(), p.wl.data(), G.data(), nxt.data());
+    fill_halo_periodic(nxt.data(), g);
+    cur.swap(nxt);
+    cu = p.ul.data(); cv = p.vl.data(); cw = p.wl.data();
+  }
+
+  // reverse, pass by pass from the last; ob is the adjoint of the pass's
+  // output state, carry that of its limited velocities coming from the pass
+  // above (whose input velocities they were)
+  std::vector<double> P0b(n, 0.0), Ub(n, 0.0), Vb(n, 0.0), Wb(n, 0.0);
   std::vector<double> ob(n, 0.0);
   for (int k = 0; k < g.nz; ++k)
     for (int j = 0; j < g.ny; ++j)
       for (int i = 0; i < g.nx; ++i) ob[g.at(i, j, k)] = psib[g.at(i, j, k)];
-  if (iord == 1) {
-    rev_advance(g, P0.data(), U.data(), V.data(), W.data(), G.data(), ob.data(), P0b.data(),
-                Ub.data(), Vb.data(), Wb.data());
-  } else {
+  std::vector<double> cuu(n, 0.0), cvv(n, 0.0), cww(n, 0.0);  // the carry
+  for (int m = iord; m >= 2; --m) {
+    Pass& p = pass[m - 2];
+    std::vector<double> Pb(n, 0.0);
+    std::vector<double> ulb = cuu, vlb = cvv, wlb = cww;
+    rev_advance(g, p.P.data(), p.ul.data(), p.vl.data(), p.wl.data(), G.data(), ob.data(),
+                Pb.data(), ulb.data(), vlb.data(), wlb.data());
+    rev_halo_periodic(ulb.data(), g);
+    rev_halo_periodic(vlb.data(), g);
+    rev_halo_wface(wlb.data(), g);
     std::vector<double> utb(n, 0.0), vtb(n, 0.0), wtb(n, 0.0);
-    std::vector<double> ulb(n, 0.0), vlb(n, 0.0), wlb(n, 0.0), bub(n, 0.0), bdb(n, 0.0);
-    double* velb[3] = {nonosc ? ulb.data() : utb.data(), nonosc ? vlb.data() : vtb.data(),
-                       nonosc ? wlb.data() : wtb.data()};
-    const double* vel[3] = {nonosc ? ul.data() : ut.data(), nonosc ? vl.data() : vt.data(),
-                            nonosc ? wl.data() : wt.data()};
-    rev_advance(g, P1.data(), vel[0], vel[1], vel[2], G.data(), ob.data(), P1b.data(), velb[0],
-                velb[1], velb[2]);
-    rev_halo_periodic(velb[0], g);
-    rev_halo_periodic(velb[1], g);
-    rev_halo_wface(velb[2], g);
     if (nonosc) {
-      rev_limit(g, ut.data(), vt.data(), wt.data(), bu.data(), bd.data(), ulb.data(), vlb.data(),
-                wlb.data(), utb.data(), vtb.data(), wtb.data(), bub.data(), bdb.data());
+      std::vector<double> bub(n, 0.0), bdb(n, 0.0);
+      rev_limit(g, p.ut.data(), p.vt.data(), p.wt.data(), p.bu.data(), p.bd.data(), ulb.data(),
+                vlb.data(), wlb.data(), utb.data(), vtb.data(), wtb.data(), bub.data(),
+                bdb.data());
       rev_halo_periodic(bub.data(), g);
       rev_halo_periodic(bdb.data(), g);
-      rev_beta(g, P0.data(), P1.data(), ut.data(), vt.data(), wt.data(), G.data(), bub.data(),
-               bdb.data(), P0b.data(), P1b.data(), utb.data(), vtb.data(), wtb.data());
+      rev_beta(g, P0.data(), p.P.data(), p.ut.data(), p.vt.data(), p.wt.data(), G.data(),
+               bub.data(), bdb.data(), P0b.data(), Pb.data(), utb.data(), vtb.data(),
+               wtb.data());
       rev_halo_periodic(utb.data(), g);
       rev_halo_periodic(vtb.data(), g);
       rev_halo_wface(wtb.data(), g);
+    } else {
+      utb = ulb;
+      vtb = vlb;
+      wtb = wlb;
     }
-    rev_pseudo(g, P1.data(), U.data(), V.data(), W.data(), G.data(), utb.data(), vtb.data(),
-               wtb.data(), P1b.data(), Ub.data(), Vb.data(), Wb.data());
-    rev_halo_periodic(P1b.data(), g);
-    rev_advance(g, P0.data(), U.data(), V.data(), W.data(), G.data(), P1b.data(), P0b.data(),
-                Ub.data(), Vb.data(), Wb.data());
+    // the pass's input velocities: U, V, W for the first corrective pass,
+    // else the limited velocities of the pass below
+    const bool first = m == 2;
+    const Pass* below = first ? nullptr : &pass[m - 3];
+    std::vector<double> tu(n, 0.0), tv(n, 0.0), tw(n, 0.0);
+    rev_pseudo(g, p.P.data(), first ? U.data() : below->ul.data(),
+               first ? V.data() : below->vl.data(), first ? W.data() : below->wl.data(),
+               G.data(), utb.data(), vtb.data(), wtb.data(), Pb.data(),
+               first ? Ub.data() : tu.data(), first ? Vb.data() : tv.data(),
+               first ? Wb.data() : tw.data());
+    if (!first) {
+      rev_halo_periodic(tu.data(), g);
+      rev_halo_periodic(tv.data(), g);
+      rev_halo_wface(tw.data(), g);
+      cuu.swap(tu); cvv.swap(tv); cww.swap(tw);
+    }
+    rev_halo_periodic(Pb.data(), g);  // the pass's input state had its halo filled
+    ob.swap(Pb);
   }
+  rev_advance(g, P0.data(), U.data(), V.data(), W.data(), G.data(), ob.data(), P0b.data(),
+              Ub.data(), Vb.data(), Wb.data());
   rev_halo_periodic(P0b.data(), g);
   rev_halo_periodic(Ub.data(), g);
   rev_halo_periodic(Vb.data(), g);

@@ -65,8 +65,8 @@ MUTANTS = [
      "if (p_first) { if (p_is_bdL) *bdLb += cpb; } else { *buRb += cpb; }",
      "if (p_first) { if (p_is_bdL) *buRb += cpb; } else { *bdLb += cpb; }"),
     ("adjoint skips folding the psi1 halo",
-     "    rev_halo_periodic(P1b.data(), g);\n    rev_advance(",
-     "    rev_advance("),
+     "    rev_halo_periodic(Pb.data(), g);  // the pass's input state had its halo filled\n",
+     "\n"),
     ("adjoint breaks bound ties the other way",
      "if (!(hi >= P[c])) { hi = P[c]; hip = &Pb[c]; }",
      "if (!(hi > P[c])) { hi = P[c]; hip = &Pb[c]; }"),

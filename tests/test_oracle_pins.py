@@ -381,7 +381,8 @@ def _inner(a, b, h=H):
 
 
 @pytest.mark.parametrize("iord,nonosc,nsteps", [(1, 0, 1), (2, 0, 1), (2, 1, 1), (2, 1, 3),
-                                                (2, 0, 3)])
+                                                (2, 0, 3), (3, 0, 1), (3, 1, 1), (3, 1, 2),
+                                                (4, 1, 1)])
 def test_adjoint_dot_product_against_tlm(iord, nonosc, nsteps):
     """<L dx, dy> = <dx, L^T dy> with L the dual-number tangent-linear model
     (an independent derivative of the forward code) and L^T the hand-written
@@ -415,7 +416,8 @@ def test_adjoint_dot_product_on_rotating_cone():
     assert abs(lhs - rhs) <= 1e-12 * abs(lhs)
 
 
-def test_adjoint_gradient_matches_central_differences():
+@pytest.mark.parametrize("iord", [2, 3])
+def test_adjoint_gradient_matches_central_differences(iord):
     """dJ/dx from the reverse mode against central differences of
     J = sum (psi_T - psi_obs)^2 G, in random directions of psi_0 and of the
     Courant fields (relative error <= 1e-6, h = 1e-6 |x|)."""
@@ -425,12 +427,12 @@ def test_adjoint_gradient_matches_central_differences():
     obs = P[0] + pad(0.05 * rng.standard_normal(c.psi.shape), H)
 
     def J(p, u, v, w):
-        out = oracle.run(p, u, v, w, P[4], h=H, iord=2, nonosc=1, nsteps=3)
+        out = oracle.run(p, u, v, w, P[4], h=H, iord=iord, nonosc=1, nsteps=3)
         return float(np.sum(interior((out - obs) ** 2 * P[4], H)))
 
-    out = oracle.run(*P, h=H, iord=2, nonosc=1, nsteps=3)
+    out = oracle.run(*P, h=H, iord=iord, nonosc=1, nsteps=3)
     dJ = 2.0 * (out - obs) * P[4]
-    pb, ub, vb, wb = oracle.adjoint(*P, dJ, h=H, iord=2, nonosc=1, nsteps=3)
+    pb, ub, vb, wb = oracle.adjoint(*P, dJ, h=H, iord=iord, nonosc=1, nsteps=3)
     grads = [pb, ub, vb, wb]
     for trial in range(6):
         d = [pad(rng.standard_normal(c.psi.shape), H) for _ in range(4)]
