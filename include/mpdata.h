@@ -143,26 +143,27 @@ MPDATA_API int mpdata_step_host(mpdata_ctx *c, void *psi_host, const void *u_hos
  * min(a,b) = a if a <= b, sign(0) = 0).  The advance reverses gather
  * without atomics; the limiter and beta reverses, and the FP32
  * pseudo-velocity reverse, add with atomics, so results can differ in the
- * last bits between runs.  The first call allocates the adjoint scratch
- * (46 fields).
- * Errors: EINVAL (iord > 2, null pointer), EALIGN, ENOMEM, ECUDA. */
+ * last bits between runs.  Any iord: the corrective passes are reversed in
+ * turn.  The first call allocates the adjoint scratch (36 fields plus 11
+ * per corrective pass).
+ * Errors: EINVAL (null pointer), EALIGN, ENOMEM, ECUDA. */
 MPDATA_API int mpdata_adjoint_step(mpdata_ctx *c, const void *psi_n, const void *u,
                                    const void *v, const void *w, const void *g, void *psi_bar,
                                    void *u_bar, void *v_bar, void *w_bar);
 
 /* Taped steps: the adjoint without forward recomputation.
- * mpdata_tape_bytes gives the size of one step's tape (11 fields: psi1, the
+ * mpdata_tape_bytes gives the size of one step's tape: 11 fields for each
+ * corrective pass (max(iord-1, 1) blocks): the pass's input state, its
  * unlimited and limited pseudo-velocities, the two betas and the two
- * reciprocals 1/(in+eps), 1/(out+eps) of the limiter's flux sums, which
- * FP32 contexts leave unused).
+ * reciprocals 1/(in+eps), 1/(out+eps) of the limiter's flux sums (which
+ * FP32 contexts do not use).
  * mpdata_step_tape runs one forward step psi_in -> psi_out (distinct, halo
  * filled) -- with the fused kernel where mpdata_step would run it, else the
  * staged kernels -- and keeps its intermediates (interior points) in the
  * caller-owned DEVICE buffer tape (16-byte aligned).
  * mpdata_adjoint_step_tape is mpdata_adjoint_step for a step whose tape
  * was recorded from the same psi_n, u, v, w, g.
- * Errors: EINVAL (iord > 2, null pointer, psi_in == psi_out), EALIGN,
- * ENOMEM, ECUDA. */
+ * Errors: EINVAL (null pointer, psi_in == psi_out), EALIGN, ENOMEM, ECUDA. */
 MPDATA_API int mpdata_tape_bytes(mpdata_ctx *c, size_t *bytes);
 MPDATA_API int mpdata_step_tape(mpdata_ctx *c, const void *psi_in, void *psi_out,
                                 const void *u, const void *v, const void *w, const void *g,

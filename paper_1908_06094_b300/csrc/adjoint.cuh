@@ -134,12 +134,16 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
 }
 
 // Velocity adjoints of the advance reverse into fields: added (ADD) or
-// stored (the fields' first writer; the closed top face gets 0).
+// stored (the fields' first writer; the closed top face gets 0), with the
+// carried adjoints au, av, aw of the same velocities added when not null.
 template <class T, bool ADD>
 struct VelOut {
   T *ub, *vb, *wb;
+  const T *au, *av, *aw;
   __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t, T cb) const {
     T* f = fam == 0 ? ub : fam == 1 ? vb : wb;
+    const T* a = fam == 0 ? au : fam == 1 ? av : aw;
+    if (a) cb += a[q];
     f[q] = ADD ? f[q] + cb : cb;
   }
   __device__ __forceinline__ void closed(int64_t q) const {
@@ -150,11 +154,16 @@ struct VelOut {
 // The limiter's reverse applied to each limited-velocity adjoint as the
 // advance reverse produces it (the limiter reverse is its only reader):
 // stores the unlimited-velocity adjoints and scatters the beta adjoints.
+// au, av, aw (when not null): further adjoints of the same limited
+// velocities, from the next pass that took them as its input velocities.
 template <class T>
 struct LimitOut {
   const T *ut, *vt, *wt, *bu, *bd;
   T *utb, *vtb, *wtb, *bub, *bdb;
+  const T *au, *av, *aw;
   __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t n, T lb) const {
+    const T* a = fam == 0 ? au : fam == 1 ? av : aw;
+    if (a) lb += a[q];
     const T* U = fam == 0 ? ut : fam == 1 ? vt : wt;
     T* Ub = fam == 0 ? utb : fam == 1 ? vtb : wtb;
     rev_limit_face(lb, U[q], bu[q], bd[q], bu[n], bd[n], &Ub[q], &bub[q], &bdb[q], &bub[n],

@@ -355,34 +355,50 @@ int mass_launch(mpdata_ctx* c, const T* psi, const T* G, double* out) {
 
 // ------------------------------------------------------------- adjoint --
 
-// psi1, Ut, Vt, Wt, beta-up, beta-down, 1/(in+eps), 1/(out+eps), Ul, Vl, Wl
+// A step's tape: one block per corrective pass m = 2..iord (one block for
+// iord 1, unused): the pass's input state psi^(m-1), Ut, Vt, Wt,
+// beta-up, beta-down, 1/(in+eps), 1/(out+eps), Ul, Vl, Wl.
 constexpr int kTapeFields = 11;
-constexpr int kAdjFields = 10 + 24 + kTapeFields + 1;  // adjoints, weights, tape, psi^(n+1)
+int tape_passes(const mpdata_ctx* c) { return c->iord >= 2 ? c->iord - 1 : 1; }
+
+// The adjoint scratch: psi1-bar (two, one per alternate pass), psi^n-bar,
+// the pseudo-velocity adjoints, the carried limited-velocity adjoints
+// (iord >= 3), the beta adjoints, the FP64 pseudo-velocity weights, the
+// tape of mpdata_adjoint_step and its recomputed psi^(n+1).
+enum {
+  kAdjP1b = 0, kAdjP0b = 1, kAdjUtb = 2, kAdjCarry = 5, kAdjBub = 8, kAdjBdb = 9,
+  kAdjP1b2 = 10, kAdjWts = 11, kAdjTape = 35
+};
 
 size_t field_pad(const mpdata_ctx* c) {
   return ((size_t)c->g.total * c->esize + 255) & ~(size_t)255;
 }
 
+size_t adj_fields(const mpdata_ctx* c) {
+  return kAdjTape + (size_t)kTapeFields * tape_passes(c) + 1;
+}
+
 int adjoint_scratch(mpdata_ctx* c) {
   if (c->adjbuf) return MPDATA_OK;
-  if (cudaMalloc(&c->adjbuf, kAdjFields * field_pad(c)) != cudaSuccess) {
+  if (cudaMalloc(&c->adjbuf, adj_fields(c) * field_pad(c)) != cudaSuccess) {
     cudaGetLastError();
     c->adjbuf = nullptr;
     return MPDATA_ENOMEM;
   }
-  c->a_out = (char*)c->adjbuf + (size_t)(kAdjFields - 1) * field_pad(c);
+  c->a_out = (char*)c->adjbuf + (adj_fields(c) - 1) * field_pad(c);
   return MPDATA_OK;
 }
 
+// The block of corrective pass m (m = 2..iord) of the tape at base.
 template <class T>
 struct Tape {
   T *p1, *ut, *vt, *wt, *bu, *bd, *ri, *ro, *ul, *vl, *wl;
 };
 
 template <class T>
-Tape<T> tape_view(const mpdata_ctx* c, void* base) {
-  char* p = (char*)base;
+Tape<T> tape_view(const mpdata_ctx* c, const void* base, int m = 2) {
   const size_t f = field_pad(c);
+  char* p = (char*)base + (size_t)(m - 2) * kTapeFields * f;
   Tape<T> t;
   T** slots[kTapeFields] = {&t.p1, &t.ut, &t.vt, &t.wt, &t.bu, &t.bd,
                             &t.ri, &t.ro, &t.ul, &t.vl, &t.wl};
@@ -400,13 +416,14 @@ int halo_fold_launch(mpdata_ctx* c, T* f) {
 }
 
 // One forward step psi_in -> psi_out that keeps its intermediates in the
-// tape (iord 1 or 2): the fused kernel where the plain step would run it,
-// else the staged kernels.
+// tape at base: the fused kernel where the plain step would run it (iord
+// 2), else the staged kernels, pass by pass.
 template <class T>
 int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const T* W,
-              const T* G, Tape<T> tp) {
+              const T* G, const void* base) {
   using namespace mpd::staged;
   if (use_fused(c)) {  // the fused step writes the tape and the output's halo itself
+    const Tape<T> tp = tape_view<T>(c, base);
     const mpd::fused2::TapeOut<T> to{tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd,
                                      tp.ri, tp.ro, tp.ul, tp.vl, tp.wl};
     return fused_launch<T>(c, psi, out, U, V, W, G, &to);
@@ -419,25 +436,45 @@ int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const
   if (c->iord == 1) {
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, out));
   } else {
-    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, tp.p1));
-    pseudo_launch<T>(c, tp.p1, U, V, W, G, tp.ut, tp.vt, tp.wt);
-    if (c->nonosc) {
-      MPD_LAUNCH(c, MPDATA_STAGE_BETA, beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd, tp.ri, tp.ro));
-      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                            g, tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, fx, fy, fz, tp.ul, tp.vl, tp.wl));
-    } else {
-      MPD_LAUNCH(c, MPDATA_STAGE_LIMIT, flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt, fx, fy, fz));
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G,
+                                                             tape_view<T>(c, base, 2).p1));
+    const T *cu = U, *cv = V, *cw = W;  // the pass's input velocities
+    for (int m = 2; m <= c->iord; ++m) {
+      const Tape<T> tp = tape_view<T>(c, base, m);
+      T* dest = m == c->iord ? out : tape_view<T>(c, base, m + 1).p1;
+      pseudo_launch<T>(c, tp.p1, cu, cv, cw, G, tp.ut, tp.vt, tp.wt);
+      if (c->nonosc) {
+        MPD_LAUNCH(c, MPDATA_STAGE_BETA,
+                   beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G,
+                                                             tp.bu, tp.bd, tp.ri, tp.ro));
+        MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
+                   limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt,
+                                                                tp.bu, tp.bd, fx, fy, fz, tp.ul,
+                                                                tp.vl, tp.wl));
+        cu = tp.ul; cv = tp.vl; cw = tp.wl;
+      } else {
+        MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
+                   flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt, fx,
+                                                             fy, fz));
+        cu = tp.ut; cv = tp.vt; cw = tp.wt;
+      }
+      MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+                 advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, fx, fy, fz, G, dest));
     }
-    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, fx, fy, fz, G, out));
   }
   MPD_CHECK_LAUNCH(c, "taped forward step");
   return halo_launch<T>(c, out, MPDATA_HALO_CELL);
 }
 
-// The reverse kernels of one step, from its tape.
+// The reverse kernels of one step, from its tape: the corrective passes in
+// reverse order, then the donor pass.  Pass m's pseudo-velocity reverse
+// gives the adjoint of its input velocities: U, V, W (into ub, vb, wb) for
+// m = 2, else the limited velocities of pass m-1, carried to that pass's
+// advance reverse.
 template <class T>
-int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V, const T* W,
-                 const T* G, T* psib, T* ub, T* vb, T* wb) {
+int adjoint_tape(mpdata_ctx* c, const void* tape, const T* psi, const T* U, const T* V,
+                 const T* W, const T* G, T* psib, T* ub, T* vb, T* wb) {
   using namespace mpd::adj;
   int rc = adjoint_scratch(c);
   if (rc) return rc;
@@ -446,11 +483,13 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
   cudaStream_t s = c->stream;
   const size_t f = field_pad(c);
   char* base = (char*)c->adjbuf;
-  T *p1b = (T*)(base + 0 * f), *p0b = (T*)(base + 1 * f);
-  T *utb = (T*)(base + 2 * f), *vtb = (T*)(base + 3 * f), *wtb = (T*)(base + 4 * f);
-  // fields 5..7 are unused (the limited-velocity adjoints live in registers)
-  T *bub = (T*)(base + 8 * f), *bdb = (T*)(base + 9 * f);
-  T* wts = (T*)(base + 10 * f);  // 24 weight fields, g.total apart
+  auto field = [&](int q) { return (T*)(base + (size_t)q * f); };
+  T *p0b = field(kAdjP0b), *utb = field(kAdjUtb), *vtb = field(kAdjUtb + 1);
+  T* wtb = field(kAdjUtb + 2);
+  T *cub = field(kAdjCarry), *cvb = field(kAdjCarry + 1), *cwb = field(kAdjCarry + 2);
+  T *bub = field(kAdjBub), *bdb = field(kAdjBdb);
+  T* pbuf[2] = {field(kAdjP1b), field(kAdjP1b2)};  // psi^(m-1)-bar, alternating
+  T* wts = field(kAdjWts);                         // 24 weight fields, g.total apart
   const size_t fb = (size_t)g.total * sizeof(T);
   // The gather-form advance reverses store their outputs; only the fields
   // that atomic scatters reach first must start at zero: p0b (beta-bound
@@ -481,45 +520,68 @@ int adjoint_tape(mpdata_ctx* c, Tape<T> tp, const T* psi, const T* U, const T* V
   using Store = std::false_type;
   using Add = std::true_type;
   if (c->iord == 1) {
-    adv(MPDATA_STAGE_ADVANCE, psi, U, V, W, psib, nullptr, p0b, VelOut<T, true>{ub, vb, wb},
-        Store{});
+    adv(MPDATA_STAGE_ADVANCE, psi, U, V, W, psib, nullptr, p0b,
+        VelOut<T, true>{ub, vb, wb, nullptr, nullptr, nullptr}, Store{});
   } else {
-    if (c->nonosc) {  // the limiter reverse rides on the final advance reverse
-      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ul, tp.vl, tp.wl, psib, nullptr, p1b,
-          LimitOut<T>{tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, utb, vtb, wtb, bub, bdb}, Store{});
-    } else {
-      adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ut, tp.vt, tp.wt, psib, nullptr, p1b,
-          VelOut<T, false>{utb, vtb, wtb}, Store{});
-    }
-    if (c->nonosc) {
-      MPD_LAUNCH(c, MPDATA_STAGE_BETA, rev_beta_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                           g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu, tp.bd,
-                                           tp.ri, tp.ro, bub, bdb, p0b, p1b, utb, vtb, wtb));
-    }
-    {
+    const T* ob = psib;  // adjoint of the pass's output state
+    for (int m = c->iord; m >= 2; --m) {
+      const Tape<T> tp = tape_view<T>(c, tape, m);
+      T* Pb = pbuf[(c->iord - m) & 1];
+      // adjoint of this pass's limited velocities from the pass above
+      const bool carried = m < c->iord;
+      const T *au = carried ? cub : nullptr, *av = carried ? cvb : nullptr;
+      const T* aw = carried ? cwb : nullptr;
+      if (c->nonosc) {  // the limiter reverse rides on the final advance reverse
+        adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ul, tp.vl, tp.wl, ob, nullptr, Pb,
+            LimitOut<T>{tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, utb, vtb, wtb, bub, bdb, au, av, aw},
+            Store{});
+        MPD_LAUNCH(c, MPDATA_STAGE_BETA, rev_beta_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                                             g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu,
+                                             tp.bd, tp.ri, tp.ro, bub, bdb, p0b, Pb, utb, vtb,
+                                             wtb));
+      } else {
+        adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ut, tp.vt, tp.wt, ob, nullptr, Pb,
+            VelOut<T, false>{utb, vtb, wtb, au, av, aw}, Store{});
+      }
+      // the pass's input velocities and where their adjoints go
+      const bool first = m == 2;
+      const Tape<T> below = tape_view<T>(c, tape, first ? 2 : m - 1);
+      const T* iu = first ? U : (c->nonosc ? below.ul : below.ut);
+      const T* iv = first ? V : (c->nonosc ? below.vl : below.vt);
+      const T* iw = first ? W : (c->nonosc ? below.wl : below.wt);
+      T *tu = first ? ub : cub, *tv = first ? vb : cvb, *tw = first ? wb : cwb;
+      if (!first) {  // the carry was read above: clear it for the pass below
+        T* carry[3] = {cub, cvb, cwb};
+        for (int q = 0; q < 3; ++q) {
+          cudaError_t e = cudaMemsetAsync(carry[q], 0, fb, s);
+          if (e != cudaSuccess) return cuda_fail(c, e, "adjoint carry clear");
+        }
+      }
       namespace M = mpd::march;
       if constexpr (std::is_same<T, float>::value) {
         // one pass, shared accumulators
         auto kern = M::march_kernel<T, RevPseudoAcc<T>>;
         if (!c->kc_rev) c->kc_rev = march_chunk(c, kern, false);
-        const RevPseudoAcc<T> op{utb, vtb, wtb, p1b, ub, vb, wb};
+        const RevPseudoAcc<T> op{utb, vtb, wtb, Pb, tu, tv, tw};
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                    kern<<<M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s>>>(
-                       g, tp.p1, U, V, W, G, op, c->kc_rev));
+                       g, tp.p1, iu, iv, iw, G, op, c->kc_rev));
       } else {
         auto kern = M::march_kernel<T, RevPseudo<T>>;
         if (!c->kc_rev) c->kc_rev = march_chunk(c, kern, true);
-        const RevPseudo<T> op{utb, vtb, wtb, wts, g.total, ub, vb, wb};
+        const RevPseudo<T> op{utb, vtb, wtb, wts, g.total, tu, tv, tw};
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                    kern<<<M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s>>>(
-                       g, tp.p1, U, V, W, G, op, c->kc_rev));
+                       g, tp.p1, iu, iv, iw, G, op, c->kc_rev));
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-                   rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, p1b, ub, vb, wb));
+                   rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, Pb, tu, tv, tw));
       }
+      ob = Pb;
     }
     // psib (read last by the final advance reverse) takes the result
     // directly; p0b is cleared as it is read
-    adv(MPDATA_STAGE_DONOR, psi, U, V, W, p1b, p0b, psib, VelOut<T, true>{ub, vb, wb}, Add{});
+    adv(MPDATA_STAGE_DONOR, psi, U, V, W, ob, p0b, psib,
+        VelOut<T, true>{ub, vb, wb, nullptr, nullptr, nullptr}, Add{});
   }
   if (c->iord == 1) {  // there the reverse read psib while writing p0b
     cudaError_t e = cudaMemcpyAsync(psib, p0b, fb, cudaMemcpyDeviceToDevice, s);
@@ -539,11 +601,11 @@ int adjoint_step(mpdata_ctx* c, const T* psi, const T* U, const T* V, const T* W
                  T* psib, T* ub, T* vb, T* wb) {
   int rc = adjoint_scratch(c);
   if (rc) return rc;
-  Tape<T> tp = tape_view<T>(c, (char*)c->adjbuf + (size_t)(10 + 24) * field_pad(c));
+  const void* tape = (char*)c->adjbuf + (size_t)kAdjTape * field_pad(c);
   // the recomputed psi^(n+1) goes to the context's second psi scratch
   T* out = (T*)c->a_out;
-  if ((rc = step_tape<T>(c, psi, out, U, V, W, G, tp))) return rc;
-  return adjoint_tape<T>(c, tp, psi, U, V, W, G, psib, ub, vb, wb);
+  if ((rc = step_tape<T>(c, psi, out, U, V, W, G, tape))) return rc;
+  return adjoint_tape<T>(c, tape, psi, U, V, W, G, psib, ub, vb, wb);
 }
 
 int check_fields(const void* const* ptrs, int n) {
@@ -752,7 +814,6 @@ int mpdata_adjoint_step(mpdata_ctx* c, const void* psi_n, const void* u, const v
                         const void* w, const void* g, void* psi_bar, void* u_bar, void* v_bar,
                         void* w_bar) {
   if (!c) return MPDATA_EINVAL;
-  if (c->iord > 2) return MPDATA_EINVAL;
   const void* f[9] = {psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
   int rc = check_fields(f, 9);
   if (rc) return rc;
@@ -767,39 +828,37 @@ int mpdata_adjoint_step(mpdata_ctx* c, const void* psi_n, const void* u, const v
 
 int mpdata_tape_bytes(mpdata_ctx* c, size_t* bytes) {
   if (!c || !bytes) return MPDATA_EINVAL;
-  *bytes = kTapeFields * field_pad(c);
+  *bytes = (size_t)kTapeFields * tape_passes(c) * field_pad(c);
   return MPDATA_OK;
 }
 
 int mpdata_step_tape(mpdata_ctx* c, const void* psi_in, void* psi_out, const void* u,
                      const void* v, const void* w, const void* g, void* tape) {
-  if (!c || c->iord > 2) return MPDATA_EINVAL;
+  if (!c) return MPDATA_EINVAL;
   const void* f[7] = {psi_in, psi_out, u, v, w, g, tape};
   int rc = check_fields(f, 7);
   if (rc) return rc;
   if (psi_in == psi_out) return MPDATA_EINVAL;
   if (c->dtype == MPDATA_F64)
     return step_tape<double>(c, (const double*)psi_in, (double*)psi_out, (const double*)u,
-                             (const double*)v, (const double*)w, (const double*)g,
-                             tape_view<double>(c, tape));
+                             (const double*)v, (const double*)w, (const double*)g, tape);
   return step_tape<float>(c, (const float*)psi_in, (float*)psi_out, (const float*)u,
-                          (const float*)v, (const float*)w, (const float*)g,
-                          tape_view<float>(c, tape));
+                          (const float*)v, (const float*)w, (const float*)g, tape);
 }
 
 int mpdata_adjoint_step_tape(mpdata_ctx* c, const void* tape, const void* psi_n, const void* u,
                              const void* v, const void* w, const void* g, void* psi_bar,
                              void* u_bar, void* v_bar, void* w_bar) {
-  if (!c || c->iord > 2) return MPDATA_EINVAL;
+  if (!c) return MPDATA_EINVAL;
   const void* f[10] = {tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
   int rc = check_fields(f, 10);
   if (rc) return rc;
   if (c->dtype == MPDATA_F64)
-    return adjoint_tape<double>(c, tape_view<double>(c, (void*)tape), (const double*)psi_n,
+    return adjoint_tape<double>(c, tape, (const double*)psi_n,
                                 (const double*)u, (const double*)v, (const double*)w,
                                 (const double*)g, (double*)psi_bar, (double*)u_bar,
                                 (double*)v_bar, (double*)w_bar);
-  return adjoint_tape<float>(c, tape_view<float>(c, (void*)tape), (const float*)psi_n,
+  return adjoint_tape<float>(c, tape, (const float*)psi_n,
                              (const float*)u, (const float*)v, (const float*)w, (const float*)g,
                              (float*)psi_bar, (float*)u_bar, (float*)v_bar, (float*)w_bar);
 }

@@ -59,7 +59,7 @@ def _gpu_adjoint(c, iord, nonosc, nsteps, dy, dtype=torch.float64, variant="auto
 
 
 @pytest.mark.parametrize("shape", [(9, 8, 5), (21, 13, 7), (37, 30, 3)])
-@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1), (3, 0), (3, 1), (4, 1)])
 @pytest.mark.parametrize("nsteps", [1, 3])
 @pytest.mark.parametrize("variant", ["staged", "fused"])
 def test_adjoint_parity_f64(shape, iord, nonosc, nsteps, variant):
@@ -78,7 +78,7 @@ def test_adjoint_parity_f64(shape, iord, nonosc, nsteps, variant):
 
 
 @pytest.mark.parametrize("shape", [(9, 8, 5), (21, 13, 7), (40, 35, 6)])
-@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1)])
+@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1), (3, 1)])
 @pytest.mark.parametrize("variant", ["fused", "staged"])
 def test_adjoint_parity_f32_against_f64_oracle(shape, iord, nonosc, variant):
     """FP32 adjoint on FP32-rounded inputs against the FP64 oracle adjoint,
@@ -151,6 +151,25 @@ def test_checkpointing_does_not_change_the_gradient(ckpt, dtype):
     tol = 1e-12 if dtype == torch.float64 else 1e-5
     for a, b in zip(grads, [t.grad.cpu().double().numpy() for t in x2]):
         assert rel_err(a, b) <= tol
+    m.close()
+
+
+def test_autograd_iord3_against_oracle():
+    """The differentiable run at iord 3 (two corrective passes per step,
+    tapes of two blocks, checkpoints every 2 of 5 steps) against the oracle
+    adjoint of the same steps."""
+    from paper_1908_06094_b300 import MPDATA, mpdata_run
+    c = synth.random_case(21, 13, 7, seed=9, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
+    m = MPDATA(c.nx, c.ny, c.nz, halo=H, iord=3, nonoscillatory=True, dtype=torch.float64)
+    P = [synth.pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    rng = np.random.default_rng(10)
+    dy = synth.pad(rng.standard_normal(c.psi.shape), H)
+    x = [to_dev(a, torch.float64).requires_grad_(True) for a in P[:4]]
+    out = mpdata_run(m, *x, to_dev(P[4], torch.float64), 5, 2)
+    torch.sum(out * to_dev(dy, torch.float64)).backward()
+    ref = oracle.adjoint(*P, dy, h=H, iord=3, nonosc=1, nsteps=5)
+    for a, b in zip([t.grad.cpu().numpy() for t in x], ref):
+        assert rel_err(synth.interior(a, H), synth.interior(b, H)) <= 5 * ADJ_TOL
     m.close()
 
 
