@@ -165,6 +165,28 @@ def _dist():
     return ws, rank, local
 
 
+def replica_seed(rank: int) -> int:
+    """The seed of a rank's replica: every rank advances its own synthetic
+    problem of the same size (weak scaling, no data-path collective)."""
+    return 1234 + rank
+
+
+def job_throughput(ms_local: float, units_local: float, ws: int, device=None):
+    """Whole-job throughput over ws ranks: the units all ranks processed over
+    the slowest rank's time (ms), with the time and the units reduced across
+    the process group (MAX and SUM) when ws > 1.  Returns (units/s, ms)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t[1:].clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_local, units_local = float(mx.item()), float(sm.item())
+    return units_local / (ms_local / 1e3), ms_local
+
+
 # The sources a stage's dominant kernel is built and launched from: a DRAM
 # figure taken with ncu stays valid while these files are unchanged.
 STAGE_SOURCES = {
@@ -235,7 +257,7 @@ def run_ours(args, wl_name):
     wl = WORKLOADS[wl_name]
     dt = torch.float64 if wl["dtype"] == "f64" else torch.float32
     h = wl["halo"]
-    case = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=1234 + rank)
+    case = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=replica_seed(rank))
     padded = [synth.pad(x, h) for x in (case.psi, case.u, case.v, case.w, case.g)]
     if dt == torch.float32:
         padded = [x.astype(np.float32) for x in padded]
@@ -283,17 +305,12 @@ def run_ours(args, wl_name):
             stage_ms[name] = (t, k)
     _capi.mpdata_profile(m._ctx, False)
     m1 = mass_out.item()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    value, ms = job_throughput(ms, npts * args.steps, ws, dev)
     clocks = None
     if sampler:
         sampler.stop()
         clocks = sampler.summary(wall0, wall1)
 
-    value = ws * npts * args.steps / (ms / 1e3)
     out = None
     if rank == 0:
         hbm, peak_kind = _peaks()
