@@ -7,7 +7,8 @@ and it imports nothing from the library.
 
 All arrays are float64, C-contiguous, halo-padded [nz+2h][ny+2h][nx+2h].
 Inputs are read at interior points only; outputs are padded with their halos
-filled (periodic in i and j, edge copy in k).
+filled (periodic in i and j, edge copy in k).  ``kbc``: the vertical
+boundary, 0 zero-flux (closed top and bottom faces) or 1 periodic in k.
 
 Parity pins live in ``tests/test_oracle_pins.py``.  Parity unpinned: the exact
 values of the limited iord=2 field beyond what those invariants and closed
@@ -46,13 +47,13 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB) -> str:
 def _bind(path):
     lib = ctypes.CDLL(path)
     I = ctypes.c_int
-    lib.orc_fill_halo.argtypes = [I, I, I, I, I, _D]
-    lib.orc_run.argtypes = [I, I, I, I, I, I, I] + [_D] * 6 + [_D] * 11
-    lib.orc_pseudo_velocity.argtypes = [I, I, I, I] + [_D] * 8
+    lib.orc_fill_halo.argtypes = [I, I, I, I, I, I, _D]
+    lib.orc_run.argtypes = [I, I, I, I, I, I, I, I] + [_D] * 6 + [_D] * 11
+    lib.orc_pseudo_velocity.argtypes = [I, I, I, I, I] + [_D] * 8
     lib.orc_mass.argtypes = [I, I, I, I, _D, _D]
     lib.orc_mass.restype = ctypes.c_double
-    lib.orc_tlm.argtypes = [I, I, I, I, I, I, I] + [_D] * 11
-    lib.orc_adjoint.argtypes = [I, I, I, I, I, I, I] + [_D] * 9
+    lib.orc_tlm.argtypes = [I, I, I, I, I, I, I, I] + [_D] * 11
+    lib.orc_adjoint.argtypes = [I, I, I, I, I, I, I, I] + [_D] * 9
     return lib
 
 
@@ -93,15 +94,15 @@ def _dims(a, h):
     return nx, ny, nz
 
 
-def fill_halo(f: np.ndarray, h: int, kind: int = 0) -> np.ndarray:
+def fill_halo(f: np.ndarray, h: int, kind: int = 0, kbc: int = 0) -> np.ndarray:
     """Fill the halo of a padded field in place (kind 1: vertical faces)."""
     nx, ny, nz = _dims(f, h)
-    _load().orc_fill_halo(nx, ny, nz, h, kind, _p(f))
+    _load().orc_fill_halo(nx, ny, nz, h, kbc, kind, _p(f))
     return f
 
 
 def run(psi, u, v, w, g, h: int, iord: int = 2, nonosc: int = 1, nsteps: int = 1,
-        stages: bool = False):
+        stages: bool = False, kbc: int = 0):
     """nsteps MPDATA steps.  Returns psi^(n+nsteps) (padded), and with
     ``stages`` also a dict of the last corrective pass's intermediates."""
     nx, ny, nz = _dims(psi, h)
@@ -109,17 +110,18 @@ def run(psi, u, v, w, g, h: int, iord: int = 2, nonosc: int = 1, nsteps: int = 1
     out = np.zeros_like(arrs[0])
     names = ["psi1", "ut", "vt", "wt", "mx", "mn", "bu", "bd", "ul", "vl", "wl"]
     st = {k: np.zeros_like(arrs[0]) for k in names} if stages else {}
-    _load().orc_run(nx, ny, nz, h, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(out),
+    _load().orc_run(nx, ny, nz, h, kbc, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(out),
                     *[_p(st.get(k)) for k in names])
     return (out, st) if stages else out
 
 
-def pseudo_velocity(psi, u, v, w, g, h: int):
+def pseudo_velocity(psi, u, v, w, g, h: int, kbc: int = 0):
     """Antidiffusive pseudo-velocities (Ut, Vt, Wt) of field psi."""
     nx, ny, nz = _dims(psi, h)
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (psi, u, v, w, g)]
     ut, vt, wt = (np.zeros_like(arrs[0]) for _ in range(3))
-    _load().orc_pseudo_velocity(nx, ny, nz, h, *[_p(a) for a in arrs], _p(ut), _p(vt), _p(wt))
+    _load().orc_pseudo_velocity(nx, ny, nz, h, kbc, *[_p(a) for a in arrs], _p(ut), _p(vt),
+                                _p(wt))
     return ut, vt, wt
 
 
@@ -131,24 +133,26 @@ def mass(psi, g, h: int) -> float:
 
 
 def tlm(psi, u, v, w, g, dpsi, du, dv, dw, h: int, iord: int = 2, nonosc: int = 1,
-        nsteps: int = 1):
+        nsteps: int = 1, kbc: int = 0):
     """Tangent-linear model: (psi_out, dpsi_out) along direction (dpsi, dU, dV, dW)."""
     nx, ny, nz = _dims(psi, h)
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (psi, u, v, w, g, dpsi, du, dv, dw)]
     out = np.zeros_like(arrs[0])
     dout = np.zeros_like(arrs[0])
-    _load().orc_tlm(nx, ny, nz, h, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(out), _p(dout))
+    _load().orc_tlm(nx, ny, nz, h, kbc, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(out),
+                    _p(dout))
     return out, dout
 
 
-def adjoint(psi, u, v, w, g, psib, h: int, iord: int = 2, nonosc: int = 1, nsteps: int = 1):
+def adjoint(psi, u, v, w, g, psib, h: int, iord: int = 2, nonosc: int = 1, nsteps: int = 1,
+            kbc: int = 0):
     """Reverse mode of nsteps steps.  psib: dJ/dpsi_T (padded, interior used).
     Returns (dJ/dpsi_0, dJ/dU, dJ/dV, dJ/dW), padded with zero halos."""
     nx, ny, nz = _dims(psi, h)
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (psi, u, v, w, g)]
     pb = np.array(psib, dtype=np.float64, order="C", copy=True)
     ub, vb, wb = (np.zeros_like(arrs[0]) for _ in range(3))
-    _load().orc_adjoint(nx, ny, nz, h, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(pb),
+    _load().orc_adjoint(nx, ny, nz, h, kbc, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(pb),
                         _p(ub), _p(vb), _p(wb))
     inner = np.zeros_like(pb)
     sl = (slice(h, h + nz), slice(h, h + ny), slice(h, h + nx))

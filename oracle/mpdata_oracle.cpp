@@ -46,10 +46,15 @@ const double EPS = 1e-15;
 
 struct Grid {
   int nx, ny, nz, h;
+  bool kper;        // periodic in k (else zero-flux top and bottom faces)
   long px, py, pz;  // padded extents
-  Grid(int nx_, int ny_, int nz_, int h_) : nx(nx_), ny(ny_), nz(nz_), h(h_) {
+  Grid(int nx_, int ny_, int nz_, int h_, int kbc = 0)
+      : nx(nx_), ny(ny_), nz(nz_), h(h_), kper(kbc == 1) {
     px = nx + 2L * h; py = ny + 2L * h; pz = nz + 2L * h;
   }
+  // whether the vertical face above level k carries flux (the top face
+  // k = nz-1 is closed unless k is periodic)
+  bool zface(int k) const { return kper || k < nz - 1; }
   long size() const { return px * py * pz; }
   long at(int i, int j, int k) const { return ((k + h) * py + (j + h)) * px + (i + h); }
 };
@@ -92,7 +97,8 @@ template <class T> inline T donor(T L, T R, T C) {
 inline int wrap(int i, int n) { int r = i % n; return r < 0 ? r + n : r; }
 
 /* Cell-centred fields (psi, G) and the horizontal face fields (U, V):
-   periodic in i and j, corners included; the k halo copies the edge level. */
+   periodic in i and j, corners included; the k halo copies the edge level
+   (periodic k: the level nz away). */
 template <class T> void fill_halo_periodic(T* f, const Grid& g) {
   for (int k = 0; k < g.nz; ++k) {
     for (int j = 0; j < g.ny; ++j)
@@ -104,7 +110,7 @@ template <class T> void fill_halo_periodic(T* f, const Grid& g) {
   }
   for (int k = -g.h; k < g.nz + g.h; ++k) {
     if (k >= 0 && k < g.nz) continue;
-    int ks = k < 0 ? 0 : g.nz - 1;
+    int ks = g.kper ? wrap(k, g.nz) : (k < 0 ? 0 : g.nz - 1);
     for (int j = -g.h; j < g.ny + g.h; ++j)
       for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, j, ks)];
   }
@@ -115,6 +121,7 @@ template <class T> void fill_halo_periodic(T* f, const Grid& g) {
    carry no flux (pivbz = 0 in Listing 7), nor does anything beyond them. */
 template <class T> void fill_halo_wface(T* f, const Grid& g) {
   fill_halo_periodic(f, g);
+  if (g.kper) return;  // periodic k: every face is open, the halo wraps
   for (int k = -g.h; k < g.nz + g.h; ++k) {
     if (k >= 0 && k < g.nz - 1) continue;
     for (int j = -g.h; j < g.ny + g.h; ++j)
@@ -191,7 +198,7 @@ void pseudo_velocity(const Grid& g, const T* P, const T* u, const T* v, const T*
           T Wb = quarter * (w[L] + w[R] + w[L - Z] + w[R - Z]);
           vt[c] = (oabs(V) - V * V / Gf) * A - V * (Ub * Bx + Wb * Bz) / Gf;
         }
-        if (k < g.nz - 1) {  // z face between c and c+Z (interior faces only)
+        if (g.zface(k)) {  // z face between c and c+Z (open faces only)
           long L = c, R = c + Z;
           T W = w[c];
           T Gf = half * (G[L] + G[R]);
@@ -274,7 +281,7 @@ void limit_velocities(const Grid& g, const T* ut, const T* vt, const T* wt, cons
         long c = g.at(i, j, k);
         ul[c] = limit_face(ut[c], bu[c], bd[c], bu[c + X], bd[c + X]);
         vl[c] = limit_face(vt[c], bu[c], bd[c], bu[c + Y], bd[c + Y]);
-        wl[c] = (k < g.nz - 1) ? limit_face(wt[c], bu[c], bd[c], bu[c + Z], bd[c + Z]) : T(0.0);
+        wl[c] = g.zface(k) ? limit_face(wt[c], bu[c], bd[c], bu[c + Z], bd[c + Z]) : T(0.0);
       }
 }
 
@@ -354,7 +361,7 @@ void mpdata_step(const Grid& g, int iord, int nonosc, const T* psi_in, const T* 
 void rev_halo_periodic(double* a, const Grid& g) {
   for (int k = -g.h; k < g.nz + g.h; ++k) {
     if (k >= 0 && k < g.nz) continue;
-    int ks = k < 0 ? 0 : g.nz - 1;
+    int ks = g.kper ? wrap(k, g.nz) : (k < 0 ? 0 : g.nz - 1);
     for (int j = -g.h; j < g.ny + g.h; ++j)
       for (int i = -g.h; i < g.nx + g.h; ++i) {
         a[g.at(i, j, ks)] += a[g.at(i, j, k)];
@@ -380,7 +387,7 @@ void rev_halo_periodic(double* a, const Grid& g) {
 /* Reverse of fill_halo_wface: the closed faces were overwritten with zero,
    so their adjoints are dropped; the rest is the periodic reverse. */
 void rev_halo_wface(double* a, const Grid& g) {
-  for (int k = -g.h; k < g.nz + g.h; ++k) {
+  for (int k = -g.h; k < g.nz + g.h && !g.kper; ++k) {
     if (k >= 0 && k < g.nz - 1) continue;
     for (int j = -g.h; j < g.ny + g.h; ++j)
       for (int i = -g.h; i < g.nx + g.h; ++i) a[g.at(i, j, k)] = 0.0;
@@ -467,7 +474,7 @@ void rev_pseudo(const Grid& g, const double* P, const double* u, const double* v
                         Pb, &ub[c], vb, wb);
         rev_face_pseudo(vtb[c], P, c, c + Y, X, Z, v[c], 0.5 * (G[c] + G[c + Y]), u, w, X, Z,
                         Pb, &vb[c], ub, wb);
-        if (k < g.nz - 1)
+        if (g.zface(k))
           rev_face_pseudo(wtb[c], P, c, c + Z, X, Y, w[c], 0.5 * (G[c] + G[c + Z]), u, v, X, Y,
                           Pb, &wb[c], ub, vb);
       }
@@ -504,7 +511,7 @@ void rev_limit(const Grid& g, const double* ut, const double* vt, const double* 
       for (int i = 0; i < g.nx; ++i) {
         long c = g.at(i, j, k);
         for (int d = 0; d < 3; ++d) {
-          if (d == 2 && k == g.nz - 1) continue;  // closed top face: constant
+          if (d == 2 && !g.zface(k)) continue;  // closed top face: constant
           long r = c + D[d];
           rev_limit_face(lb3[d][c], vt3[d][c], bu[c], bd[c], bu[r], bd[r], &tb3[d][c], &bub[c],
                          &bdb[c], &bub[r], &bdb[r]);
@@ -558,7 +565,7 @@ void rev_beta(const Grid& g, const double* P0, const double* P, const double* ut
         double outb = -db * bd / dout;
         for (int d = 0; d < 3; ++d) {
           // top/bottom closed faces carry constant zero fluxes
-          bool has_p = !(d == 2 && k == g.nz - 1), has_m = !(d == 2 && k == 0);
+          bool has_p = !(d == 2 && !g.zface(k)), has_m = !(d == 2 && !g.kper && k == 0);
           double fpb = -inb * (fp[d] <= 0 ? 1.0 : 0.0) + outb * (fp[d] >= 0 ? 1.0 : 0.0);
           double fmb = inb * (fm[d] >= 0 ? 1.0 : 0.0) - outb * (fm[d] <= 0 ? 1.0 : 0.0);
           if (has_p) rev_donor(fpb, P[c], P[c + D[d]], vt3[d][c], &Pb[c], &Pb[c + D[d]], &tb3[d][c]);
@@ -701,21 +708,23 @@ extern "C" {
 
 int orc_version() { return 1; }
 
-/* Halo fill.  kind 0: cell/horizontal-face field (periodic i-j, k copy);
+/* Every entry point takes the vertical boundary kbc: 0 zero-flux (closed
+   top and bottom faces, k halo an edge copy), 1 periodic in k.
+   Halo fill.  kind 0: cell/horizontal-face field (periodic i-j, k copy);
    kind 1: vertical-face field (periodic i-j, zero boundary faces). */
-void orc_fill_halo(int nx, int ny, int nz, int h, int kind, double* f) {
-  Grid g(nx, ny, nz, h);
+void orc_fill_halo(int nx, int ny, int nz, int h, int kbc, int kind, double* f) {
+  Grid g(nx, ny, nz, h, kbc);
   if (kind == 1) fill_halo_wface(f, g); else fill_halo_periodic(f, g);
 }
 
 /* nsteps MPDATA steps; psi_out gets the padded result with its halo filled.
    The optional stage pointers (may be null) receive the intermediates of the
    last corrective pass of the last step. */
-void orc_run(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps,
+void orc_run(int nx, int ny, int nz, int h, int kbc, int iord, int nonosc, int nsteps,
              const double* psi_in, const double* U, const double* V, const double* W,
              const double* G, double* psi_out, double* psi1, double* ut, double* vt, double* wt,
              double* mx, double* mn, double* bu, double* bd, double* ul, double* vl, double* wl) {
-  Grid g(nx, ny, nz, h);
+  Grid g(nx, ny, nz, h, kbc);
   Stages st{psi1, ut, vt, wt, mx, mn, bu, bd, ul, vl, wl};
   std::vector<double> cur(psi_in, psi_in + g.size()), nxt(g.size());
   for (int s = 0; s < nsteps; ++s) {
@@ -727,10 +736,10 @@ void orc_run(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps,
 }
 
 /* Pseudo-velocities of a given field P with Courant fields U, V, W. */
-void orc_pseudo_velocity(int nx, int ny, int nz, int h, const double* Pin, const double* Uin,
+void orc_pseudo_velocity(int nx, int ny, int nz, int h, int kbc, const double* Pin, const double* Uin,
                          const double* Vin, const double* Win, const double* Gin, double* ut,
                          double* vt, double* wt) {
-  Grid g(nx, ny, nz, h);
+  Grid g(nx, ny, nz, h, kbc);
   long n = g.size();
   std::vector<double> P(Pin, Pin + n), U(Uin, Uin + n), V(Vin, Vin + n), W(Win, Win + n),
       G(Gin, Gin + n);
@@ -755,11 +764,11 @@ double orc_mass(int nx, int ny, int nz, int h, const double* psi, const double* 
 /* Tangent-linear model of nsteps steps (dual numbers through the forward
    code): returns psi_out and its directional derivative dpsi_out along
    (dpsi, dU, dV, dW).  G is held fixed. */
-void orc_tlm(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps, const double* psi,
+void orc_tlm(int nx, int ny, int nz, int h, int kbc, int iord, int nonosc, int nsteps, const double* psi,
              const double* U, const double* V, const double* W, const double* G,
              const double* dpsi, const double* dU, const double* dV, const double* dW,
              double* psi_out, double* dpsi_out) {
-  Grid g(nx, ny, nz, h);
+  Grid g(nx, ny, nz, h, kbc);
   long n = g.size();
   std::vector<Dual> p(n), u(n), v(n), w(n), gg(n), o(n);
   for (long q = 0; q < n; ++q) {
@@ -781,10 +790,10 @@ void orc_tlm(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps, co
    (interior) on entry and dJ/dpsi at step 0 on exit; ubar, vbar, wbar are
    incremented by dJ/dU, dJ/dV, dJ/dW.  The forward states are recomputed
    from psi (all stored; the oracle is for small grids).  G is held fixed. */
-void orc_adjoint(int nx, int ny, int nz, int h, int iord, int nonosc, int nsteps,
+void orc_adjoint(int nx, int ny, int nz, int h, int kbc, int iord, int nonosc, int nsteps,
                  const double* psi, const double* U, const double* V, const double* W,
                  const double* G, double* psib, double* ubar, double* vbar, double* wbar) {
-  Grid g(nx, ny, nz, h);
+  Grid g(nx, ny, nz, h, kbc);
   long n = g.size();
   std::vector<std::vector<double>> states(nsteps > 0 ? nsteps : 1, std::vector<double>(n));
   std::vector<double> cur(psi, psi + n);

@@ -90,16 +90,20 @@ def _uv_from_corner_streamfunction(psi_c: np.ndarray):
     return u, v
 
 
-def outflow_courant_max(u, v, w, g) -> float:
+def outflow_courant_max(u, v, w, g, kbc: int = 0) -> float:
     """Largest per-cell outflow Courant sum (a validity bound on the inputs).
 
     For cell c it is the sum over the three directions of the outward-pointing
     face values, divided by G_c; the donor-cell pass keeps psi >= 0 when it is
-    at most 1.  W's bottom face (k-1/2 at k=0) is the zero boundary.
+    at most 1.  W's bottom face (k-1/2 at k=0) is the zero boundary, or with
+    kbc = 1 (periodic k) the top face.
     """
     u_m = np.roll(u, 1, axis=-1)
     v_m = np.roll(v, 1, axis=-2)
-    w_m = np.concatenate([np.zeros_like(w[..., :1, :, :]), w[..., :-1, :, :]], axis=-3)
+    if kbc == 1:
+        w_m = np.roll(w, 1, axis=-3)
+    else:
+        w_m = np.concatenate([np.zeros_like(w[..., :1, :, :]), w[..., :-1, :, :]], axis=-3)
     out = (np.maximum(u, 0) - np.minimum(u_m, 0) + np.maximum(v, 0) - np.minimum(v_m, 0)
            + np.maximum(w, 0) - np.minimum(w_m, 0))
     return float(np.max(out / g))
@@ -232,8 +236,9 @@ def latlon_3d(nx: int = 256, ny: int = 256, nz: int = 64, seed: int = DEFAULT_SE
 def random_case(nx: int, ny: int, nz: int, seed: int = DEFAULT_SEED,
                 cmax: float = 0.2, psi_lo: float = 0.0, psi_hi: float = 1.0,
                 g_lo: float = 0.5, g_hi: float = 1.5, iord: int = 2,
-                nonosc: int = 1) -> Case:
-    """Unstructured random inputs (divergent flow), for parity on odd sizes."""
+                nonosc: int = 1, kbc: int = 0) -> Case:
+    """Unstructured random inputs (divergent flow), for parity on odd sizes.
+    kbc = 1 (periodic k) keeps the top face's W; else it is the closed face."""
     rng = np.random.default_rng(seed)
     shp = (nz, ny, nx)
     psi = rng.uniform(psi_lo, psi_hi, size=shp)
@@ -241,40 +246,45 @@ def random_case(nx: int, ny: int, nz: int, seed: int = DEFAULT_SEED,
     u = rng.uniform(-cmax, cmax, size=shp) * g
     v = rng.uniform(-cmax, cmax, size=shp) * g
     w = rng.uniform(-cmax, cmax, size=shp) * g
-    w[-1] = 0.0
-    s = outflow_courant_max(u, v, w, g)
+    if kbc != 1:
+        w[-1] = 0.0
+    s = outflow_courant_max(u, v, w, g, kbc)
     if s > 1.0:
         f = 0.98 / s
         u *= f
         v *= f
         w *= f
     return Case("random", nx, ny, nz, psi, u, v, w, g, iord=iord, nonosc=nonosc,
-                meta=dict(seed=seed))
+                meta=dict(seed=seed, kbc=kbc))
 
 
 def nondivergent_case(nx: int, ny: int, nz: int, seed: int = DEFAULT_SEED,
                       cmax: float = 0.3, const: Optional[float] = 1.7,
-                      g_lo: float = 0.5, g_hi: float = 1.5) -> Case:
+                      g_lo: float = 0.5, g_hi: float = 1.5, kbc: int = 0) -> Case:
     """Random but discretely non-divergent G-weighted flow.
 
     Horizontal part from a random corner stream function per level; an x-z
     stream function chi at (i+1/2, j, k+1/2), zero on the bottom and top
-    faces, adds U and W parts whose divergence also cancels exactly.  G is
-    random and positive.  psi is the constant ``const`` (or random if None).
+    faces (with kbc = 1, periodic in k instead), adds U and W parts whose
+    divergence also cancels exactly.  G is random and positive.  psi is the
+    constant ``const`` (or random if None).
     """
     rng = np.random.default_rng(seed)
     shp = (nz, ny, nx)
     psi_c = rng.uniform(-1.0, 1.0, size=shp)
     u, v = _uv_from_corner_streamfunction(psi_c)
     chi = np.zeros((nz + 1, ny, nx))
-    if nz > 1:
+    if kbc == 1:
+        chi[1:] = rng.uniform(-1.0, 1.0, size=(nz, ny, nx))
+        chi[0] = chi[nz]  # chi(-1/2) is chi(nz-1/2)
+    elif nz > 1:
         chi[1:nz] = rng.uniform(-1.0, 1.0, size=(nz - 1, ny, nx))
     # U(i+1/2, j, k) -= chi(i+1/2, j, k+1/2) - chi(i+1/2, j, k-1/2)
     u = u - (chi[1:] - chi[:-1])
     # W(i, j, k+1/2) = chi(i+1/2, j, k+1/2) - chi(i-1/2, j, k+1/2)
     w = chi[1:] - np.roll(chi[1:], 1, axis=-1)
     g = rng.uniform(g_lo, g_hi, size=shp)
-    s = outflow_courant_max(u, v, w, g)
+    s = outflow_courant_max(u, v, w, g, kbc)
     f = cmax / s
     u, v, w = u * f, v * f, w * f
     psi = np.full(shp, const) if const is not None else rng.uniform(0.5, 1.5, size=shp)
@@ -282,12 +292,13 @@ def nondivergent_case(nx: int, ny: int, nz: int, seed: int = DEFAULT_SEED,
 
 
 def uniform_shift_case(nx: int, ny: int, nz: int, axis: str, sign: int,
-                       seed: int = DEFAULT_SEED) -> Case:
+                       seed: int = DEFAULT_SEED, kbc: int = 0) -> Case:
     """Courant number exactly +-1 along one axis, 0 along the others, G = 1.
 
     psi is uniform in [1, 2): any two values are within a factor of two, so
     the differences the scheme forms are exact in binary floating point.
-    For axis 'z' the boundary faces stay zero (W = sign inside only).
+    For axis 'z' the boundary faces stay zero (W = sign inside only), unless
+    kbc = 1 (periodic k: every face).
     """
     rng = np.random.default_rng(seed)
     shp = (nz, ny, nx)
@@ -300,7 +311,10 @@ def uniform_shift_case(nx: int, ny: int, nz: int, axis: str, sign: int,
     elif axis == "y":
         v[:] = float(sign)
     elif axis == "z":
-        w[:-1] = float(sign)
+        if kbc == 1:
+            w[:] = float(sign)
+        else:
+            w[:-1] = float(sign)
     else:
         raise ValueError(axis)
     g = np.ones(shp)

@@ -50,8 +50,8 @@ MUTANTS = [
      "const long nb[6] = {-X, X, -Y, Y, -Z, Z};\n#pragma omp parallel for",
      "const long nb[6] = {-X, -X, -Y, Y, -Z, Z};\n#pragma omp parallel for"),
     ("top face left open",
-     "  fill_halo_periodic(f, g);\n  for (int k = -g.h; k < g.nz + g.h; ++k) {\n    if (k >= 0 && k < g.nz - 1) continue;",
-     "  fill_halo_periodic(f, g);\n  for (int k = -g.h; k < g.nz + g.h; ++k) {\n    if (k >= 0 && k < g.nz) continue;"),
+     "  if (g.kper) return;  // periodic k: every face is open, the halo wraps\n  for (int k = -g.h; k < g.nz + g.h; ++k) {\n    if (k >= 0 && k < g.nz - 1) continue;",
+     "  if (g.kper) return;  // periodic k: every face is open, the halo wraps\n  for (int k = -g.h; k < g.nz + g.h; ++k) {\n    if (k >= 0 && k < g.nz) continue;"),
     ("advance forgets 1/G",
      "out[c] = P[c] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) / G[c];",
      "out[c] = P[c] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm));"),
@@ -73,6 +73,9 @@ MUTANTS = [
     ("adjoint forgets d|U|/dU",
      "*Ub += ub * (sg * A - 2.0 * U / Gf * A - X / Gf);",
      "*Ub += ub * (-2.0 * U / Gf * A - X / Gf);"),
+    ("periodic k halo copies the edge level",
+     "int ks = g.kper ? wrap(k, g.nz) : (k < 0 ? 0 : g.nz - 1);\n    for (int j = -g.h; j < g.ny + g.h; ++j)\n      for (int i = -g.h; i < g.nx + g.h; ++i) f[",
+     "int ks = (k < 0 ? 0 : g.nz - 1);\n    for (int j = -g.h; j < g.ny + g.h; ++j)\n      for (int i = -g.h; i < g.nx + g.h; ++i) f["),
     ("y halo not wrapped",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, wrap(j, g.ny), k)];",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, j < 0 ? 0 : g.ny - 1, k)];"),
@@ -103,8 +106,10 @@ def _pin_battery():
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("x", -0.4),
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("y", 0.4),
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("z", -0.4),
-        lambda: pins.test_adjoint_dot_product_against_tlm(2, 1, 1),
-        lambda: pins.test_adjoint_dot_product_against_tlm(2, 0, 1),
+        lambda: pins.test_adjoint_dot_product_against_tlm(2, 1, 1, 0),
+        lambda: pins.test_adjoint_dot_product_against_tlm(2, 0, 1, 0),
+        pins.test_halo_fill_periodic_k_matches_numpy_pad,
+        lambda: pins.test_courant_one_shift_vertical_periodic(2, 1, 1),
         pins.test_adjoint_dot_product_on_rotating_cone,
     ]
     failed = 0

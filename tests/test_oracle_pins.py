@@ -50,6 +50,19 @@ def test_halo_fill_matches_numpy_pad():
         assert np.array_equal(w, refw)
 
 
+def test_halo_fill_periodic_k_matches_numpy_pad():
+    """With a periodic vertical boundary both field kinds wrap in all three
+    directions (numpy.pad(wrap)); no face is closed."""
+    rng = np.random.default_rng(6)
+    for (nx, ny, nz, h) in [(7, 5, 3, 2), (4, 9, 1, 2), (3, 3, 2, 3)]:
+        a = rng.standard_normal((nz, ny, nx))
+        ref = np.pad(a, h, mode="wrap")
+        for kind in (0, 1):
+            f = pad(a, h, fill=np.nan)
+            oracle.fill_halo(f, h, kind=kind, kbc=1)
+            assert np.array_equal(f, ref)
+
+
 # ------------------------------------------------ donor cell: Fourier pins --
 
 def _upwind_symbol(c, theta):
@@ -166,6 +179,39 @@ def test_courant_one_shift_vertical_zero_flux(iord, nonosc):
     assert np.array_equal(out[1:-1], p[:-2])
     assert np.array_equal(out[0], np.zeros_like(p[0]))
     assert np.array_equal(out[-1], p[-1] + p[-2])
+
+
+@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 0), (2, 1), (3, 1)])
+@pytest.mark.parametrize("sign", [1, -1])
+def test_courant_one_shift_vertical_periodic(iord, nonosc, sign):
+    """Periodic k, W = +-1 on every face: the levels roll by one per step,
+    bit for bit, the top level wrapping to the bottom."""
+    c = synth.uniform_shift_case(5, 4, 6, "z", sign, seed=2, kbc=1)
+    P = [pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    out = interior(oracle.run(*P, h=H, iord=iord, nonosc=nonosc, nsteps=3, kbc=1), H)
+    assert np.array_equal(out, np.roll(c.psi, 3 * sign, axis=0))
+
+
+@pytest.mark.parametrize("iord,nonosc", [(1, 0), (2, 1), (3, 1)])
+def test_mass_conservation_periodic_k(iord, nonosc):
+    """Periodic k with flux through the top face: sum psi G is conserved."""
+    c = synth.random_case(11, 9, 6, seed=8, cmax=0.3, kbc=1)
+    assert np.max(np.abs(c.w[-1])) > 0.01  # the top face carries flux
+    P = [pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    m0 = oracle.mass(P[0], P[4], H)
+    out = oracle.run(*P, h=H, iord=iord, nonosc=nonosc, nsteps=5, kbc=1)
+    assert abs(oracle.mass(out, P[4], H) - m0) <= 1e-14 * abs(m0)
+    assert np.max(np.abs(interior(out, H) - c.psi)) > 1e-3
+
+
+@pytest.mark.parametrize("nz", [1, 4])
+def test_constant_preservation_periodic_k(nz):
+    """Periodic k, discretely non-divergent flow with flux through every
+    vertical face: a constant stays constant (limiter on, 100 steps)."""
+    c = synth.nondivergent_case(12, 10, nz, seed=4, cmax=0.45, const=1.7, kbc=1)
+    P = [pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    out = oracle.run(*P, h=H, iord=2, nonosc=1, nsteps=100, kbc=1)
+    assert np.max(np.abs(interior(out, H) - 1.7)) <= 1e-14 * 1.7 * 10
 
 
 # --------------------------------------------------- pseudo-velocity limit --
@@ -380,21 +426,22 @@ def _inner(a, b, h=H):
     return float(np.sum(interior(a, h) * interior(b, h)))
 
 
-@pytest.mark.parametrize("iord,nonosc,nsteps", [(1, 0, 1), (2, 0, 1), (2, 1, 1), (2, 1, 3),
-                                                (2, 0, 3), (3, 0, 1), (3, 1, 1), (3, 1, 2),
-                                                (4, 1, 1)])
-def test_adjoint_dot_product_against_tlm(iord, nonosc, nsteps):
+@pytest.mark.parametrize("iord,nonosc,nsteps,kbc", [
+    (1, 0, 1, 0), (2, 0, 1, 0), (2, 1, 1, 0), (2, 1, 3, 0), (2, 0, 3, 0), (3, 0, 1, 0),
+    (3, 1, 1, 0), (3, 1, 2, 0), (4, 1, 1, 0), (1, 0, 1, 1), (2, 1, 2, 1), (3, 1, 1, 1)])
+def test_adjoint_dot_product_against_tlm(iord, nonosc, nsteps, kbc):
     """<L dx, dy> = <dx, L^T dy> with L the dual-number tangent-linear model
     (an independent derivative of the forward code) and L^T the hand-written
-    reverse mode, to 1e-12 relative."""
-    c = synth.random_case(9, 8, 5, seed=41, cmax=0.25, psi_lo=0.2, psi_hi=1.5)
+    reverse mode, to 1e-12 relative (kbc 1: periodic k, open top face)."""
+    c = synth.random_case(9, 8, 5, seed=41, cmax=0.25, psi_lo=0.2, psi_hi=1.5, kbc=kbc)
     rng = np.random.default_rng(42)
     P = [pad(x, H) for x in (c.psi, c.u, c.v, c.w, c.g)]
     dx = [pad(rng.standard_normal(c.psi.shape), H) for _ in range(4)]
     dy = pad(rng.standard_normal(c.psi.shape), H)
-    _, tl = oracle.tlm(*P, *dx, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps)
+    _, tl = oracle.tlm(*P, *dx, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps, kbc=kbc)
     lhs = _inner(tl, dy)
-    pb, ub, vb, wb = oracle.adjoint(*P, dy, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps)
+    pb, ub, vb, wb = oracle.adjoint(*P, dy, h=H, iord=iord, nonosc=nonosc, nsteps=nsteps,
+                                    kbc=kbc)
     rhs = _inner(dx[0], pb) + _inner(dx[1], ub) + _inner(dx[2], vb) + _inner(dx[3], wb)
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1e-30), (lhs, rhs)
 
