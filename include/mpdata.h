@@ -69,7 +69,7 @@ enum mpdata_status {
 };
 
 enum mpdata_dtype { MPDATA_F64 = 0, MPDATA_F32 = 1 };
-enum mpdata_kbc { MPDATA_K_ZEROFLUX = 0 };
+enum mpdata_kbc { MPDATA_K_ZEROFLUX = 0, MPDATA_K_PERIODIC = 1 };
 enum mpdata_halo_kind {
   MPDATA_HALO_CELL = 0,  /* psi, G, U, V: periodic i-j, edge copy in k   */
   MPDATA_HALO_WFACE = 1  /* W: periodic i-j, closed faces (zero) in k    */
@@ -89,7 +89,10 @@ enum mpdata_variant {
  *   iord        number of passes, 1 (donor cell only) to 8;
  *   nonoscillatory  0 or 1 (the limiter of every corrective pass);
  *   dtype       MPDATA_F64 or MPDATA_F32 (storage and arithmetic);
- *   k_bc        MPDATA_K_ZEROFLUX (closed top and bottom, Listing 7);
+ *   k_bc        MPDATA_K_ZEROFLUX (closed top and bottom, Listing 7) or
+ *               MPDATA_K_PERIODIC (k wraps like i and j; every vertical
+ *               face carries flux, W at level k is the face k+1/2 and the
+ *               one at nz-1 joins the top level to the bottom one);
  *   cuda_stream a cudaStream_t (NULL = the legacy default stream).
  * Allocates the scratch of one step on the current device.
  * Errors: EINVAL (sizes/options/out == NULL), EDEVICE, ENOMEM. */
@@ -196,7 +199,8 @@ MPDATA_API int mpdata_mass(mpdata_ctx *c, const void *psi, const void *g, double
  *
  * Each domain has its own grid and Courant fields and ntracers tracers that
  * share them.  One batch step advances every tracer of every domain by one
- * MPDATA step (iord 2) from one tracer buffer into the other (ping-pong).
+ * MPDATA step (iord 2, zero-flux vertical boundary) from one tracer buffer
+ * into the other (ping-pong).
  * Domains need nx, ny >= 2*halo and halo >= 2.  The work is split into items
  * (domain, column tile, level chunk, tracer) that the CTAs of one persistent
  * kernel take from an atomic counter; the tracers of one tile are

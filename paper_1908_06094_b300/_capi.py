@@ -22,6 +22,7 @@ MPDATA_ERANGE = -6
 MPDATA_F64 = 0
 MPDATA_F32 = 1
 MPDATA_K_ZEROFLUX = 0
+MPDATA_K_PERIODIC = 1
 MPDATA_HALO_CELL = 0
 MPDATA_HALO_WFACE = 1
 MPDATA_FUSED = 0

@@ -122,9 +122,12 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
   minus(xm, cu[xm]);
   plus(1, yp, cv[q]);
   minus(ym, cv[ym]);
-  if (c.k < g.nz - 1) plus(2, q + g.pxy, cw[q]);
+  if (zopen(g, c.k)) plus(2, at(g, c.i, c.j, kadj(g, c.k + 1)), cw[q]);
   else out.closed(q);
-  if (c.k > 0) minus(q - g.pxy, cw[q - g.pxy]);
+  if (zopen(g, c.k - 1)) {
+    const int64_t qm = at(g, c.i, c.j, kadj(g, c.k - 1));
+    minus(qm, cw[qm]);
+  }
   if (ADD_P) {
     Pb[q] = Pin[q] + acc;
     Pin[q] = T(0);
@@ -198,7 +201,7 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
   bub[q] = bdb[q] = T(0);  // the only reader: leave them zero for the next step
   const int64_t nb[6] = {at(g, wrap_dn(i, g.nx), j, k), at(g, wrap_up(i, g.nx), j, k),
                          at(g, i, wrap_dn(j, g.ny), k), at(g, i, wrap_up(j, g.ny), k),
-                         at(g, i, j, clampk(k - 1, g.nz)), at(g, i, j, clampk(k + 1, g.nz))};
+                         at(g, i, j, kadj(g, k - 1)), at(g, i, j, kadj(g, k + 1))};
   T hi = P0[q], lo = P0[q];
   T* hip = &P0b[q];
   T* lop = &P0b[q];
@@ -219,8 +222,8 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
   T Cp[3], Cm[3], Pr[3], Pl[3], fp[3], fm[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    hp[d] = !(d == 2 && k == g.nz - 1);
-    hm[d] = !(d == 2 && k == 0);
+    hp[d] = d != 2 || zopen(g, k);
+    hm[d] = d != 2 || zopen(g, k - 1);
     Cp[d] = hp[d] ? vel[d][q] : T(0);
     Pr[d] = P[nb[2 * d + 1]];
     fp[d] = donor(pc, Pr[d], Cp[d]);
@@ -441,7 +444,9 @@ struct RevPseudoAcc {
     const int s3 = k % 3, s2 = k & 1;
     T* p0 = a.p + s3 * kStrip + cb;
     T* pq = a.p + (top ? s3 : (s3 == 2 ? 0 : s3 + 1)) * kStrip + cb;  // "+z" level, clamped
-    T* pm = a.p + (k > 0 ? (s3 == 0 ? 2 : s3 - 1) : s3) * kStrip + cb;  // "-z" level, clamped
+    // "-z" level: k-1 (a virtual level -1 under periodic k), clamped to k
+    // at a zero-flux bottom
+    T* pm = a.p + (k > 0 || at.kper ? (s3 == 0 ? 2 : s3 - 1) : s3) * kStrip + cb;
     // psi1-bar, same level
     add<1, 0>(p0, x.wl + y.wl + z.wl);
     add<1, 1>(p0, x.wr + y.w1p + z.w1p);
@@ -486,7 +491,7 @@ struct RevPseudoAcc {
       add<1, 1>(w0, x.c2);
       add<2, 0>(w0, y.c2);
     }
-    if (k > 0) {  // W-bar at the open face k-1/2
+    if (k > 0 || at.kper) {  // W-bar at the open face k-1/2
       T* wm = a.w + (s2 ^ 1) * kStrip + cb;
       add<1, 0>(wm, x.c2 + y.c2);
       add<1, 1>(wm, x.c2);
@@ -496,7 +501,9 @@ struct RevPseudoAcc {
   // Sum the strips of one accumulator level (base f) into dst at level kf
   // and clear them.
   __device__ __forceinline__ void flush_one(T* f, T* dst, int kf, const Geo& g) const {
-    const int64_t ok = (int64_t)kf * g.pxy;
+    // virtual levels -1 and nz (periodic k) are the levels nz-1 and 0
+    const int kg = kf < 0 ? kf + g.nz : (kf >= g.nz ? kf - g.nz : kf);
+    const int64_t ok = (int64_t)kg * g.pxy;
 #pragma unroll
     for (int m = 0; m < kPos; ++m) {
       const Pos& P = pos[m];
@@ -522,8 +529,8 @@ struct RevPseudoAcc {
   __device__ __forceinline__ void flush(Acc& a, int k, bool after, const Geo& g, int i0,
                                        int j0, int k0, int k1, int t) const {
     if (!after) {
-      if (k > 0) {
-        flush_one(a.p + ((k - 1) % 3) * kStrip, pb, k - 1, g);
+      if (k > 0 || g.kper) {
+        flush_one(a.p + ((k + 2) % 3) * kStrip, pb, k - 1, g);  // slot of k-1
         flush_one(a.w + ((k - 1) & 1) * kStrip, wb, k - 1, g);
       }
       flush_one(a.u + (k & 1) * kStrip, ub, k, g);
@@ -531,7 +538,7 @@ struct RevPseudoAcc {
     } else {
       flush_one(a.p + ((k1 - 1) % 3) * kStrip, pb, k1 - 1, g);
       flush_one(a.w + ((k1 - 1) & 1) * kStrip, wb, k1 - 1, g);
-      if (k1 < g.nz) {
+      if (k1 < g.nz || g.kper) {
         flush_one(a.p + (k1 % 3) * kStrip, pb, k1, g);
         flush_one(a.u + (k1 & 1) * kStrip, ub, k1, g);
         flush_one(a.v + (k1 & 1) * kStrip, vb, k1, g);
@@ -548,6 +555,9 @@ __global__ void rev_pg_kernel(Geo g, const T* __restrict__ wts, T* Pb, T* ub, T*
   const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
   const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
   const int64_t F = g.total;
+  const bool kper = g.kper != 0;
+  const int kb = kadj(g, k - 1), ka = kadj(g, k + 1);  // the levels below and above
+  const bool below = kper || k >= 1;                   // the face k-1/2 is open
   auto W = [&](int fam, int w, int a, int b, int d) -> T {
     return wts[((int64_t)fam * kNW + w) * F + at(g, a, b, d)];
   };
@@ -558,36 +568,42 @@ __global__ void rev_pg_kernel(Geo g, const T* __restrict__ wts, T* Pb, T* ub, T*
   // y faces: A, B1 (x), B2 (z, clamped)
   s += W(1, kWL, i, j, k) + W(1, kWR, i, jm, k);
   s += W(1, kW1P, im, j, k) + W(1, kW1P, im, jm, k) + W(1, kW1M, ip, j, k) + W(1, kW1M, ip, jm, k);
-  // clamped z neighbours of the x and y faces: q is the "+z" point of the
-  // faces at level kf with clamp(kf+1) == k, the "-z" point where clamp(kf-1) == k
+  // z neighbours of the x and y faces: q is the "+z" point of the faces at
+  // level kf with kadj(kf+1) == k, the "-z" point where kadj(kf-1) == k
+  // (clamped at a zero-flux bottom and top, wrapped under periodic k)
   auto zgather = [&](int kf, int w) {
     s += W(0, w, i, j, kf) + W(0, w, im, j, kf) + W(1, w, i, j, kf) + W(1, w, i, jm, kf);
   };
-  if (k >= 1) zgather(k - 1, kW2P);
-  if (k == nz - 1) zgather(k, kW2P);
-  if (k + 1 <= nz - 1) zgather(k + 1, kW2M);
-  if (k == 0) zgather(k, kW2M);
-  // z faces (levels kf in [0, nz-2]; the top level holds zeros)
+  if (kper) {
+    zgather(kb, kW2P);
+    zgather(ka, kW2M);
+  } else {
+    if (k >= 1) zgather(k - 1, kW2P);
+    if (k == nz - 1) zgather(k, kW2P);
+    if (k + 1 <= nz - 1) zgather(k + 1, kW2M);
+    if (k == 0) zgather(k, kW2M);
+  }
+  // z faces (a zero-flux top level holds zeros)
   s += W(2, kWL, i, j, k);
-  if (k >= 1) s += W(2, kWR, i, j, k - 1);
+  if (below) s += W(2, kWR, i, j, kb);
   s += W(2, kW1P, im, j, k) + W(2, kW1M, ip, j, k) + W(2, kW2P, i, jm, k) + W(2, kW2M, i, jp, k);
-  if (k >= 1)
-    s += W(2, kW1P, im, j, k - 1) + W(2, kW1M, ip, j, k - 1) + W(2, kW2P, i, jm, k - 1) +
-         W(2, kW2M, i, jp, k - 1);
+  if (below)
+    s += W(2, kW1P, im, j, kb) + W(2, kW1M, ip, j, kb) + W(2, kW2P, i, jm, kb) +
+         W(2, kW2M, i, jp, kb);
   const int64_t q = at(g, i, j, k);
   Pb[q] += s;
   // cross averages: U (face i+1/2) in y faces and z faces, V in x and z, W in x and y
   T su = W(1, kC1, i, j, k) + W(1, kC1, i, jm, k) + W(1, kC1, ip, j, k) + W(1, kC1, ip, jm, k);
   su += W(2, kC1, i, j, k) + W(2, kC1, ip, j, k);
-  if (k >= 1) su += W(2, kC1, i, j, k - 1) + W(2, kC1, ip, j, k - 1);
+  if (below) su += W(2, kC1, i, j, kb) + W(2, kC1, ip, j, kb);
   ub[q] += su;
   T sv = W(0, kC1, i, j, k) + W(0, kC1, im, j, k) + W(0, kC1, i, jp, k) + W(0, kC1, im, jp, k);
   sv += W(2, kC2, i, j, k) + W(2, kC2, i, jp, k);
-  if (k >= 1) sv += W(2, kC2, i, j, k - 1) + W(2, kC2, i, jp, k - 1);
+  if (below) sv += W(2, kC2, i, j, kb) + W(2, kC2, i, jp, kb);
   vb[q] += sv;
-  if (k <= nz - 2) {  // open vertical face
-    T sw = W(0, kC2, i, j, k) + W(0, kC2, im, j, k) + W(0, kC2, i, j, k + 1) + W(0, kC2, im, j, k + 1);
-    sw += W(1, kC2, i, j, k) + W(1, kC2, i, jm, k) + W(1, kC2, i, j, k + 1) + W(1, kC2, i, jm, k + 1);
+  if (zopen(g, k)) {  // open vertical face
+    T sw = W(0, kC2, i, j, k) + W(0, kC2, im, j, k) + W(0, kC2, i, j, ka) + W(0, kC2, im, j, ka);
+    sw += W(1, kC2, i, j, k) + W(1, kC2, i, jm, k) + W(1, kC2, i, j, ka) + W(1, kC2, i, jm, ka);
     wb[q] += sw;
   }
 }

@@ -645,7 +645,7 @@ int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, in
   if (iord >= 2 && halo < 2) return MPDATA_EINVAL;
   if (nonosc != 0 && nonosc != 1) return MPDATA_EINVAL;
   if (dtype != MPDATA_F64 && dtype != MPDATA_F32) return MPDATA_EINVAL;
-  if (k_bc != MPDATA_K_ZEROFLUX) return MPDATA_EINVAL;
+  if (k_bc != MPDATA_K_ZEROFLUX && k_bc != MPDATA_K_PERIODIC) return MPDATA_EINVAL;
   if (nz > 65535) return MPDATA_ERANGE;
   // padded extents must fit the 32-bit index arithmetic of a row/plane
   if ((int64_t)(nx + 2 * halo) * (ny + 2 * halo) > (int64_t)1 << 31) return MPDATA_ERANGE;
@@ -654,7 +654,7 @@ int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, in
   mpdata_ctx* c = new (std::nothrow) mpdata_ctx();
   if (!c) return MPDATA_ENOMEM;
   std::memset(c, 0, sizeof(*c));
-  c->g = mpd::make_geo(nx, ny, nz, halo);
+  c->g = mpd::make_geo(nx, ny, nz, halo, k_bc == MPDATA_K_PERIODIC ? 1 : 0);
   c->iord = iord;
   c->nonosc = nonosc;
   c->dtype = dtype;

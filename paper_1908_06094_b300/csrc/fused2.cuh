@@ -19,6 +19,8 @@
 // Intermediates that neighbours need (psi1, Ut, Vt, betas, x/y fluxes) go to
 // shared-memory rings; Wt and the vertical fluxes stay in registers.
 #pragma once
+#include <climits>
+
 #include "grid.cuh"
 
 namespace mpd {
@@ -92,12 +94,22 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     rcol = (int64_t)wrapj(j0 + ry) * g.px + wrapi(i0 + rx);
   }
   const int64_t pxy = g.pxy;
-  auto clampk_ = [&](int k) { return k < 0 ? 0 : (k >= nz ? nz - 1 : k); };
+  const bool kper = g.kper != 0;
+  // the level of plane k: clamped (edge copy) or, periodic in k, wrapped
+  // (any distance: the march runs up to 5 planes past the grid)
+  auto clampk_ = [&](int k) {
+    return kper ? ((k % nz) + nz) % nz : (k < 0 ? 0 : (k >= nz ? nz - 1 : k));
+  };
+  // the planes a stage runs on: the chunk's range widened by the stage's
+  // depth, cut to the grid unless k is periodic (then every plane is real)
+  const int klo = kper ? INT_MIN / 2 : 0, khi = kper ? INT_MAX / 2 : nz - 1;
+  // the face above plane k carries flux
+  auto zface = [&](int k) { return kper || (k >= 0 && k < nz - 1); };
   // per-thread column pointers (plane 0); plane k is + k*pxy (warp-uniform)
   const int64_t c0 = g.off0 + col, rc0 = g.off0 + rcol;
   auto ld = [&](const T* f, int k, int64_t c) { return f[c + (int64_t)clampk_(k) * pxy]; };
   // vertical face value with the closed bottom and top faces
-  auto ldw = [&](int k, int64_t c) { return (k < 0 || k >= nz - 1) ? zero : W[c + (int64_t)k * pxy]; };
+  auto ldw = [&](int k, int64_t c) { return zface(k) ? W[c + (int64_t)clampk_(k) * pxy] : zero; };
   // shared-memory views
   T* p0s = sm + L::P0S;
   T* us = sm + L::US;
@@ -173,7 +185,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     const int64_t o3 = (int64_t)clampk_(t + 3) * pxy;
     const T pn_next = P0[c0 + o5];
     const T un_next = U[c0 + o4], vn_next = V[c0 + o4], gn_next = G[c0 + o4];
-    const T wn_next = (t + 4 >= 0 && t + 4 < nz - 1) ? W[c0 + o4] : zero;  // closed faces
+    const T wn_next = zface(t + 4) ? W[c0 + o4] : zero;  // closed faces
     T rp_next = zero, ru_next = zero, rv_next = zero;
     if (ringer) {
       rp_next = P0[rc0 + o3];
@@ -183,7 +195,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     __syncthreads();
     // ---- A: psi1 on plane a = t+2 ---------------------------------------
     const int a = t + 2;
-    if (a >= max(0, k0 - 3) && a <= min(nz - 1, k1 + 1)) {
+    if (a >= max(klo, k0 - 3) && a <= min(khi, k1 + 1)) {
       const T* pa = p0s + (a & 1) * L::RN + s3;
       const T* ua = us + (a & 1) * L::RN + s3;
       const T* va = vs + (a & 1) * L::RN + s3;
@@ -191,17 +203,17 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T fxm = donor(pa[-1], p2, ua[-1]);
       const T fyp = donor(p2, pa[RX], v2);
       const T fym = donor(pa[-RX], p2, va[-RX]);
-      const T fzp = donor(p2, p3, w2);  // w2 = 0 on the top face
-      const T fzm = donor(p1, p2, w1);  // w1 = 0 on the bottom face
+      const T fzp = donor(p2, p3, w2);  // w2 = 0 on a zero-flux top face
+      const T fzm = donor(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
       q2 = p2 - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) * rcp(g2);
       P1(a, 0) = q2;
     }
     __syncthreads();
     // ---- B: pseudo-velocities on plane b = t+1 ---------------------------
     const int b = t + 1;
-    const bool runB = b >= max(0, k0 - 2) && b <= min(nz - 1, k1);
+    const bool runB = b >= max(klo, k0 - 2) && b <= min(khi, k1);
     if (runB) {
-      const int bp = min(b + 1, nz - 1), bm = max(b - 1, 0);
+      const int bp = min(b + 1, khi), bm = max(b - 1, klo);
       const T qp = (bp == b) ? q1 : q2;  // own psi1 at the clamped b+1
       const T qm = (bm == b) ? q1 : q0;  // own psi1 at the clamped b-1
       const T* gb = gs + s2;
@@ -227,7 +239,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       }
       {  // z face (used on x in [-1, TX], y in [-1, TY])
         T res = zero;
-        if (b < nz - 1) {  // the top face is closed
+        if (zface(b)) {  // a zero-flux top face is closed
           const T* ub1 = us + ((b + 1) & 1) * L::RN + s3;
           const T* vb1 = vs + ((b + 1) & 1) * L::RN + s3;
           const T s1p = P1(b + 1, 1) + P1(b, 1), s1m = P1(b + 1, -1) + P1(b, -1);
@@ -241,8 +253,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     }
     __syncthreads();
     // ---- C: limiter bounds and betas on plane b = t+1 --------------------
-    if (LIMIT && b >= max(0, k0 - 1) && b <= min(nz - 1, k1)) {  // used on tile + 1
-      const int bp = min(b + 1, nz - 1), bm = max(b - 1, 0);
+    if (LIMIT && b >= max(klo, k0 - 1) && b <= min(khi, k1)) {  // used on tile + 1
+      const int bp = min(b + 1, khi), bm = max(b - 1, klo);
       const T qp = (bp == b) ? q1 : q2, qm = (bm == b) ? q1 : q0;
       const T* pb = p0s + (b & 1) * L::RN + s3;
       const T pxm = P1(b, -1), pxp = P1(b, 1), pym = P1(b, -EX), pyp = P1(b, EX);
@@ -254,8 +266,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T fxm = donor(pxm, q1, uts[s2 - 1]);
       const T fyp = donor(q1, pyp, vtB);
       const T fym = donor(pym, q1, vts[s2 - EX]);
-      const T fzp = donor(q1, qp, wtB);  // wtB = 0 on the top face
-      const T fzm = donor(qm, q1, wtA);  // wtA = 0 on the bottom face
+      const T fzp = donor(q1, qp, wtB);  // wtB = 0 on a zero-flux top face
+      const T fzm = donor(qm, q1, wtA);  // wtA = 0 on a zero-flux bottom face
       const T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
       const T ou = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
       const T ri = rcp(in + eps), ro = rcp(ou + eps);
@@ -267,7 +279,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     }
     __syncthreads();
     // ---- D: limited donor fluxes of plane t and face t+1/2 ---------------
-    if (t >= max(0, k0 - 1) && t <= k1 - 1) {
+    if (t >= max(klo, k0 - 1) && t <= k1 - 1) {
       const T* bu0 = sm + L::BUS + (t & 1) * L::SN + s2;
       const T* bd0 = sm + L::BDS + (t & 1) * L::SN + s2;
       T u = utA;  // used on x in [-1, TX-1], y in [0, TY-1]
@@ -277,7 +289,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       if (LIMIT) v = limit_face(v, buA, bdA, bu0[EX], bd0[EX]);
       fys[s2] = donor(q0, P1(t, EX), v);
       T f = zero, w = zero;
-      if (t < nz - 1) {
+      if (zface(t)) {
         w = wtA;
         if (LIMIT) w = limit_face(w, buA, bdA, buB, bdB);
         f = donor(q0, q1, w);
@@ -305,13 +317,17 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     __syncthreads();
     // ---- E: advance and write psi^(n+1) on plane t ------------------------
     if (t >= k0 && writes) {
-      const T fzm = t > 0 ? fzA : zero;
+      const T fzm = zface(t - 1) ? fzA : zero;
       const T r = q0 - ((fxs[s2] - fxs[s2 - 1]) + (fys[s2] - fys[s2 - EX]) + (fzB - fzm)) * rcp(g0);
       const int ni = (gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0);
       const int nj = (gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0);
-      const int klo = (t == 0) ? -g.h : t, khi = (t == nz - 1) ? nz - 1 + g.h : t;
-      for (int kk = klo; kk <= khi; ++kk) {
-        if (kk != t && kk >= 0 && kk < nz) continue;
+      // the levels holding this value: t, and its k-halo images -- edge
+      // copies of the bottom and top levels, or under periodic k the
+      // levels t + m nz within [-h, nz + h)
+      const int ilo = kper ? t - ((t + g.h) / nz) * nz : ((t == 0) ? -g.h : t);
+      const int ihi = kper ? nz - 1 + g.h : ((t == nz - 1) ? nz - 1 + g.h : t);
+      for (int kk = ilo; kk <= ihi; kk += kper ? nz : 1) {
+        if (!kper && kk != t && kk >= 0 && kk < nz) continue;
         const int64_t pk = g.off0 + (int64_t)kk * g.pxy;
         for (int a2 = 0; a2 <= (ni != 0); ++a2) {
           const int ii = gi + a2 * ni * g.nx;

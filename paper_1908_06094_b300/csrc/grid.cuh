@@ -2,9 +2,10 @@
 //
 // Every field is [nz+2h][ny+2h][nx+2h], i fastest.  The step kernels never
 // read a halo: periodic neighbours in i and j are taken by wrapping the
-// interior index, the k neighbours of psi by clamping (edge copy), and the
-// vertical faces k = -1/2 and k = nz-1/2 are closed (the boundary factor
-// pivbz = 0 of Listing 7), so what the caller leaves in the halos never
+// interior index; in k (zero-flux boundary) the neighbours of psi by
+// clamping (edge copy) and the vertical faces k = -1/2 and k = nz-1/2 are
+// closed (the boundary factor pivbz = 0 of Listing 7), or (periodic k) by
+// wrapping with every face open.  What the caller leaves in the halos never
 // matters.
 #pragma once
 #include <cstdint>
@@ -13,15 +14,16 @@ namespace mpd {
 
 struct Geo {
   int nx, ny, nz, h;
+  int kper;      // 1: periodic in k; 0: closed (zero-flux) bottom and top faces
   int64_t px;    // padded row length (elements)
   int64_t pxy;   // padded plane size (elements)
   int64_t off0;  // offset of interior point (0,0,0)
   int64_t total; // padded field size (elements)
 };
 
-inline Geo make_geo(int nx, int ny, int nz, int h) {
+inline Geo make_geo(int nx, int ny, int nz, int h, int kper = 0) {
   Geo g;
-  g.nx = nx; g.ny = ny; g.nz = nz; g.h = h;
+  g.nx = nx; g.ny = ny; g.nz = nz; g.h = h; g.kper = kper;
   g.px = nx + 2 * (int64_t)h;
   g.pxy = g.px * (ny + 2 * (int64_t)h);
   g.off0 = h * g.pxy + h * g.px + h;
@@ -35,6 +37,17 @@ __host__ __device__ __forceinline__ int64_t at(const Geo& g, int i, int j, int k
 __device__ __forceinline__ int wrap_up(int i, int n) { return i + 1 == n ? 0 : i + 1; }
 __device__ __forceinline__ int wrap_dn(int i, int n) { return i == 0 ? n - 1 : i - 1; }
 __device__ __forceinline__ int clampk(int k, int nz) { return k < 0 ? 0 : (k >= nz ? nz - 1 : k); }
+// The level of a vertical neighbour k (-1 <= k <= nz): wrapped when k is
+// periodic, else clamped (the edge copy of psi).
+__device__ __forceinline__ int kadj(const Geo& g, int k) {
+  if (g.kper) return k < 0 ? k + g.nz : (k >= g.nz ? k - g.nz : k);
+  return k < 0 ? 0 : (k >= g.nz ? g.nz - 1 : k);
+}
+// Whether the vertical face above level k (k = -1: the bottom face) carries
+// flux: all do when k is periodic, else the bottom and top faces are closed.
+__device__ __forceinline__ bool zopen(const Geo& g, int k) {
+  return g.kper || (k >= 0 && k < g.nz - 1);
+}
 
 template <class T> struct Eps;
 template <> struct Eps<double> { static constexpr double v = 1e-15; };

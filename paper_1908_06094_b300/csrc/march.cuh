@@ -59,7 +59,8 @@ struct FaceIn {
 // column c = tx+1 of the tile-plus-ring planes, its level k.
 struct CellAt {
   int r, c, k;
-  bool own;  // an interior cell (false: the periodic image past a ragged edge)
+  bool own;   // an interior cell (false: the periodic image past a ragged edge)
+  bool kper;  // the grid is periodic in k
 };
 
 // Ops without shared accumulators.
@@ -169,10 +170,10 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
   // register queues: psi and pair sums at k (and k-1), W pairs at k-1/2
   T pc = P[o + k0 * pxy], pi = P[oi + k0 * pxy], pj = P[oj + k0 * pxy];
   T sx = pc + pi, exx = sx + eps, sy = pc + pj, eyy = sy + eps;
-  const int64_t ob = (k0 > 0 ? k0 - 1 : 0) * pxy;
+  const int64_t ob = (int64_t)kadj(g, k0 - 1) * pxy;  // the level below the chunk
   T sxm = P[o + ob] + P[oi + ob], sym = P[o + ob] + P[oj + ob];
   T pwxm = zero, pwym = zero;
-  if (k0 > 0) {
+  if (zopen(g, k0 - 1)) {  // the face below the chunk
     pwxm = cw[o + ob] + cw[oi + ob];
     pwym = cw[o + ob] + cw[oj + ob];
   }
@@ -184,7 +185,7 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
   };
   const T* rvel = rkind == 1 ? cv : cu;
   auto load = [&](int k) {
-    const int64_t ok = k * pxy, on = (k == g.nz - 1 ? k : k + 1) * pxy;
+    const int64_t ok = k * pxy, on = (int64_t)kadj(g, k + 1) * pxy;
     In v;
     v.pcn = P[o + on]; v.pin = P[oi + on]; v.pjn = P[oj + on];
     v.uc = cu[o + ok]; v.vc = cv[o + ok]; v.wc = cw[o + ok];
@@ -200,7 +201,7 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
   };
   for (int k = k0; k < k1; ++k) {
     const int64_t ok = k * pxy;
-    const bool top = k == g.nz - 1;
+    const bool top = !zopen(g, k);  // the face above k is closed (zero-flux top)
     const In in = load(k);
     const T pcn = in.pcn, pin = in.pin, pjn = in.pjn;
     const T sxn = pcn + pin, exn = sxn + eps, syn = pcn + pjn, eyn = syn + eps;
@@ -267,7 +268,7 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
                         s.sz[ty + 2][tx + 1] - s.sz[ty][tx + 1],
                         s.ez[ty + 2][tx + 1] + s.sz[ty][tx + 1],
                         s.puz[ty][tx + 1] + s.puz[ty][tx], s.pvz[ty + 1][tx] + s.pvz[ty][tx]},
-              top, CellAt{ty + 1, tx + 1, k, own}, in.ol, acc);
+              top, CellAt{ty + 1, tx + 1, k, own, g.kper != 0}, in.ol, acc);
     }
     if constexpr (Op::kAccum) {
       __syncthreads();

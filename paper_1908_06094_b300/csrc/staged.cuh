@@ -29,7 +29,7 @@ __device__ __forceinline__ Cell cell_of(const Geo& g) {
 // Vertical-face value with the closed bottom and top faces.
 template <class T>
 __device__ __forceinline__ T wface(const T* w, const Geo& g, int i, int j, int k) {
-  return (k < 0 || k >= g.nz - 1) ? T(0) : w[at(g, i, j, k)];
+  return zopen(g, k) ? w[at(g, i, j, kadj(g, k))] : T(0);
 }
 
 // Donor-cell fluxes through the three "+" faces of every cell.
@@ -43,7 +43,7 @@ __global__ void flux_kernel(Geo g, const T* __restrict__ P, const T* __restrict_
   T p = P[q];
   fx[q] = donor(p, P[at(g, wrap_up(c.i, g.nx), c.j, c.k)], cu[q]);
   fy[q] = donor(p, P[at(g, c.i, wrap_up(c.j, g.ny), c.k)], cv[q]);
-  fz[q] = (c.k < g.nz - 1) ? donor(p, P[q + g.pxy], cw[q]) : T(0);
+  fz[q] = zopen(g, c.k) ? donor(p, P[at(g, c.i, c.j, kadj(g, c.k + 1))], cw[q]) : T(0);
 }
 
 // Flux divergence and advance (Listings 8/9): out = P - (1/G) sum dF.
@@ -58,7 +58,7 @@ __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
   int64_t q = at(g, c.i, c.j, c.k);
   T fxm = fx[at(g, wrap_dn(c.i, g.nx), c.j, c.k)];
   T fym = fy[at(g, c.i, wrap_dn(c.j, g.ny), c.k)];
-  T fzm = c.k > 0 ? fz[q - g.pxy] : T(0);
+  T fzm = zopen(g, c.k - 1) ? fz[at(g, c.i, c.j, kadj(g, c.k - 1))] : T(0);
   out[q] = P[q] - ((fx[q] - fxm) + (fy[q] - fym) + (fz[q] - fzm)) * rcp(G[q]);
 }
 
@@ -75,7 +75,7 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
   const int i = c.i, j = c.j, k = c.k;
   const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
   const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
-  const int kp = clampk(k + 1, g.nz), km = clampk(k - 1, g.nz);
+  const int kp = kadj(g, k + 1), km = kadj(g, k - 1);
   auto p = [&](int a, int b, int d) { return P[at(g, a, b, d)]; };
   const int64_t q = at(g, i, j, k);
   const T pc = P[q];
@@ -98,13 +98,13 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
     vt[q] = pseudo_velocity(cv[q], G[q] + G[at(g, i, jp, k)], pc, p(i, jp, k), s1p, s1m, s2p,
                             s2m, us, ws);
   }
-  if (k < g.nz - 1) {  // z face between (k) and (k+1); the top face is closed
-    const T s1p = p(ip, j, k + 1) + p(ip, j, k), s1m = p(im, j, k + 1) + p(im, j, k);
-    const T s2p = p(i, jp, k + 1) + p(i, jp, k), s2m = p(i, jm, k + 1) + p(i, jm, k);
-    const T us = cu[q] + cu[q + g.pxy] + cu[at(g, im, j, k)] + cu[at(g, im, j, k + 1)];
-    const T vs = cv[q] + cv[q + g.pxy] + cv[at(g, i, jm, k)] + cv[at(g, i, jm, k + 1)];
-    wt[q] = pseudo_velocity(cw[q], G[q] + G[q + g.pxy], pc, p(i, j, k + 1), s1p, s1m, s2p, s2m,
-                            us, vs);
+  if (zopen(g, k)) {  // z face between (k) and (k+1); a zero-flux top face is closed
+    const int64_t qp = at(g, i, j, kp);
+    const T s1p = p(ip, j, kp) + p(ip, j, k), s1m = p(im, j, kp) + p(im, j, k);
+    const T s2p = p(i, jp, kp) + p(i, jp, k), s2m = p(i, jm, kp) + p(i, jm, k);
+    const T us = cu[q] + cu[qp] + cu[at(g, im, j, k)] + cu[at(g, im, j, kp)];
+    const T vs = cv[q] + cv[qp] + cv[at(g, i, jm, k)] + cv[at(g, i, jm, kp)];
+    wt[q] = pseudo_velocity(cw[q], G[q] + G[qp], pc, P[qp], s1p, s1m, s2p, s2m, us, vs);
   } else {
     wt[q] = T(0);
   }
@@ -127,7 +127,7 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
   const int i = c.i, j = c.j, k = c.k;
   const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
   const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
-  const int kp = clampk(k + 1, g.nz), km = clampk(k - 1, g.nz);
+  const int kp = kadj(g, k + 1), km = kadj(g, k - 1);
   const int64_t q = at(g, i, j, k);
   const int64_t nb[6] = {at(g, im, j, k), at(g, ip, j, k), at(g, i, jm, k),
                          at(g, i, jp, k), at(g, i, j, km), at(g, i, j, kp)};
@@ -140,8 +140,8 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
   T fxm = donor(P[nb[0]], pc, ut[nb[0]]);
   T fyp = donor(pc, P[nb[3]], vt[q]);
   T fym = donor(P[nb[2]], pc, vt[nb[2]]);
-  T fzp = k < g.nz - 1 ? donor(pc, P[nb[5]], wt[q]) : zero;
-  T fzm = k > 0 ? donor(P[nb[4]], pc, wt[nb[4]]) : zero;
+  T fzp = zopen(g, k) ? donor(pc, P[nb[5]], wt[q]) : zero;
+  T fzm = zopen(g, k - 1) ? donor(P[nb[4]], pc, wt[nb[4]]) : zero;
   T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
   T out = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
   const T ri = rcp(in + eps), ro = rcp(out + eps);
@@ -170,10 +170,12 @@ __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restri
   T lx = limit_face(ut[q], buc, bdc, bu[qx], bd[qx]);
   T ly = limit_face(vt[q], buc, bdc, bu[qy], bd[qy]);
   T lz = T(0);
-  if (c.k < g.nz - 1) lz = limit_face(wt[q], buc, bdc, bu[q + g.pxy], bd[q + g.pxy]);
+  const bool oz = zopen(g, c.k);
+  const int64_t qz = at(g, c.i, c.j, kadj(g, c.k + 1));
+  if (oz) lz = limit_face(wt[q], buc, bdc, bu[qz], bd[qz]);
   fx[q] = donor(pc, P[qx], lx);
   fy[q] = donor(pc, P[qy], ly);
-  fz[q] = c.k < g.nz - 1 ? donor(pc, P[q + g.pxy], lz) : T(0);
+  fz[q] = oz ? donor(pc, P[qz], lz) : T(0);
   if (ul) { ul[q] = lx; vl[q] = ly; wl[q] = lz; }
 }
 
@@ -231,20 +233,22 @@ __device__ __forceinline__ int64_t padded_at(const Geo& g, const HaloCell& c) {
 __device__ __forceinline__ int64_t halo_source(const Geo& g, const HaloCell& c) {
   const int is = ((c.ii % g.nx) + g.nx) % g.nx;
   const int js = ((c.jj % g.ny) + g.ny) % g.ny;
-  const int ks = c.kk < 0 ? 0 : (c.kk >= g.nz ? g.nz - 1 : c.kk);
+  const int ks = g.kper ? ((c.kk % g.nz) + g.nz) % g.nz
+                       : (c.kk < 0 ? 0 : (c.kk >= g.nz ? g.nz - 1 : c.kk));
   return at(g, is, js, ks);
 }
 
-// Fill: CELL (kind 0) periodic images in i and j, edge copy in k; WFACE
-// (kind 1) the same, except that the faces k < 0 and k >= nz-1 (the closed
-// bottom and top faces, interior included) are 0.
+// Fill: CELL (kind 0) periodic images in i and j, edge copy in k (periodic
+// k: the level nz away); WFACE (kind 1) the same, except that with closed
+// vertical boundaries the faces k < 0 and k >= nz-1 (the bottom and top
+// faces, interior included) are 0.
 template <class T>
 __global__ void halo_kernel(Geo g, T* __restrict__ f, int kind) {
-  const bool top = kind == 1;
+  const bool top = kind == 1 && !g.kper;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= halo_count(g, top)) return;
   const HaloCell c = halo_cell(g, top, t);
-  const bool closed = kind == 1 && (c.kk < 0 || c.kk >= g.nz - 1);
+  const bool closed = top && (c.kk < 0 || c.kk >= g.nz - 1);
   f[padded_at(g, c)] = closed ? T(0) : f[halo_source(g, c)];
 }
 

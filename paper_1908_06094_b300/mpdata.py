@@ -22,7 +22,7 @@ class MPDATA:
     """
 
     def __init__(self, nx, ny, nz, halo=2, iord=2, nonoscillatory=True,
-                 dtype=torch.float64, device=None, variant=None):
+                 dtype=torch.float64, device=None, variant=None, k_bc=C.MPDATA_K_ZEROFLUX):
         if dtype not in _DT:
             raise TypeError(f"dtype must be float64 or float32, got {dtype}")
         self.nx, self.ny, self.nz, self.h = nx, ny, nz, halo
@@ -30,8 +30,8 @@ class MPDATA:
         self.device = torch.device(device if device is not None else "cuda")
         with torch.cuda.device(self.device):
             stream = torch.cuda.current_stream(self.device).cuda_stream
-            self._ctx = C.mpdata_init(nx, ny, nz, halo, iord, self.nonosc, _DT[dtype],
-                                      C.MPDATA_K_ZEROFLUX, stream)
+            self._ctx = C.mpdata_init(nx, ny, nz, halo, iord, self.nonosc, _DT[dtype], k_bc,
+                                      stream)
         if variant is not None:
             C.mpdata_set_variant(self._ctx, variant)
         self.shape = padded_shape(nx, ny, nz, halo)

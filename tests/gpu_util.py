@@ -11,7 +11,7 @@ def to_dev(a, dtype):
 
 
 def run_library(case, dtype, iord=None, nonosc=None, nsteps=1, h=None, variant=None,
-                psi=None, halo_fill=np.nan):
+                psi=None, halo_fill=np.nan, k_bc=0):
     """Advance case.psi by nsteps on the GPU; returns the padded result (float64)."""
     import torch
     from paper_1908_06094_b300 import MPDATA
@@ -19,7 +19,7 @@ def run_library(case, dtype, iord=None, nonosc=None, nsteps=1, h=None, variant=N
     iord = case.iord if iord is None else iord
     nonosc = case.nonosc if nonosc is None else nonosc
     m = MPDATA(case.nx, case.ny, case.nz, halo=h, iord=iord, nonoscillatory=nonosc,
-               dtype=dtype, variant=variant)
+               dtype=dtype, variant=variant, k_bc=k_bc)
     P = [synth.pad(x, h, fill=halo_fill) for x in (case.psi if psi is None else psi,
                                                    case.u, case.v, case.w, case.g)]
     d = [to_dev(x, dtype) for x in P]
