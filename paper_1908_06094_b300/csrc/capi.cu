@@ -210,10 +210,18 @@ template <class T> struct FusedShape;
 template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 8, MINB = 1; };
 template <> struct FusedShape<float> { static constexpr int TX = 32, TY = 16, MINB = 1; };
 
-template <class T, bool LIMIT, bool TAPE = false>
+template <class T, bool LIMIT, bool TAPE = false, bool KPER = false>
 auto fused_kernel_ptr() {
   using F = FusedShape<T>;
-  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, TAPE>;
+  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, TAPE, KPER>;
+}
+
+// The instance for the context's limiter and vertical boundary.
+template <class T, bool TAPE>
+auto fused_pick(const mpdata_ctx* c) {
+  if (c->g.kper)
+    return c->nonosc ? fused_kernel_ptr<T, true, TAPE, true>() : fused_kernel_ptr<T, false, TAPE, true>();
+  return c->nonosc ? fused_kernel_ptr<T, true, TAPE>() : fused_kernel_ptr<T, false, TAPE>();
 }
 
 template <class T>
@@ -236,20 +244,16 @@ int fused_setup(mpdata_ctx* c) {
   c->fused_ok = 0;
   if (c->iord != 2 || g.nx < 2 * g.h || g.ny < 2 * g.h) return MPDATA_OK;
   const size_t bytes = fused_smem<T>();
-  auto k1 = fused_kernel_ptr<T, true>();
-  auto k0 = fused_kernel_ptr<T, false>();
-  auto kt1 = fused_kernel_ptr<T, true, true>();
-  auto kt0 = fused_kernel_ptr<T, false, true>();
+  auto kplain = fused_pick<T, false>(c);
+  auto ktape = fused_pick<T, true>(c);
   const int ib = (int)bytes;
-  if (cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess ||
-      cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess ||
-      cudaFuncSetAttribute(kt1, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess ||
-      cudaFuncSetAttribute(kt0, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess) {
+  if (cudaFuncSetAttribute(kplain, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess ||
+      cudaFuncSetAttribute(ktape, cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess) {
     cudaGetLastError();
     return MPDATA_OK;  // not eligible on this device: the staged kernels run
   }
   int occ = 0, sms = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, c->nonosc ? k1 : k0, fused_threads<T>(), bytes);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kplain, fused_threads<T>(), bytes);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   cudaGetLastError();
   if (occ < 1) return MPDATA_OK;
@@ -288,13 +292,8 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
                kern<<<grid, fused_threads<T>(), bytes, c->stream>>>(g, c->kchunk, in, U, V, W, G,
                                                                    out, tp));
   };
-  if (tape) {
-    if (c->nonosc) go(fused_kernel_ptr<T, true, true>());
-    else go(fused_kernel_ptr<T, false, true>());
-  } else {
-    if (c->nonosc) go(fused_kernel_ptr<T, true>());
-    else go(fused_kernel_ptr<T, false>());
-  }
+  if (tape) go(fused_pick<T, true>(c));
+  else go(fused_pick<T, false>(c));
   MPD_CHECK_LAUNCH(c, "fused step kernel");
   return MPDATA_OK;
 }

@@ -60,7 +60,8 @@ struct TapeOut {
 // whether the tape keeps the limiter's reciprocals
 template <class T> struct TapesReciprocals { static constexpr bool v = sizeof(T) == 8; };
 
-template <class T, int TX, int TY, bool LIMIT, bool TAPE = false, int UNROLL = 1>
+template <class T, int TX, int TY, bool LIMIT, bool TAPE = false, int UNROLL = 1,
+          bool KPER = false>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
                                            const T* __restrict__ P0, const T* __restrict__ U,
                                            const T* __restrict__ V, const T* __restrict__ W,
@@ -94,7 +95,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     rcol = (int64_t)wrapj(j0 + ry) * g.px + wrapi(i0 + rx);
   }
   const int64_t pxy = g.pxy;
-  const bool kper = g.kper != 0;
+  constexpr bool kper = KPER;  // periodic in k (g.kper): a compile-time variant
   // the level of plane k: clamped (edge copy) or, periodic in k, wrapped
   // (any distance: the march runs up to 5 planes past the grid)
   auto clampk_ = [&](int k) {
@@ -109,7 +110,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   const int64_t c0 = g.off0 + col, rc0 = g.off0 + rcol;
   auto ld = [&](const T* f, int k, int64_t c) { return f[c + (int64_t)clampk_(k) * pxy]; };
   // vertical face value with the closed bottom and top faces
-  auto ldw = [&](int k, int64_t c) { return zface(k) ? W[c + (int64_t)clampk_(k) * pxy] : zero; };
+  auto ldw = [&](int k, int64_t c) {
+    if constexpr (KPER) return W[c + (int64_t)clampk_(k) * pxy];
+    else return (k < 0 || k >= nz - 1) ? zero : W[c + (int64_t)k * pxy];
+  };
   // shared-memory views
   T* p0s = sm + L::P0S;
   T* us = sm + L::US;
@@ -159,6 +163,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   T riA = zero, roA = zero, riB = zero, roB = zero;  // their 1/(in+eps), 1/(out+eps) (FP64 tape)
   T fzA = zero, fzB = zero;              // vertical fluxes at faces t-1/2, t+1/2
 
+  // periodic k: the wrapped levels of planes t+3, t+4, t+5, advanced by one
+  // level per plane (no division in the loop)
+  int l3 = clampk_(t0 + 3), l4 = clampk_(t0 + 4), l5 = clampk_(t0 + 5);
+
   __syncthreads();  // the shared memory may still be read by a previous tile
   for (int tg = t0; tg < k1; tg += UNROLL) {
 #pragma unroll
@@ -181,8 +189,9 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     }
     // loads one plane ahead (used from the next iteration on); the plane
     // offsets are the same for every thread
-    const int64_t o5 = (int64_t)clampk_(t + 5) * pxy, o4 = (int64_t)clampk_(t + 4) * pxy;
-    const int64_t o3 = (int64_t)clampk_(t + 3) * pxy;
+    const int64_t o5 = (int64_t)(KPER ? l5 : clampk_(t + 5)) * pxy;
+    const int64_t o4 = (int64_t)(KPER ? l4 : clampk_(t + 4)) * pxy;
+    const int64_t o3 = (int64_t)(KPER ? l3 : clampk_(t + 3)) * pxy;
     const T pn_next = P0[c0 + o5];
     const T un_next = U[c0 + o4], vn_next = V[c0 + o4], gn_next = G[c0 + o4];
     const T wn_next = zface(t + 4) ? W[c0 + o4] : zero;  // closed faces
@@ -324,8 +333,12 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       // the levels holding this value: t, and its k-halo images -- edge
       // copies of the bottom and top levels, or under periodic k the
       // levels t + m nz within [-h, nz + h)
-      const int ilo = kper ? t - ((t + g.h) / nz) * nz : ((t == 0) ? -g.h : t);
-      const int ihi = kper ? nz - 1 + g.h : ((t == nz - 1) ? nz - 1 + g.h : t);
+      int ilo = (t == 0) ? -g.h : t, ihi = (t == nz - 1) ? nz - 1 + g.h : t;
+      if constexpr (KPER) {
+        ilo = t;
+        while (ilo - nz >= -g.h) ilo -= nz;
+        ihi = nz - 1 + g.h;
+      }
       for (int kk = ilo; kk <= ihi; kk += kper ? nz : 1) {
         if (!kper && kk != t && kk >= 0 && kk < nz) continue;
         const int64_t pk = g.off0 + (int64_t)kk * g.pxy;
@@ -350,22 +363,23 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     buA = buB; bdA = bdB;
     if (kTapeR) { riA = riB; roA = roB; }
     fzA = fzB;
+    if constexpr (KPER) { l3 = l4; l4 = l5; l5 = l5 + 1 == nz ? 0 : l5 + 1; }
     // The next iteration publishes into slots nobody reads after this point
     // of the current one; its first barrier orders the rest.
   }
   }
 }
 
-template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false>
+template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false, bool KPER = false>
 __global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
              const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
              T* __restrict__ out, TapeOut<T> tape) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k0 = blockIdx.z * kchunk;
-  step_tile2<T, TX, TY, LIMIT, TAPE>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
-                                     min(g.nz, k0 + kchunk), P0, U, V, W, G, out, smem_raw,
-                                     tape);
+  step_tile2<T, TX, TY, LIMIT, TAPE, 1, KPER>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
+                                              min(g.nz, k0 + kchunk), P0, U, V, W, G, out,
+                                              smem_raw, tape);
 }
 
 }  // namespace fused2
