@@ -48,7 +48,7 @@ def _bind(path):
     lib = ctypes.CDLL(path)
     I = ctypes.c_int
     lib.orc_fill_halo.argtypes = [I, I, I, I, I, I, _D]
-    lib.orc_run.argtypes = [I, I, I, I, I, I, I, I] + [_D] * 6 + [_D] * 11
+    lib.orc_run.argtypes = [I] * 9 + [_D] * 6 + [_D] * 11
     lib.orc_pseudo_velocity.argtypes = [I, I, I, I, I] + [_D] * 8
     lib.orc_mass.argtypes = [I, I, I, I, _D, _D]
     lib.orc_mass.restype = ctypes.c_double
@@ -101,16 +101,21 @@ def fill_halo(f: np.ndarray, h: int, kind: int = 0, kbc: int = 0) -> np.ndarray:
     return f
 
 
+DFL, ABS, IGA = 1, 2, 4  # option flags of the corrective passes
+
+
 def run(psi, u, v, w, g, h: int, iord: int = 2, nonosc: int = 1, nsteps: int = 1,
-        stages: bool = False, kbc: int = 0):
+        stages: bool = False, kbc: int = 0, opts: int = 0):
     """nsteps MPDATA steps.  Returns psi^(n+nsteps) (padded), and with
-    ``stages`` also a dict of the last corrective pass's intermediates."""
+    ``stages`` also a dict of the last corrective pass's intermediates.
+    opts: DFL (divergent-flow term), ABS (signed fields), IGA (infinite
+    gauge), or'ed."""
     nx, ny, nz = _dims(psi, h)
     arrs = [np.ascontiguousarray(x, dtype=np.float64) for x in (psi, u, v, w, g)]
     out = np.zeros_like(arrs[0])
     names = ["psi1", "ut", "vt", "wt", "mx", "mn", "bu", "bd", "ul", "vl", "wl"]
     st = {k: np.zeros_like(arrs[0]) for k in names} if stages else {}
-    _load().orc_run(nx, ny, nz, h, kbc, iord, nonosc, nsteps, *[_p(a) for a in arrs], _p(out),
+    _load().orc_run(nx, ny, nz, h, kbc, iord, nonosc, opts, nsteps, *[_p(a) for a in arrs], _p(out),
                     *[_p(st.get(k)) for k in names])
     return (out, st) if stages else out
 

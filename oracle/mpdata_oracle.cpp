@@ -31,6 +31,17 @@
  * epsilon = 1e-15 in every ratio.  Ties: max(a,b) = a if a >= b, min(a,b) = a
  * if a <= b, and |x| has derivative sign(x) with sign(0) = 0.
  *
+ * Options of the corrective passes (bit flags, forward only; the paper does
+ * not describe them, they follow the MPDATA literature):
+ *   1 DFL  divergent-flow term added to the pseudo-velocities (Smolarkiewicz
+ *          1984);
+ *   2 ABS  signed fields: A and B are formed from |psi|, and the limiter
+ *          takes its factors by the direction of the flux, not of the
+ *          velocity (the two agree where psi >= 0);
+ *   4 IGA  infinite gauge: the limit c -> infinity of the scheme applied to
+ *          psi + c (Smolarkiewicz & Clark 1986): linear pseudo-fluxes that
+ *          are themselves the corrective fluxes.
+ *
  * The scalar type is a template parameter so that the same code, run on dual
  * numbers, gives the exact tangent-linear model used to pin the adjoint.
  */
@@ -57,6 +68,11 @@ struct Grid {
   bool zface(int k) const { return kper || k < nz - 1; }
   long size() const { return px * py * pz; }
   long at(int i, int j, int k) const { return ((k + h) * py + (j + h)) * px + (i + h); }
+};
+
+struct Opts {
+  bool dfl, abs, iga;
+  explicit Opts(int f = 0) : dfl(f & 1), abs(f & 2), iga(f & 4) {}
 };
 
 /* ---------------------------------------------------------------- scalars */
@@ -216,14 +232,95 @@ void pseudo_velocity(const Grid& g, const T* P, const T* u, const T* v, const T*
       }
 }
 
+/* Infinite-gauge pseudo-fluxes (option IGA).  For psi + c the pseudo-velocity
+   of a face behaves as 1/c and its donor flux tends, as c grows, to c times
+   it; that limit replaces both the pseudo-velocity and its flux:
+     Ft = (|U| - U^2/Gf) (P_R - P_L)/2 - U (Vbar Ny + Wbar Nz) / Gf,
+     Ny = (P_R,j+1 + P_L,j+1 - P_R,j-1 - P_L,j-1)/8,
+   i.e. c A -> (P_R - P_L)/2 and c B -> (numerator of B)/8, the denominators
+   P_R + P_L + eps and the four-point sum + eps being 2c and 4c in the limit.
+   Vbar, Wbar and Gf as in pseudo_velocity.  Ft on a closed top face is 0. */
+template <class T>
+void pseudo_flux_iga(const Grid& g, const T* P, const T* u, const T* v, const T* w, const T* G,
+                     T* fu, T* fv, T* fw) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+  const T half(0.5), quarter(0.25), eighth(0.125);
+  // one face: right cell at c + d; cross directions e1, e2 with their face
+  // Courant fields c1, c2
+  auto face = [&](long c, long d, long e1, long e2, T C, const T* c1, const T* c2) {
+    const long L = c, R = c + d;
+    const T Gf = half * (G[L] + G[R]);
+    const T dA = half * (P[R] - P[L]);
+    const T n1 = eighth * (P[R + e1] + P[L + e1] - P[R - e1] - P[L - e1]);
+    const T n2 = eighth * (P[R + e2] + P[L + e2] - P[R - e2] - P[L - e2]);
+    const T m1 = quarter * (c1[L] + c1[R] + c1[L - e1] + c1[R - e1]);
+    const T m2 = quarter * (c2[L] + c2[R] + c2[L - e2] + c2[R - e2]);
+    return (oabs(C) - C * C / Gf) * dA - C * (m1 * n1 + m2 * n2) / Gf;
+  };
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        fu[c] = face(c, X, Y, Z, u[c], v, w);
+        fv[c] = face(c, Y, X, Z, v[c], u, w);
+        fw[c] = g.zface(k) ? face(c, Z, X, Y, w[c], u, v) : T(0.0);
+      }
+}
+
+/* Divergent-flow term (option DFL; Smolarkiewicz 1984).  In a divergent flow
+   the donor-cell scheme's first-order error has a further part, which the
+   pseudo-velocity cancels with -1/2 U (dt div v): with the divergence of the
+   G-weighted Courant numbers of a cell,
+     D_c = (U_c - U_c-X) + (V_c - V_c-Y) + (W_c - W_c-Z),
+   averaged over the face's two cells and divided by the face's G,
+     Ut += -(1/4) U (D_L + D_R) / Gf,
+   and the same for Vt and Wt (the closed faces' W are 0 in the halo). */
+template <class T>
+void add_divergent_flow_term(const Grid& g, const T* u, const T* v, const T* w, const T* G,
+                             T* ut, T* vt, T* wt) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+  const T half(0.5), quarter(0.25);
+  auto D = [&](long c) { return (u[c] - u[c - X]) + (v[c] - v[c - Y]) + (w[c] - w[c - Z]); };
+  auto term = [&](long L, long R, T C) {
+    return -quarter * C * (D(L) + D(R)) / (half * (G[L] + G[R]));
+  };
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        ut[c] = ut[c] + term(c, c + X, u[c]);
+        vt[c] = vt[c] + term(c, c + Y, v[c]);
+        if (g.zface(k)) wt[c] = wt[c] + term(c, c + Z, w[c]);
+      }
+}
+
+/* Flux divergence and advance with the face fluxes given (the infinite-gauge
+   corrective pass, whose pseudo-fluxes are fluxes already):
+   out = P - (1/G) sum_d [F_c+d/2 - F_c-d/2]. */
+template <class T>
+void advance_fluxes(const Grid& g, const T* P, const T* fu, const T* fv, const T* fw, const T* G,
+                    T* out) {
+  const long X = 1, Y = g.px, Z = g.px * g.py;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < g.nz; ++k)
+    for (int j = 0; j < g.ny; ++j)
+      for (int i = 0; i < g.nx; ++i) {
+        long c = g.at(i, j, k);
+        out[c] = P[c] - ((fu[c] - fu[c - X]) + (fv[c] - fv[c - Y]) + (fw[c] - fw[c - Z])) / G[c];
+      }
+}
+
 /* Non-oscillatory limiter (Smolarkiewicz & Grabowski 1990), G-weighted.
    Bounds over the 7-point stencil of both psi^n (P0) and psi^(m-1) (P);
    unlimited antidiffusive fluxes f = F(P_L, P_R, Ut); incoming and outgoing
    flux sums; beta-up = (max - P) G / (in + eps), beta-down =
-   (P - min) G / (out + eps); output: betas (halo-filled) in bu, bd. */
+   (P - min) G / (out + eps); output: betas (halo-filled) in bu, bd.  With
+   `unit` (infinite gauge) the face values ut, vt, wt are the fluxes. */
 template <class T>
 void limiter_betas(const Grid& g, const T* P0, const T* P, const T* ut, const T* vt, const T* wt,
-                   const T* G, T* mx, T* mn, T* bu, T* bd) {
+                   const T* G, T* mx, T* mn, T* bu, T* bd, bool unit = false) {
   const long X = 1, Y = g.px, Z = g.px * g.py;
   const T eps(EPS), zero(0.0);
   const long nb[6] = {-X, X, -Y, Y, -Z, Z};
@@ -244,12 +341,13 @@ void limiter_betas(const Grid& g, const T* P0, const T* P, const T* ut, const T*
         mx[c] = hi;
         mn[c] = lo;
         // fluxes through the six faces: the "+" faces and the "-" faces
-        T fxp = donor(P[c], P[c + X], ut[c]);
-        T fxm = donor(P[c - X], P[c], ut[c - X]);
-        T fyp = donor(P[c], P[c + Y], vt[c]);
-        T fym = donor(P[c - Y], P[c], vt[c - Y]);
-        T fzp = donor(P[c], P[c + Z], wt[c]);
-        T fzm = donor(P[c - Z], P[c], wt[c - Z]);
+        auto fl = [&](T L, T R, T C) { return unit ? C : donor(L, R, C); };
+        T fxp = fl(P[c], P[c + X], ut[c]);
+        T fxm = fl(P[c - X], P[c], ut[c - X]);
+        T fyp = fl(P[c], P[c + Y], vt[c]);
+        T fym = fl(P[c - Y], P[c], vt[c - Y]);
+        T fzp = fl(P[c], P[c + Z], wt[c]);
+        T fzm = fl(P[c - Z], P[c], wt[c - Z]);
         T in = (omax(fxm, zero) - omin(fxp, zero)) + (omax(fym, zero) - omin(fyp, zero)) +
                (omax(fzm, zero) - omin(fzp, zero));
         T out = (omax(fxp, zero) - omin(fxm, zero)) + (omax(fyp, zero) - omin(fym, zero)) +
@@ -270,18 +368,26 @@ template <class T> inline T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
   return cpos * omax(Ut, zero) + cneg * omin(Ut, zero);
 }
 
+/* With `sgn` (signed fields, P = psi^(m-1)) a face whose upwind value is
+   negative carries its flux against its velocity: beta-up and beta-down
+   trade places there, which limits the flux by its own direction. */
 template <class T>
 void limit_velocities(const Grid& g, const T* ut, const T* vt, const T* wt, const T* bu,
-                      const T* bd, T* ul, T* vl, T* wl) {
+                      const T* bd, T* ul, T* vl, T* wl, const T* P = nullptr, bool sgn = false) {
   const long X = 1, Y = g.px, Z = g.px * g.py;
+  auto lim = [&](T Ut, long L, long R) {
+    const bool flip = sgn && val(val(Ut) >= 0.0 ? P[L] : P[R]) < 0.0;
+    return flip ? limit_face(Ut, bd[L], bu[L], bd[R], bu[R])
+                : limit_face(Ut, bu[L], bd[L], bu[R], bd[R]);
+  };
 #pragma omp parallel for schedule(static)
   for (int k = 0; k < g.nz; ++k)
     for (int j = 0; j < g.ny; ++j)
       for (int i = 0; i < g.nx; ++i) {
         long c = g.at(i, j, k);
-        ul[c] = limit_face(ut[c], bu[c], bd[c], bu[c + X], bd[c + X]);
-        vl[c] = limit_face(vt[c], bu[c], bd[c], bu[c + Y], bd[c + Y]);
-        wl[c] = g.zface(k) ? limit_face(wt[c], bu[c], bd[c], bu[c + Z], bd[c + Z]) : T(0.0);
+        ul[c] = lim(ut[c], c, c + X);
+        vl[c] = lim(vt[c], c, c + Y);
+        wl[c] = g.zface(k) ? lim(wt[c], c, c + Z) : T(0.0);
       }
 }
 
@@ -298,9 +404,10 @@ template <class T> void copy_out(double* dst, const std::vector<T>& src) {
 /* One MPDATA step.  Inputs are read at their interior points only. */
 template <class T>
 void mpdata_step(const Grid& g, int iord, int nonosc, const T* psi_in, const T* Uin,
-                 const T* Vin, const T* Win, const T* Gin, T* psi_out, const Stages* st) {
+                 const T* Vin, const T* Win, const T* Gin, T* psi_out, const Stages* st,
+                 Opts o = Opts()) {
   const long n = g.size();
-  std::vector<T> P0(n), P(n), Pn(n), U(n), V(n), W(n), G(n);
+  std::vector<T> P0(n), P(n), Pn(n), U(n), V(n), W(n), G(n), Pa(o.abs ? n : 0);
   std::vector<T> ut(n), vt(n), wt(n), ul(n), vl(n), wl(n), mx(n), mn(n), bu(n), bd(n);
   for (int k = 0; k < g.nz; ++k)
     for (int j = 0; j < g.ny; ++j)
@@ -321,15 +428,23 @@ void mpdata_step(const Grid& g, int iord, int nonosc, const T* psi_in, const T* 
   // 3. corrective passes
   const T *cu = U.data(), *cv = V.data(), *cw = W.data();
   for (int m = 2; m <= iord; ++m) {
-    pseudo_velocity(g, P.data(), cu, cv, cw, G.data(), ut.data(), vt.data(), wt.data());
+    if (o.iga) {
+      pseudo_flux_iga(g, P.data(), cu, cv, cw, G.data(), ut.data(), vt.data(), wt.data());
+    } else if (o.abs) {  // A and B of |psi^(m-1)|
+      for (long q = 0; q < n; ++q) Pa[q] = oabs(P[q]);
+      pseudo_velocity(g, Pa.data(), cu, cv, cw, G.data(), ut.data(), vt.data(), wt.data());
+    } else {
+      pseudo_velocity(g, P.data(), cu, cv, cw, G.data(), ut.data(), vt.data(), wt.data());
+    }
+    if (o.dfl) add_divergent_flow_term(g, cu, cv, cw, G.data(), ut.data(), vt.data(), wt.data());
     fill_halo_periodic(ut.data(), g);
     fill_halo_periodic(vt.data(), g);
     fill_halo_wface(wt.data(), g);
     if (nonosc) {
       limiter_betas(g, P0.data(), P.data(), ut.data(), vt.data(), wt.data(), G.data(), mx.data(),
-                    mn.data(), bu.data(), bd.data());
+                    mn.data(), bu.data(), bd.data(), o.iga);
       limit_velocities(g, ut.data(), vt.data(), wt.data(), bu.data(), bd.data(), ul.data(),
-                       vl.data(), wl.data());
+                       vl.data(), wl.data(), P.data(), o.abs && !o.iga);
     } else {
       std::copy(ut.begin(), ut.end(), ul.begin());
       std::copy(vt.begin(), vt.end(), vl.begin());
@@ -338,7 +453,10 @@ void mpdata_step(const Grid& g, int iord, int nonosc, const T* psi_in, const T* 
     fill_halo_periodic(ul.data(), g);
     fill_halo_periodic(vl.data(), g);
     fill_halo_wface(wl.data(), g);
-    advance(g, P.data(), ul.data(), vl.data(), wl.data(), G.data(), Pn.data());
+    if (o.iga)
+      advance_fluxes(g, P.data(), ul.data(), vl.data(), wl.data(), G.data(), Pn.data());
+    else
+      advance(g, P.data(), ul.data(), vl.data(), wl.data(), G.data(), Pn.data());
     fill_halo_periodic(Pn.data(), g);
     if (st && m == iord) {
       copy_out(st->ut, ut); copy_out(st->vt, vt); copy_out(st->wt, wt);
@@ -719,8 +837,9 @@ void orc_fill_halo(int nx, int ny, int nz, int h, int kbc, int kind, double* f) 
 
 /* nsteps MPDATA steps; psi_out gets the padded result with its halo filled.
    The optional stage pointers (may be null) receive the intermediates of the
-   last corrective pass of the last step. */
-void orc_run(int nx, int ny, int nz, int h, int kbc, int iord, int nonosc, int nsteps,
+   last corrective pass of the last step.  opts: the option flags (DFL 1,
+   ABS 2, IGA 4). */
+void orc_run(int nx, int ny, int nz, int h, int kbc, int iord, int nonosc, int opts, int nsteps,
              const double* psi_in, const double* U, const double* V, const double* W,
              const double* G, double* psi_out, double* psi1, double* ut, double* vt, double* wt,
              double* mx, double* mn, double* bu, double* bd, double* ul, double* vl, double* wl) {
@@ -729,7 +848,7 @@ void orc_run(int nx, int ny, int nz, int h, int kbc, int iord, int nonosc, int n
   std::vector<double> cur(psi_in, psi_in + g.size()), nxt(g.size());
   for (int s = 0; s < nsteps; ++s) {
     mpdata_step<double>(g, iord, nonosc, cur.data(), U, V, W, G, nxt.data(),
-                        s == nsteps - 1 ? &st : nullptr);
+                        s == nsteps - 1 ? &st : nullptr, Opts(opts));
     cur.swap(nxt);
   }
   std::memcpy(psi_out, cur.data(), sizeof(double) * g.size());

@@ -6,12 +6,13 @@ on a temporary copy, compiled and loaded in place of the real build for the
 duration of one check.
 """
 import os
-import tempfile
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_variants as vpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "mpdata_oracle.cpp")
 
@@ -76,14 +77,42 @@ MUTANTS = [
     ("periodic k halo copies the edge level",
      "int ks = g.kper ? wrap(k, g.nz) : (k < 0 ? 0 : g.nz - 1);\n    for (int j = -g.h; j < g.ny + g.h; ++j)\n      for (int i = -g.h; i < g.nx + g.h; ++i) f[",
      "int ks = (k < 0 ? 0 : g.nz - 1);\n    for (int j = -g.h; j < g.ny + g.h; ++j)\n      for (int i = -g.h; i < g.nx + g.h; ++i) f["),
+    ("divergent-flow term takes 1/2 instead of 1/4",
+     "return -quarter * C * (D(L) + D(R)) / (half * (G[L] + G[R]));",
+     "return -half * C * (D(L) + D(R)) / (half * (G[L] + G[R]));"),
+    ("divergent-flow term not divided by the face G",
+     "return -quarter * C * (D(L) + D(R)) / (half * (G[L] + G[R]));",
+     "return -quarter * C * (D(L) + D(R));"),
+    ("divergent-flow divergence drops the V difference",
+     "return (u[c] - u[c - X]) + (v[c] - v[c - Y]) + (w[c] - w[c - Z]);",
+     "return (u[c] - u[c - X]) + (w[c] - w[c - Z]);"),
+    ("divergent-flow divergence drops the W difference",
+     "return (u[c] - u[c - X]) + (v[c] - v[c - Y]) + (w[c] - w[c - Z]);",
+     "return (u[c] - u[c - X]) + (v[c] - v[c - Y]);"),
+    ("infinite gauge cross numerator takes 1/4",
+     "const T n1 = eighth * (P[R + e1]",
+     "const T n1 = quarter * (P[R + e1]"),
+    ("infinite gauge A loses its 1/2",
+     "const T dA = half * (P[R] - P[L]);",
+     "const T dA = (P[R] - P[L]);"),
+    ("infinite gauge limiter takes donor fluxes",
+     "auto fl = [&](T L, T R, T C) { return unit ? C : donor(L, R, C); };",
+     "auto fl = [&](T L, T R, T C) { return donor(L, R, C); };"),
+    ("signed limiter keeps the velocity's direction",
+     "const bool flip = sgn && val(val(Ut) >= 0.0 ? P[L] : P[R]) < 0.0;",
+     "const bool flip = false && sgn;"),
+    ("signed variant forms A and B from psi",
+     "for (long q = 0; q < n; ++q) Pa[q] = oabs(P[q]);",
+     "for (long q = 0; q < n; ++q) Pa[q] = P[q];"),
     ("y halo not wrapped",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, wrap(j, g.ny), k)];",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, j < 0 ? 0 : g.ny - 1, k)];"),
 ]
 
 
-def _pin_battery():
-    """Fast pin checks; each returns normally or raises."""
+def _pin_battery(stop_at_first: bool = False):
+    """Fast pin checks, the cheapest first; each returns normally or raises.
+    Returns how many failed (with stop_at_first: 0 or 1)."""
     checks = [
         pins.test_halo_fill_matches_numpy_pad,
         lambda: pins.test_donor_cell_fourier_1d(0.3, 1.0, "x"),
@@ -102,7 +131,6 @@ def _pin_battery():
         pins.test_limiter_monotone_step_3d,
         lambda: pins.test_positivity(0),
         lambda: pins.test_positivity(1),
-        lambda: pins.test_convergence_order(2, 0, 1.9, 2.3),
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("x", -0.4),
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("y", 0.4),
         lambda: pins.test_limiter_inactive_on_smooth_monotone_data("z", -0.4),
@@ -111,6 +139,13 @@ def _pin_battery():
         pins.test_halo_fill_periodic_k_matches_numpy_pad,
         lambda: pins.test_courant_one_shift_vertical_periodic(2, 1, 1),
         pins.test_adjoint_dot_product_on_rotating_cone,
+        lambda: pins.test_convergence_order(2, 0, 1.9, 2.3),
+        lambda: vpins.test_dfl_restores_second_order_in_divergent_flow("x", True),
+        lambda: vpins.check_dfl_2d("xy", (24, 48, 96)),
+        lambda: vpins.check_dfl_2d("xz", (24, 48, 96)),
+        lambda: vpins.test_iga_is_the_limit_of_a_growing_gauge(1),
+        lambda: vpins.test_abs_is_odd_in_psi(2, 1, 0),
+        lambda: vpins.test_limited_signed_step_makes_no_new_extrema(vpins.ABS),
     ]
     failed = 0
     for chk in checks:
@@ -118,24 +153,40 @@ def _pin_battery():
             chk()
         except Exception:      # an assertion, or NaN/shape trouble the mistake caused
             failed += 1
+            if stop_at_first:
+                break
     return failed
+
+
+@pytest.fixture(scope="module")
+def mutant_libs(tmp_path_factory):
+    """Every mutant compiled up front, several g++ processes at a time;
+    a mutant whose anchor is not found exactly once maps to None."""
+    d = tmp_path_factory.mktemp("mutants")
+    src = open(SRC).read()
+
+    def build_one(idx, orig, mut):
+        if src.count(orig) != 1:
+            return None
+        p = d / f"mutant{idx}.cpp"
+        p.write_text(src.replace(orig, mut))
+        return oracle.build(force=True, src=str(p), out=str(d / f"libmutant{idx}.so"))
+
+    with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+        futs = {name: ex.submit(build_one, i, orig, mut)
+                for i, (name, orig, mut) in enumerate(MUTANTS)}
+        return {name: f.result() for name, f in futs.items()}
 
 
 @pytest.mark.slow
 @pytest.mark.parametrize("name,orig,mut", MUTANTS, ids=[m[0] for m in MUTANTS])
-def test_planted_mistake_is_caught(name, orig, mut):
-    src = open(SRC).read()
-    assert src.count(orig) == 1, f"mutation anchor not unique/found: {name}"
-    with tempfile.TemporaryDirectory() as d:
-        p = os.path.join(d, "mutant.cpp")
-        with open(p, "w") as f:
-            f.write(src.replace(orig, mut))
-        lib = oracle.build(force=True, src=p, out=os.path.join(d, "libmutant.so"))
-        prev = oracle.use_library(lib)
-        try:
-            failed = _pin_battery()
-        finally:
-            oracle.restore_library(prev)
+def test_planted_mistake_is_caught(name, orig, mut, mutant_libs):
+    assert open(SRC).read().count(orig) == 1, f"mutation anchor not unique/found: {name}"
+    prev = oracle.use_library(mutant_libs[name])
+    try:
+        failed = _pin_battery(stop_at_first=True)
+    finally:
+        oracle.restore_library(prev)
     assert failed >= 1, f"no pin caught the planted mistake: {name}"
 
 
