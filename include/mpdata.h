@@ -103,10 +103,35 @@ MPDATA_API int mpdata_init(mpdata_ctx **out, int nx, int ny, int nz, int halo, i
 MPDATA_API int mpdata_set_stream(mpdata_ctx *c, void *cuda_stream);
 
 /* Choose the kernel organisation (mpdata_variant); all give the same step
- * to rounding.  The fused kernel runs only when iord == 2 and nx, ny >= 2h;
- * other contexts use the staged kernels whatever is chosen.
- * Errors: EINVAL. */
+ * to rounding.  The fused kernel runs only when iord == 2, nx, ny >= 2h and
+ * no option is set; other contexts use the staged kernels whatever is
+ * chosen.  Errors: EINVAL. */
 MPDATA_API int mpdata_set_variant(mpdata_ctx *c, int variant);
+
+/* Options of the corrective passes (bit flags).  The paper defers the
+ * antidiffusive passes to the MPDATA literature (Sec. 5); these are that
+ * literature's standard variants:
+ *   DFL  the divergent-flow term (Smolarkiewicz 1984): each pseudo-velocity
+ *        gains -(1/4) U (D_L + D_R) / G_face, D_c = the sum over the three
+ *        directions of the cell's Courant-number differences (second order
+ *        in divergent flows);
+ *   ABS  signed fields: A and B are formed from |psi|, and the limiter
+ *        applies its factors by the direction of each antidiffusive flux
+ *        rather than of its velocity (identical results where psi >= 0);
+ *   IGA  the infinite gauge (Smolarkiewicz & Clark 1986): the limit of the
+ *        scheme applied to psi + c as c grows; the corrective flux of a face
+ *        is (|U| - U^2/Gf)(psi_R - psi_L)/2 - U (Vbar N_y + Wbar N_z)/(8 Gf)
+ *        with N the numerators of B.  A linear scheme, for signed fields.
+ * IGA takes no other option and iord <= 2.  With any option the step runs
+ * on the staged kernels, and the adjoint calls (mpdata_adjoint_step,
+ * mpdata_step_tape, mpdata_adjoint_step_tape) return EINVAL. */
+enum mpdata_option { MPDATA_OPT_DFL = 1, MPDATA_OPT_ABS = 2, MPDATA_OPT_IGA = 4 };
+
+/* Set the option bits of a context (0: the basic scheme, the default).
+ * Errors: EINVAL (unknown bits, IGA with another option or iord > 2; the
+ * options are left unchanged). */
+MPDATA_API int mpdata_set_options(mpdata_ctx *c, int opts);
+MPDATA_API int mpdata_get_options(mpdata_ctx *c, int *opts);
 
 /* Advance psi (in/out, device) by nsteps MPDATA steps with Courant fields
  * u, v, w and metric g (device, read-only).  nsteps >= 0.  With the fused

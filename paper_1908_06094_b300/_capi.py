@@ -28,6 +28,9 @@ MPDATA_HALO_WFACE = 1
 MPDATA_FUSED = 0
 MPDATA_STAGED = 1
 MPDATA_AUTO = 2
+MPDATA_OPT_DFL = 1
+MPDATA_OPT_ABS = 2
+MPDATA_OPT_IGA = 4
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"libmpdata_b300.so not built (expected at {LIB_PATH}); "
@@ -56,6 +59,8 @@ SIGNATURES = {
     "mpdata_init": (_i, [_ctxpp, _i, _i, _i, _i, _i, _i, _i, _i, _c]),
     "mpdata_set_stream": (_i, [_c, _c]),
     "mpdata_set_variant": (_i, [_c, _i]),
+    "mpdata_set_options": (_i, [_c, _i]),
+    "mpdata_get_options": (_i, [_c, _ip]),
     "mpdata_step": (_i, [_c, _c, _c, _c, _c, _c, _i]),
     "mpdata_step_out": (_i, [_c, _c, _c, _c, _c, _c, _c]),
     "mpdata_step_host": (_i, [_c, _c, _c, _c, _c, _c, _i]),
@@ -138,6 +143,16 @@ def mpdata_set_stream(ctx, cuda_stream):
 
 def mpdata_set_variant(ctx, variant):
     _check(lib.mpdata_set_variant(ctx, variant), "mpdata_set_variant", ctx)
+
+
+def mpdata_set_options(ctx, opts):
+    _check(lib.mpdata_set_options(ctx, opts), "mpdata_set_options", ctx)
+
+
+def mpdata_get_options(ctx) -> int:
+    out = ctypes.c_int()
+    _check(lib.mpdata_get_options(ctx, ctypes.byref(out)), "mpdata_get_options", ctx)
+    return out.value
 
 
 def mpdata_step(ctx, psi, u, v, w, g, nsteps):

@@ -21,6 +21,7 @@ using mpd::Geo;
 struct mpdata_ctx {
   Geo g;
   int iord, nonosc, dtype, kbc, variant, device;
+  int opts;  // corrective-pass options (MPDATA_OPT_* bits)
   size_t esize;
   cudaStream_t stream;
   // scratch of one step (one allocation)
@@ -53,6 +54,11 @@ namespace {
 int cuda_fail(mpdata_ctx* c, cudaError_t e, const char* where) {
   if (c) std::snprintf(c->err, sizeof(c->err), "%s: %s", where, cudaGetErrorString(e));
   return MPDATA_ECUDA;
+}
+
+int fail(mpdata_ctx* c, int code, const char* what) {
+  if (c) std::snprintf(c->err, sizeof(c->err), "%s", what);
+  return code;
 }
 
 #define MPD_CHECK_LAUNCH(c, where)                      \
@@ -132,11 +138,15 @@ int march_chunk(mpdata_ctx* c, K kernel, bool pipe_bound) {
 
 // The pseudo-velocity stage: FP64 on the k-marching common-denominator
 // kernel (bound by FP64 instruction count), FP32 on the cell-parallel one.
-template <class T>
+template <class T, int OPT = 0>
 void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W, const T* G,
                    T* ut, T* vt, T* wt) {
   const Geo& g = c->g;
-  if constexpr (std::is_same<T, double>::value) {
+  if constexpr (OPT != 0) {  // the options' terms: cell-parallel kernel
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+               mpd::staged::pseudo_kernel<T, OPT><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
+                   g, P, U, V, W, G, ut, vt, wt));
+  } else if constexpr (std::is_same<T, double>::value) {
     namespace M = mpd::march;
     auto kern = M::march_kernel<double, M::PseudoMerged>;
     if (!c->kc_fwd) c->kc_fwd = march_chunk(c, kern, true);
@@ -152,10 +162,11 @@ void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W
 
 // One MPDATA step, staged organisation (one kernel per stage).
 // psi_out may equal psi_in: psi_in is last read (by the limiter) before the
-// final advance writes psi_out.
-template <class T>
-int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T* V,
-                const T* W, const T* G) {
+// final advance writes psi_out.  OPT: the corrective-pass options.
+template <class T, int OPT>
+int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T* V,
+                    const T* W, const T* G) {
+  constexpr bool kUnit = (OPT & mpd::kOptIGA) != 0;  // pseudo-fluxes are the fluxes
   using namespace mpd::staged;
   const Geo& g = c->g;
   const dim3 grid = cell_grid(g);
@@ -177,17 +188,20 @@ int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T*
     T** tset = (cu == setA[0]) ? setB : setA;  // unlimited pseudo-velocities
     T** lset = (tset == setA) ? setB : setA;   // limited ones (next pass's input)
     const bool more = m < c->iord;
-    pseudo_launch<T>(c, cur, cu, cv, cw, G, tset[0], tset[1], tset[2]);
+    pseudo_launch<T, OPT>(c, cur, cu, cv, cw, G, tset[0], tset[1], tset[2]);
+    const T *ffx = fx, *ffy = fy, *ffz = fz;  // the pass's face fluxes
     if (c->nonosc) {
       MPD_LAUNCH(c, MPDATA_STAGE_BETA,
-                 beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, cur, tset[0], tset[1],
-                                                             tset[2], G, (T*)c->bu, (T*)c->bd,
-                                                             nullptr, nullptr));
+                 (beta_kernel<T, kUnit><<<grid, kCellBlock, 0, s>>>(
+                     g, psi, cur, tset[0], tset[1], tset[2], G, (T*)c->bu, (T*)c->bd, nullptr,
+                     nullptr)));
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                 limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                 (limflux_kernel<T, OPT><<<grid, kCellBlock, 0, s>>>(
                      g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
                      more ? lset[0] : nullptr, more ? lset[1] : nullptr,
-                     more ? lset[2] : nullptr));
+                     more ? lset[2] : nullptr)));
+    } else if (kUnit) {  // the unlimited pseudo-fluxes themselves
+      ffx = tset[0]; ffy = tset[1]; ffz = tset[2];
     } else {
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
                  flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, tset[0], tset[1], tset[2],
@@ -195,13 +209,28 @@ int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T*
     }
     T* dest = !more ? psi_out : (cur == (T*)c->psi1 ? (T*)c->psi2 : (T*)c->psi1);
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, fx, fy, fz, G, dest));
+               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, ffx, ffy, ffz, G, dest));
     MPD_CHECK_LAUNCH(c, "corrective pass");
     cur = dest;
     T** vset = c->nonosc ? lset : tset;
     cu = vset[0]; cv = vset[1]; cw = vset[2];
   }
   return MPDATA_OK;
+}
+
+template <class T>
+int step_staged(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T* V,
+                const T* W, const T* G) {
+  using namespace mpd;
+  switch (c->opts) {
+    case 0: return step_staged_opt<T, 0>(c, psi_in, psi_out, U, V, W, G);
+    case kOptDFL: return step_staged_opt<T, kOptDFL>(c, psi_in, psi_out, U, V, W, G);
+    case kOptABS: return step_staged_opt<T, kOptABS>(c, psi_in, psi_out, U, V, W, G);
+    case kOptDFL | kOptABS:
+      return step_staged_opt<T, kOptDFL | kOptABS>(c, psi_in, psi_out, U, V, W, G);
+    case kOptIGA: return step_staged_opt<T, kOptIGA>(c, psi_in, psi_out, U, V, W, G);
+    default: return fail(c, MPDATA_EINVAL, "unsupported option set");
+  }
 }
 
 // Tile shape of the fused kernel (one thread per column of the tile + 2
@@ -299,7 +328,7 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
 }
 
 bool use_fused(const mpdata_ctx* c) {
-  if (!c->fused_ok) return false;
+  if (!c->fused_ok || c->opts != 0) return false;
   if (c->variant == MPDATA_AUTO) return c->dtype == MPDATA_F32;
   return c->variant == MPDATA_FUSED;
 }
@@ -692,6 +721,24 @@ int mpdata_set_variant(mpdata_ctx* c, int variant) {
   return MPDATA_OK;
 }
 
+int mpdata_set_options(mpdata_ctx* c, int opts) {
+  if (!c) return MPDATA_EINVAL;
+  const int all = MPDATA_OPT_DFL | MPDATA_OPT_ABS | MPDATA_OPT_IGA;
+  if (opts & ~all) return fail(c, MPDATA_EINVAL, "unknown option bits");
+  if ((opts & MPDATA_OPT_IGA) && (opts & (MPDATA_OPT_DFL | MPDATA_OPT_ABS)))
+    return fail(c, MPDATA_EINVAL, "the infinite gauge takes no other option");
+  if ((opts & MPDATA_OPT_IGA) && c->iord > 2)
+    return fail(c, MPDATA_EINVAL, "the infinite gauge is defined for iord <= 2");
+  c->opts = opts;
+  return MPDATA_OK;
+}
+
+int mpdata_get_options(mpdata_ctx* c, int* opts) {
+  if (!c || !opts) return MPDATA_EINVAL;
+  *opts = c->opts;
+  return MPDATA_OK;
+}
+
 int mpdata_step(mpdata_ctx* c, void* psi, const void* u, const void* v, const void* w,
                 const void* g, int nsteps) {
   if (!c || nsteps < 0) return MPDATA_EINVAL;
@@ -813,6 +860,7 @@ int mpdata_adjoint_step(mpdata_ctx* c, const void* psi_n, const void* u, const v
                         const void* w, const void* g, void* psi_bar, void* u_bar, void* v_bar,
                         void* w_bar) {
   if (!c) return MPDATA_EINVAL;
+  if (c->opts) return fail(c, MPDATA_EINVAL, "options have no adjoint");
   const void* f[9] = {psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
   int rc = check_fields(f, 9);
   if (rc) return rc;
@@ -834,6 +882,7 @@ int mpdata_tape_bytes(mpdata_ctx* c, size_t* bytes) {
 int mpdata_step_tape(mpdata_ctx* c, const void* psi_in, void* psi_out, const void* u,
                      const void* v, const void* w, const void* g, void* tape) {
   if (!c) return MPDATA_EINVAL;
+  if (c->opts) return fail(c, MPDATA_EINVAL, "options have no adjoint");
   const void* f[7] = {psi_in, psi_out, u, v, w, g, tape};
   int rc = check_fields(f, 7);
   if (rc) return rc;
@@ -849,6 +898,7 @@ int mpdata_adjoint_step_tape(mpdata_ctx* c, const void* tape, const void* psi_n,
                              const void* v, const void* w, const void* g, void* psi_bar,
                              void* u_bar, void* v_bar, void* w_bar) {
   if (!c) return MPDATA_EINVAL;
+  if (c->opts) return fail(c, MPDATA_EINVAL, "options have no adjoint");
   const void* f[10] = {tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
   int rc = check_fields(f, 10);
   if (rc) return rc;

@@ -219,4 +219,31 @@ __device__ __forceinline__ T pseudo_velocity(T U, T gsum, T pl, T pr, T s1p, T s
   return diff * A - q * cross;
 }
 
+// Corrective-pass options (bit flags; the MPDATA literature's variants).
+enum : int { kOptDFL = 1, kOptABS = 2, kOptIGA = 4 };
+
+// Infinite-gauge pseudo-flux of one face (option IGA), the same ingredients
+// as pseudo_velocity: the limit c -> infinity of c times the pseudo-velocity
+// of psi + c (Smolarkiewicz & Clark 1986), where cA -> (pr - pl)/2 and
+// cB -> (s+ - s-)/8:
+//   Ft = (|U| - U^2/Gf) (pr - pl)/2 - U (vsum (s1p - s1m) + wsum (s2p - s2m)) / (32 Gf).
+// Ft is itself the corrective flux of the face.
+template <class T>
+__device__ __forceinline__ T pseudo_flux_iga(T U, T gsum, T pl, T pr, T s1p, T s1m, T s2p,
+                                             T s2m, T vsum, T wsum) {
+  const T rG = T(2) * rcp(gsum);                       // 1/Gf
+  const T q = U * rG;
+  const T diff = absv(U) - U * q;                      // |U| - U^2/Gf
+  const T cross = T(0.03125) * (vsum * (s1p - s1m) + wsum * (s2p - s2m));
+  return diff * (T(0.5) * (pr - pl)) - q * cross;
+}
+
+// Divergent-flow term of one face (option DFL; Smolarkiewicz 1984): with
+// dsum = D_L + D_R, the divergences of the G-weighted Courant numbers of
+// the face's two cells,  -(1/4) U dsum / Gf.
+template <class T>
+__device__ __forceinline__ T divergent_flow_term(T U, T gsum, T dsum) {
+  return T(-0.5) * U * dsum * rcp(gsum);
+}
+
 }  // namespace mpd

@@ -64,30 +64,48 @@ __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
 
 // Antidiffusive pseudo-velocities on the "+" faces of every cell
 // (Smolarkiewicz 1984; G-weighted form of Smolarkiewicz & Margolin 1998).
-template <class T>
+// OPT (kOpt* bits): ABS forms A and B from |psi|; IGA gives the
+// infinite-gauge pseudo-fluxes instead; DFL adds the divergent-flow term.
+template <class T, int OPT = 0>
 __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
                               const T* __restrict__ cv, const T* __restrict__ cw,
                               const T* __restrict__ G, T* __restrict__ ut, T* __restrict__ vt,
                               T* __restrict__ wt) {
   Cell c = cell_of(g);
   if (!c.ok) return;
-  const T eps = Eps<T>::v, half = T(0.5), quarter = T(0.25);
   const int i = c.i, j = c.j, k = c.k;
   const int ip = wrap_up(i, g.nx), im = wrap_dn(i, g.nx);
   const int jp = wrap_up(j, g.ny), jm = wrap_dn(j, g.ny);
   const int kp = kadj(g, k + 1), km = kadj(g, k - 1);
-  auto p = [&](int a, int b, int d) { return P[at(g, a, b, d)]; };
+  auto p = [&](int a, int b, int d) {
+    const T x = P[at(g, a, b, d)];
+    return (OPT & kOptABS) ? absv(x) : x;
+  };
+  auto face = [&](T U, T gsum, T pl, T pr, T s1p, T s1m, T s2p, T s2m, T vsum, T wsum) {
+    if constexpr ((OPT & kOptIGA) != 0)
+      return pseudo_flux_iga(U, gsum, pl, pr, s1p, s1m, s2p, s2m, vsum, wsum);
+    else
+      return pseudo_velocity(U, gsum, pl, pr, s1p, s1m, s2p, s2m, vsum, wsum);
+  };
+  // divergence of the Courant numbers of cell (a, b, d) (closed faces 0)
+  auto div = [&](int a, int b, int d) {
+    return (cu[at(g, a, b, d)] - cu[at(g, wrap_dn(a, g.nx), b, d)]) +
+           (cv[at(g, a, b, d)] - cv[at(g, a, wrap_dn(b, g.ny), d)]) +
+           (wface(cw, g, a, b, d) - wface(cw, g, a, b, d - 1));
+  };
   const int64_t q = at(g, i, j, k);
-  const T pc = P[q];
-  (void)eps; (void)half; (void)quarter;
+  const T pc = p(i, j, k);
   {  // x face between (i) and (ip)
     const T s1p = p(ip, jp, k) + p(i, jp, k), s1m = p(ip, jm, k) + p(i, jm, k);
     const T s2p = p(ip, j, kp) + p(i, j, kp), s2m = p(ip, j, km) + p(i, j, km);
     const T vs = cv[q] + cv[at(g, ip, j, k)] + cv[at(g, i, jm, k)] + cv[at(g, ip, jm, k)];
     const T ws = wface(cw, g, i, j, k) + wface(cw, g, ip, j, k) + wface(cw, g, i, j, k - 1) +
                  wface(cw, g, ip, j, k - 1);
-    ut[q] = pseudo_velocity(cu[q], G[q] + G[at(g, ip, j, k)], pc, p(ip, j, k), s1p, s1m, s2p,
-                            s2m, vs, ws);
+    const T gs = G[q] + G[at(g, ip, j, k)];
+    T r = face(cu[q], gs, pc, p(ip, j, k), s1p, s1m, s2p, s2m, vs, ws);
+    if constexpr ((OPT & kOptDFL) != 0)
+      r = r + divergent_flow_term(cu[q], gs, div(i, j, k) + div(ip, j, k));
+    ut[q] = r;
   }
   {  // y face between (j) and (jp)
     const T s1p = p(ip, jp, k) + p(ip, j, k), s1m = p(im, jp, k) + p(im, j, k);
@@ -95,8 +113,11 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
     const T us = cu[q] + cu[at(g, i, jp, k)] + cu[at(g, im, j, k)] + cu[at(g, im, jp, k)];
     const T ws = wface(cw, g, i, j, k) + wface(cw, g, i, jp, k) + wface(cw, g, i, j, k - 1) +
                  wface(cw, g, i, jp, k - 1);
-    vt[q] = pseudo_velocity(cv[q], G[q] + G[at(g, i, jp, k)], pc, p(i, jp, k), s1p, s1m, s2p,
-                            s2m, us, ws);
+    const T gs = G[q] + G[at(g, i, jp, k)];
+    T r = face(cv[q], gs, pc, p(i, jp, k), s1p, s1m, s2p, s2m, us, ws);
+    if constexpr ((OPT & kOptDFL) != 0)
+      r = r + divergent_flow_term(cv[q], gs, div(i, j, k) + div(i, jp, k));
+    vt[q] = r;
   }
   if (zopen(g, k)) {  // z face between (k) and (k+1); a zero-flux top face is closed
     const int64_t qp = at(g, i, j, kp);
@@ -104,7 +125,11 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
     const T s2p = p(i, jp, kp) + p(i, jp, k), s2m = p(i, jm, kp) + p(i, jm, k);
     const T us = cu[q] + cu[qp] + cu[at(g, im, j, k)] + cu[at(g, im, j, kp)];
     const T vs = cv[q] + cv[qp] + cv[at(g, i, jm, k)] + cv[at(g, i, jm, kp)];
-    wt[q] = pseudo_velocity(cw[q], G[q] + G[qp], pc, P[qp], s1p, s1m, s2p, s2m, us, vs);
+    const T gs = G[q] + G[qp];
+    T r = face(cw[q], gs, pc, p(i, j, kp), s1p, s1m, s2p, s2m, us, vs);
+    if constexpr ((OPT & kOptDFL) != 0)
+      r = r + divergent_flow_term(cw[q], gs, div(i, j, k) + div(i, j, kp));
+    wt[q] = r;
   } else {
     wt[q] = T(0);
   }
@@ -115,7 +140,8 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
 // the scale factors beta-up, beta-down (Smolarkiewicz & Grabowski 1990).
 // With rin != nullptr the reciprocals 1/(in+eps) and 1/(out+eps) are kept
 // too (the adjoint's tape).
-template <class T>
+// UNIT (infinite gauge): the face values ut, vt, wt are the fluxes.
+template <class T, bool UNIT = false>
 __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict__ P,
                             const T* __restrict__ ut, const T* __restrict__ vt,
                             const T* __restrict__ wt, const T* __restrict__ G,
@@ -136,12 +162,13 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
                       P0[nb[3]], P[nb[3]], P0[nb[4]], P[nb[4]], P0[nb[5]], P[nb[5]]};
   T hi, lo;
   bounds(vals, hi, lo);
-  T fxp = donor(pc, P[nb[1]], ut[q]);
-  T fxm = donor(P[nb[0]], pc, ut[nb[0]]);
-  T fyp = donor(pc, P[nb[3]], vt[q]);
-  T fym = donor(P[nb[2]], pc, vt[nb[2]]);
-  T fzp = zopen(g, k) ? donor(pc, P[nb[5]], wt[q]) : zero;
-  T fzm = zopen(g, k - 1) ? donor(P[nb[4]], pc, wt[nb[4]]) : zero;
+  auto fl = [&](T L, T R, T C) { return UNIT ? C : donor(L, R, C); };
+  T fxp = fl(pc, P[nb[1]], ut[q]);
+  T fxm = fl(P[nb[0]], pc, ut[nb[0]]);
+  T fyp = fl(pc, P[nb[3]], vt[q]);
+  T fym = fl(P[nb[2]], pc, vt[nb[2]]);
+  T fzp = zopen(g, k) ? fl(pc, P[nb[5]], wt[q]) : zero;
+  T fzm = zopen(g, k - 1) ? fl(P[nb[4]], pc, wt[nb[4]]) : zero;
   T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
   T out = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
   const T ri = rcp(in + eps), ro = rcp(out + eps);
@@ -155,7 +182,10 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
 
 // Second half: limited velocities on the "+" faces and their donor fluxes.
 // With ul != nullptr the limited velocities are kept for a further pass.
-template <class T>
+// OPT: with ABS a face whose upwind value is negative carries its flux
+// against its velocity, so beta-up and beta-down trade places there; with
+// IGA the limited values are the fluxes.
+template <class T, int OPT = 0>
 __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ ut,
                                const T* __restrict__ vt, const T* __restrict__ wt,
                                const T* __restrict__ bu, const T* __restrict__ bd,
@@ -167,15 +197,25 @@ __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restri
   const int64_t qx = at(g, wrap_up(c.i, g.nx), c.j, c.k);
   const int64_t qy = at(g, c.i, wrap_up(c.j, g.ny), c.k);
   T pc = P[q], buc = bu[q], bdc = bd[q];
-  T lx = limit_face(ut[q], buc, bdc, bu[qx], bd[qx]);
-  T ly = limit_face(vt[q], buc, bdc, bu[qy], bd[qy]);
+  auto lim = [&](T Ut, int64_t qn) {
+    if constexpr ((OPT & kOptABS) != 0) {
+      if ((Ut >= T(0) ? pc : P[qn]) < T(0)) return limit_face(Ut, bdc, buc, bd[qn], bu[qn]);
+    }
+    return limit_face(Ut, buc, bdc, bu[qn], bd[qn]);
+  };
+  auto fl = [&](T R, T C) {
+    if constexpr ((OPT & kOptIGA) != 0) return C;
+    else return donor(pc, R, C);
+  };
+  T lx = lim(ut[q], qx);
+  T ly = lim(vt[q], qy);
   T lz = T(0);
   const bool oz = zopen(g, c.k);
   const int64_t qz = at(g, c.i, c.j, kadj(g, c.k + 1));
-  if (oz) lz = limit_face(wt[q], buc, bdc, bu[qz], bd[qz]);
-  fx[q] = donor(pc, P[qx], lx);
-  fy[q] = donor(pc, P[qy], ly);
-  fz[q] = oz ? donor(pc, P[qz], lz) : T(0);
+  if (oz) lz = lim(wt[q], qz);
+  fx[q] = fl(P[qx], lx);
+  fy[q] = fl(P[qy], ly);
+  fz[q] = oz ? fl(P[qz], lz) : T(0);
   if (ul) { ul[q] = lx; vl[q] = ly; wl[q] = lz; }
 }
 

@@ -22,7 +22,8 @@ class MPDATA:
     """
 
     def __init__(self, nx, ny, nz, halo=2, iord=2, nonoscillatory=True,
-                 dtype=torch.float64, device=None, variant=None, k_bc=C.MPDATA_K_ZEROFLUX):
+                 dtype=torch.float64, device=None, variant=None, k_bc=C.MPDATA_K_ZEROFLUX,
+                 options=0):
         if dtype not in _DT:
             raise TypeError(f"dtype must be float64 or float32, got {dtype}")
         self.nx, self.ny, self.nz, self.h = nx, ny, nz, halo
@@ -34,6 +35,12 @@ class MPDATA:
                                       stream)
         if variant is not None:
             C.mpdata_set_variant(self._ctx, variant)
+        if options:
+            try:
+                C.mpdata_set_options(self._ctx, options)
+            except Exception:
+                self.close()
+                raise
         self.shape = padded_shape(nx, ny, nz, halo)
 
     def close(self):
