@@ -392,6 +392,7 @@ def run_ours(args, wl_name):
                           "f32": measure_adjoint(dev, torch.float32)}
         out["batched"] = measure_batched(dev)
         out["fp32"] = measure_config(dev, "latlon512_f32")
+        out["options"] = measure_options(dev)
         out["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": ncores,
                                "kind": "oracle",
                                "sample": f"{cpu_steps} full steps of the same workload "
@@ -452,6 +453,57 @@ def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(gbs / hbm, 4),
                          "launch_ms": round(per, 5)}}
+
+
+def measure_options(dev, steps=20, warmup=3):
+    """The corrective-pass options (DFL, ABS, IGA) on both workloads, measured
+    like the headline (device-resident inputs, CUDA events, per-stage event
+    timing), against the basic step of the same context shape.  ABS and IGA
+    advance a signed tracer (the lat-lon tracer minus 1/2)."""
+    import torch
+    import synth
+    from paper_1908_06094_b300 import MPDATA, _capi
+    opts = {"basic": 0, "dfl": _capi.MPDATA_OPT_DFL, "abs": _capi.MPDATA_OPT_ABS,
+            "iga": _capi.MPDATA_OPT_IGA}
+    res = {}
+    for wl_name in ("latlon256_f64", "latlon512_f32"):
+        wl = WORKLOADS[wl_name]
+        dt = torch.float64 if wl["dtype"] == "f64" else torch.float32
+        h = wl["halo"]
+        c = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=1234)
+        d = [torch.from_numpy(synth.pad(x, h)).to(dev, dt).contiguous()
+             for x in (c.psi, c.u, c.v, c.w, c.g)]
+        signed = d[0] - 0.5
+        npts = wl["nx"] * wl["ny"] * wl["nz"]
+        stream = torch.cuda.current_stream(dev)
+        row = {}
+        for name, o in opts.items():
+            m = MPDATA(wl["nx"], wl["ny"], wl["nz"], halo=h, dtype=dt, device=dev, options=o)
+            psi = (signed if o & (_capi.MPDATA_OPT_ABS | _capi.MPDATA_OPT_IGA) else d[0]).clone()
+            m.step(psi, *d[1:], nsteps=warmup)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                m.step(psi, *d[1:], nsteps=1)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = e0.elapsed_time(e1) / steps
+            # the stage split from a few more steps with per-launch events
+            _capi.mpdata_profile(m._ctx, True)
+            m.step(psi, *d[1:], nsteps=5)
+            torch.cuda.synchronize(dev)
+            st = {n: _capi.mpdata_profile_read(m._ctx, sid) for n, sid in _capi.STAGES.items()}
+            _capi.mpdata_profile(m._ctx, False)
+            m.close()
+            row[name] = {"value": npts / (ms / 1e3), "unit": UNIT, "ms_per_step": round(ms, 4),
+                         "stage_ms_per_step": {n: round(v[0] / 5, 4)
+                                               for n, v in st.items() if v[1]}}
+        for name in opts:
+            row[name]["vs_basic_time"] = round(row[name]["ms_per_step"] /
+                                               row["basic"]["ms_per_step"], 3)
+        res[wl_name] = row
+    return res
 
 
 def measure_adjoint(dev, dtype, nsteps=20, ckpt=5, reps=2):
