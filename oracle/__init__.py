@@ -54,6 +54,9 @@ def _bind(path):
     lib.orc_mass.restype = ctypes.c_double
     lib.orc_tlm.argtypes = [I, I, I, I, I, I, I, I] + [_D] * 11
     lib.orc_adjoint.argtypes = [I, I, I, I, I, I, I, I] + [_D] * 9
+    L = ctypes.c_long
+    _L = ctypes.POINTER(ctypes.c_long)
+    lib.orc_edge_run.argtypes = [L, L, I, I, _L, _L, _D, _D, _D, _D, _D, ctypes.c_double, _D]
     return lib
 
 
@@ -163,3 +166,25 @@ def adjoint(psi, u, v, w, g, psib, h: int, iord: int = 2, nonosc: int = 1, nstep
     sl = (slice(h, h + nz), slice(h, h + ny), slice(h, h + nx))
     inner[sl] = pb[sl]
     return inner, ub, vb, wb
+
+
+def edge_run(case, nsteps: int = 1, pD=None):
+    """nsteps applications of the edge-based flux stages on an
+    ``synth.octahedral.EdgeCase`` through its connectivity tables; returns
+    the new pD (nz, nr, nc).  ``pD`` overrides the case's initial field."""
+    p = np.array(case.pD if pD is None else pD, dtype=np.float64, order="C", copy=True)
+    N, E, nz = case.nnodes, case.nedges, case.nz
+    arr = lambda a: np.ascontiguousarray(a, dtype=np.float64)
+    idx = lambda a: np.ascontiguousarray(a, dtype=np.int64)
+    e2n, n2e = idx(case.e2n), idx(case.n2e)
+    sgn, vn, wn, rho, vol = (arr(x) for x in (case.n2e_sign, case.vn, case.wn, case.rho,
+                                               case.vol))
+    Lp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_long))
+    _load().orc_edge_run(N, E, nz, nsteps, Lp(e2n), Lp(n2e), _p(sgn), _p(vn), _p(wn), _p(rho),
+                         _p(vol), float(case.pivbz), _p(p))
+    return p
+
+
+def edge_mass(case, pD) -> float:
+    """sum over nodes and levels of vol * rho * pD."""
+    return float(np.sum(case.vol[None] * case.rho * pD))

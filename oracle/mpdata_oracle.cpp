@@ -818,6 +818,76 @@ void adjoint_step(const Grid& g, int iord, int nonosc, const double* psi_in, con
       }
 }
 
+/* ============================================ edge-based flux stages (Sec. 5)
+
+   The subset of MPDATA that Listings 5, 7, 8 and 9 show, on a mesh given by
+   connectivity tables (indirect addressing):
+     1. upwind flux on every edge e and level k (Listings 4/5):
+          flux = max(0, vn) pD(first node) + min(0, vn) pD(second node);
+     2. upwind flux through the vertical faces of every node (Listing 7):
+          face k (1 <= k <= nz-1, between levels k-1 and k)
+          fluz_k = max(0, W_k) pD_{k-1} + min(0, W_k) pD_k,
+          and the boundary faces fluz_0 = pivbz fluz_1, fluz_nz = pivbz fluz_{nz-1};
+     3. flux divergence over the node's dual cell (compute_fluxdiv, Listing 8):
+          divVD = (sum_j sign_j flux(edge_j) + fluz_{k+1} - fluz_k) / vol;
+     4. advance (advance_solution, Listing 8): pD = pD - divVD / rho.
+   The paper names steps 3 and 4 without their bodies; these are the plain
+   finite-volume divergence (sign +1 where the node is the edge's first node,
+   the edge's flux leaving it) and the density-weighted update.
+   Fields are level-major: node field [k][n], edge field [k][e], vertical
+   faces [k][n] for k = 0..nz. */
+
+struct EdgeMesh {
+  long N, E;
+  int nz;
+  const long* e2n;     // [E][2]
+  const long* n2e;     // [N][6]
+  const double* sgn;   // [N][6]
+};
+
+void edge_upwind_flux(const EdgeMesh& m, const double* pD, const double* vn, double* flux) {
+#pragma omp parallel for schedule(static)
+  for (long e = 0; e < m.E; ++e) {
+    const long ip1 = m.e2n[2 * e], ip2 = m.e2n[2 * e + 1];
+    for (int k = 0; k < m.nz; ++k) {
+      const double v = vn[k * m.E + e];
+      const double zpos = std::max(0.0, v), zneg = std::min(0.0, v);
+      flux[k * m.E + e] = pD[k * m.N + ip1] * zpos + pD[k * m.N + ip2] * zneg;
+    }
+  }
+}
+
+void edge_upwind_fluz(const EdgeMesh& m, const double* pD, const double* W, double pivbz,
+                      double* fluz) {
+#pragma omp parallel for schedule(static)
+  for (long n = 0; n < m.N; ++n) {
+    for (int k = 1; k < m.nz; ++k) {
+      const double w = W[k * m.N + n];
+      fluz[k * m.N + n] = std::max(0.0, w) * pD[(k - 1) * m.N + n] +
+                          std::min(0.0, w) * pD[k * m.N + n];
+    }
+    fluz[n] = pivbz * fluz[m.N + n];
+    fluz[m.nz * m.N + n] = pivbz * fluz[(m.nz - 1) * m.N + n];
+  }
+}
+
+void edge_fluxdiv(const EdgeMesh& m, const double* flux, const double* fluz, const double* vol,
+                  double* div) {
+#pragma omp parallel for schedule(static)
+  for (long n = 0; n < m.N; ++n)
+    for (int k = 0; k < m.nz; ++k) {
+      double s = 0.0;
+      for (int j = 0; j < 6; ++j) s += m.sgn[6 * n + j] * flux[k * m.E + m.n2e[6 * n + j]];
+      s += fluz[(k + 1) * m.N + n] - fluz[k * m.N + n];
+      div[k * m.N + n] = s / vol[n];
+    }
+}
+
+void edge_advance(const EdgeMesh& m, double* pD, const double* div, const double* rho) {
+#pragma omp parallel for schedule(static)
+  for (long q = 0; q < m.N * m.nz; ++q) pD[q] = pD[q] - div[q] / rho[q];
+}
+
 }  // namespace
 
 /* =============================================================== C ABI */
@@ -924,6 +994,22 @@ void orc_adjoint(int nx, int ny, int nz, int h, int kbc, int iord, int nonosc, i
   }
   for (int s = nsteps - 1; s >= 0; --s)
     adjoint_step(g, iord, nonosc, states[s].data(), U, V, W, G, psib, ubar, vbar, wbar);
+}
+
+/* nsteps applications of the edge-based flux stages (Listings 5, 7, 8):
+   pD (level-major [nz][N]) is advanced in place.  W has nz+1 faces; its
+   faces 0 and nz are never read. */
+void orc_edge_run(long N, long E, int nz, int nsteps, const long* e2n, const long* n2e,
+                  const double* sgn, const double* vn, const double* W, const double* rho,
+                  const double* vol, double pivbz, double* pD) {
+  EdgeMesh m{N, E, nz, e2n, n2e, sgn};
+  std::vector<double> flux(E * nz), fluz(N * (nz + 1)), div(N * nz);
+  for (int s = 0; s < nsteps; ++s) {
+    edge_upwind_flux(m, pD, vn, flux.data());
+    edge_upwind_fluz(m, pD, W, pivbz, fluz.data());
+    edge_fluxdiv(m, flux.data(), fluz.data(), vol, div.data());
+    edge_advance(m, pD, div.data(), rho);
+  }
 }
 
 }  // extern "C"

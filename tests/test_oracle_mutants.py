@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_edge as epins
 import test_oracle_variants as vpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "mpdata_oracle.cpp")
@@ -104,6 +105,26 @@ MUTANTS = [
     ("signed variant forms A and B from psi",
      "for (long q = 0; q < n; ++q) Pa[q] = oabs(P[q]);",
      "for (long q = 0; q < n; ++q) Pa[q] = P[q];"),
+    ("edge flux takes the downwind node",
+     "flux[k * m.E + e] = pD[k * m.N + ip1] * zpos + pD[k * m.N + ip2] * zneg;",
+     "flux[k * m.E + e] = pD[k * m.N + ip2] * zpos + pD[k * m.N + ip1] * zneg;"),
+    ("vertical edge-stage flux takes the downwind level",
+     "fluz[k * m.N + n] = std::max(0.0, w) * pD[(k - 1) * m.N + n] +\n"
+     "                          std::min(0.0, w) * pD[k * m.N + n];",
+     "fluz[k * m.N + n] = std::max(0.0, w) * pD[k * m.N + n] +\n"
+     "                          std::min(0.0, w) * pD[(k - 1) * m.N + n];"),
+    ("edge divergence ignores the edge signs",
+     "for (int j = 0; j < 6; ++j) s += m.sgn[6 * n + j] * flux[k * m.E + m.n2e[6 * n + j]];",
+     "for (int j = 0; j < 6; ++j) s += flux[k * m.E + m.n2e[6 * n + j]];"),
+    ("top boundary flux copies the bottom face",
+     "fluz[m.nz * m.N + n] = pivbz * fluz[(m.nz - 1) * m.N + n];",
+     "fluz[m.nz * m.N + n] = pivbz * fluz[m.N + n];"),
+    ("edge advance forgets rho",
+     "for (long q = 0; q < m.N * m.nz; ++q) pD[q] = pD[q] - div[q] / rho[q];",
+     "for (long q = 0; q < m.N * m.nz; ++q) pD[q] = pD[q] - div[q];"),
+    ("edge divergence forgets the dual volume",
+     "div[k * m.N + n] = s / vol[n];",
+     "div[k * m.N + n] = s;"),
     ("y halo not wrapped",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, wrap(j, g.ny), k)];",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, j < 0 ? 0 : g.ny - 1, k)];"),
@@ -139,6 +160,10 @@ def _pin_battery(stop_at_first: bool = False):
         pins.test_halo_fill_periodic_k_matches_numpy_pad,
         lambda: pins.test_courant_one_shift_vertical_periodic(2, 1, 1),
         pins.test_adjoint_dot_product_on_rotating_cone,
+        lambda: epins.test_mass_conservation_closed(True),
+        lambda: epins.test_courant_one_shift_along_each_colour(2, 1),
+        lambda: epins.test_vertical_courant_one_shift_with_closed_ends(1),
+        epins.test_open_boundaries_copy_the_adjacent_face,
         lambda: pins.test_convergence_order(2, 0, 1.9, 2.3),
         lambda: vpins.test_dfl_restores_second_order_in_divergent_flow("x", True),
         lambda: vpins.check_dfl_2d("xy", (24, 48, 96)),
