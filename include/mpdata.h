@@ -336,6 +336,71 @@ MPDATA_API const char *mpdata_last_error_string(mpdata_ctx *c);
 /* Library version (major*10000 + minor*100 + patch). */
 MPDATA_API int mpdata_version(void);
 
+/* ------------------------------------------------------------------------
+ * Edge-based flux stages on a structured triangular patch.
+ *
+ * The subset of the MPDATA dwarf the paper shows on its octahedral grid
+ * (Sec. 5): the upwind flux on every edge (Listings 4/5), the vertical
+ * upwind flux on every node (Listings 6/7), their divergence over each
+ * node's dual cell and the advance (the calls of Listing 8, composed into
+ * one kernel as Listing 9 composes its stages):
+ *   flux_e   = max(0, vn_e) pD(first node) + min(0, vn_e) pD(second node);
+ *   fluz_k   = max(0, W_k) pD_{k-1} + min(0, W_k) pD_k    (faces 1..nz-1),
+ *   fluz_0   = pivbz fluz_1,  fluz_nz = pivbz fluz_{nz-1};
+ *   divVD    = (sum over the node's own edges of flux - sum over the
+ *               edges ending at it of flux + fluz_{k+1} - fluz_k) / vol;
+ *   pD_out   = pD - divVD / rho.
+ * The paper names the last two calls without their bodies; these are the
+ * plain finite-volume divergence and density-weighted update.
+ *
+ * The patch: nr x nc nodes, periodic in both directions (one parallelogram
+ * of the octahedral grid without its corner irregularities).  Structured
+ * numbering, direct access (Figs. 9 and 11): node (r, c) owns the edges of
+ * colours 0: (r,c)->(r,c+1), 1: (r,c)->(r+1,c), 2: (r,c)->(r+1,c+1); a
+ * positive vn moves mass from the first node to the second.  With nr or
+ * nc equal to 1 a colour's edges join a node to itself and carry no net
+ * flux.  DEVICE fields of the context's dtype, level-major, C-contiguous,
+ * 16-byte aligned, no halo:
+ *   pD, rho    [nz][nr][nc]       nodes (rho > 0)
+ *   vn         [nz][nr][3][nc]    edges, (row, colour, column) per level
+ *   wn         [nz+1][nr][nc]     vertical faces, face k between levels k-1
+ *                                 and k; faces 0 and nz are never read
+ *   vol        [nr][nc]           dual volume of each node (> 0)
+ * ---------------------------------------------------------------------- */
+typedef struct mpdata_edge mpdata_edge; /* opaque, library-owned */
+
+/* Create a context for one patch: nr, nc >= 1, nz >= 2 (the boundary
+ * faces take their flux from an interior face), dtype MPDATA_F64 or
+ * MPDATA_F32, pivbz the boundary factor (0: closed top and bottom).
+ * Allocates the staged organisation's scratch (5 nz + 1 node planes).
+ * Errors: EINVAL, ERANGE (nz > 65534 or nr > 524280), EDEVICE, ENOMEM. */
+MPDATA_API int mpdata_edge_init(mpdata_edge **out, int nr, int nc, int nz, int dtype,
+                                double pivbz, void *cuda_stream);
+MPDATA_API int mpdata_edge_set_stream(mpdata_edge *e, void *cuda_stream);
+
+/* MPDATA_FUSED (one kernel; also MPDATA_AUTO, the default) or
+ * MPDATA_STAGED (four kernels, one per call of Listing 8). Errors: EINVAL. */
+MPDATA_API int mpdata_edge_set_variant(mpdata_edge *e, int variant);
+
+/* One application of the four stages: pD_out = step(pD_in); the two
+ * buffers must be distinct.  Asynchronous on the context's stream.
+ * Errors: EINVAL (null pointer, pD_in == pD_out), EALIGN, ECUDA. */
+MPDATA_API int mpdata_edge_step(mpdata_edge *e, const void *pD_in, void *pD_out,
+                                const void *vn, const void *wn, const void *rho,
+                                const void *vol);
+
+/* Nodes per thread of the fused kernel: 1, or 4 (consecutive columns read
+ * as 16-byte vectors; FP32 with nc a multiple of 4, the default there); 0
+ * restores the default.  Errors: EINVAL (other values, or 4 where it does
+ * not apply). */
+MPDATA_API int mpdata_edge_set_width(mpdata_edge *e, int width);
+MPDATA_API int mpdata_edge_get_width(mpdata_edge *e, int *width);
+
+/* Kernel launches issued so far (-1 for NULL). */
+MPDATA_API long long mpdata_edge_launch_count(mpdata_edge *e);
+MPDATA_API const char *mpdata_edge_last_error_string(mpdata_edge *e);
+MPDATA_API void mpdata_edge_destroy(mpdata_edge *e);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@ thin Python binding over it.
 * ``MPDATA``  -- the same calls taking torch CUDA tensors (pointer and stream
   marshalling only: every step of the method runs in the library's kernels);
 * ``MPDATABatch`` -- many domains x tracers in one persistent launch;
+* ``EdgeMPDATA`` -- the edge-based flux stages on a triangular patch;
 * ``MPDATAFunction`` / ``mpdata_run`` -- autograd over the forward and
   adjoint steps with checkpoint-and-recompute.
 
@@ -13,7 +14,8 @@ library raises ImportError (there is no fallback path).
 """
 import importlib
 
-__all__ = ["_capi", "MPDATA", "padded_shape", "MPDATAFunction", "mpdata_run", "MPDATABatch"]
+__all__ = ["_capi", "MPDATA", "padded_shape", "MPDATAFunction", "mpdata_run", "MPDATABatch",
+           "EdgeMPDATA"]
 
 
 def __getattr__(name):
@@ -22,6 +24,8 @@ def __getattr__(name):
     if name in ("MPDATA", "padded_shape"):
         mod = importlib.import_module(".mpdata", __name__)
         return getattr(mod, name)
+    if name == "EdgeMPDATA":
+        return importlib.import_module(".edge", __name__).EdgeMPDATA
     if name == "MPDATABatch":
         return importlib.import_module(".batch", __name__).MPDATABatch
     if name in ("MPDATAFunction", "mpdata_run"):

@@ -60,6 +60,15 @@ SIGNATURES = {
     "mpdata_set_stream": (_i, [_c, _c]),
     "mpdata_set_variant": (_i, [_c, _i]),
     "mpdata_set_options": (_i, [_c, _i]),
+    "mpdata_edge_init": (_i, [_ctxpp, _i, _i, _i, _i, ctypes.c_double, _c]),
+    "mpdata_edge_set_stream": (_i, [_c, _c]),
+    "mpdata_edge_set_variant": (_i, [_c, _i]),
+    "mpdata_edge_step": (_i, [_c, _c, _c, _c, _c, _c, _c]),
+    "mpdata_edge_set_width": (_i, [_c, _i]),
+    "mpdata_edge_get_width": (_i, [_c, _ip]),
+    "mpdata_edge_launch_count": (ctypes.c_longlong, [_c]),
+    "mpdata_edge_last_error_string": (ctypes.c_char_p, [_c]),
+    "mpdata_edge_destroy": (None, [_c]),
     "mpdata_get_options": (_i, [_c, _ip]),
     "mpdata_step": (_i, [_c, _c, _c, _c, _c, _c, _i]),
     "mpdata_step_out": (_i, [_c, _c, _c, _c, _c, _c, _c]),
