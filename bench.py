@@ -192,6 +192,7 @@ def job_throughput(ms_local: float, units_local: float, ws: int, device=None):
 STAGE_SOURCES = {
     "pseudo": ("march.cuh", "grid.cuh"),                # FP64 k-marching pseudo-velocity
     "fused": ("fused2.cuh", "grid.cuh", "capi.cu"),     # FP32 fused step (+ its chunking)
+    "edge": ("edge.cuh", "edge.cu", "grid.cuh"),        # edge-based flux stages
 }
 
 
@@ -393,6 +394,7 @@ def run_ours(args, wl_name):
         out["batched"] = measure_batched(dev)
         out["fp32"] = measure_config(dev, "latlon512_f32")
         out["options"] = measure_options(dev)
+        out["octahedral_edge"] = measure_edge(dev)
         out["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": ncores,
                                "kind": "oracle",
                                "sample": f"{cpu_steps} full steps of the same workload "
@@ -635,6 +637,120 @@ def run_reference(args, wl_name):
                     "d2h_bytes_per_step": 0}}
 
 
+# The paper's own workload for its flux stages (Sec. 5, Listings 5-9): the
+# global grid of Table 2 / Fig. 14 (71424 nodes, 80 levels) as a periodic
+# 279 x 256 triangular patch, open vertical boundaries.
+EDGE_SHAPE = (279, 256, 80)
+# words moved per node-level (Table 2's counting, every 3D field counted,
+# 2D fields ignored): fused reads pD, 3 vn, W, rho and writes pD; staged
+# adds the edge fluxes (3 w + 3 r), the vertical fluxes (1 w + 1 r), the
+# divergence (1 w + 1 r) and the second and third reads of pD
+EDGE_WORDS = {"fused": 7, "staged": 19}
+# FP64 pipe operations per node-level of the fused kernel: 1 DMUL + 5 DFMA
+# (edge fluxes), 2 DMUL (vertical fluxes), 2 DADD, 1 DMUL (vol rho), the
+# reciprocal (3 DFMA after the hardware seed) and the final DFMA
+EDGE_FP64_OPS = 15
+
+
+def _edge_case():
+    from synth import octahedral as octa
+    nr, nc, nz = EDGE_SHAPE
+    return octa.edge_case(nr, nc, nz, seed=1234, pivbz=1.0)
+
+
+def measure_edge(dev, reps=20, cpu_seconds=5.0):
+    """The edge-based flux stages on the 71424 x 80 patch, both dtypes, both
+    organisations: median of reps launches with L2 flushed before each
+    (CUDA events on the launching stream).  Units: node-level updates/s."""
+    import torch
+    from paper_1908_06094_b300 import EdgeMPDATA
+    import oracle
+    hbm, _ = _peaks()
+    c = _edge_case()
+    nr, nc, nz = EDGE_SHAPE
+    npts = nr * nc * nz
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"workload": f"periodic triangular patch {nr}x{nc} nodes (71424), {nz} levels, pivbz 1",
+           "unit": "node-level updates/s", "l2": "flushed (256 MB write) before each launch"}
+    for dt in (torch.float64, torch.float32):
+        name = "f64" if dt == torch.float64 else "f32"
+        esize = 8 if dt == torch.float64 else 4
+        f = {k: torch.from_numpy(getattr(c, k)).to(dev, dt).contiguous()
+             for k in ("pD", "vn", "wn", "rho", "vol")}
+        outb = torch.empty_like(f["pD"])
+        row = {}
+        for var, vname in ((0, "fused"), (1, "staged")):
+            e = EdgeMPDATA(nr, nc, nz, dtype=dt, pivbz=1.0, variant=var, device=dev)
+            for _ in range(3):
+                e.step(f["pD"], outb, f["vn"], f["wn"], f["rho"], f["vol"])
+            torch.cuda.synchronize(dev)
+            ts = []
+            for _ in range(reps):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                e.step(f["pD"], outb, f["vn"], f["wn"], f["rho"], f["vol"])
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1))
+            ts.sort()
+            ms = ts[len(ts) // 2]
+            algo = EDGE_WORDS[vname] * esize * npts
+            gbs = algo / (ms / 1e3) / 1e9
+            r = {"value": npts / (ms / 1e3), "ms": round(ms, 5), "launches": 1 if var == 0 else 4,
+                 "algorithmic_bytes": algo, "achieved_gbs": round(gbs, 1),
+                 "hbm_frac": round(gbs / hbm, 4)}
+            if var == 0:
+                r["width"] = e.width()
+                src = _source_hash("edge")
+                r["traffic"] = _traffic_from_profiles(f"edge_fused_{name}", "octa71424x80", src)
+                if dt == torch.float64:
+                    ach = EDGE_FP64_OPS * npts / (ms / 1e3) / 1e9
+                    r["fp64_ops_frac"] = round(ach / (FP64_PEAK_GFLOPS / 2), 4)
+            else:
+                r["traffic"] = _traffic_from_profiles(f"edge_staged_{name}", "octa71424x80",
+                                                      _source_hash("edge"))
+            row[vname] = r
+            e.close()
+        row["staged_over_fused_time"] = round(row["staged"]["ms"] / row["fused"]["ms"], 3)
+        res[name] = row
+    N, E = nr * nc, 3 * nr * nc
+    res["table2_accesses_per_plane"] = {"without_fusion": 2 * E + 10 * N, "with_fusion": 5 * N,
+                                        "ratio": round((2 * E + 10 * N) / (5 * N), 3)}
+    # the oracle (the same stages through the connectivity tables), host cores
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        oracle.edge_run(c, nsteps=1)
+        k += 1
+        if time.perf_counter() - t0 >= cpu_seconds:
+            break
+    res["cpu_baseline"] = {"value": npts * k / (time.perf_counter() - t0),
+                           "unit": "node-level updates/s", "cores": os.cpu_count() or 1,
+                           "kind": "oracle", "sample": f"{k} full steps of the same patch"}
+    return res
+
+
+def edge_probe(dtype_name: str, variant: int):
+    """Five launches of the edge stages on the 71424 x 80 patch (a
+    profiler's capture)."""
+    import torch
+    from paper_1908_06094_b300 import EdgeMPDATA
+    dt = torch.float64 if dtype_name == "f64" else torch.float32
+    c = _edge_case()
+    nr, nc, nz = EDGE_SHAPE
+    f = {k: torch.from_numpy(getattr(c, k)).to("cuda", dt).contiguous()
+         for k in ("pD", "vn", "wn", "rho", "vol")}
+    outb = torch.empty_like(f["pD"])
+    e = EdgeMPDATA(nr, nc, nz, dtype=dt, pivbz=1.0, variant=variant)
+    for _ in range(5):
+        e.step(f["pD"], outb, f["vn"], f["wn"], f["rho"], f["vol"])
+    torch.cuda.synchronize()
+    e.close()
+    print("edge probe ok", flush=True)
+
+
 def adjoint_probe(dtype_name: str):
     """The adjoint configuration's grid (256x256x64 lat-lon flow) through the
     public autograd path, twice: 4 steps with checkpoints every 2, then
@@ -670,9 +786,14 @@ def main():
                     help="skip the e2e and CPU-baseline legs")
     ap.add_argument("--adjoint-probe", choices=["f64", "f32"], default=None,
                     help="run a short adjoint workload for a profiler's launch list and exit")
+    ap.add_argument("--edge-probe", choices=["f64", "f32"], default=None,
+                    help="run five edge-stage launches (--variant 0 fused, 1 staged) and exit")
     args = ap.parse_args()
     if args.adjoint_probe:
         adjoint_probe(args.adjoint_probe)
+        return
+    if args.edge_probe:
+        edge_probe(args.edge_probe, 0 if args.variant is None else args.variant)
         return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
