@@ -57,6 +57,7 @@ def _bind(path):
     L = ctypes.c_long
     _L = ctypes.POINTER(ctypes.c_long)
     lib.orc_edge_run.argtypes = [L, L, I, I, _L, _L, _D, _D, _D, _D, _D, ctypes.c_double, _D]
+    lib.orc_cells_sum.argtypes = [L, I, ctypes.POINTER(ctypes.c_int), _D, ctypes.c_double, _D]
     return lib
 
 
@@ -188,3 +189,14 @@ def edge_run(case, nsteps: int = 1, pD=None):
 def edge_mass(case, pD) -> float:
     """sum over nodes and levels of vol * rho * pD."""
     return float(np.sum(case.vol[None] * case.rho * pD))
+
+
+def cells_sum(table, A, fac: float = 1.0):
+    """B = fac * (sum of A over each cell's three neighbours), table [3][ncells]
+    (int32), A [nz][ncells]."""
+    t = np.ascontiguousarray(table, dtype=np.int32)
+    a = np.ascontiguousarray(A, dtype=np.float64)
+    out = np.empty_like(a)
+    _load().orc_cells_sum(a.shape[1], a.shape[0], t.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                          _p(a), float(fac), _p(out))
+    return out

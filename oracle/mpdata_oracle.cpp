@@ -1012,4 +1012,17 @@ void orc_edge_run(long N, long E, int nz, int nsteps, const long* e2n, const lon
   }
 }
 
+/* The cell-neighbour reduction of Table 1 (the on_cells operation of
+   Fig. 5): for every cell s and level k, B = fac * (A at its three
+   neighbours, summed in table order).  t: neighbour table [3][ncells]
+   (any numbering); A, B: [nz][ncells]. */
+void orc_cells_sum(long ncells, int nz, const int* t, const double* A, double fac, double* B) {
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < nz; ++k)
+    for (long s = 0; s < ncells; ++s) {
+      const double* a = A + k * ncells;
+      B[k * ncells + s] = (a[t[s]] + a[t[ncells + s]] + a[t[2 * ncells + s]]) * fac;
+    }
+}
+
 }  // extern "C"

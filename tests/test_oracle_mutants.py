@@ -12,6 +12,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_oracle_cells as cpins
 import test_oracle_edge as epins
 import test_oracle_variants as vpins
 
@@ -125,6 +126,12 @@ MUTANTS = [
     ("edge divergence forgets the dual volume",
      "div[k * m.N + n] = s / vol[n];",
      "div[k * m.N + n] = s;"),
+    ("cell sum reads the first neighbour twice",
+     "B[k * ncells + s] = (a[t[s]] + a[t[ncells + s]] + a[t[2 * ncells + s]]) * fac;",
+     "B[k * ncells + s] = (a[t[s]] + a[t[ncells + s]] + a[t[s]]) * fac;"),
+    ("cell sum ignores its factor",
+     "B[k * ncells + s] = (a[t[s]] + a[t[ncells + s]] + a[t[2 * ncells + s]]) * fac;",
+     "B[k * ncells + s] = (a[t[s]] + a[t[ncells + s]] + a[t[2 * ncells + s]]);"),
     ("y halo not wrapped",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, wrap(j, g.ny), k)];",
      "for (int i = -g.h; i < g.nx + g.h; ++i) f[g.at(i, j, k)] = f[g.at(i, j < 0 ? 0 : g.ny - 1, k)];"),
@@ -164,6 +171,8 @@ def _pin_battery(stop_at_first: bool = False):
         lambda: epins.test_courant_one_shift_along_each_colour(2, 1),
         lambda: epins.test_vertical_courant_one_shift_with_closed_ends(1),
         epins.test_open_boundaries_copy_the_adjacent_face,
+        lambda: cpins.test_constant_and_total("SN"),
+        lambda: cpins.test_delta_response_is_the_edge_neighbours("UN"),
         lambda: pins.test_convergence_order(2, 0, 1.9, 2.3),
         lambda: vpins.test_dfl_restores_second_order_in_divergent_flow("x", True),
         lambda: vpins.check_dfl_2d("xy", (24, 48, 96)),
