@@ -395,6 +395,7 @@ def run_ours(args, wl_name):
         out["fp32"] = measure_config(dev, "latlon512_f32")
         out["options"] = measure_options(dev)
         out["octahedral_edge"] = measure_edge(dev)
+        out["table1_cells"] = measure_cells(dev)
         out["cpu_baseline"] = {"value": cpu_rate, "unit": UNIT, "cores": ncores,
                                "kind": "oracle",
                                "sample": f"{cpu_steps} full steps of the same workload "
@@ -732,6 +733,95 @@ def measure_edge(dev, reps=20, cpu_seconds=5.0):
     return res
 
 
+def measure_cells(dev, reps=15):
+    """Table 1 on the B300: the cell-neighbour sum B = sum of A over the
+    three edge neighbours, and the two-stage operator (B = fac1 x sum A,
+    C = fac2 x sum B: two launches), under structured numbering with direct
+    access (SN DA) and with its table (SN IA), a mesh library's numbering
+    through its table (UN IA) and a Hilbert numbering (HN IA).  Bandwidth =
+    required transfer / time as in Table 1, the required transfer being
+    each launch's input and output fields (2 words per cell-level per
+    launch); median of reps with L2 flushed before each.  The paper's patch
+    (128 x 128 x 80 nodes) holds 21 MB per FP64 field, inside the B300's
+    126 MB L2, so a 512 x 512 x 80 patch (335 MB per field) is measured
+    too."""
+    import torch
+    from paper_1908_06094_b300 import CellsReduction
+    from synth import cells
+    hbm, _ = _peaks()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {"unit": "GB/s (required transfer / time)", "l2": "flushed before each measurement",
+           "paper_p100_gbs": {"SN DA": [211, 226], "SN IA": [270, 269], "UN IA": [130, 135],
+                              "HN IA": [256, 240]}}
+    for (nr, nc, nz) in ((128, 128, 80), (512, 512, 80)):
+        for dt in (torch.float64, torch.float32):
+            esize = 8 if dt == torch.float64 else 4
+            n = 2 * nr * nc * nz
+            row = {}
+            for numbering, access in (("SN", "direct"), ("SN", "indirect"), ("UN", "indirect"),
+                                      ("HN", "indirect")):
+                if access == "direct":
+                    red = CellsReduction(nz, dtype=dt, nr=nr, nc=nc, device=dev)
+                else:
+                    red = CellsReduction(nz, dtype=dt, table=cells.c2c(nr, nc, numbering),
+                                         device=dev)
+                A = torch.from_numpy(cells.field(nr, nc, nz, seed=1, numbering=numbering)).to(
+                    dev, dt).contiguous()
+                B = torch.empty_like(A)
+                Cf = torch.empty_like(A)
+                out = {}
+                for op in ("sum", "two_stage"):
+                    def run():
+                        red.sum(A, B, 1.0)
+                        if op == "two_stage":
+                            red.sum(B, Cf, 0.5)
+                    for _ in range(3):
+                        run()
+                    ts = []
+                    for _ in range(reps):
+                        flush.zero_()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        run()
+                        e1.record(stream)
+                        torch.cuda.synchronize(dev)
+                        ts.append(e0.elapsed_time(e1))
+                    ts.sort()
+                    ms = ts[len(ts) // 2]
+                    words = 2 if op == "sum" else 4
+                    out[op] = {"us": round(ms * 1e3, 2),
+                               "gbs": round(words * esize * n / (ms / 1e3) / 1e9, 1)}
+                row[f"{numbering} {'DA' if access == 'direct' else 'IA'}"] = out
+                red.close()
+            res[f"{nr}x{nc}x{nz}_{'f64' if esize == 8 else 'f32'}"] = row
+    res["hbm_peak_gbs"] = hbm
+    return res
+
+
+def cells_probe(dtype_name: str, numbering: str):
+    """Three launches of the cell-neighbour sum on the 512 x 512 x 80 patch
+    (direct access for SN, the table for UN and HN; a profiler's capture)."""
+    import torch
+    from paper_1908_06094_b300 import CellsReduction
+    from synth import cells
+    dt = torch.float64 if dtype_name == "f64" else torch.float32
+    nr, nc, nz = 512, 512, 80
+    if numbering == "SN":
+        red = CellsReduction(nz, dtype=dt, nr=nr, nc=nc)
+    else:
+        red = CellsReduction(nz, dtype=dt, table=cells.c2c(nr, nc, numbering))
+    A = torch.from_numpy(cells.field(nr, nc, nz, seed=1, numbering=numbering)).to(
+        "cuda", dt).contiguous()
+    B = torch.empty_like(A)
+    for _ in range(3):
+        red.sum(A, B, 1.0)
+    torch.cuda.synchronize()
+    red.close()
+    print("cells probe ok", flush=True)
+
+
 def edge_probe(dtype_name: str, variant: int):
     """Five launches of the edge stages on the 71424 x 80 patch (a
     profiler's capture)."""
@@ -788,7 +878,13 @@ def main():
                     help="run a short adjoint workload for a profiler's launch list and exit")
     ap.add_argument("--edge-probe", choices=["f64", "f32"], default=None,
                     help="run five edge-stage launches (--variant 0 fused, 1 staged) and exit")
+    ap.add_argument("--cells-probe", default=None,
+                    help="f32:SN|UN|HN or f64:...: three cell-sum launches and exit")
     args = ap.parse_args()
+    if args.cells_probe:
+        dtn, num = args.cells_probe.split(":")
+        cells_probe(dtn, num)
+        return
     if args.adjoint_probe:
         adjoint_probe(args.adjoint_probe)
         return

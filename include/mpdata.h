@@ -401,6 +401,45 @@ MPDATA_API long long mpdata_edge_launch_count(mpdata_edge *e);
 MPDATA_API const char *mpdata_edge_last_error_string(mpdata_edge *e);
 MPDATA_API void mpdata_edge_destroy(mpdata_edge *e);
 
+/* ------------------------------------------------------------------------
+ * Cell-neighbour reduction (Table 1).
+ *
+ * The on_cells operation of Fig. 5 that Table 1 times under different
+ * numberings and access methods: for every cell s and level k
+ *   B[k][s] = fac * (A[k][n0] + A[k][n1] + A[k][n2]),
+ * n0, n1, n2 the three cells across s's edges, summed in that order; the
+ * two-stage operator of Table 1 is two calls (A -> B with fac1, B -> C with
+ * fac2).  Fields are DEVICE arrays [nz][ncells] of the context's dtype in
+ * the numbering's storage order, 16-byte aligned.
+ *
+ * Access methods (Sec. 3.2):
+ *   direct    structured numbering of the triangles of a periodic nr x nc
+ *             patch: cell (row r, colour, column c) -> (2 r + colour) nc + c,
+ *             colour 0 the upward triangle (r,c), (r,c+1), (r+1,c+1) and 1
+ *             the downward (r,c), (r+1,c+1), (r+1,c); the neighbours, found
+ *             by index arithmetic, are D(r-1,c), D(r,c+1), D(r,c) for U(r,c)
+ *             and U(r,c), U(r+1,c), U(r,c-1) for D(r,c);
+ *   indirect  a neighbour table [3][ncells] of int32 in any numbering (the
+ *             structured one, a mesh library's, a space-filling curve's).
+ * ---------------------------------------------------------------------- */
+typedef struct mpdata_cells mpdata_cells; /* opaque, library-owned */
+
+/* table == NULL: direct access, structured numbering, ncells = 2 nr nc.
+ * table != NULL: indirect access; HOST array [3][ncells], every entry in
+ * [0, ncells) (checked), copied to the device (nr, nc ignored).
+ * Errors: EINVAL (sizes, dtype, a table entry out of range), ERANGE
+ * (ncells >= 2^31), EDEVICE, ENOMEM. */
+MPDATA_API int mpdata_cells_init(mpdata_cells **out, long long ncells, int nz, int dtype,
+                                 const int *table, int nr, int nc, void *cuda_stream);
+MPDATA_API int mpdata_cells_set_stream(mpdata_cells *c, void *cuda_stream);
+
+/* B = fac * neighbour sum of A (A and B distinct).  Asynchronous on the
+ * context's stream.  Errors: EINVAL (null, A == B), EALIGN, ECUDA. */
+MPDATA_API int mpdata_cells_sum(mpdata_cells *c, const void *A, void *B, double fac);
+MPDATA_API long long mpdata_cells_launch_count(mpdata_cells *c);
+MPDATA_API const char *mpdata_cells_last_error_string(mpdata_cells *c);
+MPDATA_API void mpdata_cells_destroy(mpdata_cells *c);
+
 #ifdef __cplusplus
 }
 #endif

@@ -6,6 +6,7 @@ thin Python binding over it.
   marshalling only: every step of the method runs in the library's kernels);
 * ``MPDATABatch`` -- many domains x tracers in one persistent launch;
 * ``EdgeMPDATA`` -- the edge-based flux stages on a triangular patch;
+* ``CellsReduction`` -- the cell-neighbour reduction of Table 1;
 * ``MPDATAFunction`` / ``mpdata_run`` -- autograd over the forward and
   adjoint steps with checkpoint-and-recompute.
 
@@ -15,7 +16,7 @@ library raises ImportError (there is no fallback path).
 import importlib
 
 __all__ = ["_capi", "MPDATA", "padded_shape", "MPDATAFunction", "mpdata_run", "MPDATABatch",
-           "EdgeMPDATA"]
+           "EdgeMPDATA", "CellsReduction"]
 
 
 def __getattr__(name):
@@ -24,6 +25,8 @@ def __getattr__(name):
     if name in ("MPDATA", "padded_shape"):
         mod = importlib.import_module(".mpdata", __name__)
         return getattr(mod, name)
+    if name == "CellsReduction":
+        return importlib.import_module(".cells", __name__).CellsReduction
     if name == "EdgeMPDATA":
         return importlib.import_module(".edge", __name__).EdgeMPDATA
     if name == "MPDATABatch":

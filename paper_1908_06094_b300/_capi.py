@@ -69,6 +69,12 @@ SIGNATURES = {
     "mpdata_edge_launch_count": (ctypes.c_longlong, [_c]),
     "mpdata_edge_last_error_string": (ctypes.c_char_p, [_c]),
     "mpdata_edge_destroy": (None, [_c]),
+    "mpdata_cells_init": (_i, [_ctxpp, ctypes.c_longlong, _i, _i, _ip, _i, _i, _c]),
+    "mpdata_cells_set_stream": (_i, [_c, _c]),
+    "mpdata_cells_sum": (_i, [_c, _c, _c, ctypes.c_double]),
+    "mpdata_cells_launch_count": (ctypes.c_longlong, [_c]),
+    "mpdata_cells_last_error_string": (ctypes.c_char_p, [_c]),
+    "mpdata_cells_destroy": (None, [_c]),
     "mpdata_get_options": (_i, [_c, _ip]),
     "mpdata_step": (_i, [_c, _c, _c, _c, _c, _c, _i]),
     "mpdata_step_out": (_i, [_c, _c, _c, _c, _c, _c, _c]),

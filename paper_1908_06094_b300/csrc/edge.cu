@@ -59,15 +59,16 @@ int edge_step(mpdata_edge* e, const T* pD, T* out, const T* vn, const T* W, cons
   const T pv = (T)e->pivbz;
   cudaStream_t s = e->stream;
   if (e->variant != MPDATA_STAGED) {
+    bool vec = false;
     if constexpr (std::is_same<T, float>::value) {
       if (e->width == 4) {
         const dim3 g((p.nc / 4 + BX4 - 1) / BX4, (p.nr + BY - 1) / BY, p.nz);
         edge_fused4_kernel<<<g, dim3(BX4, BY), 0, s>>>(p, pD, vn, W, rho, vol, pv, out);
-        e->launches += 1;
-        goto done;
+        vec = true;
       }
     }
-    edge_fused_kernel<T><<<node_grid(p, p.nz), blk, 0, s>>>(p, pD, vn, W, rho, vol, pv, out);
+    if (!vec)
+      edge_fused_kernel<T><<<node_grid(p, p.nz), blk, 0, s>>>(p, pD, vn, W, rho, vol, pv, out);
     e->launches += 1;
   } else {
     T *flux = (T*)e->flux, *fluz = (T*)e->fluz, *div = (T*)e->div;
@@ -77,7 +78,6 @@ int edge_step(mpdata_edge* e, const T* pD, T* out, const T* vn, const T* W, cons
     edge_advance_kernel<T><<<node_grid(p, p.nz), blk, 0, s>>>(p, pD, div, rho, out);
     e->launches += 4;
   }
-done:
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return edge_fail(e, MPDATA_ECUDA, "edge step", ce);
   return MPDATA_OK;
