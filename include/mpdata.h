@@ -103,9 +103,9 @@ MPDATA_API int mpdata_init(mpdata_ctx **out, int nx, int ny, int nz, int halo, i
 MPDATA_API int mpdata_set_stream(mpdata_ctx *c, void *cuda_stream);
 
 /* Choose the kernel organisation (mpdata_variant); all give the same step
- * to rounding.  The fused kernel runs only when iord == 2, nx, ny >= 2h and
- * no option is set; other contexts use the staged kernels whatever is
- * chosen.  Errors: EINVAL. */
+ * to rounding.  The fused kernel runs only when iord == 2 and nx, ny >= 2h,
+ * and with an option set only in FP32; other contexts use the staged
+ * kernels whatever is chosen.  Errors: EINVAL. */
 MPDATA_API int mpdata_set_variant(mpdata_ctx *c, int variant);
 
 /* Options of the corrective passes (bit flags).  The paper defers the
@@ -122,9 +122,10 @@ MPDATA_API int mpdata_set_variant(mpdata_ctx *c, int variant);
  *        scheme applied to psi + c as c grows; the corrective flux of a face
  *        is (|U| - U^2/Gf)(psi_R - psi_L)/2 - U (Vbar N_y + Wbar N_z)/(8 Gf)
  *        with N the numerators of B.  A linear scheme, for signed fields.
- * IGA takes no other option and iord <= 2.  With any option the step runs
- * on the staged kernels, and the adjoint calls (mpdata_adjoint_step,
- * mpdata_step_tape, mpdata_adjoint_step_tape) return EINVAL. */
+ * IGA takes no other option and iord <= 2.  With an option an FP32 step
+ * runs on the fused kernel (iord 2) and an FP64 step on the staged ones;
+ * the adjoint calls (mpdata_adjoint_step, mpdata_step_tape,
+ * mpdata_adjoint_step_tape) return EINVAL. */
 enum mpdata_option { MPDATA_OPT_DFL = 1, MPDATA_OPT_ABS = 2, MPDATA_OPT_IGA = 4 };
 
 /* Set the option bits of a context (0: the basic scheme, the default).

@@ -245,9 +245,36 @@ auto fused_kernel_ptr() {
   return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, TAPE, KPER>;
 }
 
-// The instance for the context's limiter and vertical boundary.
+template <class T, bool LIMIT, bool KPER, int OPT>
+auto fused_opt_ptr() {
+  using F = FusedShape<T>;
+  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, false, KPER, OPT>;
+}
+
+// FP32 instances with corrective-pass options (FP64 runs options on the
+// staged kernels); the basic instance for opts == 0.
+template <bool LIMIT, bool KPER>
+auto fused_opt_pick(int opts) {
+  using namespace mpd;
+  switch (opts) {
+    case kOptDFL: return fused_opt_ptr<float, LIMIT, KPER, kOptDFL>();
+    case kOptABS: return fused_opt_ptr<float, LIMIT, KPER, kOptABS>();
+    case kOptDFL | kOptABS: return fused_opt_ptr<float, LIMIT, KPER, kOptDFL | kOptABS>();
+    case kOptIGA: return fused_opt_ptr<float, LIMIT, KPER, kOptIGA>();
+    default: return fused_opt_ptr<float, LIMIT, KPER, 0>();
+  }
+}
+
+// The instance for the context's limiter, vertical boundary and options.
 template <class T, bool TAPE>
 auto fused_pick(const mpdata_ctx* c) {
+  if constexpr (std::is_same<T, float>::value && !TAPE) {
+    if (c->opts) {
+      if (c->g.kper)
+        return c->nonosc ? fused_opt_pick<true, true>(c->opts) : fused_opt_pick<false, true>(c->opts);
+      return c->nonosc ? fused_opt_pick<true, false>(c->opts) : fused_opt_pick<false, false>(c->opts);
+    }
+  }
   if (c->g.kper)
     return c->nonosc ? fused_kernel_ptr<T, true, TAPE, true>() : fused_kernel_ptr<T, false, TAPE, true>();
   return c->nonosc ? fused_kernel_ptr<T, true, TAPE>() : fused_kernel_ptr<T, false, TAPE>();
@@ -328,7 +355,8 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
 }
 
 bool use_fused(const mpdata_ctx* c) {
-  if (!c->fused_ok || c->opts != 0) return false;
+  // options run fused in FP32 only (FP64 takes the staged kernels)
+  if (!c->fused_ok || (c->opts != 0 && c->dtype != MPDATA_F32)) return false;
   if (c->variant == MPDATA_AUTO) return c->dtype == MPDATA_F32;
   return c->variant == MPDATA_FUSED;
 }
@@ -729,7 +757,17 @@ int mpdata_set_options(mpdata_ctx* c, int opts) {
     return fail(c, MPDATA_EINVAL, "the infinite gauge takes no other option");
   if ((opts & MPDATA_OPT_IGA) && c->iord > 2)
     return fail(c, MPDATA_EINVAL, "the infinite gauge is defined for iord <= 2");
+  const int prev = c->opts;
   c->opts = opts;
+  if (c->dtype == MPDATA_F32 && c->fused_ok) {  // the option instance's shared memory
+    const int ib = (int)fused_smem<float>();
+    if (cudaFuncSetAttribute(fused_pick<float, false>(c),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, ib) != cudaSuccess) {
+      cudaGetLastError();
+      c->opts = prev;
+      return fail(c, MPDATA_ECUDA, "fused kernel attribute");
+    }
+  }
   return MPDATA_OK;
 }
 

@@ -61,7 +61,7 @@ struct TapeOut {
 template <class T> struct TapesReciprocals { static constexpr bool v = sizeof(T) == 8; };
 
 template <class T, int TX, int TY, bool LIMIT, bool TAPE = false, int UNROLL = 1,
-          bool KPER = false>
+          bool KPER = false, int OPT = 0>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
                                            const T* __restrict__ P0, const T* __restrict__ U,
                                            const T* __restrict__ V, const T* __restrict__ W,
@@ -126,6 +126,22 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   T* fxs = sm + L::FXS;
   T* fys = sm + L::FYS;
   auto P1 = [&](int k, int o) -> T& { return p1s[(k & 3) * L::SN + s2 + o]; };
+  // corrective-pass options (kOpt* bits): ABS forms A and B from |psi1|, IGA
+  // uses the infinite-gauge pseudo-fluxes (which are the corrective fluxes),
+  // DFL adds the divergent-flow term
+  constexpr bool kABS = (OPT & kOptABS) != 0, kIGA = (OPT & kOptIGA) != 0;
+  constexpr bool kDFL = (OPT & kOptDFL) != 0;
+  auto ap = [&](T v) { return kABS ? absv(v) : v; };
+  auto pseudo = [&](T C, T gsum, T pl, T pr, T s1p, T s1m, T s2p, T s2m, T c1, T c2) {
+    if constexpr (kIGA) return pseudo_flux_iga(C, gsum, pl, pr, s1p, s1m, s2p, s2m, c1, c2);
+    else return pseudo_velocity(C, gsum, pl, pr, s1p, s1m, s2p, s2m, c1, c2);
+  };
+  // the corrective flux of a face: the donor flux of its (limited) velocity,
+  // or, in the infinite gauge, the value itself
+  auto cflux = [&](T L_, T R_, T C) {
+    if constexpr (kIGA) return C;
+    else return donor(L_, R_, C);
+  };
 
   // Stages B, C and D are computed on every column, not only on the region
   // the next stage reads (no divergent branches); the extra lanes read
@@ -230,20 +246,33 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T* ub = us + (b & 1) * L::RN + s3;
       const T* wb = ws + (b & 1) * L::SN + s2;
       const T* wbm = ws + ((b - 1) & 1) * L::SN + s2;
+      // DFL: the divergence of the Courant numbers of the cell at plane b,
+      // own column (closed faces' W are 0 in the queue)
+      const T dc = kDFL ? (u1 - ub[-1]) + (v1 - vb[-RX]) + (w1 - w0) : zero;
       {  // x face (used on x in [-2, TX], y in [-1, TY]; computed everywhere)
-        const T s1p = P1(b, EX + 1) + P1(b, EX), s1m = P1(b, -EX + 1) + P1(b, -EX);
-        const T s2p = P1(bp, 1) + qp, s2m = P1(bm, 1) + qm;
+        const T s1p = ap(P1(b, EX + 1)) + ap(P1(b, EX)), s1m = ap(P1(b, -EX + 1)) + ap(P1(b, -EX));
+        const T s2p = ap(P1(bp, 1)) + ap(qp), s2m = ap(P1(bm, 1)) + ap(qm);
         const T vsum = v1 + vb[1] + vb[-RX] + vb[-RX + 1];
         const T wsum = w1 + wb[1] + w0 + wbm[1];
-        utB = pseudo_velocity(u1, g1 + gb[1], q1, P1(b, 1), s1p, s1m, s2p, s2m, vsum, wsum);
+        const T gsum = g1 + gb[1];
+        utB = pseudo(u1, gsum, ap(q1), ap(P1(b, 1)), s1p, s1m, s2p, s2m, vsum, wsum);
+        if constexpr (kDFL) {  // + the cell at x+1
+          const T dr = (ub[1] - u1) + (vb[1] - vb[-RX + 1]) + (wb[1] - wbm[1]);
+          utB = utB + divergent_flow_term(u1, gsum, dc + dr);
+        }
         uts[s2] = utB;
       }
       {  // y face (used on x in [-1, TX], y in [-2, TY])
-        const T s1p = P1(b, EX + 1) + P1(b, 1), s1m = P1(b, EX - 1) + P1(b, -1);
-        const T s2p = P1(bp, EX) + qp, s2m = P1(bm, EX) + qm;
+        const T s1p = ap(P1(b, EX + 1)) + ap(P1(b, 1)), s1m = ap(P1(b, EX - 1)) + ap(P1(b, -1));
+        const T s2p = ap(P1(bp, EX)) + ap(qp), s2m = ap(P1(bm, EX)) + ap(qm);
         const T usum = u1 + ub[RX] + ub[-1] + ub[RX - 1];
         const T wsum = w1 + wb[EX] + w0 + wbm[EX];
-        vtB = pseudo_velocity(v1, g1 + gb[EX], q1, P1(b, EX), s1p, s1m, s2p, s2m, usum, wsum);
+        const T gsum = g1 + gb[EX];
+        vtB = pseudo(v1, gsum, ap(q1), ap(P1(b, EX)), s1p, s1m, s2p, s2m, usum, wsum);
+        if constexpr (kDFL) {  // + the cell at y+1
+          const T dr = (ub[RX] - ub[RX - 1]) + (vb[RX] - v1) + (wb[EX] - wbm[EX]);
+          vtB = vtB + divergent_flow_term(v1, gsum, dc + dr);
+        }
         vts[s2] = vtB;
       }
       {  // z face (used on x in [-1, TX], y in [-1, TY])
@@ -251,11 +280,16 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         if (zface(b)) {  // a zero-flux top face is closed
           const T* ub1 = us + ((b + 1) & 1) * L::RN + s3;
           const T* vb1 = vs + ((b + 1) & 1) * L::RN + s3;
-          const T s1p = P1(b + 1, 1) + P1(b, 1), s1m = P1(b + 1, -1) + P1(b, -1);
-          const T s2p = P1(b + 1, EX) + P1(b, EX), s2m = P1(b + 1, -EX) + P1(b, -EX);
+          const T s1p = ap(P1(b + 1, 1)) + ap(P1(b, 1)), s1m = ap(P1(b + 1, -1)) + ap(P1(b, -1));
+          const T s2p = ap(P1(b + 1, EX)) + ap(P1(b, EX));
+          const T s2m = ap(P1(b + 1, -EX)) + ap(P1(b, -EX));
           const T usum = u1 + u2 + ub[-1] + ub1[-1];
           const T vsum = v1 + v2 + vb[-RX] + vb1[-RX];
-          res = pseudo_velocity(w1, g1 + g2, q1, q2, s1p, s1m, s2p, s2m, usum, vsum);
+          res = pseudo(w1, g1 + g2, ap(q1), ap(q2), s1p, s1m, s2p, s2m, usum, vsum);
+          if constexpr (kDFL) {  // + the cell at plane b+1
+            const T dr = (u2 - ub1[-1]) + (v2 - vb1[-RX]) + (w2 - w1);
+            res = res + divergent_flow_term(w1, g1 + g2, dc + dr);
+          }
         }
         wtB = res;
       }
@@ -271,12 +305,12 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
                           pxm, pxp, pym, pyp, qm, qp};
       T hi, lo;
       bounds(vals, hi, lo);
-      const T fxp = donor(q1, pxp, utB);
-      const T fxm = donor(pxm, q1, uts[s2 - 1]);
-      const T fyp = donor(q1, pyp, vtB);
-      const T fym = donor(pym, q1, vts[s2 - EX]);
-      const T fzp = donor(q1, qp, wtB);  // wtB = 0 on a zero-flux top face
-      const T fzm = donor(qm, q1, wtA);  // wtA = 0 on a zero-flux bottom face
+      const T fxp = cflux(q1, pxp, utB);
+      const T fxm = cflux(pxm, q1, uts[s2 - 1]);
+      const T fyp = cflux(q1, pyp, vtB);
+      const T fym = cflux(pym, q1, vts[s2 - EX]);
+      const T fzp = cflux(q1, qp, wtB);  // wtB = 0 on a zero-flux top face
+      const T fzm = cflux(qm, q1, wtA);  // wtA = 0 on a zero-flux bottom face
       const T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
       const T ou = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
       const T ri = rcp(in + eps), ro = rcp(ou + eps);
@@ -291,17 +325,26 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     if (t >= max(klo, k0 - 1) && t <= k1 - 1) {
       const T* bu0 = sm + L::BUS + (t & 1) * L::SN + s2;
       const T* bd0 = sm + L::BDS + (t & 1) * L::SN + s2;
+      // the limited velocity; with ABS a face whose upwind psi1 is negative
+      // carries its flux against its velocity: beta-up and beta-down trade
+      // places there
+      auto lim = [&](T C, T pr, T buR, T bdR) {
+        if constexpr (kABS) {
+          if ((C >= zero ? q0 : pr) < zero) return limit_face(C, bdA, buA, bdR, buR);
+        }
+        return limit_face(C, buA, bdA, buR, bdR);
+      };
       T u = utA;  // used on x in [-1, TX-1], y in [0, TY-1]
-      if (LIMIT) u = limit_face(u, buA, bdA, bu0[1], bd0[1]);
-      fxs[s2] = donor(q0, P1(t, 1), u);
+      if (LIMIT) u = lim(u, P1(t, 1), bu0[1], bd0[1]);
+      fxs[s2] = cflux(q0, P1(t, 1), u);
       T v = vtA;  // used on x in [0, TX-1], y in [-1, TY-1]
-      if (LIMIT) v = limit_face(v, buA, bdA, bu0[EX], bd0[EX]);
-      fys[s2] = donor(q0, P1(t, EX), v);
+      if (LIMIT) v = lim(v, P1(t, EX), bu0[EX], bd0[EX]);
+      fys[s2] = cflux(q0, P1(t, EX), v);
       T f = zero, w = zero;
       if (zface(t)) {
         w = wtA;
-        if (LIMIT) w = limit_face(w, buA, bdA, buB, bdB);
-        f = donor(q0, q1, w);
+        if (LIMIT) w = lim(w, q1, buB, bdB);
+        f = cflux(q0, q1, w);
       }
       fzB = f;
       if (TAPE && t >= k0 && writes) {
@@ -370,14 +413,15 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   }
 }
 
-template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false, bool KPER = false>
+template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false, bool KPER = false,
+          int OPT = 0>
 __global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
              const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
              T* __restrict__ out, TapeOut<T> tape) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k0 = blockIdx.z * kchunk;
-  step_tile2<T, TX, TY, LIMIT, TAPE, 1, KPER>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
+  step_tile2<T, TX, TY, LIMIT, TAPE, 1, KPER, OPT>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
                                               min(g.nz, k0 + kchunk), P0, U, V, W, G, out,
                                               smem_raw, tape);
 }

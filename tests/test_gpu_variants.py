@@ -40,10 +40,10 @@ def _case(opts, shape, seed, kbc):
     return c
 
 
-def _gpu(c, dtype, iord, nonosc, opts, nsteps, kbc):
+def _gpu(c, dtype, iord, nonosc, opts, nsteps, kbc, variant=None):
     from paper_1908_06094_b300 import MPDATA
     m = MPDATA(c.nx, c.ny, c.nz, halo=H, iord=iord, nonoscillatory=nonosc, dtype=dtype,
-               k_bc=kbc, options=opts)
+               k_bc=kbc, options=opts, variant=variant)
     d = [to_dev(synth.pad(x, H, fill=np.nan), dtype) for x in (c.psi, c.u, c.v, c.w, c.g)]
     m.step(*d, nsteps=nsteps)
     torch.cuda.synchronize()
@@ -77,14 +77,19 @@ def test_variant_f64_parity(name, shape, iord, nonosc, kbc):
         assert rel_err(got, ref) <= F64_TOL * nsteps, nsteps
 
 
+@pytest.mark.parametrize("variant", ["fused", "staged"])
 @pytest.mark.parametrize("name", list(OPTS))
-@pytest.mark.parametrize("shape", [(37, 29, 9), (16, 16, 1)])
+@pytest.mark.parametrize("shape", [(37, 29, 9), (16, 16, 1), (70, 40, 20)])
 @pytest.mark.parametrize("nonosc", [0, 1])
-def test_variant_f32_against_f64_oracle(name, shape, nonosc):
+@pytest.mark.parametrize("kbc", [0, 1])
+def test_variant_f32_against_f64_oracle(name, shape, nonosc, kbc, variant):
+    """FP32 options on the fused kernel (the FP32 default) and the staged
+    ones, both vertical boundaries; (70, 40, 20) splits the fused kernel's
+    levels into chunks."""
     opts = OPTS[name]
-    c = rounded_inputs(_case(opts, shape, seed=55, kbc=0), torch.float32)
-    ref = _oracle(c, 2, nonosc, opts, 2, 0)
-    got = _gpu(c, torch.float32, 2, nonosc, opts, 2, 0)
+    c = rounded_inputs(_case(opts, shape, seed=55, kbc=kbc), torch.float32)
+    ref = _oracle(c, 2, nonosc, opts, 2, kbc)
+    got = _gpu(c, torch.float32, 2, nonosc, opts, 2, kbc, {"fused": 0, "staged": 1}[variant])
     assert rel_err(got, ref) <= 2 * F32_TOL
 
 
@@ -136,6 +141,20 @@ def test_option_errors_on_device():
     ctx3 = _capi.mpdata_init(8, 8, 4, 2, 3, 1, _capi.MPDATA_F64)
     assert L.mpdata_set_options(ctx3, _capi.MPDATA_OPT_IGA) == _capi.MPDATA_EINVAL
     _capi.mpdata_destroy(ctx3)
+
+
+def test_fp32_options_run_the_fused_kernel():
+    """With an option set an FP32 context still steps with one launch."""
+    from paper_1908_06094_b300 import MPDATA, _capi
+    c = synth.random_case(40, 36, 10, seed=7)
+    for name, o in OPTS.items():
+        m = MPDATA(c.nx, c.ny, c.nz, halo=H, dtype=torch.float32, options=o)
+        d = [to_dev(synth.pad(x, H), torch.float32) for x in (c.psi, c.u, c.v, c.w, c.g)]
+        out = torch.empty_like(d[0])
+        n0 = _capi.mpdata_launch_count(m._ctx)
+        m.step_out(d[0], out, *d[1:])
+        assert _capi.mpdata_launch_count(m._ctx) - n0 == 1, name
+        m.close()
 
 
 def test_options_off_again_restores_the_basic_step():
