@@ -142,17 +142,21 @@ template <class T, int OPT = 0>
 void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W, const T* G,
                    T* ut, T* vt, T* wt) {
   const Geo& g = c->g;
-  if constexpr (OPT != 0) {  // the options' terms: cell-parallel kernel
+  if constexpr (std::is_same<T, double>::value) {
+    // FP64: the k-marching kernel, with the options' terms (IGA: its own
+    // face operation; ABS, DFL: flags of the common-denominator one)
+    namespace M = mpd::march;
+    constexpr bool kIGA = (OPT & mpd::kOptIGA) != 0, kDFL = (OPT & mpd::kOptDFL) != 0;
+    using Op = std::conditional_t<kIGA, M::PseudoIGA, M::PseudoMergedT<kDFL>>;
+    auto kern = M::march_kernel<double, Op, OPT>;
+    if (!c->kc_fwd) c->kc_fwd = march_chunk(c, M::march_kernel<double, M::PseudoMerged>, true);
+    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
+               kern<<<M::march_grid(g, c->kc_fwd), dim3(M::TX, M::TY), 0, c->stream>>>(
+                   g, P, U, V, W, G, Op{ut, vt, wt}, c->kc_fwd));
+  } else if constexpr (OPT != 0) {  // FP32 staged with options: cell-parallel kernel
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                mpd::staged::pseudo_kernel<T, OPT><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
                    g, P, U, V, W, G, ut, vt, wt));
-  } else if constexpr (std::is_same<T, double>::value) {
-    namespace M = mpd::march;
-    auto kern = M::march_kernel<double, M::PseudoMerged>;
-    if (!c->kc_fwd) c->kc_fwd = march_chunk(c, kern, true);
-    MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-               kern<<<M::march_grid(g, c->kc_fwd), dim3(M::TX, M::TY), 0, c->stream>>>(
-                   g, P, U, V, W, G, M::PseudoMerged{ut, vt, wt}, c->kc_fwd));
   } else {
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                mpd::staged::pseudo_kernel<T><<<cell_grid(g), kCellBlock, 0, c->stream>>>(

@@ -49,10 +49,12 @@ __device__ __forceinline__ double times4(double x) {
 // pl, pr psi1 left and right, DA = S_own + eps, N1 = S(+1) - S(-1) and
 // D1 = S(+1) + S(-1) + eps in the first cross direction, N2, D2 in the
 // second, s1, s2 the sums of the four cross-direction Courant numbers
-// (first, second).  N1/D1 = 2 B1 and N2/D2 = 2 B2.
+// (first, second).  N1/D1 = 2 B1 and N2/D2 = 2 B2.  dsum (the divergent-
+// flow option only, else 0): D_L + D_R, the Courant-number divergences of
+// the face's two cells.
 template <class T>
 struct FaceIn {
-  T U, gsum, pl, pr, DA, N1, D1, N2, D2, s1, s2;
+  T U, gsum, pl, pr, DA, N1, D1, N2, D2, s1, s2, dsum;
 };
 
 // Where the calling thread's cell sits: shared-memory row r = ty+1 and
@@ -67,7 +69,10 @@ struct CellAt {
 struct NoAcc {};
 
 // Forward, FP64: the common-denominator form (see the header comment).
-struct PseudoMerged {
+// DFL: with the divergent-flow term -(1/2) U dsum / Gs, which over the
+// common denominator adds -2 U dsum D_A D_1 D_2 to the numerator.
+template <bool DFL = false>
+struct PseudoMergedT {
   using Acc = NoAcc;
   struct Load {};
   static constexpr bool kAccum = false;
@@ -79,9 +84,43 @@ struct PseudoMerged {
     const double t1 = fma(f.U * -8.0, f.U, fabs(f.U) * g4);  // 4 (|U| Gs - 2 U^2)
     const double D12 = f.D1 * f.D2;
     const double inner = fma(f.s1 * f.N1, f.D2, (f.s2 * f.N2) * f.D1);
-    const double num = fma(-(f.U * f.DA), inner, D12 * (t1 * NA));
-    const double den = (g4 * f.DA) * D12;
+    double num = fma(-(f.U * f.DA), inner, D12 * (t1 * NA));
+    double den;
+    if constexpr (DFL) {
+      const double dad = f.DA * D12;
+      num = fma(-2.0 * f.U * f.dsum, dad, num);
+      den = g4 * dad;
+    } else {
+      den = (g4 * f.DA) * D12;
+    }
     (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = num * rcp(den);
+  }
+  __device__ __forceinline__ void cell(int64_t q, const FaceIn<double>& fx,
+                                      const FaceIn<double>& fy, const FaceIn<double>& fz,
+                                      bool top, CellAt, Load, Acc&) const {
+    face(0, q, fx);
+    face(1, q, fy);
+    if (top) wt[q] = 0.0;
+    else face(2, q, fz);
+  }
+};
+using PseudoMerged = PseudoMergedT<false>;
+
+// Forward, FP64, infinite gauge: the limit of c times the pseudo-velocity
+// of psi + c, whose ratios are cA -> (pr - pl)/2 and cB -> N/8:
+//   Ft = (|U| - U^2/Gf)(pr - pl)/2 - U (s1 N1 + s2 N2) / (32 Gf),
+// one reciprocal of Gs per face.
+struct PseudoIGA {
+  using Acc = NoAcc;
+  struct Load {};
+  static constexpr bool kAccum = false;
+  __device__ __forceinline__ Load load(int64_t) const { return {}; }
+  double *ut, *vt, *wt;
+  __device__ __forceinline__ void face(int fam, int64_t q, const FaceIn<double>& f) const {
+    const double q2 = 2.0 * f.U * rcp(f.gsum);                   // U / Gf
+    const double diff = fabs(f.U) - f.U * q2;                     // |U| - U^2/Gf
+    const double cross = 0.03125 * fma(f.s1, f.N1, f.s2 * f.N2);  // (s1 N1 + s2 N2)/32
+    (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = fma(diff, 0.5 * (f.pr - f.pl), -q2 * cross);
   }
   __device__ __forceinline__ void cell(int64_t q, const FaceIn<double>& fx,
                                       const FaceIn<double>& fy, const FaceIn<double>& fz,
@@ -120,11 +159,15 @@ template <class Op> struct MarchMinB<float, Op> { static constexpr int v = 3; };
 // cells of level k and a barrier op.flush(acc, k, false, ...) writes out
 // the accumulator levels no later cell of the CTA touches, after the last
 // level op.flush(acc, k1-1, true, ...) the rest.
-template <class T, class Op>
+// OPT (kOpt* bits, forward ops only): ABS reads |psi| wherever psi enters
+// (A and B of |psi|); DFL hands each face its dsum.
+template <class T, class Op, int OPT = 0>
 __global__ void __launch_bounds__(TX * TY, MarchMinB<T, Op>::v)
 march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
              const T* __restrict__ cv, const T* __restrict__ cw, const T* __restrict__ G, Op op,
              int kc) {
+  constexpr bool kABS = (OPT & kOptABS) != 0, kDFL = (OPT & kOptDFL) != 0;
+  auto lp = [&](int64_t a) { return kABS ? absv(P[a]) : P[a]; };
   // op is a per-thread copy: accumulating ops keep their flush positions in it
   // accumulating ops order the plane's reuse by their own barrier: one copy
   __shared__ Plane<T> sm[Op::kAccum ? 1 : 2];
@@ -136,6 +179,9 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
   const int i = (i0 + tx) % g.nx, j = (j0 + ty) % g.ny;
   const int64_t o = at(g, i, j, 0), oi = at(g, wrap_up(i, g.nx), j, 0);
   const int64_t oj = at(g, i, wrap_up(j, g.ny), 0);
+  // DFL: the cells at i-1 and j-1 (their Courant numbers close the
+  // divergences of the faces' two cells)
+  const int64_t oim = at(g, wrap_dn(i, g.nx), j, 0), ojm = at(g, i, wrap_dn(j, g.ny), 0);
 
   // ring task: rows j0-1 and j0+TY (threads 0 .. 2TX-1), columns i0-1 and
   // i0+TX (the next 2TY threads)
@@ -168,33 +214,42 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
     op.setup(g, i0, j0, t);
   }
   // register queues: psi and pair sums at k (and k-1), W pairs at k-1/2
-  T pc = P[o + k0 * pxy], pi = P[oi + k0 * pxy], pj = P[oj + k0 * pxy];
+  T pc = lp(o + k0 * pxy), pi = lp(oi + k0 * pxy), pj = lp(oj + k0 * pxy);
   T sx = pc + pi, exx = sx + eps, sy = pc + pj, eyy = sy + eps;
   const int64_t ob = (int64_t)kadj(g, k0 - 1) * pxy;  // the level below the chunk
-  T sxm = P[o + ob] + P[oi + ob], sym = P[o + ob] + P[oj + ob];
-  T pwxm = zero, pwym = zero;
+  T sxm = lp(o + ob) + lp(oi + ob), sym = lp(o + ob) + lp(oj + ob);
+  T pwxm = zero, pwym = zero, wm = zero;  // wm: own W at the face below (DFL)
   if (zopen(g, k0 - 1)) {  // the face below the chunk
     pwxm = cw[o + ob] + cw[oi + ob];
     pwym = cw[o + ob] + cw[oj + ob];
+    wm = cw[o + ob];
   }
   // Everything level k reads from memory (n: level k+1, clamped).
   struct In {
     T pcn, pin, pjn, uc, vc, wc, cvi, cuj, cwi, cwj, cun, cvn, gc, gi, gj, gn;
     T ra, rb, rcn, rv0, rv1, rvn;  // ring task: psi at k (two points), k+1; Courant
+    T ui, uim, vj, vjm, wn;        // DFL: U at i+-1, V at j+-1, own W one face up
     typename Op::Load ol;
   };
   const T* rvel = rkind == 1 ? cv : cu;
   auto load = [&](int k) {
     const int64_t ok = k * pxy, on = (int64_t)kadj(g, k + 1) * pxy;
     In v;
-    v.pcn = P[o + on]; v.pin = P[oi + on]; v.pjn = P[oj + on];
+    v.pcn = lp(o + on); v.pin = lp(oi + on); v.pjn = lp(oj + on);
     v.uc = cu[o + ok]; v.vc = cv[o + ok]; v.wc = cw[o + ok];
     v.cvi = cv[oi + ok]; v.cuj = cu[oj + ok]; v.cwi = cw[oi + ok]; v.cwj = cw[oj + ok];
     v.cun = cu[o + on]; v.cvn = cv[o + on];
     v.gc = G[o + ok]; v.gi = G[oi + ok]; v.gj = G[oj + ok]; v.gn = G[o + on];
     if (rkind) {
-      v.ra = P[ro + ok]; v.rb = P[rn + ok]; v.rcn = P[ro + on];
+      v.ra = lp(ro + ok); v.rb = lp(rn + ok); v.rcn = lp(ro + on);
       v.rv0 = rvel[ro + ok]; v.rv1 = rvel[rn + ok]; v.rvn = rvel[ro + on];
+    }
+    if constexpr (kDFL) {
+      v.ui = cu[oi + ok]; v.uim = cu[oim + ok];
+      v.vj = cv[oj + ok]; v.vjm = cv[ojm + ok];
+      v.wn = zopen(g, k + 1) ? cw[o + on] : zero;  // the face above level k+1
+    } else {
+      v.ui = v.uim = v.vj = v.vjm = v.wn = zero;
     }
     v.ol = op.load(o + ok);
     return v;
@@ -255,20 +310,35 @@ march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
     __syncthreads();
     if (own || Op::kAccum) {  // accumulating ops run whole warps (zero weights past the edge)
       const int64_t q = o + ok;
+      // DFL: D_L + D_R per face: the own-direction Courant numbers two faces
+      // apart, and the cross directions' pair sums differenced (the closed
+      // faces' W are zero)
+      T dx = zero, dy = zero, dz = zero;
+      if constexpr (kDFL) {
+        const T wo = top ? zero : wc;  // own W at face k+1/2
+        dx = (in.ui - in.uim) + (s.pvx[ty + 1][tx] - s.pvx[ty][tx]) + (pwx - pwxm);
+        dy = (in.vj - in.vjm) + (s.puy[ty][tx + 1] - s.puy[ty][tx]) + (pwy - pwym);
+        dz = (in.wn - wm) + (s.puz[ty][tx + 1] - s.puz[ty][tx]) +
+             (s.pvz[ty + 1][tx] - s.pvz[ty][tx]);
+        wm = wo;
+      }
       op.cell(q,
               FaceIn<T>{uc, in.gc + in.gi, pc, pi, exx, s.sx[ty + 2][tx] - s.sx[ty][tx],
                         s.ex[ty + 2][tx] + s.sx[ty][tx], sxn - sxm, exn + sxm,
-                        s.pvx[ty + 1][tx] + s.pvx[ty][tx], pwx + pwxm},
+                        s.pvx[ty + 1][tx] + s.pvx[ty][tx], pwx + pwxm, dx},
               FaceIn<T>{vc, in.gc + in.gj, pc, pj, eyy, s.sy[ty][tx + 2] - s.sy[ty][tx],
                         s.ey[ty][tx + 2] + s.sy[ty][tx], syn - sym, eyn + sym,
-                        s.puy[ty][tx + 1] + s.puy[ty][tx], pwy + pwym},
+                        s.puy[ty][tx + 1] + s.puy[ty][tx], pwy + pwym, dy},
               FaceIn<T>{wc, in.gc + in.gn, pc, pcn, ez,
                         s.sz[ty + 1][tx + 2] - s.sz[ty + 1][tx],
                         s.ez[ty + 1][tx + 2] + s.sz[ty + 1][tx],
                         s.sz[ty + 2][tx + 1] - s.sz[ty][tx + 1],
                         s.ez[ty + 2][tx + 1] + s.sz[ty][tx + 1],
-                        s.puz[ty][tx + 1] + s.puz[ty][tx], s.pvz[ty + 1][tx] + s.pvz[ty][tx]},
+                        s.puz[ty][tx + 1] + s.puz[ty][tx], s.pvz[ty + 1][tx] + s.pvz[ty][tx],
+                        dz},
               top, CellAt{ty + 1, tx + 1, k, own, g.kper != 0}, in.ol, acc);
+    } else if constexpr (kDFL) {
+      wm = top ? zero : in.wc;
     }
     if constexpr (Op::kAccum) {
       __syncthreads();
