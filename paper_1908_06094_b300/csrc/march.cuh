@@ -31,6 +31,13 @@
 //     ring around the tile.  Threads past a ragged domain edge take the
 //     periodic image of their cell, so they supply exactly the ring values
 //     the edge cells need.
+//
+// The corrective-pass options ride on the same march: |psi| is read in
+// place of psi (signed fields), the infinite gauge is its own face
+// operation (one reciprocal, no ratios), and the divergent-flow term adds
+// -2 U dsum D_A D_1 D_2 to the common numerator, dsum = D_L + D_R formed
+// from the Courant numbers two faces apart and the differences of the
+// cross-direction pair sums the march already holds.
 #pragma once
 #include "grid.cuh"
 
