@@ -102,14 +102,35 @@ def _peaks():
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
-    """nvidia-smi clock/throttle samples, stamped with the host clock."""
+    """SM clock and clock-event (throttle) samples during a timed region,
+    stamped with the host clock.  Read-only queries: NVML every 5 ms (the
+    timed regions are tens of milliseconds), else nvidia-smi every 100 ms."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
-    def __init__(self, index: int):
-        self.samples = []
+    def __init__(self, index: int, period_s: float = 0.005, nvml=None):
+        self.samples = []  # (host time, sm MHz, max sm MHz, [4 reason flags])
         self.proc = None
+        self._stop = threading.Event()
+        self.source = None
+        try:
+            if nvml is None:
+                import pynvml as nvml
+            nvml.nvmlInit()
+            h = nvml.nvmlDeviceGetHandleByIndex(index)
+            self._nvml, self._h = nvml, h
+            self._bits = [nvml.nvmlClocksEventReasonHwSlowdown,
+                          nvml.nvmlClocksEventReasonHwThermalSlowdown,
+                          nvml.nvmlClocksEventReasonSwThermalSlowdown,
+                          nvml.nvmlClocksEventReasonSwPowerCap]
+            self.source = "nvml"
+            self.t = threading.Thread(target=self._poll, args=(period_s,), daemon=True)
+            self.t.start()
+            return
+        except Exception:
+            self.source = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={index}", f"--query-gpu={self.Q}",
@@ -118,16 +139,37 @@ class ClockSampler:
         except Exception:
             self.proc = None
             return
+        self.source = "nvidia-smi"
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
 
+    def _poll(self, period_s):
+        n, h = self._nvml, self._h
+        while not self._stop.is_set():
+            try:
+                sm = n.nvmlDeviceGetClockInfo(h, n.NVML_CLOCK_SM)
+                mx = n.nvmlDeviceGetMaxClockInfo(h, n.NVML_CLOCK_SM)
+                r = n.nvmlDeviceGetCurrentClocksEventReasons(h)
+                self.samples.append((time.time(), float(sm), float(mx),
+                                     [bool(r & b) for b in self._bits]))
+            except Exception:
+                pass
+            self._stop.wait(period_s)
+
     def _read(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
         for line in self.proc.stdout:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 8:
-                self.samples.append((time.time(), parts))
+                self.samples.append((time.time(), num(parts[0]), num(parts[1]),
+                                     [parts[4 + q].lower() == "active" for q in range(4)]))
 
     def stop(self):
+        self._stop.set()
         if self.proc:
             self.proc.terminate()
             try:
@@ -136,24 +178,17 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self, t0: float, t1: float):
-        rows = [p for (t, p) in self.samples if t0 <= t <= t1]
+        rows = [x for x in self.samples if t0 <= x[0] <= t1]
         if not rows:   # region shorter than the sampling period: take the nearest
-            rows = [p for (t, p) in self.samples if t0 - 0.25 <= t <= t1 + 0.25]
+            rows = [x for x in self.samples if t0 - 0.25 <= x[0] <= t1 + 0.25]
         if not rows:
             return None
-
-        def num(x):
-            try:
-                return float(x)
-            except ValueError:
-                return None
-        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
-        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[q] for r in rows for q in range(4) if r[4 + q].lower() == "active"})
+        sm = [x[1] for x in rows if x[1] is not None]
+        mx = [x[2] for x in rows if x[2] is not None]
+        reasons = sorted({self.NAMES[q] for x in rows for q in range(4) if x[3][q]})
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "source": self.source}
 
 
 # -------------------------------------------------------------- our arm --

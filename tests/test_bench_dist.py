@@ -64,3 +64,49 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     monkeypatch.setenv("LOCAL_RANK", "1")
     args = argparse.Namespace(steps=3, warmup=3, gpus=2, cpu_seconds=1.0)
     assert bench.run_reference(args, "latlon256_f64") is None
+
+
+class _FakeNVML:
+    """Stands in for pynvml: SM clock 1900 MHz of 2032, power cap active."""
+    NVML_CLOCK_SM = 1
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonSwPowerCap = 0x4
+
+    def nvmlInit(self):
+        pass
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        return ("gpu", i)
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return 1900
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return 2032
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        return 0x4 | 0x1   # power cap, and a bit the summary does not report
+
+
+def test_clock_sampler_reads_nvml_during_the_region():
+    import time
+    s = bench.ClockSampler(0, period_s=0.002, nvml=_FakeNVML())
+    t0 = time.time()
+    time.sleep(0.05)
+    t1 = time.time()
+    s.stop()
+    out = s.summary(t0, t1)
+    assert out["source"] == "nvml" and out["samples"] >= 5
+    assert out["sm_mhz"] == 1900.0 and out["sm_max_mhz"] == 2032.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_without_a_gpu_reports_nothing():
+    class NoNVML(_FakeNVML):
+        def nvmlInit(self):
+            raise RuntimeError("no driver")
+    s = bench.ClockSampler(0, nvml=NoNVML())
+    s.stop()
+    assert s.summary(0.0, 1e18) is None or s.source == "nvidia-smi"
