@@ -101,6 +101,52 @@ def _peaks():
 
 # ------------------------------------------------------------------ clocks --
 
+class _CtypesNVML:
+    """The few read-only NVML calls the sampler uses, through the driver's
+    libnvidia-ml (for hosts without the pynvml module)."""
+    NVML_CLOCK_SM = 1
+    # clock-event reason bits of the NVML API
+    nvmlClocksEventReasonSwPowerCap = 0x4
+    nvmlClocksEventReasonHwSlowdown = 0x8
+    nvmlClocksEventReasonSwThermalSlowdown = 0x20
+    nvmlClocksEventReasonHwThermalSlowdown = 0x40
+
+    def __init__(self):
+        import ctypes
+        self._c = ctypes
+        self._lib = ctypes.CDLL("libnvidia-ml.so.1")
+
+    def _ok(self, rc, what):
+        if rc != 0:
+            raise RuntimeError(f"{what}: NVML error {rc}")
+
+    def nvmlInit(self):
+        self._ok(self._lib.nvmlInit_v2(), "nvmlInit")
+
+    def nvmlDeviceGetHandleByIndex(self, i):
+        h = self._c.c_void_p()
+        self._ok(self._lib.nvmlDeviceGetHandleByIndex_v2(self._c.c_uint(i), self._c.byref(h)),
+                 "handle")
+        return h
+
+    def _uint(self, fn, h, *args):
+        v = self._c.c_uint()
+        self._ok(fn(h, *args, self._c.byref(v)), fn.__name__)
+        return v.value
+
+    def nvmlDeviceGetClockInfo(self, h, kind):
+        return self._uint(self._lib.nvmlDeviceGetClockInfo, h, self._c.c_int(kind))
+
+    def nvmlDeviceGetMaxClockInfo(self, h, kind):
+        return self._uint(self._lib.nvmlDeviceGetMaxClockInfo, h, self._c.c_int(kind))
+
+    def nvmlDeviceGetCurrentClocksEventReasons(self, h):
+        v = self._c.c_ulonglong()
+        self._ok(self._lib.nvmlDeviceGetCurrentClocksThrottleReasons(h, self._c.byref(v)),
+                 "reasons")
+        return v.value
+
+
 class ClockSampler:
     """SM clock and clock-event (throttle) samples during a timed region,
     stamped with the host clock.  Read-only queries: NVML every 5 ms (the
@@ -117,7 +163,10 @@ class ClockSampler:
         self.source = None
         try:
             if nvml is None:
-                import pynvml as nvml
+                try:
+                    import pynvml as nvml
+                except ImportError:
+                    nvml = _CtypesNVML()
             nvml.nvmlInit()
             h = nvml.nvmlDeviceGetHandleByIndex(index)
             self._nvml, self._h = nvml, h
