@@ -307,6 +307,21 @@ def _traffic_from_profiles(stage: str, workload: str, src_hash: str):
     return None
 
 
+def _oracle_sample(call, units_per_call: float, seconds: float, unit: str, sample: str):
+    """The CPU oracle as it stands, timed on the host cores: call() repeated
+    until ``seconds`` have passed (at least once); units/s."""
+    t0 = time.perf_counter()
+    k = 0
+    while True:
+        call()
+        k += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": units_per_call * k / dt, "unit": unit, "cores": os.cpu_count() or 1,
+            "kind": "oracle", "sample": f"{k} x {sample}"}
+
+
 def _oracle_rate(wl, seconds: float, psi, fields, h):
     """Updates/s of the CPU oracle on the full workload grid, stepping until
     ``seconds`` have passed (at least one step)."""
@@ -473,7 +488,7 @@ def run_ours(args, wl_name):
         ncores = os.cpu_count() or 1
         cpu_rate, cpu_steps = _oracle_rate(wl, args.cpu_seconds, padded[0].astype("float64"),
                                            [x.astype("float64") for x in padded[1:]], h)
-        out["adjoint"] = {"f64": measure_adjoint(dev, torch.float64),
+        out["adjoint"] = {"f64": measure_adjoint(dev, torch.float64, cpu_seconds=3.0),
                           "f32": measure_adjoint(dev, torch.float32)}
         out["batched"] = measure_batched(dev)
         out["fp32"] = measure_config(dev, "latlon512_f32")
@@ -590,10 +605,22 @@ def measure_options(dev, steps=20, warmup=3):
             row[name]["vs_basic_time"] = round(row[name]["ms_per_step"] /
                                                row["basic"]["ms_per_step"], 3)
         res[wl_name] = row
+    # the oracle with each option, on the FP64 grid (host cores)
+    import oracle
+    wl = WORKLOADS["latlon256_f64"]
+    c = synth.latlon_3d(wl["nx"], wl["ny"], wl["nz"], seed=1234)
+    P = [synth.pad(x, 2) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    npts = wl["nx"] * wl["ny"] * wl["nz"]
+    res["cpu_baseline"] = {
+        name: _oracle_sample(
+            lambda o=o: oracle.run(P[0] - (0.5 if o & (oracle.ABS | oracle.IGA) else 0.0),
+                                   *P[1:], h=2, iord=2, nonosc=1, opts=o), npts, 1.5,
+            UNIT, f"one step of latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']}")
+        for name, o in (("dfl", oracle.DFL), ("abs", oracle.ABS), ("iga", oracle.IGA))}
     return res
 
 
-def measure_adjoint(dev, dtype, nsteps=20, ckpt=5, reps=2):
+def measure_adjoint(dev, dtype, nsteps=20, ckpt=5, reps=2, cpu_seconds=0.0):
     """Forward and backward (recompute + adjoint) time of nsteps steps with
     checkpointing, on the 256x256x64 lat-lon case (the adjoint config)."""
     import numpy as np
@@ -624,9 +651,19 @@ def measure_adjoint(dev, dtype, nsteps=20, ckpt=5, reps=2):
         if r > 0 and (best is None or f + b < best[0] + best[1]):
             best = (f, b)
     m.close()
-    return {"fwd_ms": round(best[0], 3), "bwd_ms": round(best[1], 3),
-            "ratio": round(best[1] / best[0], 3), "steps": nsteps, "ckpt": ckpt,
-            "grid": "256x256x64", "backward": "recompute per segment + adjoint steps"}
+    out = {"fwd_ms": round(best[0], 3), "bwd_ms": round(best[1], 3),
+           "ratio": round(best[1] / best[0], 3), "steps": nsteps, "ckpt": ckpt,
+           "grid": "256x256x64", "backward": "recompute per segment + adjoint steps"}
+    if cpu_seconds > 0:
+        import oracle
+        dy = synth.pad(rng.standard_normal(c.psi.shape), h)
+        npts = c.nx * c.ny * c.nz
+        out["cpu_baseline"] = _oracle_sample(
+            lambda: oracle.adjoint(*padded, dy, h=h, iord=2, nonosc=1, nsteps=1), npts,
+            cpu_seconds, "reverse-step cell-updates/s (GPU: steps x cells / bwd time)",
+            "one reverse step of the same grid (forward recomputed)")
+        out["value_gpu"] = nsteps * npts / (best[1] / 1e3)
+    return out
 
 
 def measure_batched(dev, steps=20, warmup=3):
@@ -661,12 +698,23 @@ def measure_batched(dev, steps=20, warmup=3):
     value = n * steps / (ms / 1e3)
     b.close()
     gbs = value * 10 / 1e9
+    # the oracle on the batch's tracers, domain by domain (FP64, host cores)
+    import oracle
+
+    def one_pass():
+        for c in cases:
+            P = [synth.pad(getattr(c, k), h) for k in ("u", "v", "w", "g")]
+            oracle.run(synth.pad(c.psi[0], h), *P, h=h, iord=2, nonosc=1, nsteps=1)
+    tracer_pts_per_pass = sum(c.nx * c.ny * c.nz for c in cases)
+    cpu = _oracle_sample(one_pass, tracer_pts_per_pass, 3.0, "tracer-point updates/s",
+                         "one step of the first tracer of each of the 64 domains")
     return {"metric": "tracer-point updates/s", "value": value, "ms_per_step": ms / steps,
             "tracer_points": n, "domains": 64, "tracers": 8, "dtype": "f32",
             "config": cfg, "launches_per_step": 1,
             "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                          "frac": round(gbs / hbm, 4),
-                         "algorithmic_bytes_per_update": 10}}
+                         "algorithmic_bytes_per_update": 10},
+            "cpu_baseline": cpu}
 
 
 # --------------------------------------------------------- reference arm --
@@ -881,6 +929,14 @@ def measure_cells(dev, reps=15):
                 red.close()
             res[f"{nr}x{nc}x{nz}_{'f64' if esize == 8 else 'f32'}"] = row
     res["hbm_peak_gbs"] = hbm
+    # the oracle's table-driven sum, host cores, on the larger patch
+    import oracle
+    nr, nc, nz = 512, 512, 80
+    t = cells.c2c(nr, nc, "SN")
+    A = cells.field(nr, nc, nz, seed=1)
+    res["cpu_baseline"] = _oracle_sample(lambda: oracle.cells_sum(t, A, 1.0), 2 * nr * nc * nz,
+                                         2.0, "cell-level updates/s",
+                                         "the sum on the 512x512x80 patch, SN table")
     return res
 
 
