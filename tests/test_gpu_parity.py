@@ -255,3 +255,40 @@ def test_profile_and_launch_count():
     assert tot == n1 - n0
     _capi.mpdata_profile(m._ctx, False)
     m.close()
+
+
+def _exact_mass(psi, g):
+    """sum of the interior products psi*G, each rounded once, summed exactly."""
+    import math
+    return math.fsum((np.asarray(psi, dtype=np.float64) * np.asarray(g, dtype=np.float64)).ravel())
+
+
+def test_latlon_256_f64_fifty_steps():
+    """The 3D FP64 configuration run for its 50 steps: the FP64 error stays
+    within the per-step bound times the step count, and mass is conserved."""
+    c = synth.latlon_3d(256, 256, 64)
+    ref = _oracle(c, 2, 1, 50)
+    got = run_library(c, torch.float64, 2, 1, 50)
+    assert rel_err(got, ref) <= 50 * F64_TOL
+    # mass: the products psi*G summed exactly (a running sum of 4.2M terms
+    # would itself be off by ~1e-13 relative)
+    m0 = _exact_mass(c.psi, c.g)
+    assert abs(_exact_mass(synth.interior(got, c.halo), c.g) - m0) <= 1e-13 * m0
+
+
+def test_latlon_512_f32_five_steps_error_and_drift():
+    """The 3D FP32 configuration over 5 steps against the FP64 oracle on the
+    same FP32-rounded inputs: max-abs and L2 errors relative to max |psi|
+    and the mass drift (FP64 sums of the FP32 fields)."""
+    c = rounded_inputs(synth.latlon_3d(512, 512, 128), torch.float32)
+    ref = _oracle(c, 2, 1, 5)
+    got = run_library(c, torch.float32, 2, 1, 5)
+    h = c.halo
+    gi, ri = synth.interior(got, h), synth.interior(ref, h)
+    scale = float(np.abs(ri).max())
+    max_abs = float(np.abs(gi - ri).max()) / scale
+    l2 = float(np.sqrt(np.mean((gi - ri) ** 2))) / scale
+    assert max_abs <= 5 * F32_TOL, max_abs
+    assert l2 <= 5 * F32_TOL / 10, l2
+    m0 = _exact_mass(c.psi, c.g)
+    assert abs(_exact_mass(gi, c.g) - m0) <= 1e-6 * m0
