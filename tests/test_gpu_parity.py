@@ -292,3 +292,24 @@ def test_latlon_512_f32_five_steps_error_and_drift():
     assert l2 <= 5 * F32_TOL / 10, l2
     m0 = _exact_mass(c.psi, c.g)
     assert abs(_exact_mass(gi, c.g) - m0) <= 1e-6 * m0
+
+
+@pytest.mark.parametrize("variant", list(VARIANTS))
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("iord,h", [(1, 1), (2, 3), (2, 4), (5, 2), (8, 3)])
+@pytest.mark.parametrize("nonosc", [0, 1])
+def test_iord_and_halo_range(iord, h, nonosc, dtype, variant):
+    """The documented ranges beyond the defaults: the donor cell alone with a
+    one-cell halo, deeper halos (the output's halo filled to its depth) and
+    up to eight passes."""
+    c = synth.random_case(23, 17, 6, seed=iord * 10 + h, cmax=0.25)
+    if dtype == torch.float32:
+        c = rounded_inputs(c, dtype)
+    ref = _oracle(c, iord, nonosc, 2, h=h)
+    got = run_library(c, dtype, iord, nonosc, 2, h=h, variant=VARIANTS[variant])
+    tol = (F64_TOL if dtype == torch.float64 else F32_TOL) * 2 * max(1, iord - 1)
+    assert rel_err(got, ref) <= tol
+    inner = synth.interior(got, h)
+    ref_halo = np.pad(np.pad(inner, ((0, 0), (h, h), (h, h)), mode="wrap"),
+                      ((h, h), (0, 0), (0, 0)), mode="edge")
+    assert np.array_equal(got, ref_halo)
