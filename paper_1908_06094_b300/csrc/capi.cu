@@ -27,6 +27,7 @@ struct mpdata_ctx {
   // scratch of one step (one allocation)
   void* scratch;
   void *psi1, *psi2, *fx, *fy, *fz, *ut, *vt, *wt, *bu, *bd, *ul, *vl, *wl;
+  void* rg;  // 1/G, shared by the advances of one FP64 staged step (iord >= 2)
   double* part;
   // fused kernel launch shape (chosen in init)
   int fused_ok, nchunks, kchunk;
@@ -177,12 +178,19 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
   cudaStream_t s = c->stream;
   const T* psi = psi_in;
   T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
+  // FP64: the donor advance keeps 1/G for the corrective advances
+  T* rg = (T*)c->rg;
   // pass 1: donor cell
   T* cur = c->iord == 1 ? psi_out : (T*)c->psi1;
   MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
              flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
-  MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-             advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur));
+  if (rg) {
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+               (advance_kernel<T, 1><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur, rg)));
+  } else {
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur));
+  }
   MPD_CHECK_LAUNCH(c, "donor pass");
   // corrective passes
   const T *cu = U, *cv = V, *cw = W;
@@ -212,8 +220,14 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
                                                              fx, fy, fz));
     }
     T* dest = !more ? psi_out : (cur == (T*)c->psi1 ? (T*)c->psi2 : (T*)c->psi1);
-    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, ffx, ffy, ffz, G, dest));
+    if (rg) {
+      MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+                 (advance_kernel<T, 2><<<grid, kCellBlock, 0, s>>>(g, cur, ffx, ffy, ffz, G, dest,
+                                                                  rg)));
+    } else {
+      MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+                 advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, ffx, ffy, ffz, G, dest));
+    }
     MPD_CHECK_LAUNCH(c, "corrective pass");
     cur = dest;
     T** vset = c->nonosc ? lset : tset;
@@ -725,7 +739,8 @@ int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, in
   c->stream = (cudaStream_t)stream;
   const size_t fbytes = ((size_t)c->g.total * c->esize + 255) & ~(size_t)255;
   const int nfields = iord >= 2 ? (iord >= 3 ? 13 : 9) : 3;
-  const size_t bytes = fbytes * nfields + sizeof(double) * mpd::MASS_BLOCKS;
+  const int nrg = (dtype == MPDATA_F64 && iord >= 2) ? 1 : 0;
+  const size_t bytes = fbytes * (nfields + nrg) + sizeof(double) * mpd::MASS_BLOCKS;
   if (cudaMalloc(&c->scratch, bytes) != cudaSuccess) {
     cudaGetLastError();
     delete c;
@@ -735,7 +750,8 @@ int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, in
   void** slots[13] = {&c->fx, &c->fy, &c->fz, &c->psi1, &c->ut, &c->vt, &c->wt, &c->bu,
                       &c->bd, &c->psi2, &c->ul, &c->vl, &c->wl};
   for (int q = 0; q < nfields; ++q) *slots[q] = p + q * fbytes;
-  c->part = (double*)(p + nfields * fbytes);
+  c->rg = nrg ? p + nfields * fbytes : nullptr;
+  c->part = (double*)(p + (nfields + nrg) * fbytes);
   if (dtype == MPDATA_F64) fused_setup<double>(c); else fused_setup<float>(c);
   *out = c;
   return MPDATA_OK;

@@ -329,10 +329,13 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       // carries its flux against its velocity: beta-up and beta-down trade
       // places there
       auto lim = [&](T C, T pr, T buR, T bdR) {
+        T uL = buA, dL = bdA, uR = buR, dR = bdR;
         if constexpr (kABS) {
-          if ((C >= zero ? q0 : pr) < zero) return limit_face(C, bdA, buA, bdR, buR);
+          if (!ge0(ge0(C) ? q0 : pr)) {
+            uL = bdA; dL = buA; uR = bdR; dR = buR;
+          }
         }
-        return limit_face(C, buA, bdA, buR, bdR);
+        return limit_face(C, uL, dL, uR, dR);
       };
       T u = utA;  // used on x in [-1, TX-1], y in [0, TY-1]
       if (LIMIT) u = lim(u, P1(t, 1), bu0[1], bd0[1]);

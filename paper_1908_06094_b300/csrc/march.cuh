@@ -9,7 +9,7 @@
 // stage, the costliest of the step, is bound by its count of FP64
 // instructions, not by memory.  Two changes against the cell-parallel form
 // (one thread computes the three faces of its cell from scratch, about 140
-// FP64 instructions per cell) bring the FP64 forward to about 90:
+// FP64 instructions per cell) bring the FP64 forward to about 86:
 //
 //  1. Each face needs four ratios -- A, two B's and 1/G_face -- and the four
 //     divisions (a reciprocal seed plus a refinement each) dominate.  They
@@ -19,6 +19,9 @@
 //     with Gs = G_L + G_R, N_A/D_A = A, N_1/D_1 = 2B_1, N_2/D_2 = 2B_2 and
 //     S1, S2 the sums of the four cross-direction Courant numbers; in exact
 //     arithmetic this is the same rational function as the per-ratio form.
+//     U is then factored out of the numerator, |U| Gs - 2U^2 being
+//     U (sgn(U) Gs - 2U) with the sign moved onto Gs as a bit: 17 FP64
+//     instructions a face.
 //     The denominators are >= epsilon for non-negative psi, so the product
 //     stays in the normal range (it would overflow only for |psi| ~ 1e90).
 //  2. Every psi pair sum S (psi_L + psi_R across a face) is used by five
@@ -52,6 +55,12 @@ __device__ __forceinline__ double times4(double x) {
   return __hiloint2double(__double2hiint(x) + (2 << 20), __double2loint(x));
 }
 
+// |x| with the sign of s (x >= 0): a sign-bit move on the high words.
+__device__ __forceinline__ double sign_of(double x, double s) {
+  return __hiloint2double(__double2hiint(x) | (__double2hiint(s) & (int)0x80000000),
+                          __double2loint(x));
+}
+
 // The ingredients of one face: U its Courant number, gsum = G_L + G_R,
 // pl, pr psi1 left and right, DA = S_own + eps, N1 = S(+1) - S(-1) and
 // D1 = S(+1) + S(-1) + eps in the first cross direction, N2, D2 in the
@@ -75,9 +84,11 @@ struct CellAt {
 // Ops without shared accumulators.
 struct NoAcc {};
 
-// Forward, FP64: the common-denominator form (see the header comment).
+// Forward, FP64: the common-denominator form (see the header comment),
+//   Ut = U [4 (sgn(U) Gs - 2U) N_A D_1 D_2 - D_A (S1 N_1 D_2 + S2 N_2 D_1)]
+//        / (4 Gs D_A D_1 D_2).
 // DFL: with the divergent-flow term -(1/2) U dsum / Gs, which over the
-// common denominator adds -2 U dsum D_A D_1 D_2 to the numerator.
+// common denominator adds -2 dsum D_A D_1 D_2 to the bracket.
 template <bool DFL = false>
 struct PseudoMergedT {
   using Acc = NoAcc;
@@ -88,19 +99,13 @@ struct PseudoMergedT {
   __device__ __forceinline__ void face(int fam, int64_t q, const FaceIn<double>& f) const {
     const double g4 = times4(f.gsum);
     const double NA = f.pr - f.pl;
-    const double t1 = fma(f.U * -8.0, f.U, fabs(f.U) * g4);  // 4 (|U| Gs - 2 U^2)
+    const double t1 = fma(f.U, -8.0, sign_of(g4, f.U));  // 4 (sgn(U) Gs - 2U)
     const double D12 = f.D1 * f.D2;
     const double inner = fma(f.s1 * f.N1, f.D2, (f.s2 * f.N2) * f.D1);
-    double num = fma(-(f.U * f.DA), inner, D12 * (t1 * NA));
-    double den;
-    if constexpr (DFL) {
-      const double dad = f.DA * D12;
-      num = fma(-2.0 * f.U * f.dsum, dad, num);
-      den = g4 * dad;
-    } else {
-      den = (g4 * f.DA) * D12;
-    }
-    (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = num * rcp(den);
+    double num = fma(-f.DA, inner, D12 * (t1 * NA));
+    const double dad = f.DA * D12;
+    if constexpr (DFL) num = fma(-2.0 * f.dsum, dad, num);
+    (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = (f.U * num) * rcp(g4 * dad);
   }
   __device__ __forceinline__ void cell(int64_t q, const FaceIn<double>& fx,
                                       const FaceIn<double>& fy, const FaceIn<double>& fz,

@@ -49,17 +49,27 @@ __global__ void flux_kernel(Geo g, const T* __restrict__ P, const T* __restrict_
 // Flux divergence and advance (Listings 8/9): out = P - (1/G) sum dF.
 // P and out may be the same buffer (each thread reads and writes only its
 // own point), so neither is declared __restrict__.
-template <class T>
+// RG: 0 forms 1/G here; 1 forms it and also stores it to rg; 2 reads it from
+// rg (stored by an earlier advance of the same step with the same G: the
+// FP64 corrective passes skip the reciprocal's three FMAs for one load).
+template <class T, int RG = 0>
 __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
                                const T* __restrict__ fy, const T* __restrict__ fz,
-                               const T* __restrict__ G, T* out) {
+                               const T* __restrict__ G, T* out, T* rg = nullptr) {
   Cell c = cell_of(g);
   if (!c.ok) return;
   int64_t q = at(g, c.i, c.j, c.k);
   T fxm = fx[at(g, wrap_dn(c.i, g.nx), c.j, c.k)];
   T fym = fy[at(g, c.i, wrap_dn(c.j, g.ny), c.k)];
   T fzm = zopen(g, c.k - 1) ? fz[at(g, c.i, c.j, kadj(g, c.k - 1))] : T(0);
-  out[q] = P[q] - ((fx[q] - fxm) + (fy[q] - fym) + (fz[q] - fzm)) * rcp(G[q]);
+  T r;
+  if constexpr (RG == 2) {
+    r = rg[q];
+  } else {
+    r = rcp(G[q]);
+    if constexpr (RG == 1) rg[q] = r;
+  }
+  out[q] = P[q] - ((fx[q] - fxm) + (fy[q] - fym) + (fz[q] - fzm)) * r;
 }
 
 // Antidiffusive pseudo-velocities on the "+" faces of every cell
@@ -198,10 +208,13 @@ __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restri
   const int64_t qy = at(g, c.i, wrap_up(c.j, g.ny), c.k);
   T pc = P[q], buc = bu[q], bdc = bd[q];
   auto lim = [&](T Ut, int64_t qn) {
+    T uL = buc, dL = bdc, uR = bu[qn], dR = bd[qn];
     if constexpr ((OPT & kOptABS) != 0) {
-      if ((Ut >= T(0) ? pc : P[qn]) < T(0)) return limit_face(Ut, bdc, buc, bd[qn], bu[qn]);
+      if (!ge0(ge0(Ut) ? pc : P[qn])) {
+        uL = bdc; dL = buc; uR = bd[qn]; dR = bu[qn];
+      }
     }
-    return limit_face(Ut, buc, bdc, bu[qn], bd[qn]);
+    return limit_face(Ut, uL, dL, uR, dR);
   };
   auto fl = [&](T R, T C) {
     if constexpr ((OPT & kOptIGA) != 0) return C;
