@@ -80,13 +80,17 @@ __device__ __forceinline__ void rev_limit_face(T lb, T Ut, T buL, T bdL, T buR, 
 // upwind partial Fb*C of each of its six faces where it is the upwind value
 // (C > 0 on its "+" faces, C < 0 on its "-" faces; both partials vanish at
 // C = 0), and hands the velocity adjoint Fb*(upwind value) (L + R at
-// C = 0) of each of its own three "+" faces to out(fam, q, n, cb) (n the
-// face's right cell), and its closed top face to out.closed(q).  ADD_P:
+// C = 0) of each of its own three "+" faces to out(fam, q, n, cb, pre) (n
+// the face's right cell, pre = out.pre(fam, q, n), the values out reads),
+// and its closed top face to out.closed(q).  ADD_P:
 // Pb = Pin + the gathered sum and Pin is cleared (its only reader; Pin and
 // Pb distinct), else Pb = the sum (the field's first writer).  Pb must not
 // alias ob.  S: s comes
 // precomputed in sf (FP64, where six neighbour reciprocals would cost 24
 // FP64 instructions), else it is formed from ob and G.
+// Every load is issued before the first store: the kernel is bound by load
+// latency, and with output fields that are not restrict-qualified a load
+// placed after a store could not be moved above it.
 template <class T, bool ADD_P, bool S, class Out>
 __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
                                           const T* __restrict__ cu, const T* __restrict__ cv,
@@ -96,40 +100,47 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
-  auto s_at = [&](int64_t n) { return S ? sf[n] : ob[n] * rcp(G[n]); };
-  const T sq = s_at(q), pc = P[q];
-  T acc = ob[q];
-  // "+" face to neighbour n with Courant number C (q is its left value)
-  auto plus = [&](int fam, int64_t n, T C) {
-    const T Fb = s_at(n) - sq;
-    const bool ge = ge0(C), le = le0(C);
-    T cb;
-    if (ge && le) {
-      cb = Fb * (pc + P[n]);
-    } else {
-      if (ge) acc += Fb * C;
-      cb = Fb * (ge ? pc : P[n]);
-    }
-    out(fam, q, n, cb);
-  };
-  // "-" face from neighbour n (q is its right value)
-  auto minus = [&](int64_t n, T C) {
-    if (!ge0(C)) acc += (sq - s_at(n)) * C;
-  };
+  const bool zt = zopen(g, c.k), zb = zopen(g, c.k - 1);
   const int64_t xp = at(g, wrap_up(c.i, g.nx), c.j, c.k), xm = at(g, wrap_dn(c.i, g.nx), c.j, c.k);
   const int64_t yp = at(g, c.i, wrap_up(c.j, g.ny), c.k), ym = at(g, c.i, wrap_dn(c.j, g.ny), c.k);
-  plus(0, xp, cu[q]);
-  minus(xm, cu[xm]);
-  plus(1, yp, cv[q]);
-  minus(ym, cv[ym]);
-  if (zopen(g, c.k)) plus(2, at(g, c.i, c.j, kadj(g, c.k + 1)), cw[q]);
+  // a closed face takes q as an in-bounds stand-in (its values are unused)
+  const int64_t zp = zt ? at(g, c.i, c.j, kadj(g, c.k + 1)) : q;
+  const int64_t zm = zb ? at(g, c.i, c.j, kadj(g, c.k - 1)) : q;
+  auto s_at = [&](int64_t n) { return S ? sf[n] : ob[n] * rcp(G[n]); };
+  const T obq = ob[q], pc = P[q];
+  const T sq = S ? sf[q] : obq * rcp(G[q]);
+  const T sxp = s_at(xp), sxm = s_at(xm), syp = s_at(yp), sym = s_at(ym);
+  const T szp = s_at(zp), szm = s_at(zm);
+  const T pxp = P[xp], pyp = P[yp], pzp = P[zp];
+  const T cx = cu[q], cy = cv[q], cz = cw[q], cxm = cu[xm], cym = cv[ym], czm = cw[zm];
+  const T pin = ADD_P ? Pin[q] : T(0);
+  const typename Out::Pre ox = out.pre(0, q, xp), oy = out.pre(1, q, yp), oz = out.pre(2, q, zp);
+  T acc = obq;
+  // "+" face to neighbour n with Courant number C (q is its left value)
+  auto plus = [&](T sn, T pn, T C) {
+    const T Fb = sn - sq;
+    const bool ge = ge0(C), le = le0(C);
+    if (ge && le) return Fb * (pc + pn);
+    if (ge) acc += Fb * C;
+    return Fb * (ge ? pc : pn);
+  };
+  // "-" face from neighbour n (q is its right value)
+  auto minus = [&](T sn, T C) {
+    if (!ge0(C)) acc += (sq - sn) * C;
+  };
+  const T bx = plus(sxp, pxp, cx);
+  minus(sxm, cxm);
+  const T by = plus(syp, pyp, cy);
+  minus(sym, cym);
+  T bz = T(0);
+  if (zt) bz = plus(szp, pzp, cz);
+  if (zb) minus(szm, czm);
+  out(0, q, xp, bx, ox);
+  out(1, q, yp, by, oy);
+  if (zt) out(2, q, zp, bz, oz);
   else out.closed(q);
-  if (zopen(g, c.k - 1)) {
-    const int64_t qm = at(g, c.i, c.j, kadj(g, c.k - 1));
-    minus(qm, cw[qm]);
-  }
   if (ADD_P) {
-    Pb[q] = Pin[q] + acc;
+    Pb[q] = pin + acc;
     Pin[q] = T(0);
   } else {
     Pb[q] = acc;
@@ -143,11 +154,18 @@ template <class T, bool ADD>
 struct VelOut {
   T *ub, *vb, *wb;
   const T *au, *av, *aw;
-  __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t, T cb) const {
+  struct Pre { T a, f; };
+  __device__ __forceinline__ Pre pre(int fam, int64_t q, int64_t) const {
+    const T* a = fam == 0 ? au : fam == 1 ? av : aw;
+    const T* f = fam == 0 ? ub : fam == 1 ? vb : wb;
+    return Pre{a ? a[q] : T(0), ADD ? f[q] : T(0)};
+  }
+  __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t, T cb,
+                                             const Pre& p) const {
     T* f = fam == 0 ? ub : fam == 1 ? vb : wb;
     const T* a = fam == 0 ? au : fam == 1 ? av : aw;
-    if (a) cb += a[q];
-    f[q] = ADD ? f[q] + cb : cb;
+    if (a) cb += p.a;
+    f[q] = ADD ? p.f + cb : cb;
   }
   __device__ __forceinline__ void closed(int64_t q) const {
     if (!ADD) wb[q] = T(0);
@@ -164,12 +182,18 @@ struct LimitOut {
   const T *ut, *vt, *wt, *bu, *bd;
   T *utb, *vtb, *wtb, *bub, *bdb;
   const T *au, *av, *aw;
-  __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t n, T lb) const {
+  struct Pre { T a, U, buL, bdL, buR, bdR; };
+  __device__ __forceinline__ Pre pre(int fam, int64_t q, int64_t n) const {
     const T* a = fam == 0 ? au : fam == 1 ? av : aw;
-    if (a) lb += a[q];
     const T* U = fam == 0 ? ut : fam == 1 ? vt : wt;
+    return Pre{a ? a[q] : T(0), U[q], bu[q], bd[q], bu[n], bd[n]};
+  }
+  __device__ __forceinline__ void operator()(int fam, int64_t q, int64_t n, T lb,
+                                             const Pre& p) const {
+    const T* a = fam == 0 ? au : fam == 1 ? av : aw;
+    if (a) lb += p.a;
     T* Ub = fam == 0 ? utb : fam == 1 ? vtb : wtb;
-    rev_limit_face(lb, U[q], bu[q], bd[q], bu[n], bd[n], &Ub[q], &bub[q], &bdb[q], &bub[n],
+    rev_limit_face(lb, p.U, p.buL, p.bdL, p.buR, p.bdR, &Ub[q], &bub[q], &bdb[q], &bub[n],
                    &bdb[n]);
   }
   __device__ __forceinline__ void closed(int64_t q) const { wtb[q] = T(0); }
