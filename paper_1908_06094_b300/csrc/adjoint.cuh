@@ -332,6 +332,9 @@ __device__ __forceinline__ T sgn0(T U) {
 //   w1p, w1m = t1 (1 - B1'), -t1 (1 + B1') with t1 = m4 s1 / D1,
 //            m4 = -ub qh / 4 (w2p, w2m the same with s2, D2, B2');
 //   c1, c2 = m4 B1', m4 B2'.
+// The factors 1/4 ride on the reciprocal: rq = 1/(4 (G_L+G_R)) (the 4 an
+// exponent step) and qq = -U rq = -qh/4, so that m4 = ub qq, 4 qh = -16 qq,
+// 2 U qh = -8 U qq and X8 rG2 / 4 = X8 rq: two FP64 products a face fewer.
 // The eight weights and the direct adjoint ub * dUt/dU of one face (see
 // above), for the face adjoint ub.
 template <class T>
@@ -341,14 +344,14 @@ struct FaceW {
 
 template <class T>
 __device__ __forceinline__ FaceW<T> face_weights(const march::FaceIn<T>& f, T ubv) {
-  const T rd = rcp(f.DA), rd1 = rcp(f.D1), rd2 = rcp(f.D2), rG2 = rcp(f.gsum);
+  const T rd = rcp(f.DA), rd1 = rcp(f.D1), rd2 = rcp(f.D2), rq = rcp(march::times4(f.gsum));
   const T A = (f.pr - f.pl) * rd, B1 = f.N1 * rd1, B2 = f.N2 * rd2;
-  const T qh = f.U * rG2;
-  const T Dd = fma_rn(f.U * T(-2), qh, absv(f.U));
+  const T qq = -f.U * rq;
+  const T Dd = fma_rn(f.U * T(8), qq, absv(f.U));
   const T X8 = fma_rn(f.s2, B2, f.s1 * B1);
-  const T dU = fma_rn(X8 * rG2, T(-0.25), A * fma_rn(qh, T(-4), sgn0(f.U)));
+  const T dU = fma_rn(-X8, rq, A * fma_rn(qq, T(16), sgn0(f.U)));
   const T Abr = ubv * Dd * rd;
-  const T m4 = ubv * qh * T(-0.25);
+  const T m4 = ubv * qq;
   const T t1 = m4 * f.s1 * rd1, t2 = m4 * f.s2 * rd2;
   return FaceW<T>{fma_rn(-Abr, A, -Abr), fma_rn(-Abr, A, Abr), fma_rn(-t1, B1, t1),
                   fma_rn(-t1, B1, -t1),  fma_rn(-t2, B2, t2),  fma_rn(-t2, B2, -t2),
@@ -383,18 +386,21 @@ struct RevPseudo {
   __device__ __forceinline__ void cell(int64_t q, const march::FaceIn<T>& fx,
                                       const march::FaceIn<T>& fy, const march::FaceIn<T>& fz,
                                       bool top, march::CellAt, Load l, Acc&) const {
+    // the accumulators' old values are read before the first store (the
+    // weight stores could alias them as far as the compiler knows)
+    const T u0 = ub[q], v0 = vb[q], w0 = top ? T(0) : wb[q];
     const FaceW<T> x = face_weights(fx, l.x);
     store(0, q, x);
-    ub[q] += x.du;
+    ub[q] = u0 + x.du;
     const FaceW<T> y = face_weights(fy, l.y);
     store(1, q, y);
-    vb[q] += y.du;
+    vb[q] = v0 + y.du;
     if (top) {
       store(2, q, FaceW<T>{});
     } else {
       const FaceW<T> z = face_weights(fz, l.z);
       store(2, q, z);
-      wb[q] += z.du;
+      wb[q] = w0 + z.du;
     }
   }
 };
@@ -585,6 +591,9 @@ __global__ void rev_pg_kernel(Geo g, const T* __restrict__ wts, T* Pb, T* ub, T*
   auto W = [&](int fam, int w, int a, int b, int d) -> T {
     return wts[((int64_t)fam * kNW + w) * F + at(g, a, b, d)];
   };
+  // the accumulators' old values, read before the first store
+  const int64_t q = at(g, i, j, k);
+  const T p0 = Pb[q], u0 = ub[q], v0 = vb[q], w0 = zopen(g, k) ? wb[q] : T(0);
   T s = T(0);
   // x faces: A, B1 (y), B2 (z, clamped)
   s += W(0, kWL, i, j, k) + W(0, kWR, im, j, k);
@@ -614,21 +623,20 @@ __global__ void rev_pg_kernel(Geo g, const T* __restrict__ wts, T* Pb, T* ub, T*
   if (below)
     s += W(2, kW1P, im, j, kb) + W(2, kW1M, ip, j, kb) + W(2, kW2P, i, jm, kb) +
          W(2, kW2M, i, jp, kb);
-  const int64_t q = at(g, i, j, k);
-  Pb[q] += s;
+  Pb[q] = p0 + s;
   // cross averages: U (face i+1/2) in y faces and z faces, V in x and z, W in x and y
   T su = W(1, kC1, i, j, k) + W(1, kC1, i, jm, k) + W(1, kC1, ip, j, k) + W(1, kC1, ip, jm, k);
   su += W(2, kC1, i, j, k) + W(2, kC1, ip, j, k);
   if (below) su += W(2, kC1, i, j, kb) + W(2, kC1, ip, j, kb);
-  ub[q] += su;
+  ub[q] = u0 + su;
   T sv = W(0, kC1, i, j, k) + W(0, kC1, im, j, k) + W(0, kC1, i, jp, k) + W(0, kC1, im, jp, k);
   sv += W(2, kC2, i, j, k) + W(2, kC2, i, jp, k);
   if (below) sv += W(2, kC2, i, j, kb) + W(2, kC2, i, jp, kb);
-  vb[q] += sv;
+  vb[q] = v0 + sv;
   if (zopen(g, k)) {  // open vertical face
     T sw = W(0, kC2, i, j, k) + W(0, kC2, im, j, k) + W(0, kC2, i, j, ka) + W(0, kC2, im, j, ka);
     sw += W(1, kC2, i, j, k) + W(1, kC2, i, jm, k) + W(1, kC2, i, j, ka) + W(1, kC2, i, jm, ka);
-    wb[q] += sw;
+    wb[q] = w0 + sw;
   }
 }
 

@@ -54,6 +54,7 @@ constexpr int TX = 32, TY = 8, KC = 8;
 __device__ __forceinline__ double times4(double x) {
   return __hiloint2double(__double2hiint(x) + (2 << 20), __double2loint(x));
 }
+__device__ __forceinline__ float times4(float x) { return x * 4.0f; }
 
 // |x| with the sign of s (x >= 0): a sign-bit move on the high words.
 __device__ __forceinline__ double sign_of(double x, double s) {
