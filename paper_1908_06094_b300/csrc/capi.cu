@@ -139,21 +139,30 @@ int march_chunk(mpdata_ctx* c, K kernel, bool pipe_bound) {
 
 // The pseudo-velocity stage: FP64 on the k-marching common-denominator
 // kernel (bound by FP64 instruction count), FP32 on the cell-parallel one.
-template <class T, int OPT = 0>
+// FLUX (FP64 without the signed-field or infinite-gauge options): also
+// store the donor fluxes of the pseudo-velocities in fx, fy, fz.
+template <class T, int OPT = 0, bool FLUX = false>
 void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W, const T* G,
-                   T* ut, T* vt, T* wt) {
+                   T* ut, T* vt, T* wt, T* fx = nullptr, T* fy = nullptr, T* fz = nullptr) {
   const Geo& g = c->g;
   if constexpr (std::is_same<T, double>::value) {
     // FP64: the k-marching kernel, with the options' terms (IGA: its own
     // face operation; ABS, DFL: flags of the common-denominator one)
     namespace M = mpd::march;
     constexpr bool kIGA = (OPT & mpd::kOptIGA) != 0, kDFL = (OPT & mpd::kOptDFL) != 0;
-    using Op = std::conditional_t<kIGA, M::PseudoIGA, M::PseudoMergedT<kDFL>>;
+    static_assert(!FLUX || (OPT & (mpd::kOptABS | mpd::kOptIGA)) == 0, "FLUX: signed psi only");
+    using Op = std::conditional_t<kIGA, M::PseudoIGA, M::PseudoMergedT<kDFL, FLUX>>;
+    Op op{ut, vt, wt};
+    if constexpr (FLUX) {
+      op.fx = fx;
+      op.fy = fy;
+      op.fz = fz;
+    }
     auto kern = M::march_kernel<double, Op, OPT>;
     if (!c->kc_fwd) c->kc_fwd = march_chunk(c, M::march_kernel<double, M::PseudoMerged>, true);
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                kern<<<M::march_grid(g, c->kc_fwd), dim3(M::TX, M::TY), 0, c->stream>>>(
-                   g, P, U, V, W, G, Op{ut, vt, wt}, c->kc_fwd));
+                   g, P, U, V, W, G, op, c->kc_fwd));
   } else if constexpr (OPT != 0) {  // FP32 staged with options: cell-parallel kernel
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
                mpd::staged::pseudo_kernel<T, OPT><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
@@ -172,6 +181,12 @@ template <class T, int OPT>
 int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, const T* V,
                     const T* W, const T* G) {
   constexpr bool kUnit = (OPT & mpd::kOptIGA) != 0;  // pseudo-fluxes are the fluxes
+  // FP64 without the signed-field or infinite-gauge options: the pseudo-
+  // velocity stage also stores the donor fluxes of the pseudo-velocities in
+  // fx, fy, fz (the donor pass's fluxes are dead by then); the beta stage
+  // reads them as its fluxes and the limiter scales them in place
+  constexpr bool kFin =
+      std::is_same<T, double>::value && (OPT & (mpd::kOptABS | mpd::kOptIGA)) == 0;
   using namespace mpd::staged;
   const Geo& g = c->g;
   const dim3 grid = cell_grid(g);
@@ -200,20 +215,22 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
     T** tset = (cu == setA[0]) ? setB : setA;  // unlimited pseudo-velocities
     T** lset = (tset == setA) ? setB : setA;   // limited ones (next pass's input)
     const bool more = m < c->iord;
-    pseudo_launch<T, OPT>(c, cur, cu, cv, cw, G, tset[0], tset[1], tset[2]);
+    pseudo_launch<T, OPT, kFin>(c, cur, cu, cv, cw, G, tset[0], tset[1], tset[2], fx, fy, fz);
     const T *ffx = fx, *ffy = fy, *ffz = fz;  // the pass's face fluxes
     if (c->nonosc) {
+      const T* bf[3] = {kFin ? fx : tset[0], kFin ? fy : tset[1], kFin ? fz : tset[2]};
       MPD_LAUNCH(c, MPDATA_STAGE_BETA,
-                 (beta_kernel<T, kUnit><<<grid, kCellBlock, 0, s>>>(
-                     g, psi, cur, tset[0], tset[1], tset[2], G, (T*)c->bu, (T*)c->bd, nullptr,
+                 (beta_kernel<T, kUnit || kFin><<<grid, kCellBlock, 0, s>>>(
+                     g, psi, cur, bf[0], bf[1], bf[2], G, (T*)c->bu, (T*)c->bd, nullptr,
                      nullptr)));
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                 (limflux_kernel<T, OPT><<<grid, kCellBlock, 0, s>>>(
+                 (limflux_kernel<T, OPT, kFin><<<grid, kCellBlock, 0, s>>>(
                      g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
                      more ? lset[0] : nullptr, more ? lset[1] : nullptr,
                      more ? lset[2] : nullptr)));
     } else if (kUnit) {  // the unlimited pseudo-fluxes themselves
       ffx = tset[0]; ffy = tset[1]; ffz = tset[2];
+    } else if (kFin) {  // fx, fy, fz hold the pass's fluxes already
     } else {
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
                  flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, tset[0], tset[1], tset[2],
@@ -514,23 +531,28 @@ int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const
                advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G,
                                                              tape_view<T>(c, base, 2).p1));
     const T *cu = U, *cv = V, *cw = W;  // the pass's input velocities
+    // FP64: the pseudo-velocity stage stores the donor fluxes too, as in
+    // the plain staged step (the same kernels, so the same bits)
+    constexpr bool kFin = std::is_same<T, double>::value;
     for (int m = 2; m <= c->iord; ++m) {
       const Tape<T> tp = tape_view<T>(c, base, m);
       T* dest = m == c->iord ? out : tape_view<T>(c, base, m + 1).p1;
-      pseudo_launch<T>(c, tp.p1, cu, cv, cw, G, tp.ut, tp.vt, tp.wt);
+      pseudo_launch<T, 0, kFin>(c, tp.p1, cu, cv, cw, G, tp.ut, tp.vt, tp.wt, fx, fy, fz);
       if (c->nonosc) {
+        const T* bf[3] = {kFin ? fx : tp.ut, kFin ? fy : tp.vt, kFin ? fz : tp.wt};
         MPD_LAUNCH(c, MPDATA_STAGE_BETA,
-                   beta_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G,
-                                                             tp.bu, tp.bd, tp.ri, tp.ro));
+                   (beta_kernel<T, kFin><<<grid, kCellBlock, 0, s>>>(
+                       g, psi, tp.p1, bf[0], bf[1], bf[2], G, tp.bu, tp.bd, tp.ri, tp.ro)));
         MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                   limflux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt,
-                                                                tp.bu, tp.bd, fx, fy, fz, tp.ul,
-                                                                tp.vl, tp.wl));
+                   (limflux_kernel<T, 0, kFin><<<grid, kCellBlock, 0, s>>>(
+                       g, tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, fx, fy, fz, tp.ul, tp.vl,
+                       tp.wl)));
         cu = tp.ul; cv = tp.vl; cw = tp.wl;
       } else {
-        MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                   flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt, fx,
-                                                             fy, fz));
+        if (!kFin)
+          MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
+                     flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt,
+                                                               fx, fy, fz));
         cu = tp.ut; cv = tp.vt; cw = tp.wt;
       }
       MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,

@@ -192,9 +192,13 @@ __device__ __forceinline__ double rcp(double b) {
 // the one product (selecting between two products costs the FP64 pipe a
 // second multiply).
 template <class T>
-__device__ __forceinline__ T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
+__device__ __forceinline__ T limit_factor(T Ut, T buL, T bdL, T buR, T bdR) {
   const bool up = nonneg(Ut);
-  return mul_rn(nmin(nmin(T(1), up ? bdL : buL), up ? buR : bdR), Ut);
+  return nmin(nmin(T(1), up ? bdL : buL), up ? buR : bdR);
+}
+template <class T>
+__device__ __forceinline__ T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
+  return mul_rn(limit_factor(Ut, buL, bdL, buR, bdR), Ut);
 }
 
 // Antidiffusive pseudo-velocity on one face from its ingredients:

@@ -90,13 +90,17 @@ struct NoAcc {};
 //        / (4 Gs D_A D_1 D_2).
 // DFL: with the divergent-flow term -(1/2) U dsum / Gs, which over the
 // common denominator adds -2 dsum D_A D_1 D_2 to the bracket.
-template <bool DFL = false>
+// FLUX: it also stores each face's donor flux of Ut, F(psi_L, psi_R, Ut)
+// (psi signed: not with the signed-field option), in fx, fy, fz: the flux
+// the limiter's in/out sums and limited fluxes are formed from.
+template <bool DFL = false, bool FLUX = false>
 struct PseudoMergedT {
   using Acc = NoAcc;
   struct Load {};
   static constexpr bool kAccum = false;
   __device__ __forceinline__ Load load(int64_t) const { return {}; }
   double *ut, *vt, *wt;
+  double *fx = nullptr, *fy = nullptr, *fz = nullptr;
   __device__ __forceinline__ void face(int fam, int64_t q, const FaceIn<double>& f) const {
     const double g4 = times4(f.gsum);
     const double NA = f.pr - f.pl;
@@ -106,15 +110,21 @@ struct PseudoMergedT {
     double num = fma(-f.DA, inner, D12 * (t1 * NA));
     const double dad = f.DA * D12;
     if constexpr (DFL) num = fma(-2.0 * f.dsum, dad, num);
-    (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = (f.U * num) * rcp(g4 * dad);
+    const double Ut = (f.U * num) * rcp(g4 * dad);
+    (fam == 0 ? ut : fam == 1 ? vt : wt)[q] = Ut;
+    if constexpr (FLUX) (fam == 0 ? fx : fam == 1 ? fy : fz)[q] = donor(f.pl, f.pr, Ut);
   }
-  __device__ __forceinline__ void cell(int64_t q, const FaceIn<double>& fx,
-                                      const FaceIn<double>& fy, const FaceIn<double>& fz,
+  __device__ __forceinline__ void cell(int64_t q, const FaceIn<double>& x,
+                                      const FaceIn<double>& y, const FaceIn<double>& z,
                                       bool top, CellAt, Load, Acc&) const {
-    face(0, q, fx);
-    face(1, q, fy);
-    if (top) wt[q] = 0.0;
-    else face(2, q, fz);
+    face(0, q, x);
+    face(1, q, y);
+    if (top) {
+      wt[q] = 0.0;
+      if constexpr (FLUX) fz[q] = 0.0;
+    } else {
+      face(2, q, z);
+    }
   }
 };
 using PseudoMerged = PseudoMergedT<false>;

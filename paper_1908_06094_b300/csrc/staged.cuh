@@ -195,7 +195,11 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
 // OPT: with ABS a face whose upwind value is negative carries its flux
 // against its velocity, so beta-up and beta-down trade places there; with
 // IGA the limited values are the fluxes.
-template <class T, int OPT = 0>
+// FIN: fx, fy, fz hold on entry the unlimited donor fluxes F(psi_L, psi_R,
+// Ut) (stored by the pseudo-velocity stage), and the limited flux is the
+// limiter's factor times that flux: one product a face, psi not read (not
+// with the signed-field or infinite-gauge options).
+template <class T, int OPT = 0, bool FIN = false>
 __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ ut,
                                const T* __restrict__ vt, const T* __restrict__ wt,
                                const T* __restrict__ bu, const T* __restrict__ bd,
@@ -206,6 +210,26 @@ __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restri
   const int64_t q = at(g, c.i, c.j, c.k);
   const int64_t qx = at(g, wrap_up(c.i, g.nx), c.j, c.k);
   const int64_t qy = at(g, c.i, wrap_up(c.j, g.ny), c.k);
+  if constexpr (FIN) {
+    static_assert((OPT & (kOptABS | kOptIGA)) == 0, "FIN: signed psi only");
+    const T buc = bu[q], bdc = bd[q], ux = ut[q], vy = vt[q];
+    const bool oz = zopen(g, c.k);
+    const int64_t qz = at(g, c.i, c.j, kadj(g, c.k + 1));
+    const T wz = oz ? wt[q] : T(0);
+    const T cx = limit_factor(ux, buc, bdc, bu[qx], bd[qx]);
+    const T cy = limit_factor(vy, buc, bdc, bu[qy], bd[qy]);
+    const T cz = oz ? limit_factor(wz, buc, bdc, bu[qz], bd[qz]) : T(0);
+    const T Fx = fx[q], Fy = fy[q], Fz = oz ? fz[q] : T(0);
+    fx[q] = mul_rn(cx, Fx);
+    fy[q] = mul_rn(cy, Fy);
+    fz[q] = oz ? mul_rn(cz, Fz) : T(0);
+    if (ul) {
+      ul[q] = mul_rn(cx, ux);
+      vl[q] = mul_rn(cy, vy);
+      wl[q] = oz ? mul_rn(cz, wz) : T(0);
+    }
+    return;
+  }
   T pc = P[q], buc = bu[q], bdc = bd[q];
   auto lim = [&](T Ut, int64_t qn) {
     T uL = buc, dL = bdc, uR = bu[qn], dR = bd[qn];
