@@ -77,6 +77,15 @@ STAGE_FLOPS = {
 }
 STEP_FLOPS = 212
 
+# The FP64 staged step assigns part of the limiter's work to another kernel:
+# its pseudo-velocity kernel also forms the donor fluxes of the pseudo-
+# velocities on the three "+" faces (9 flops, 3 words written), the beta
+# kernel reads those fluxes instead of forming the six of its faces (its
+# in/out sums and betas remain: 18 flops), and the limiter reads them with
+# Ut, Vt, Wt and the betas and scales them in place (11 words).
+STAGE_FLOPS_F64 = dict(STAGE_FLOPS, pseudo=126 + 9, beta=18)
+STAGE_WORDS_F64 = dict(STAGE_WORDS, pseudo=8 + 3, limit=11)
+
 # FP64 peak of the B300 from its unit count and clock: 2 FP64 FMA lanes per
 # SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
 # peak_sustained = 2) x 148 SMs x 2.032 GHz x 2 flops per FMA.
@@ -427,13 +436,13 @@ def run_ours(args, wl_name):
             if dt == torch.float64:
                 # FP64 on the B300 runs at 1/64 of FP32: these kernels are bound by
                 # the FP64 pipe, not by HBM
-                flops = STAGE_FLOPS[dom] * npts
+                flops = STAGE_FLOPS_F64[dom] * npts
                 achieved = flops / (per_launch_ms / 1e3) / 1e9
                 roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1),
                         "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s (FP64)",
                         "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
                         "algorithmic_flops": flops,
-                        "hbm_frac": round(STAGE_WORDS[dom] * esize * npts /
+                        "hbm_frac": round(STAGE_WORDS_F64[dom] * esize * npts /
                                           (per_launch_ms / 1e3) / 1e9 / hbm, 4),
                         "launch_ms": round(per_launch_ms, 5), "peak_source":
                         "unit count x max clock (measured FMA probe: 1086)",
