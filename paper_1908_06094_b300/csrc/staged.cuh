@@ -150,7 +150,9 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
 // the scale factors beta-up, beta-down (Smolarkiewicz & Grabowski 1990).
 // With rin != nullptr the reciprocals 1/(in+eps) and 1/(out+eps) are kept
 // too (the adjoint's tape).
-// UNIT (infinite gauge): the face values ut, vt, wt are the fluxes.
+// UNIT: the face values ut, vt, wt are the fluxes themselves -- in the
+// infinite gauge, and in the FP64 staged step, whose pseudo-velocity stage
+// passes the donor fluxes it formed.
 template <class T, bool UNIT = false>
 __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict__ P,
                             const T* __restrict__ ut, const T* __restrict__ vt,
