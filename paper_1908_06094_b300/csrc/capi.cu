@@ -217,12 +217,22 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
     const bool more = m < c->iord;
     pseudo_launch<T, OPT, kFin>(c, cur, cu, cv, cw, G, tset[0], tset[1], tset[2], fx, fy, fz);
     const T *ffx = fx, *ffy = fy, *ffz = fz;  // the pass's face fluxes
+    T* dest = !more ? psi_out : (cur == (T*)c->psi1 ? (T*)c->psi2 : (T*)c->psi1);
     if (c->nonosc) {
       const T* bf[3] = {kFin ? fx : tset[0], kFin ? fy : tset[1], kFin ? fz : tset[2]};
       MPD_LAUNCH(c, MPDATA_STAGE_BETA,
                  (beta_kernel<T, kUnit || kFin><<<grid, kCellBlock, 0, s>>>(
                      g, psi, cur, bf[0], bf[1], bf[2], G, (T*)c->bu, (T*)c->bd, nullptr,
                      nullptr)));
+      if (kFin && !more && rg) {  // the last pass: limited fluxes and advance in one
+        MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+                   limadvance_kernel<T><<<grid, kCellBlock, 0, s>>>(
+                       g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz, rg,
+                       dest));
+        MPD_CHECK_LAUNCH(c, "corrective pass");
+        cur = dest;
+        continue;  // the last pass: nothing carries over
+      }
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
                  (limflux_kernel<T, OPT, kFin><<<grid, kCellBlock, 0, s>>>(
                      g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
@@ -236,7 +246,6 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
                  flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, tset[0], tset[1], tset[2],
                                                              fx, fy, fz));
     }
-    T* dest = !more ? psi_out : (cur == (T*)c->psi1 ? (T*)c->psi2 : (T*)c->psi1);
     if (rg) {
       MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
                  (advance_kernel<T, 2><<<grid, kCellBlock, 0, s>>>(g, cur, ffx, ffy, ffz, G, dest,

@@ -72,6 +72,45 @@ __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
   out[q] = P[q] - ((fx[q] - fxm) + (fy[q] - fym) + (fz[q] - fzm)) * r;
 }
 
+// The last corrective pass's limited fluxes and its advance in one kernel
+// (the FP64 staged step, whose pseudo-velocity stage formed the donor
+// fluxes F of Ut): each cell scales the fluxes of its six faces by their
+// limiter factors -- its "-" faces are its neighbours' "+" faces, scaled
+// with the same inputs, so both cells see the same bits -- and advances
+// with the stored 1/G.  The same bits as limflux_kernel<FIN> followed by
+// advance_kernel<RG = 2>, without the limited fluxes' round trip through
+// memory (6 products a cell instead of 3: the kernel is bound by neither).
+// P and out are distinct.
+template <class T>
+__global__ void limadvance_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ ut,
+                                  const T* __restrict__ vt, const T* __restrict__ wt,
+                                  const T* __restrict__ bu, const T* __restrict__ bd,
+                                  const T* __restrict__ fx, const T* __restrict__ fy,
+                                  const T* __restrict__ fz, const T* __restrict__ rg,
+                                  T* __restrict__ out) {
+  Cell c = cell_of(g);
+  if (!c.ok) return;
+  const int64_t q = at(g, c.i, c.j, c.k);
+  const int64_t xp = at(g, wrap_up(c.i, g.nx), c.j, c.k), xm = at(g, wrap_dn(c.i, g.nx), c.j, c.k);
+  const int64_t yp = at(g, c.i, wrap_up(c.j, g.ny), c.k), ym = at(g, c.i, wrap_dn(c.j, g.ny), c.k);
+  const bool zt = zopen(g, c.k), zb = zopen(g, c.k - 1);
+  // a closed face takes q as an in-bounds stand-in (its flux is 0)
+  const int64_t zp = zt ? at(g, c.i, c.j, kadj(g, c.k + 1)) : q;
+  const int64_t zm = zb ? at(g, c.i, c.j, kadj(g, c.k - 1)) : q;
+  const T buq = bu[q], bdq = bd[q];
+  // the limited flux of the face from L to R
+  auto lf = [&](T U, T F, T buL, T bdL, T buR, T bdR) {
+    return mul_rn(limit_factor(U, buL, bdL, buR, bdR), F);
+  };
+  const T fxp = lf(ut[q], fx[q], buq, bdq, bu[xp], bd[xp]);
+  const T fxm = lf(ut[xm], fx[xm], bu[xm], bd[xm], buq, bdq);
+  const T fyp = lf(vt[q], fy[q], buq, bdq, bu[yp], bd[yp]);
+  const T fym = lf(vt[ym], fy[ym], bu[ym], bd[ym], buq, bdq);
+  const T fzp = zt ? lf(wt[q], fz[q], buq, bdq, bu[zp], bd[zp]) : T(0);
+  const T fzm = zb ? lf(wt[zm], fz[zm], bu[zm], bd[zm], buq, bdq) : T(0);
+  out[q] = P[q] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) * rg[q];
+}
+
 // Antidiffusive pseudo-velocities on the "+" faces of every cell
 // (Smolarkiewicz 1984; G-weighted form of Smolarkiewicz & Margolin 1998).
 // OPT (kOpt* bits): ABS forms A and B from |psi|; IGA gives the
