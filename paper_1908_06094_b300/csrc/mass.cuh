@@ -15,15 +15,24 @@ namespace mpd {
 constexpr int MASS_BLOCKS = 1184;  // 8 per SM on 148 SMs
 constexpr int MASS_THREADS = 256;
 
+// The block's sum in a fixed order, valid in thread 0: lane l of the first
+// warp adds the values of threads l, l + 32, l + 64, ... in turn, then the
+// 32 lane sums fold pairwise by shuffles.  Only the first warp adds: a tree
+// over shared memory had its per-level adds if-converted into every thread,
+// log2(n) FP64 adds a thread on the slow FP64 pipe.  blockDim.x is a
+// multiple of 32.
 __device__ __forceinline__ double block_fold(double v, double* sh) {
   const int t = threadIdx.x;
   sh[t] = v;
   __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (t < s) sh[t] = sh[t] + sh[t + s];
-    __syncthreads();
+  double s = 0.0;
+  if (t < 32) {
+    s = sh[t];
+    for (int q = t + 32; q < (int)blockDim.x; q += 32) s += sh[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   }
-  return sh[0];
+  return s;
 }
 
 // Per-thread accumulation of psi*G into an FP64 sum.  FP64: one fused
@@ -68,7 +77,7 @@ template <> struct MassAcc<float> { using type = MassAcc32; };
 // A block takes the interior rows r0 + q*gridDim.x (q < R) of each group in
 // turn; the row bases are computed once per group and all 2R loads of a
 // point column are issued before its (fixed-order) accumulation.  Rows past
-// the end read as zeros, which add exactly nothing.
+// the end are skipped (a block-uniform test).
 template <class T>
 __global__ void __launch_bounds__(MASS_THREADS)
 mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
@@ -95,7 +104,8 @@ mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
         b[q] = ok[q] ? G[base[q] + i] : T(0);
       }
 #pragma unroll
-      for (int q = 0; q < R; ++q) acc.add(a[q], b[q]);
+      for (int q = 0; q < R; ++q)
+        if (ok[q]) acc.add(a[q], b[q]);  // rows past the end add nothing
       acc.flush();
     }
   }
