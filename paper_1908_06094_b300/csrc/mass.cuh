@@ -86,15 +86,24 @@ mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
   using Acc = typename MassAcc<T>::type;
   constexpr int R = Acc::R;
   const int rows = g.ny * g.nz;
+  // row r is (j, k) = (r % ny, r / ny); a step of gridDim.x rows moves (j, k)
+  // by (dj, dk) with one carry, so only the first row takes a division
+  const int dj = (int)(gridDim.x % g.ny), dk = (int)(gridDim.x / g.ny);
+  int j = (int)(blockIdx.x % g.ny), k = (int)(blockIdx.x / g.ny);
   Acc acc;
   for (int r0 = blockIdx.x; r0 < rows; r0 += R * gridDim.x) {
     int64_t base[R];
     bool ok[R];
 #pragma unroll
     for (int q = 0; q < R; ++q) {
-      const int r = r0 + q * gridDim.x;
-      ok[q] = r < rows;
-      base[q] = ok[q] ? at(g, 0, r % g.ny, r / g.ny) : 0;
+      ok[q] = r0 + q * (int)gridDim.x < rows;
+      base[q] = ok[q] ? at(g, 0, j, k) : 0;
+      j += dj;
+      k += dk;
+      if (j >= g.ny) {
+        j -= g.ny;
+        ++k;
+      }
     }
     for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
       T a[R], b[R];
