@@ -126,6 +126,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   const int s2 = (y + 2) * EX + (x + 2);      // radius-2 slot
   const int s3 = (y + 3) * RX + (x + 3);      // radius-3 slot
   const bool inB = !kMap || tid < Map::NB, inC = !kMap || tid < Map::NC;
+  // stage B's faces: the x faces on the tile+1 and column x = -2, the y
+  // faces on the tile+1 and row y = -2, the z faces on the tile+1
+  const bool inBx = !kMap || tid < Map::NC + TY + 2;
+  const bool inBy = !kMap || tid < Map::NC || (tid >= Map::NC + TY + 2 && tid < Map::NB);
   const bool inD = !kMap || (inC && x < TX && y < TY);  // the faces stage E reads
   auto wrapi = [&](int i) { return ((i % g.nx) + g.nx) % g.nx; };
   auto wrapj = [&](int j) { return ((j % g.ny) + g.ny) % g.ny; };
@@ -309,7 +313,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       // DFL: the divergence of the Courant numbers of the cell at plane b,
       // own column (closed faces' W are 0 in the queue)
       const T dc = kDFL ? (u1 - ub[-1]) + (v1 - vb[-RX]) + (w1 - w0) : zero;
-      {  // x face (used on x in [-2, TX], y in [-1, TY]; computed everywhere)
+      if (inBx) {  // x face (used on x in [-2, TX], y in [-1, TY])
         const T s1p = ap(P1(b, EX + 1)) + ap(P1(b, EX)), s1m = ap(P1(b, -EX + 1)) + ap(P1(b, -EX));
         const T s2p = ap(P1(bp, 1)) + ap(qp), s2m = ap(P1(bm, 1)) + ap(qm);
         const T vsum = v1 + vb[1] + vb[-RX] + vb[-RX + 1];
@@ -322,7 +326,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         }
         uts[s2] = utB;
       }
-      {  // y face (used on x in [-1, TX], y in [-2, TY])
+      if (inBy) {  // y face (used on x in [-1, TX], y in [-2, TY])
         const T s1p = ap(P1(b, EX + 1)) + ap(P1(b, 1)), s1m = ap(P1(b, EX - 1)) + ap(P1(b, -1));
         const T s2p = ap(P1(bp, EX)) + ap(qp), s2m = ap(P1(bm, EX)) + ap(qm);
         const T usum = u1 + ub[RX] + ub[-1] + ub[RX - 1];
@@ -335,7 +339,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         }
         vts[s2] = vtB;
       }
-      {  // z face (used on x in [-1, TX], y in [-1, TY])
+      if (inC) {  // z face (used on x in [-1, TX], y in [-1, TY])
         T res = zero;
         if (zface(b)) {  // a zero-flux top face is closed
           const T* ub1 = us + ((b + 1) & 1) * L::RN + s3;
