@@ -193,16 +193,20 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
   cudaStream_t s = c->stream;
   const T* psi = psi_in;
   T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
-  // FP64: the donor advance keeps 1/G for the corrective advances
+  // FP64: the donor fluxes' kernel (bound by memory) stores 1/G for all the
+  // advances of the step (bound by the FP64 pipe)
   T* rg = (T*)c->rg;
   // pass 1: donor cell
   T* cur = c->iord == 1 ? psi_out : (T*)c->psi1;
-  MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
-             flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
   if (rg) {
+    MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
+               (flux_kernel<T, true><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz, G,
+                                                                rg)));
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-               (advance_kernel<T, 1><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur, rg)));
+               (advance_kernel<T, 2><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur, rg)));
   } else {
+    MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
+               flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
                advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur));
   }

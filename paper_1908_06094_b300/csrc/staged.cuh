@@ -32,14 +32,18 @@ __device__ __forceinline__ T wface(const T* w, const Geo& g, int i, int j, int k
   return zopen(g, k) ? w[at(g, i, j, kadj(g, k))] : T(0);
 }
 
-// Donor-cell fluxes through the three "+" faces of every cell.
-template <class T>
+// Donor-cell fluxes through the three "+" faces of every cell.  RG: also
+// store 1/G in rg (the FP64 staged step: this kernel is bound by memory with
+// FP64 issue to spare, the advances that read 1/G by the FP64 pipe).
+template <class T, bool RG = false>
 __global__ void flux_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
                             const T* __restrict__ cv, const T* __restrict__ cw,
-                            T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ fz) {
+                            T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ fz,
+                            const T* __restrict__ G = nullptr, T* __restrict__ rg = nullptr) {
   Cell c = cell_of(g);
   if (!c.ok) return;
   int64_t q = at(g, c.i, c.j, c.k);
+  if constexpr (RG) rg[q] = rcp(G[q]);
   T p = P[q];
   fx[q] = donor(p, P[at(g, wrap_up(c.i, g.nx), c.j, c.k)], cu[q]);
   fy[q] = donor(p, P[at(g, c.i, wrap_up(c.j, g.ny), c.k)], cv[q]);
@@ -50,8 +54,8 @@ __global__ void flux_kernel(Geo g, const T* __restrict__ P, const T* __restrict_
 // P and out may be the same buffer (each thread reads and writes only its
 // own point), so neither is declared __restrict__.
 // RG: 0 forms 1/G here; 1 forms it and also stores it to rg; 2 reads it from
-// rg (stored by an earlier advance of the same step with the same G: the
-// FP64 corrective passes skip the reciprocal's three FMAs for one load).
+// rg (stored earlier in the same step with the same G: the FP64 advances
+// skip the reciprocal's three FMAs for one load).
 template <class T, int RG = 0>
 __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
                                const T* __restrict__ fy, const T* __restrict__ fz,
