@@ -88,8 +88,50 @@ STAGE_WORDS_F64 = dict(STAGE_WORDS, pseudo=8 + 3, limit=11)
 
 # FP64 peak of the B300 from its unit count and clock: 2 FP64 FMA lanes per
 # SM per clock (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
-# peak_sustained = 2) x 148 SMs x 2.032 GHz x 2 flops per FMA.
+# peak_sustained = 2) x 148 SMs x 2.032 GHz x 2 flops per FMA.  Reported
+# beside the rate the FP64 FMA probe measures in the same run, which is the
+# roofline's denominator.
 FP64_PEAK_GFLOPS = 2 * 148 * 2.032 * 2
+
+
+def measure_fp64_peak(dev, blocks=148 * 16, iters=4096, reps=5):
+    """The device's FP64 FMA rate (GFLOP/s): the library's probe kernel
+    (8 independent FMA chains per thread, 2368 x 256 threads), timed with
+    CUDA events on the launching stream after 3 warm-up launches; best of
+    reps launches."""
+    import torch
+    from paper_1908_06094_b300 import _capi
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(3):
+        _capi.mpdata_probe_fp64_fma(out.data_ptr(), blocks, iters, stream.cuda_stream)
+    torch.cuda.synchronize(dev)
+    best = 0.0
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = _capi.mpdata_probe_fp64_fma(out.data_ptr(), blocks, iters, stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e9)
+    return best
+
+
+def _fp64_instructions(stage: str, workload: str):
+    """FP64 instructions per interior point of a stage (or of the whole step,
+    stage "step") from a committed ncu opcode count, only if it was taken on
+    the current kernel sources (same source hash as in dram_traffic.txt)."""
+    path = os.path.join(ROOT, "profiles", "fp64_instructions.txt")
+    try:
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            st, wl, h, n = line.split()[:4]
+            if st == stage and wl == workload and h == _source_hash(None if st == "step" else st):
+                return float(n)
+    except OSError:
+        pass
+    return None
 
 
 def table2_accesses(nodes: int, edges: int, fused: bool) -> int:
@@ -348,6 +390,22 @@ def _oracle_rate(wl, seconds: float, psi, fields, h):
     return steps * n / dt, steps
 
 
+def bench_config(wl_name: str, ws: int, variant=None) -> dict:
+    """The workload description both arms print (same keys, same values)."""
+    wl = WORKLOADS[wl_name]
+    esize = 8 if wl["dtype"] == "f64" else 4
+    h = wl["halo"]
+    field_mb = esize * (wl["nx"] + 2 * h) * (wl["ny"] + 2 * h) * (wl["nz"] + 2 * h) / 1e6
+    return {"workload": f"latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']} halo {h} "
+                        f"{wl['dtype']} iord={wl['iord']} nonoscillatory",
+            "nx": wl["nx"], "ny": wl["ny"], "nz": wl["nz"], "halo": h,
+            "iord": wl["iord"], "nonoscillatory": wl["nonosc"],
+            "step": "one MPDATA step + FP64 mass reduction",
+            "l2": "no flush: the 5 input fields (%.0f MB) exceed the 126 MB L2" % (5 * field_mb),
+            "variant": {0: "fused", 1: "staged", 2: "auto"}.get(variant, "auto"),
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_ours(args, wl_name):
     import numpy as np
     import torch
@@ -394,7 +452,6 @@ def run_ours(args, wl_name):
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
     launches0 = _capi.mpdata_launch_count(m._ctx)
-    _capi.mpdata_profile(m._ctx, True)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     wall0 = time.time()
     ev0.record(stream)
@@ -407,18 +464,40 @@ def run_ours(args, wl_name):
         torch.distributed.barrier()
     ms = ev0.elapsed_time(ev1)
     launches = _capi.mpdata_launch_count(m._ctx) - launches0
-    stage_ms = {}
-    for name, sid in _capi.STAGES.items():
-        t, k = _capi.mpdata_profile_read(m._ctx, sid)
-        if k:
-            stage_ms[name] = (t, k)
-    _capi.mpdata_profile(m._ctx, False)
     m1 = mass_out.item()
     value, ms = job_throughput(ms, npts * args.steps, ws, dev)
     clocks = None
     if sampler:
         sampler.stop()
         clocks = sampler.summary(wall0, wall1)
+    # the same K steps timed 4 more times (median of 5 beside the headline),
+    # then once more with CUDA events around every launch for the per-kernel
+    # durations of the roofline; neither pass is part of the headline
+    repeat_ms = [ms]
+    for _ in range(4 if rank == 0 else 0):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        repeat_ms.append(e0.elapsed_time(e1))
+    stage_ms = {}
+    prof_ms = None
+    if rank == 0:
+        _capi.mpdata_profile(m._ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        prof_ms = e0.elapsed_time(e1)
+        for name, sid in _capi.STAGES.items():
+            t, k = _capi.mpdata_profile_read(m._ctx, sid)
+            if k:
+                stage_ms[name] = (t, k)
+        _capi.mpdata_profile(m._ctx, False)
 
     out = None
     if rank == 0:
@@ -435,18 +514,32 @@ def run_ours(args, wl_name):
                      for s_, v in stage_ms.items()}
             if dt == torch.float64:
                 # FP64 on the B300 runs at 1/64 of FP32: these kernels are bound by
-                # the FP64 pipe, not by HBM
+                # the FP64 pipe, not by HBM.  The denominator is the FP64 FMA rate
+                # the probe kernel measures on this device in this run.
+                fp64_peak = measure_fp64_peak(dev)
                 flops = STAGE_FLOPS_F64[dom] * npts
                 achieved = flops / (per_launch_ms / 1e3) / 1e9
                 roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 1),
-                        "peak": round(FP64_PEAK_GFLOPS, 1), "unit": "GFLOP/s (FP64)",
-                        "frac": round(achieved / FP64_PEAK_GFLOPS, 4), "traffic": traffic,
+                        "peak": round(fp64_peak, 1), "unit": "GFLOP/s (FP64)",
+                        "frac": round(achieved / fp64_peak, 4), "traffic": traffic,
                         "algorithmic_flops": flops,
                         "hbm_frac": round(STAGE_WORDS_F64[dom] * esize * npts /
                                           (per_launch_ms / 1e3) / 1e9 / hbm, 4),
-                        "launch_ms": round(per_launch_ms, 5), "peak_source":
-                        "unit count x max clock (measured FMA probe: 1086)",
+                        "launch_ms": round(per_launch_ms, 5),
+                        "peak_source": "measured in this run: FP64 FMA probe kernel "
+                                       "(mpdata_probe_fp64_fma), best of 5",
+                        "peak_derived": round(FP64_PEAK_GFLOPS, 1),
+                        "frac_of_derived": round(achieved / FP64_PEAK_GFLOPS, 4),
                         "stage_share": share}
+                # the whole step's floor on the FP64 pipe: its FP64 instructions per
+                # point (ncu opcode counts on the current sources) at the probe's
+                # instruction rate (one FMA = one instruction = 2 flops)
+                ninst = _fp64_instructions("step", wl_name)
+                if ninst:
+                    floor_ms = ninst * npts / (fp64_peak / 2 * 1e9) * 1e3
+                    roof["fp64_pipe_floor"] = {
+                        "instructions_per_point": ninst, "ms_per_step": round(floor_ms, 4),
+                        "step_over_floor": round((ms / args.steps) / floor_ms, 3)}
             else:
                 bytes_launch = STAGE_WORDS[dom] * esize * npts
                 achieved = bytes_launch / (per_launch_ms / 1e3) / 1e9
@@ -462,18 +555,17 @@ def run_ours(args, wl_name):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"],
             "data": "synthetic (seeded lat-lon deformational flow, Gaussian + step tracer)",
-            "config": {"workload": f"latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']} halo {h} "
-                                   f"{wl['dtype']} iord={wl['iord']} nonoscillatory",
-                       "nx": wl["nx"], "ny": wl["ny"], "nz": wl["nz"], "halo": h,
-                       "iord": wl["iord"], "nonoscillatory": wl["nonosc"],
-                       "step": "one MPDATA step + FP64 mass reduction",
-                       "l2": "no flush: the 5 input fields (%.0f MB) exceed the 126 MB L2"
-                             % (5 * esize * padded[0].size / 1e6),
-                       "variant": {0: "fused", 1: "staged", 2: "auto"}.get(args.variant, "auto"),
-                       "parallelism": f"replicas x{ws}"},
+            "config": bench_config(wl_name, ws, args.variant),
             "hbm_roofline_frac_step": round(value / ws * step_bytes / npts / 1e9 / hbm, 4),
-            "fp64_alu_frac_step": (round(value / ws * STEP_FLOPS / 1e9 / FP64_PEAK_GFLOPS, 4)
-                                   if dt == torch.float64 else None),
+            "fp64_alu_frac_step": (round(value / ws * STEP_FLOPS / 1e9 / roof["peak"], 4)
+                                   if dt == torch.float64 and roof else None),
+            "repeats": {"runs": len(repeat_ms), "ms_per_step_median":
+                        round(statistics.median(repeat_ms) / args.steps, 5),
+                        "ms_per_step_all": [round(x / args.steps, 5) for x in repeat_ms]},
+            "profiled_pass": {"ms_per_step": round(prof_ms / args.steps, 5) if prof_ms else None,
+                              "what": "the same K steps with CUDA events around every "
+                                      "launch (per-kernel durations); outside the timed "
+                                      "region"},
             "roofline": roof,
             "gpu_launches": launches,
             "mass_drift_rel": abs(m1 - m0) / abs(m0) if m0 else None,
@@ -501,6 +593,7 @@ def run_ours(args, wl_name):
                           "f32": measure_adjoint(dev, torch.float32)}
         out["batched"] = measure_batched(dev)
         out["fp32"] = measure_config(dev, "latlon512_f32")
+        out["rotation_2d"] = measure_rotation_2d(dev)
         out["options"] = measure_options(dev)
         out["octahedral_edge"] = measure_edge(dev)
         out["table1_cells"] = measure_cells(dev)
@@ -516,8 +609,10 @@ def run_ours(args, wl_name):
 
 def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
     """Another configuration measured the same way as the headline (device
-    resident inputs, CUDA events, per-stage event timing): value and the
-    roofline of its dominant kernel."""
+    resident inputs, CUDA events on the launching stream): value, then a
+    separate pass with per-launch events for the roofline of its dominant
+    kernel.  For FP32, the error of the configuration's full step count
+    (100) against the FP64 step from the same FP32-rounded inputs."""
     import numpy as np
     import torch
     import synth
@@ -538,36 +633,51 @@ def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
         m.step(*d, nsteps=1)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
-    _capi.mpdata_profile(m._ctx, True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(steps):
-        m.step(*d, nsteps=1)
-        m.mass(d[0], d[4], out=out_mass)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms = e0.elapsed_time(e1)
+
+    def timed(profile):
+        if profile:
+            _capi.mpdata_profile(m._ctx, True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            m.step(*d, nsteps=1)
+            m.mass(d[0], d[4], out=out_mass)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+    ms = timed(False)
+    ms_prof = timed(True)
     st = {n: _capi.mpdata_profile_read(m._ctx, sid) for n, sid in _capi.STAGES.items()}
     st = {n: v for n, v in st.items() if v[1]}
+    _capi.mpdata_profile(m._ctx, False)
     m1 = out_mass.item()
     m.close()
     err = None
     if dt == torch.float32:
-        # error norms of 10 FP32 steps against the FP64 step (parity-tested
-        # against the oracle to 1e-12 per step) from the same FP32-rounded
-        # inputs, relative to max |psi|
+        # error norms of the configuration's 100 FP32 steps against 100 FP64
+        # steps (the FP64 step is parity-tested against the oracle to 1e-12
+        # per step) from the same FP32-rounded inputs, relative to max |psi|;
+        # mass drift of each run over the 100 steps
+        nsteps = wl["config_steps"]
         d64 = [x.double() for x in d]
         d32 = [x.clone() for x in d]
         m64 = MPDATA(wl["nx"], wl["ny"], wl["nz"], halo=h, dtype=torch.float64, device=dev)
         m32 = MPDATA(wl["nx"], wl["ny"], wl["nz"], halo=h, dtype=torch.float32, device=dev)
         d64[0] = torch.from_numpy(padded[0]).to(dev, torch.float32).double()
         d32[0] = d64[0].float()
-        m64.step(*d64, nsteps=10)
-        m32.step(*d32, nsteps=10)
+        mass64_0 = m64.mass(d64[0], d64[4]).item()
+        mass32_0 = m32.mass(d32[0], d32[4]).item()
+        m64.step(*d64, nsteps=nsteps)
+        m32.step(*d32, nsteps=nsteps)
+        mass64 = m64.mass(d64[0], d64[4]).item()
+        mass32 = m32.mass(d32[0], d32[4]).item()
         diff = (d32[0].double() - d64[0])[h:-h, h:-h, h:-h]
         scale = float(d64[0][h:-h, h:-h, h:-h].abs().max())
-        err = {"steps": 10, "max_abs_rel": float(diff.abs().max()) / scale,
+        err = {"steps": nsteps, "max_abs_rel": float(diff.abs().max()) / scale,
                "l2_rel": float(diff.pow(2).mean().sqrt()) / scale,
+               "mass_drift_rel_f32": abs(mass32 - mass32_0) / abs(mass32_0),
+               "mass_drift_rel_f64": abs(mass64 - mass64_0) / abs(mass64_0),
+               "mass_f32_vs_f64_rel": abs(mass32 - mass64) / abs(mass64),
                "reference": "the FP64 step on the same FP32-rounded inputs"}
         m64.close()
         m32.close()
@@ -578,13 +688,89 @@ def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
     gbs = STAGE_WORDS[dom] * esize * npts / (per / 1e3) / 1e9
     value = npts * steps / (ms / 1e3)
     return {"workload": f"latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']} {wl['dtype']}",
-            "value": value, "unit": UNIT, "ms_per_step": ms / steps, "dtype": wl["dtype"],
+            "value": value, "unit": UNIT, "ms_per_step": ms / steps,
+            "profiled_ms_per_step": ms_prof / steps, "dtype": wl["dtype"],
             "hbm_roofline_frac_step": round(value * STEP_WORDS * esize / 1e9 / hbm, 4),
             "mass_drift_rel_after_steps": abs(m1 - m0) / abs(m0),
             "error_vs_f64": err,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(gbs / hbm, 4),
                          "launch_ms": round(per, 5)}}
+
+
+def measure_rotation_2d(dev, nsteps=100, reps=5):
+    """The 2D configuration: 64x64 periodic, one level, FP64, iord 2 with the
+    limiter, G = 1, solid-body rotation of a cone (max Courant 0.5), 100
+    steps.  Latency-bound (4096 points), so the unit is microseconds per step:
+    the 100 steps issued as plain calls, and replayed from one captured CUDA
+    graph; median of reps runs each.  The oracle runs the same 100 steps on
+    the host cores."""
+    import torch
+    import synth
+    import oracle
+    from paper_1908_06094_b300 import MPDATA
+    c = synth.rotation_2d(64, seed=1234)
+    h = 2
+    P = [synth.pad(x, h) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    d = [torch.from_numpy(x).to(dev).contiguous() for x in P]
+    m = MPDATA(c.nx, c.ny, c.nz, halo=h, iord=2, nonoscillatory=True, dtype=torch.float64,
+               device=dev)
+    stream = torch.cuda.current_stream(dev)
+    psi = d[0].clone()
+    m.step(psi, *d[1:], nsteps=3)
+    torch.cuda.synchronize(dev)
+
+    def run_plain():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nsteps):
+            m.step(psi, *d[1:], nsteps=1)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+    plain = sorted(run_plain() for _ in range(reps))[reps // 2]
+    # one graph of the 100 steps
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream(dev)
+    s.wait_stream(stream)
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            for _ in range(nsteps):
+                m.step(psi, *d[1:], nsteps=1)
+    stream.wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize(dev)
+
+    def run_graph():
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.replay()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1)
+    graph = sorted(run_graph() for _ in range(reps))[reps // 2]
+    # parity of the 100 graph-replayed steps from the initial field
+    psi.copy_(d[0])
+    g.replay()
+    torch.cuda.synchronize(dev)
+    ref = oracle.run(*P, h=h, iord=2, nonosc=1, nsteps=nsteps)
+    got = psi.cpu().numpy()
+    err = float(abs(got - ref)[h:-h, h:-h, h:-h].max() / abs(ref[h:-h, h:-h, h:-h]).max())
+    m.close()
+    t0 = time.perf_counter()
+    oracle.run(*P, h=h, iord=2, nonosc=1, nsteps=nsteps)
+    cpu_s = time.perf_counter() - t0
+    npts = c.nx * c.ny * c.nz
+    return {"workload": "rotation_2d 64x64x1 f64 iord=2 nonoscillatory, 100 steps",
+            "unit": "us/step", "higher_is_better": False,
+            "us_per_step_plain": round(plain / nsteps * 1e3, 2),
+            "us_per_step_graph": round(graph / nsteps * 1e3, 2),
+            "value": round(graph / nsteps * 1e3, 2),
+            "updates_per_s_graph": npts * nsteps / (graph / 1e3),
+            "max_rel_err_vs_oracle_after_100_steps": err,
+            "cpu_baseline": {"value": round(cpu_s / nsteps * 1e6, 2), "unit": "us/step",
+                             "cores": os.cpu_count() or 1, "kind": "oracle",
+                             "sample": "the same 100 steps"}}
 
 
 def measure_options(dev, steps=20, warmup=3):
@@ -791,9 +977,7 @@ def run_reference(args, wl_name):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded)",
-            "config": {"workload": f"latlon_3d {wl['nx']}x{wl['ny']}x{wl['nz']} halo {h} "
-                                   f"{wl['dtype']} iord={wl['iord']} nonoscillatory",
-                       "nx": wl["nx"], "ny": wl["ny"], "nz": wl["nz"]},
+            "config": bench_config(wl_name, ws, args.variant),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": ncores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
@@ -970,97 +1154,18 @@ def measure_cells(dev, reps=15):
     return res
 
 
-def cells_probe(dtype_name: str, numbering: str):
-    """Three launches of the cell-neighbour sum on the 512 x 512 x 80 patch
-    (direct access for SN, the table for UN and HN; a profiler's capture)."""
-    import torch
-    from paper_1908_06094_b300 import CellsReduction
-    from synth import cells
-    dt = torch.float64 if dtype_name == "f64" else torch.float32
-    nr, nc, nz = 512, 512, 80
-    if numbering == "SN":
-        red = CellsReduction(nz, dtype=dt, nr=nr, nc=nc)
-    else:
-        red = CellsReduction(nz, dtype=dt, table=cells.c2c(nr, nc, numbering))
-    A = torch.from_numpy(cells.field(nr, nc, nz, seed=1, numbering=numbering)).to(
-        "cuda", dt).contiguous()
-    B = torch.empty_like(A)
-    for _ in range(3):
-        red.sum(A, B, 1.0)
-    torch.cuda.synchronize()
-    red.close()
-    print("cells probe ok", flush=True)
-
-
-def edge_probe(dtype_name: str, variant: int):
-    """Five launches of the edge stages on the 71424 x 80 patch (a
-    profiler's capture)."""
-    import torch
-    from paper_1908_06094_b300 import EdgeMPDATA
-    dt = torch.float64 if dtype_name == "f64" else torch.float32
-    c = _edge_case()
-    nr, nc, nz = EDGE_SHAPE
-    f = {k: torch.from_numpy(getattr(c, k)).to("cuda", dt).contiguous()
-         for k in ("pD", "vn", "wn", "rho", "vol")}
-    outb = torch.empty_like(f["pD"])
-    e = EdgeMPDATA(nr, nc, nz, dtype=dt, pivbz=1.0, variant=variant)
-    for _ in range(5):
-        e.step(f["pD"], outb, f["vn"], f["wn"], f["rho"], f["vol"])
-    torch.cuda.synchronize()
-    e.close()
-    print("edge probe ok", flush=True)
-
-
-def adjoint_probe(dtype_name: str):
-    """The adjoint configuration's grid (256x256x64 lat-lon flow) through the
-    public autograd path, twice: 4 steps with checkpoints every 2, then
-    backward of sum(out^2).  Sized for a profiler's launch list."""
-    import torch
-    import synth
-    from paper_1908_06094_b300 import MPDATA, mpdata_run
-    dt = torch.float64 if dtype_name == "f64" else torch.float32
-    c = synth.latlon_3d(256, 256, 64, seed=1234)
-    h = 2
-    d = [torch.from_numpy(synth.pad(x, h)).to("cuda", dt).contiguous()
-         for x in (c.psi, c.u, c.v, c.w, c.g)]
-    m = MPDATA(c.nx, c.ny, c.nz, halo=h, dtype=dt)
-    for _ in range(2):
-        x = [t.clone().requires_grad_(True) for t in d[:4]]
-        out = mpdata_run(m, *x, d[4], 4, 2)
-        torch.sum(out * out).backward()
-    torch.cuda.synchronize()
-    m.close()
-    print("adjoint probe ok", flush=True)
-
-
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="latlon256_f64", choices=sorted(WORKLOADS))
     ap.add_argument("--variant", type=int, default=None, help="0 fused, 1 staged, 2 auto (default)")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e and CPU-baseline legs")
-    ap.add_argument("--adjoint-probe", choices=["f64", "f32"], default=None,
-                    help="run a short adjoint workload for a profiler's launch list and exit")
-    ap.add_argument("--edge-probe", choices=["f64", "f32"], default=None,
-                    help="run five edge-stage launches (--variant 0 fused, 1 staged) and exit")
-    ap.add_argument("--cells-probe", default=None,
-                    help="f32:SN|UN|HN or f64:...: three cell-sum launches and exit")
     args = ap.parse_args()
-    if args.cells_probe:
-        dtn, num = args.cells_probe.split(":")
-        cells_probe(dtn, num)
-        return
-    if args.adjoint_probe:
-        adjoint_probe(args.adjoint_probe)
-        return
-    if args.edge_probe:
-        edge_probe(args.edge_probe, 0 if args.variant is None else args.variant)
-        return
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
     out = run_reference(args, args.workload) if args.impl == "reference" else \

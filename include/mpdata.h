@@ -283,7 +283,8 @@ enum mpdata_stage {
   MPDATA_STAGE_MASS = 6,     /* mass reduction (a7)                          */
   MPDATA_STAGE_FUSED = 7,    /* fused corrective pass (a3-a6)                */
   MPDATA_STAGE_FUSED_DONOR = 8, /* fused donor pass (a2)                     */
-  MPDATA_NSTAGES = 9
+  MPDATA_STAGE_EXCHANGE = 9, /* halo strip pack/unpack of a slab            */
+  MPDATA_NSTAGES = 10
 };
 
 /* Number of kernels this context has launched since it was created. */
@@ -301,10 +302,10 @@ MPDATA_API int mpdata_profile_read(mpdata_ctx *c, int stage, double *ms, int *la
 
 /* Mass without a context and without allocating: the same deterministic
  * sum over the interior of psi*G as mpdata_mass, for callers that cannot call
- * cudaMalloc -- code running inside a global-mode stream capture (where
- * allocation is an error), applications whose device memory is all handed
- * out by their own pool or arena, and hosts that forbid allocation after
- * start-up.  (mpdata_init allocates, so those callers cannot get a context.)
+ * cudaMalloc -- applications whose device memory is all handed out by their
+ * own pool or arena, and hosts that forbid allocation after start-up (real-
+ * time or certified codes).  (mpdata_init allocates, so those callers cannot
+ * get a context.)
  * The paper has no counterpart: this is a library-interface addition.
  *   psi, g   padded DEVICE fields [nz+2h][ny+2h][nx+2h] of dtype, 16-byte
  *            aligned, read at interior points only;
@@ -316,14 +317,63 @@ MPDATA_API int mpdata_profile_read(mpdata_ctx *c, int stage, double *ms, int *la
  * (for example on two streams) race on it, so the caller must order them.
  * Each call overwrites every partial before reading it, so nothing carries
  * over from the previous call.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.
- * Limits: ny*nz <= MPDATA_MASS_NOALLOC_MAX_ROWS and (nx+2h)(ny+2h) < 2^31,
- * else MPDATA_ERANGE.  Errors: EINVAL, EALIGN, ERANGE, EDEVICE, ECUDA. */
+ * array's device address (cudaGetSymbolAddress) with that device current
+ * and keeps it for the life of the process; make that first call before any
+ * stream capture.  A cudaDeviceReset of that device makes the kept address
+ * stale: do not call this entry point on a device after resetting it.
+ * Limits: ny*nz <= MPDATA_MASS_MAX_ROWS and (nx+2h)(ny+2h) < 2^31, else
+ * MPDATA_ERANGE, checked before anything is launched.
+ * Errors: EINVAL, EALIGN, ERANGE, EDEVICE, ECUDA. */
 #define MPDATA_MASS_NOALLOC_PARTIALS 1184
-#define MPDATA_MASS_NOALLOC_MAX_ROWS 2147483647LL
+/* The mass reduction walks the ny*nz interior rows with a 32-bit counter that
+ * runs up to 16 x 1184 rows past the last one, so the row count stays below
+ * 2^31 by that margin (mpdata_init enforces the same bound). */
+#define MPDATA_MASS_MAX_ROWS (2147483647LL - 16LL * 1184LL)
+#define MPDATA_MASS_NOALLOC_MAX_ROWS MPDATA_MASS_MAX_ROWS
 MPDATA_API int mpdata_mass_noalloc(const void *psi, const void *g, int nx, int ny, int nz,
                                    int halo, int dtype, double *out_dev, void *cuda_stream);
+
+/* ------------------------------------------------------------------------
+ * Slabs of an i-j decomposed domain (Sec. 3.1.1, item 2: halo exchange and
+ * boundary conditions as a library component; Fig. 8: the grid split into
+ * partitions).  A domain of NX x NY x nz is cut into px x py slabs, one
+ * context each (sizes nx_r x ny_r x nz, halo h >= 3).  A slab's i-j halo
+ * belongs to its neighbours: its step reads the halo instead of wrapping,
+ * so one exchange of psi's halo before each step (depth 3, corners
+ * included) makes the step of every slab equal, point for point, to the
+ * step of the undivided domain under the same kernel.  U, V, W, G are
+ * exchanged once, before the first step.
+ * ------------------------------------------------------------------------ */
+enum mpdata_ij_boundary {
+  MPDATA_IJ_PERIODIC = 0, /* the context is the whole domain (default)       */
+  MPDATA_IJ_HALO = 1      /* the context is one slab: i-j halo from neighbours */
+};
+
+/* Make a context a slab (MPDATA_IJ_HALO) or the whole periodic domain
+ * again.  A slab runs the one-kernel step of iord 2 in both dtypes,
+ * whatever the variant; its output's i-j halo is left to the exchange (the
+ * k halo is still filled).  Requires iord == 2, halo >= 3, no options,
+ * nx, ny >= halo.  The adjoint calls, mpdata_fill_halo and
+ * mpdata_set_options(nonzero) return EINVAL on a slab.
+ * Errors: EINVAL, ECUDA (the kernel cannot run on this device). */
+MPDATA_API int mpdata_set_ij_boundary(mpdata_ctx *c, int mode);
+
+/* Halo strips.  Face f: 0 = -x, 1 = +x, 2 = -y, 3 = +y.
+ * mpdata_halo_pack copies the h-deep interior strip of field next to face f
+ * into buf; the neighbour across face f passes that buffer to
+ * mpdata_halo_unpack with face f ^ 1, which writes it into the halo strip
+ * beyond that face.  x faces carry the interior rows (j in [0, ny)); y
+ * faces carry whole padded rows (i in [-h, nx+h)), so exchanging x first
+ * and y second fills the halo's corners.  Levels k in [0, nz).
+ * buf: DEVICE, 16-byte aligned, mpdata_halo_strip_elems(face) elements of
+ * the context's dtype, laid out [nz][rows][cols] with (rows, cols) =
+ * (ny, h) for x faces and (h, nx + 2h) for y faces.  Both calls run one
+ * kernel on the context's stream and work in either boundary mode.
+ * Errors: EINVAL (null context, face out of range, buf == field), EALIGN,
+ * ECUDA. */
+MPDATA_API int mpdata_halo_strip_elems(mpdata_ctx *c, int face, long long *n);
+MPDATA_API int mpdata_halo_pack(mpdata_ctx *c, const void *field, int face, void *buf);
+MPDATA_API int mpdata_halo_unpack(mpdata_ctx *c, const void *buf, int face, void *field);
 
 /* Destroy a context and free its scratch (NULL is ignored). */
 MPDATA_API void mpdata_destroy(mpdata_ctx *c);
@@ -336,6 +386,17 @@ MPDATA_API const char *mpdata_last_error_string(mpdata_ctx *c);
 
 /* Library version (major*10000 + minor*100 + patch). */
 MPDATA_API int mpdata_version(void);
+
+/* Measurement helper, not part of the method: the device's FP64 FMA rate,
+ * which bounds every FP64 kernel of the step on the B300.  Launches one
+ * kernel of `blocks` CTAs x 256 threads on cuda_stream; each thread runs 8
+ * independent chains of `iters` fused multiply-adds.  *flops (HOST) receives
+ * the launch's flop count (2 per FMA); the caller times the launch (CUDA
+ * events on the same stream) and divides.  out_dev is a DEVICE double that
+ * is never written in practice (it keeps the work from being optimised
+ * away).  Errors: EINVAL (null pointer, blocks or iters < 1), ECUDA. */
+MPDATA_API int mpdata_probe_fp64_fma(double *out_dev, int blocks, int iters, void *cuda_stream,
+                                     double *flops);
 
 /* ------------------------------------------------------------------------
  * Edge-based flux stages on a structured triangular patch.

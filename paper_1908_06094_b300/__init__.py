@@ -8,7 +8,9 @@ thin Python binding over it.
 * ``EdgeMPDATA`` -- the edge-based flux stages on a triangular patch;
 * ``CellsReduction`` -- the cell-neighbour reduction of Table 1;
 * ``MPDATAFunction`` / ``mpdata_run`` -- autograd over the forward and
-  adjoint steps with checkpoint-and-recompute.
+  adjoint steps with checkpoint-and-recompute;
+* ``SlabDecomposition`` / ``SlabRank`` -- an i-j decomposed domain with the
+  halo exchange (all slabs on one device, or one slab per process).
 
 The library is loaded on first use of either; a missing or unloadable
 library raises ImportError (there is no fallback path).
@@ -16,7 +18,7 @@ library raises ImportError (there is no fallback path).
 import importlib
 
 __all__ = ["_capi", "MPDATA", "padded_shape", "MPDATAFunction", "mpdata_run", "MPDATABatch",
-           "EdgeMPDATA", "CellsReduction"]
+           "EdgeMPDATA", "CellsReduction", "SlabDecomposition", "SlabRank"]
 
 
 def __getattr__(name):
@@ -31,6 +33,8 @@ def __getattr__(name):
         return importlib.import_module(".edge", __name__).EdgeMPDATA
     if name == "MPDATABatch":
         return importlib.import_module(".batch", __name__).MPDATABatch
+    if name in ("SlabDecomposition", "SlabRank"):
+        return getattr(importlib.import_module(".slabs", __name__), name)
     if name in ("MPDATAFunction", "mpdata_run"):
         mod = importlib.import_module(".autograd", __name__)
         return getattr(mod, name)

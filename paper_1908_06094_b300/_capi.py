@@ -101,13 +101,20 @@ SIGNATURES = {
     "mpdata_batch_last_error_string": (ctypes.c_char_p, [_c]),
     "mpdata_batch_destroy": (None, [_c]),
     "mpdata_mass_noalloc": (_i, [_c, _c, _i, _i, _i, _i, _i, _c, _c]),
+    "mpdata_probe_fp64_fma": (_i, [_c, _i, _i, _c, ctypes.POINTER(ctypes.c_double)]),
+    "mpdata_set_ij_boundary": (_i, [_c, _i]),
+    "mpdata_halo_strip_elems": (_i, [_c, _i, ctypes.POINTER(ctypes.c_longlong)]),
+    "mpdata_halo_pack": (_i, [_c, _c, _i, _c]),
+    "mpdata_halo_unpack": (_i, [_c, _c, _i, _c]),
     "mpdata_profile": (_i, [_c, _i]),
     "mpdata_profile_read": (_i, [_c, _i, ctypes.POINTER(ctypes.c_double),
                                  ctypes.POINTER(ctypes.c_int)]),
 }
 
 STAGES = {"halo": 0, "donor": 1, "advance": 2, "pseudo": 3, "beta": 4, "limit": 5, "mass": 6,
-          "fused": 7, "fused_donor": 8}
+          "fused": 7, "fused_donor": 8, "exchange": 9}
+MPDATA_IJ_PERIODIC = 0
+MPDATA_IJ_HALO = 1
 
 for _name, (_res, _args) in SIGNATURES.items():
     _f = getattr(lib, _name)
@@ -284,3 +291,30 @@ def mpdata_step_tape(ctx, psi_in, psi_out, u, v, w, g, tape):
 def mpdata_adjoint_step_tape(ctx, tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar):
     _check(lib.mpdata_adjoint_step_tape(ctx, tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar,
                                         w_bar), "mpdata_adjoint_step_tape", ctx)
+
+
+def mpdata_probe_fp64_fma(out_dev, blocks, iters, cuda_stream=0) -> float:
+    """Launch the FP64 FMA-rate probe; returns the launch's flop count."""
+    flops = ctypes.c_double()
+    _check(lib.mpdata_probe_fp64_fma(out_dev, blocks, iters, cuda_stream, ctypes.byref(flops)),
+           "mpdata_probe_fp64_fma")
+    return flops.value
+
+
+def mpdata_set_ij_boundary(ctx, mode):
+    _check(lib.mpdata_set_ij_boundary(ctx, mode), "mpdata_set_ij_boundary", ctx)
+
+
+def mpdata_halo_strip_elems(ctx, face) -> int:
+    n = ctypes.c_longlong()
+    _check(lib.mpdata_halo_strip_elems(ctx, face, ctypes.byref(n)), "mpdata_halo_strip_elems",
+           ctx)
+    return n.value
+
+
+def mpdata_halo_pack(ctx, field, face, buf):
+    _check(lib.mpdata_halo_pack(ctx, field, face, buf), "mpdata_halo_pack", ctx)
+
+
+def mpdata_halo_unpack(ctx, buf, face, field):
+    _check(lib.mpdata_halo_unpack(ctx, buf, face, field), "mpdata_halo_unpack", ctx)

@@ -15,6 +15,8 @@
 // are chosen by mpdata_batch_autotune, which times every combination.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -198,7 +200,10 @@ int configure(mpdata_batch* b, int shape, int kchunk_levels) {
     t.item0 = item;
     item += (long long)t.tx * t.ty * t.nch * t.ntr;
   }
-  if (item >= (1LL << 31)) return MPDATA_ERANGE;
+  // the work counter is a 32-bit int that every CTA bumps once past the
+  // last item before it exits, so it climbs to nitems + grid - 1
+  const long long want = (long long)b->sms * occ;
+  if (item > (long long)INT_MAX - want) return MPDATA_ERANGE;
   e = cudaMemcpy(b->d_dom, tab.data(), sizeof(BDom) * b->nd, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return bfail(b, e, "descriptor upload");
   drop_graphs(b);
@@ -207,7 +212,6 @@ int configure(mpdata_batch* b, int shape, int kchunk_levels) {
   b->kchunk_levels = kchunk_levels;
   b->kern = k;
   b->smem = smem;
-  long long want = (long long)b->sms * occ;
   b->grid = (int)(want < item ? want : (item > 0 ? item : 1));
   return MPDATA_OK;
 }

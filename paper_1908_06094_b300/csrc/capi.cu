@@ -13,6 +13,7 @@
 #include "mass.cuh"
 #include "staged.cuh"
 #include "march.cuh"
+#include "exchange.cuh"
 #include "fused2.cuh"
 #include "adjoint.cuh"
 
@@ -346,7 +347,10 @@ int fused_setup(mpdata_ctx* c) {
   using F = FusedShape<T>;
   const Geo& g = c->g;
   c->fused_ok = 0;
-  if (c->iord != 2 || g.nx < 2 * g.h || g.ny < 2 * g.h) return MPDATA_OK;
+  // the periodic images a column writes need nx, ny >= 2h; a slab writes
+  // none and needs only an interior as wide as the strips it sends
+  const int minw = g.openij ? g.h : 2 * g.h;
+  if (c->iord != 2 || g.nx < minw || g.ny < minw) return MPDATA_OK;
   const size_t bytes = fused_smem<T>();
   auto kplain = fused_pick<T, false>(c);
   auto ktape = fused_pick<T, true>(c);
@@ -403,6 +407,9 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
 }
 
 bool use_fused(const mpdata_ctx* c) {
+  // a slab of a decomposed domain always runs the one-kernel step (its one
+  // halo exchange per step feeds exactly that kernel's radius-3 reads)
+  if (c->g.openij) return c->fused_ok != 0;
   // options run fused in FP32 only (FP64 takes the staged kernels)
   if (!c->fused_ok || (c->opts != 0 && c->dtype != MPDATA_F32)) return false;
   if (c->variant == MPDATA_AUTO) return c->dtype == MPDATA_F32;
@@ -725,6 +732,20 @@ int check_fields(const void* const* ptrs, int n) {
   return MPDATA_OK;
 }
 
+// One halo strip of a slab: field -> buffer (pack) or buffer -> field.
+template <class T, bool UNPACK>
+int strip_launch(mpdata_ctx* c, const void* src, void* dst, int face) {
+  const mpd::xch::Strip st = mpd::xch::strip(c->g, face, UNPACK);
+  if (st.n == 0) return MPDATA_OK;
+  const int64_t want = (st.n + 255) / 256;
+  const int blocks = (int)(want < 148 * 8 ? want : 148 * 8);
+  MPD_LAUNCH(c, MPDATA_STAGE_EXCHANGE,
+             (mpd::xch::strip_kernel<T, UNPACK><<<blocks, 256, 0, c->stream>>>(
+                 c->g, st, (const T*)src, (T*)dst)));
+  MPD_CHECK_LAUNCH(c, "halo strip kernel");
+  return MPDATA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -758,6 +779,8 @@ int mpdata_init(mpdata_ctx** out, int nx, int ny, int nz, int halo, int iord, in
   if (nz > 65535) return MPDATA_ERANGE;
   // padded extents must fit the 32-bit index arithmetic of a row/plane
   if ((int64_t)(nx + 2 * halo) * (ny + 2 * halo) > (int64_t)1 << 31) return MPDATA_ERANGE;
+  // the mass reduction counts interior rows (j, k) in 32 bits
+  if ((int64_t)ny * nz > MPDATA_MASS_MAX_ROWS) return MPDATA_ERANGE;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return MPDATA_EDEVICE;
   mpdata_ctx* c = new (std::nothrow) mpdata_ctx();
@@ -808,6 +831,7 @@ int mpdata_set_options(mpdata_ctx* c, int opts) {
   if (!c) return MPDATA_EINVAL;
   const int all = MPDATA_OPT_DFL | MPDATA_OPT_ABS | MPDATA_OPT_IGA;
   if (opts & ~all) return fail(c, MPDATA_EINVAL, "unknown option bits");
+  if (opts && c->g.openij) return fail(c, MPDATA_EINVAL, "a slab takes no option");
   if ((opts & MPDATA_OPT_IGA) && (opts & (MPDATA_OPT_DFL | MPDATA_OPT_ABS)))
     return fail(c, MPDATA_EINVAL, "the infinite gauge takes no other option");
   if ((opts & MPDATA_OPT_IGA) && c->iord > 2)
@@ -835,6 +859,7 @@ int mpdata_get_options(mpdata_ctx* c, int* opts) {
 int mpdata_step(mpdata_ctx* c, void* psi, const void* u, const void* v, const void* w,
                 const void* g, int nsteps) {
   if (!c || nsteps < 0) return MPDATA_EINVAL;
+  if (c->g.openij && !c->fused_ok) return fail(c, MPDATA_EINVAL, "slab without its step kernel");
   const void* f[5] = {psi, u, v, w, g};
   int rc = check_fields(f, 5);
   if (rc) return rc;
@@ -848,6 +873,7 @@ int mpdata_step(mpdata_ctx* c, void* psi, const void* u, const void* v, const vo
 int mpdata_step_out(mpdata_ctx* c, const void* psi_in, void* psi_out, const void* u,
                     const void* v, const void* w, const void* g) {
   if (!c) return MPDATA_EINVAL;
+  if (c->g.openij && !c->fused_ok) return fail(c, MPDATA_EINVAL, "slab without its step kernel");
   const void* f[6] = {psi_in, psi_out, u, v, w, g};
   int rc = check_fields(f, 6);
   if (rc) return rc;
@@ -889,6 +915,7 @@ int mpdata_step_host(mpdata_ctx* c, void* psi_h, const void* u_h, const void* v_
 
 int mpdata_fill_halo(mpdata_ctx* c, void* field, int kind) {
   if (!c || (kind != MPDATA_HALO_CELL && kind != MPDATA_HALO_WFACE)) return MPDATA_EINVAL;
+  if (c->g.openij) return fail(c, MPDATA_EINVAL, "a slab's halo comes from the halo exchange");
   const void* f[1] = {field};
   int rc = check_fields(f, 1);
   if (rc) return rc;
@@ -953,6 +980,7 @@ int mpdata_adjoint_step(mpdata_ctx* c, const void* psi_n, const void* u, const v
                         const void* w, const void* g, void* psi_bar, void* u_bar, void* v_bar,
                         void* w_bar) {
   if (!c) return MPDATA_EINVAL;
+  if (c->g.openij) return fail(c, MPDATA_EINVAL, "a slab has no adjoint");
   if (c->opts) return fail(c, MPDATA_EINVAL, "options have no adjoint");
   const void* f[9] = {psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
   int rc = check_fields(f, 9);
@@ -975,6 +1003,7 @@ int mpdata_tape_bytes(mpdata_ctx* c, size_t* bytes) {
 int mpdata_step_tape(mpdata_ctx* c, const void* psi_in, void* psi_out, const void* u,
                      const void* v, const void* w, const void* g, void* tape) {
   if (!c) return MPDATA_EINVAL;
+  if (c->g.openij) return fail(c, MPDATA_EINVAL, "a slab has no adjoint");
   if (c->opts) return fail(c, MPDATA_EINVAL, "options have no adjoint");
   const void* f[7] = {psi_in, psi_out, u, v, w, g, tape};
   int rc = check_fields(f, 7);
@@ -991,6 +1020,7 @@ int mpdata_adjoint_step_tape(mpdata_ctx* c, const void* tape, const void* psi_n,
                              const void* v, const void* w, const void* g, void* psi_bar,
                              void* u_bar, void* v_bar, void* w_bar) {
   if (!c) return MPDATA_EINVAL;
+  if (c->g.openij) return fail(c, MPDATA_EINVAL, "a slab has no adjoint");
   if (c->opts) return fail(c, MPDATA_EINVAL, "options have no adjoint");
   const void* f[10] = {tape, psi_n, u, v, w, g, psi_bar, u_bar, v_bar, w_bar};
   int rc = check_fields(f, 10);
@@ -1007,11 +1037,58 @@ int mpdata_adjoint_step_tape(mpdata_ctx* c, const void* tape, const void* psi_n,
 
 int mpdata_fold_halo_adjoint(mpdata_ctx* c, void* field) {
   if (!c) return MPDATA_EINVAL;
+  if (c->g.openij) return fail(c, MPDATA_EINVAL, "a slab has no adjoint");
   const void* f[1] = {field};
   int rc = check_fields(f, 1);
   if (rc) return rc;
   if (c->dtype == MPDATA_F64) return halo_fold_launch<double>(c, (double*)field);
   return halo_fold_launch<float>(c, (float*)field);
+}
+
+int mpdata_set_ij_boundary(mpdata_ctx* c, int mode) {
+  if (!c || (mode != MPDATA_IJ_PERIODIC && mode != MPDATA_IJ_HALO)) return MPDATA_EINVAL;
+  if (mode == MPDATA_IJ_HALO) {
+    if (c->iord != 2) return fail(c, MPDATA_EINVAL, "a slab runs the one-kernel step: iord 2");
+    if (c->g.h < 3) return fail(c, MPDATA_EINVAL, "a slab needs a halo of at least 3");
+    if (c->opts) return fail(c, MPDATA_EINVAL, "a slab takes no option");
+    if (c->g.nx < c->g.h || c->g.ny < c->g.h)
+      return fail(c, MPDATA_EINVAL, "a slab must be at least as wide as its halo");
+  }
+  const int prev = c->g.openij;
+  c->g.openij = mode == MPDATA_IJ_HALO ? 1 : 0;
+  if (c->dtype == MPDATA_F64) fused_setup<double>(c); else fused_setup<float>(c);
+  if (c->g.openij && !c->fused_ok) {
+    c->g.openij = prev;
+    if (c->dtype == MPDATA_F64) fused_setup<double>(c); else fused_setup<float>(c);
+    return fail(c, MPDATA_ECUDA, "the one-kernel step cannot run on this device");
+  }
+  return MPDATA_OK;
+}
+
+int mpdata_halo_strip_elems(mpdata_ctx* c, int face, long long* n) {
+  if (!c || !n || face < 0 || face > 3) return MPDATA_EINVAL;
+  *n = (long long)mpd::xch::strip(c->g, face, false).n;
+  return MPDATA_OK;
+}
+
+
+int mpdata_halo_pack(mpdata_ctx* c, const void* field, int face, void* buf) {
+  if (!c || face < 0 || face > 3) return MPDATA_EINVAL;
+  const void* f[2] = {field, buf};
+  int rc = check_fields(f, 2);
+  if (rc) return rc;
+  if (c->dtype == MPDATA_F64) return strip_launch<double, false>(c, field, buf, face);
+  return strip_launch<float, false>(c, field, buf, face);
+}
+
+int mpdata_halo_unpack(mpdata_ctx* c, const void* buf, int face, void* field) {
+  if (!c || face < 0 || face > 3) return MPDATA_EINVAL;
+  const void* f[2] = {buf, field};
+  int rc = check_fields(f, 2);
+  if (rc) return rc;
+  if (buf == field) return MPDATA_EINVAL;
+  if (c->dtype == MPDATA_F64) return strip_launch<double, true>(c, buf, field, face);
+  return strip_launch<float, true>(c, buf, field, face);
 }
 
 void mpdata_destroy(mpdata_ctx* c) {

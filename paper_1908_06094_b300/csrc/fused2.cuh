@@ -131,8 +131,17 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   const bool inBx = !kMap || tid < Map::NC + TY + 2;
   const bool inBy = !kMap || tid < Map::NC || (tid >= Map::NC + TY + 2 && tid < Map::NB);
   const bool inD = !kMap || (inC && x < TX && y < TY);  // the faces stage E reads
-  auto wrapi = [&](int i) { return ((i % g.nx) + g.nx) % g.nx; };
-  auto wrapj = [&](int j) { return ((j % g.ny) + g.ny) % g.ny; };
+  // the column of a tile cell: wrapped (periodic domain) or, on a slab of a
+  // decomposed domain, the cell itself, read from the exchanged halo (h >= 3
+  // covers the radius-3 ring); cells of a partial last tile past the halo
+  // are clamped into it -- they feed only columns past the interior, which
+  // are never written
+  auto wrapi = [&](int i) {
+    return g.openij ? min(i, g.nx + g.h - 1) : ((i % g.nx) + g.nx) % g.nx;
+  };
+  auto wrapj = [&](int j) {
+    return g.openij ? min(j, g.ny + g.h - 1) : ((j % g.ny) + g.ny) % g.ny;
+  };
   const int64_t col = (int64_t)wrapj(j0 + y) * g.px + wrapi(i0 + x);
   // radius-3 ring cell of this thread (threads < NRING)
   const bool ringer = tid < L::NRING;
@@ -212,8 +221,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   // level, where the registers they would hold across the march cost 3.7 %
   int niU = 0, njU = 0;
   if constexpr (UNROLL > 1) {
-    niU = (gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0);
-    njU = (gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0);
+    niU = g.openij ? 0 : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0));
+    njU = g.openij ? 0 : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0));
   }
 
   // The march starts 5 levels below the chunk (stages A..E are 5 levels
@@ -438,8 +447,12 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     if (t >= k0 && writes) {
       const T fzm = zface(t - 1) ? fzA : zero;
       const T r = q0 - ((fxs[s2] - fxs[s2 - 1]) + (fys[s2] - fys[s2 - EX]) + (fzB - fzm)) * rcp(g0);
-      const int ni = UNROLL > 1 ? niU : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0));
-      const int nj = UNROLL > 1 ? njU : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0));
+      // the column's periodic images in the i-j halo (none on a slab: the
+      // halo exchange fills a slab's halo)
+      const int ni = UNROLL > 1 ? niU
+                                : (g.openij ? 0 : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0)));
+      const int nj = UNROLL > 1 ? njU
+                                : (g.openij ? 0 : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0)));
       // the value and its periodic images in the halo
       auto images = [&]() {
         // the levels holding this value: t, and its k-halo images -- edge

@@ -15,6 +15,10 @@ namespace mpd {
 struct Geo {
   int nx, ny, nz, h;
   int kper;      // 1: periodic in k; 0: closed (zero-flux) bottom and top faces
+  int openij;    // 1: the grid is one slab of a decomposed domain: i-j neighbours
+                 //    past the interior are read from the halo (filled by the
+                 //    halo exchange) and no periodic images are written;
+                 // 0: periodic in i and j (the whole domain)
   int64_t px;    // padded row length (elements)
   int64_t pxy;   // padded plane size (elements)
   int64_t off0;  // offset of interior point (0,0,0)
@@ -23,7 +27,7 @@ struct Geo {
 
 inline Geo make_geo(int nx, int ny, int nz, int h, int kper = 0) {
   Geo g;
-  g.nx = nx; g.ny = ny; g.nz = nz; g.h = h; g.kper = kper;
+  g.nx = nx; g.ny = ny; g.nz = nz; g.h = h; g.kper = kper; g.openij = 0;
   g.px = nx + 2 * (int64_t)h;
   g.pxy = g.px * (ny + 2 * (int64_t)h);
   g.off0 = h * g.pxy + h * g.px + h;

@@ -2,11 +2,10 @@
 // cannot allocate device memory.
 //
 // mpdata_mass needs a context, and creating a context calls cudaMalloc for
-// the step's scratch.  Some callers cannot do that: code that runs while a
-// stream is being captured in global mode (where cudaMalloc is an error),
-// applications whose device memory is entirely handed out by their own pool
-// or arena, and hosts that forbid allocation after start-up (real-time or
-// certified codes).  This entry point needs no context: its only scratch,
+// the step's scratch.  Some callers cannot do that: applications whose
+// device memory is entirely handed out by their own pool or arena, and
+// hosts that forbid allocation after start-up (real-time or certified
+// codes).  This entry point needs no context: its only scratch,
 // the per-block partial sums of the two-level reduction, lives in the
 // file-scope array below, which every GPU that loads the library keeps
 // until the process exits.
@@ -34,7 +33,9 @@ std::mutex g_setup_lock;
 double* g_partials_addr[kMaxDevices] = {};
 
 // Device address of g_mass_partials on the current device, looked up once
-// per device (in host code the array's name is only a stand-in).
+// per device (in host code the array's name is only a stand-in) and kept for
+// the life of the process: a cudaDeviceReset of that device makes the kept
+// address stale, which the header states.
 int partials_for_current_device(double** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -75,7 +76,10 @@ extern "C" int mpdata_mass_noalloc(const void* psi, const void* g, int nx, int n
   if ((reinterpret_cast<uintptr_t>(psi) & 15u) || (reinterpret_cast<uintptr_t>(g) & 15u) ||
       (reinterpret_cast<uintptr_t>(out_dev) & 7u))
     return MPDATA_EALIGN;
-  // the reduction indexes rows (j,k) and padded planes with 32-bit integers
+  // the reduction indexes rows (j,k) and padded planes with 32-bit integers;
+  // its row counter runs up to 16 x MASS_BLOCKS rows past the last row
+  static_assert(MPDATA_MASS_NOALLOC_MAX_ROWS + 16LL * mpd::MASS_BLOCKS <= (long long)INT_MAX,
+                "the row bound leaves the row counter's margin");
   if ((int64_t)ny * nz > MPDATA_MASS_NOALLOC_MAX_ROWS) return MPDATA_ERANGE;
   if ((int64_t)(nx + 2 * (int64_t)halo) * (ny + 2 * (int64_t)halo) > (int64_t)INT_MAX)
     return MPDATA_ERANGE;

@@ -66,6 +66,23 @@ def test_init_rejects_null_out_and_oversize(capi):
                                 None) == capi.MPDATA_ERANGE
 
 
+def test_row_bound_of_the_mass_reduction(capi):
+    """ny*nz one past the mass reduction's row bound is refused before any
+    device call, by the context and by the allocation-free entry point (whose
+    argument checks all run before it touches a device, so fake aligned
+    pointers are never dereferenced)."""
+    bound = 2147483647 - 16 * 1184
+    ny, nz = 65534, bound // 65534 + 1          # ny * nz = bound + a few
+    assert ny * nz > bound and nz <= 65535
+    out = ctypes.c_void_p()
+    assert capi.lib.mpdata_init(ctypes.byref(out), 1, ny, nz, 2, 2, 1, 0, 0,
+                                None) == capi.MPDATA_ERANGE
+    fake = 1 << 20                               # 16-byte aligned, never read
+    for dt in (0, 1):
+        assert capi.lib.mpdata_mass_noalloc(fake, fake, 1, ny, nz, 2, dt, fake,
+                                            None) == capi.MPDATA_ERANGE
+
+
 def test_calls_reject_null_context(capi):
     L = capi.lib
     assert L.mpdata_step(None, None, None, None, None, None, 1) == capi.MPDATA_EINVAL

@@ -12,7 +12,7 @@ Tolerances (max |gpu - oracle| / max |oracle|):
   one output through the chain donor cell -> pseudo-velocity -> beta ->
   limited flux -> advance, each at most 0.5 ulp relative to its operand,
   and the limiter's ratios can amplify the rounding of psimax - psi by up
-  to the (bounded) flux ratio.  Measured values are reported in the design doc.
+  to the (bounded) flux ratio.  The measured errors stay below 1e-5.
 """
 import ctypes
 

@@ -1,8 +1,7 @@
 """mpdata_mass_noalloc: the mass sum for callers that cannot allocate.
 
-Callers inside a global-mode stream capture, or whose device memory is all
-owned by their own pool, or that forbid allocation after start-up, cannot
-call cudaMalloc -- and so cannot create a context, since mpdata_init
+Callers whose device memory is all owned by their own pool or arena, or
+that forbid allocation after start-up, cannot call cudaMalloc -- and so cannot create a context, since mpdata_init
 allocates the step's scratch.  mpdata_mass_noalloc serves them with its
 partial sums in a static device array.  These checks call it through the C
 ABI and compare it with mpdata_mass (the context path) on two calls in a
@@ -56,6 +55,9 @@ def test_noalloc_mass_matches_context_mass_twice(capi, dtype):
         assert rc == capi.MPDATA_OK, capi.mpdata_strerror(rc)
         torch.cuda.synchronize()
         a, b = out_na.item(), out_ctx.item()
+        # the same kernels with the same grid shape and a fixed summation
+        # order: the two paths agree bit for bit (well inside MASS_TOL)
+        assert a == b, (call, a, b)
         assert abs(a - b) <= MASS_TOL * abs(b), (call, a, b)
     # the second call took no device memory
     assert torch.cuda.mem_get_info()[0] == free_before_second
