@@ -95,7 +95,7 @@ struct TileMap {
 };
 
 template <class T, int TX, int TY, bool LIMIT, bool TAPE = false, int UNROLL = 1,
-          bool KPER = false, int OPT = 0>
+          bool KPER = false, int OPT = 0, bool MAP = (UNROLL == 1)>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
                                            const T* __restrict__ P0, const T* __restrict__ U,
                                            const T* __restrict__ V, const T* __restrict__ W,
@@ -115,7 +115,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   // thread per column in row-major order over the whole (TX+4)-wide plane
   // and runs B, C, D everywhere (the TileMap order made it 9.5 % slower).
   using Map = TileMap<TX, TY>;
-  constexpr bool kMap = UNROLL == 1;
+  constexpr bool kMap = MAP;
   int x, y;
   if constexpr (kMap) {
     Map::cell(tid, x, y);
@@ -476,15 +476,11 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
           }
         }
       };
-      // the unrolled march takes a one-store path for values without images
-      if constexpr (UNROLL > 1) {
-        if (ni == 0 && nj == 0 && (KPER ? t >= g.h && t < nz - g.h : t > 0 && t < nz - 1))
-          out[c0 + (int64_t)t * pxy] = r;
-        else
-          images();
-      } else {
+      // a value without images takes a single store
+      if (ni == 0 && nj == 0 && (KPER ? t >= g.h && t < nz - g.h : t > 0 && t < nz - 1))
+        out[c0 + (int64_t)t * pxy] = r;
+      else
         images();
-      }
     }
     // ---- shift the queues ------------------------------------------------
     p0 = p1; p1 = p2; p2 = p3; p3 = pn; pn = pn_next;
@@ -506,14 +502,14 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
 }
 
 template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false, bool KPER = false,
-          int OPT = 0>
+          int OPT = 0, int UNROLL = 1>
 __global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
              const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
              T* __restrict__ out, TapeOut<T> tape) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k0 = blockIdx.z * kchunk;
-  step_tile2<T, TX, TY, LIMIT, TAPE, 1, KPER, OPT>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
+  step_tile2<T, TX, TY, LIMIT, TAPE, UNROLL, KPER, OPT, true>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
                                               min(g.nz, k0 + kchunk), P0, U, V, W, G, out,
                                               smem_raw, tape);
 }
