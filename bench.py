@@ -571,20 +571,37 @@ def run_ours(args, wl_name):
             "mass_drift_rel": abs(m1 - m0) / abs(m0) if m0 else None,
             "clocks": clocks,
         }
-    # end-to-end through the HOST-buffer C call
+    # end-to-end through the HOST-buffer C calls: every step copies its
+    # psi, U, V, W, G from page-locked host memory and its result back
     if rank == 0 and not args.no_extras:
         host = [torch.from_numpy(x.copy()).pin_memory() for x in padded]
+        outs = [torch.empty_like(host[0]).pin_memory() for _ in range(2)]
         k = max(3, min(args.steps, 20))
-        m.step_host(*host, nsteps=1)
+        fb = padded[0].nbytes
+        # (a) the pipelined calls: a stream of k one-step problems, two in
+        # flight (copies of one overlap the step of another)
+        for q in range(3):
+            m.step_host_async(host[0], outs[q % 2], *host[1:], nsteps=1)
+        m.host_wait()
+        t0 = time.perf_counter()
+        for q in range(k):
+            m.step_host_async(host[0], outs[q % 2], *host[1:], nsteps=1)
+        m.host_wait()
+        e2e_s = time.perf_counter() - t0
+        # (b) the blocking call, one problem at a time
+        hs = [x.clone().pin_memory() for x in host]
+        m.step_host(*hs, nsteps=1)
         t0 = time.perf_counter()
         for _ in range(k):
-            m.step_host(*host, nsteps=1)
-        e2e_s = time.perf_counter() - t0
-        fb = padded[0].nbytes
+            m.step_host(*hs, nsteps=1)
+        ser_s = time.perf_counter() - t0
         out["e2e"] = {"value": npts * k / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 5 * fb,
-                      "d2h_bytes_per_step": fb,
-                      "path": "mpdata_step_host: pinned host psi,U,V,W,G -> device, 1 step, "
-                              "psi -> host, per step"}
+                      "d2h_bytes_per_step": fb, "steps": k,
+                      "path": "mpdata_step_host_async + mpdata_host_wait: per step, pinned "
+                              "host psi,U,V,W,G -> device, 1 step, psi -> host; two steps "
+                              "in flight",
+                      "blocking_call": {"value": npts * k / ser_s,
+                                        "path": "mpdata_step_host, one step per call"}}
         # CPU baseline: the oracle as it stands, all host cores, bounded sample
         ncores = os.cpu_count() or 1
         cpu_rate, cpu_steps = _oracle_rate(wl, args.cpu_seconds, padded[0].astype("float64"),
@@ -602,6 +619,96 @@ def run_ours(args, wl_name):
                                "sample": f"{cpu_steps} full steps of the same workload "
                                          f"(OMP_NUM_THREADS={os.environ.get('OMP_NUM_THREADS', ncores)})"}
     m.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return out
+
+
+def slab_grid_shape(ws: int):
+    """px x py = ws with px >= py as close to square as possible."""
+    py = max(d for d in range(1, int(ws ** 0.5) + 1) if ws % d == 0)
+    return ws // py, py
+
+
+def run_slab(args, wl_name):
+    """The workload as an i-j decomposed domain: each of the N ranks owns one
+    nx x ny x nz slab of a (px nx) x (py ny) x nz domain (weak scaling), the
+    slabs exchange psi's halo (depth 3, torch.distributed send/recv, NCCL)
+    before every one-kernel step, and the domain's mass is one FP64
+    all-reduce per step.  With N = 1 the single slab wraps onto itself (no
+    messages: its halo strips are packed and unpacked locally)."""
+    import numpy as np
+    import torch
+    import synth
+    from paper_1908_06094_b300 import _capi
+    from paper_1908_06094_b300.slabs import SlabRank
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local if ws > 1 else 0)
+    torch.cuda.set_device(dev)
+    wl = WORKLOADS[wl_name]
+    dt = torch.float64 if wl["dtype"] == "f64" else torch.float32
+    px, py = slab_grid_shape(ws)
+    NX, NY, nz, h = px * wl["nx"], py * wl["ny"], wl["nz"], 3
+    case = synth.latlon_3d(NX, NY, nz, seed=1234)
+    sl = SlabRank(NX, NY, nz, px, py, rank, halo=h, dtype=dt, device=dev) if ws > 1 else \
+        SlabRank(NX, NY, nz, 1, 1, 0, halo=h, dtype=dt, device=dev)
+    i0, nx, j0, ny = sl.i0, sl.nx, sl.j0, sl.ny
+    f = []
+    for x in (case.psi, case.u, case.v, case.w, case.g):
+        t = torch.full(sl.s.m.shape, float("nan"), dtype=dt, device=dev)
+        t[h:h + nz, h:h + ny, h:h + nx] = torch.from_numpy(
+            np.ascontiguousarray(x[:, j0:j0 + ny, i0:i0 + nx])).to(dev, dt)
+        f.append(t)
+    for t in f[1:]:
+        sl.exchange(t)
+    cur = [f[0], torch.empty_like(f[0])]
+    npts = nx * ny * nz
+
+    def step():
+        sl.exchange(cur[0])
+        sl.s.m.step_out(cur[0], cur[1], *f[1:])
+        cur.reverse()
+        return sl.mass(cur[0], f[4])
+
+    m0 = float(step())
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    launches0 = _capi.mpdata_launch_count(sl.s.m._ctx)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        mass = step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if ws > 1:
+        torch.distributed.barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = _capi.mpdata_launch_count(sl.s.m._ctx) - launches0
+    m1 = float(mass)
+    value, ms = job_throughput(ms, npts * args.steps, ws, dev)
+    out = None
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": wl["dtype"],
+               "data": "synthetic (seeded lat-lon deformational flow, Gaussian + step tracer)",
+               "config": dict(bench_config(wl_name, ws, 0), halo=h,
+                              parallelism=f"slabs {px}x{py}",
+                              domain=f"{NX}x{NY}x{nz}",
+                              step="halo exchange + one-kernel MPDATA step + FP64 mass "
+                                   "all-reduce"),
+               "gpu_launches": launches,
+               "mass_drift_rel": abs(m1 - m0) / abs(m0) if m0 else None}
+    sl.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
     return out
@@ -1165,11 +1272,18 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the e2e and CPU-baseline legs")
+    ap.add_argument("--decomp", default="replicas", choices=["replicas", "slab"],
+                    help="N > 1: independent replicas (default) or one i-j decomposed "
+                         "domain with a halo exchange")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
-    out = run_reference(args, args.workload) if args.impl == "reference" else \
-        run_ours(args, args.workload)
+    if args.impl == "reference":
+        out = run_reference(args, args.workload)
+    elif args.decomp == "slab":
+        out = run_slab(args, args.workload)
+    else:
+        out = run_ours(args, args.workload)
     if out is not None:
         print(json.dumps(out), flush=True)
 

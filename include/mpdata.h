@@ -158,6 +158,26 @@ MPDATA_API int mpdata_step_out(mpdata_ctx *c, const void *psi_in, void *psi_out,
 MPDATA_API int mpdata_step_host(mpdata_ctx *c, void *psi_host, const void *u_host, const void *v_host,
                      const void *w_host, const void *g_host, int nsteps);
 
+/* Pipelined HOST-buffer steps for a stream of problems (a library-interface
+ * addition; the paper has none): enqueues, without waiting, the copies of
+ * one problem's psi, u, v, w, g (padded, HOST, page-locked for the copies to
+ * run asynchronously) to the device, nsteps steps on the context's stream,
+ * and the copy of the result to psi_out_host (HOST; may equal psi_in_host).
+ * Two problems are in flight: one problem's host-to-device copies run on a
+ * copy stream while the previous problem steps and the one before that
+ * copies its result back on a third stream, so a stream of problems runs at
+ * the rate of the slowest of the three.  The host buffers of a problem must
+ * stay untouched until mpdata_host_wait returns.  Device buffers (two sets of
+ * five fields), the copy streams and their events are created on the first
+ * call.  Errors: EINVAL, ENOMEM, ECUDA. */
+MPDATA_API int mpdata_step_host_async(mpdata_ctx *c, const void *psi_in_host, void *psi_out_host,
+                                      const void *u_host, const void *v_host,
+                                      const void *w_host, const void *g_host, int nsteps);
+
+/* Wait until every problem enqueued by mpdata_step_host_async has been
+ * copied back.  Errors: EINVAL, ECUDA. */
+MPDATA_API int mpdata_host_wait(mpdata_ctx *c);
+
 /* Adjoint (reverse mode) of one step, iord 1 or 2, with or without the
  * limiter: the derivative of a scalar cost J through the step.
  *   psi_n          the state the step started from (DEVICE, read-only);

@@ -79,6 +79,8 @@ SIGNATURES = {
     "mpdata_step": (_i, [_c, _c, _c, _c, _c, _c, _i]),
     "mpdata_step_out": (_i, [_c, _c, _c, _c, _c, _c, _c]),
     "mpdata_step_host": (_i, [_c, _c, _c, _c, _c, _c, _i]),
+    "mpdata_step_host_async": (_i, [_c, _c, _c, _c, _c, _c, _c, _i]),
+    "mpdata_host_wait": (_i, [_c]),
     "mpdata_fill_halo": (_i, [_c, _c, _i]),
     "mpdata_adjoint_step": (_i, [_c] * 10),
     "mpdata_fold_halo_adjoint": (_i, [_c, _c]),
@@ -318,3 +320,12 @@ def mpdata_halo_pack(ctx, field, face, buf):
 
 def mpdata_halo_unpack(ctx, buf, face, field):
     _check(lib.mpdata_halo_unpack(ctx, buf, face, field), "mpdata_halo_unpack", ctx)
+
+
+def mpdata_step_host_async(ctx, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps):
+    _check(lib.mpdata_step_host_async(ctx, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps),
+           "mpdata_step_host_async", ctx)
+
+
+def mpdata_host_wait(ctx):
+    _check(lib.mpdata_host_wait(ctx), "mpdata_host_wait", ctx)

@@ -39,6 +39,14 @@ struct mpdata_ctx {
   bool adj_zero;
   // device copies for the HOST-buffer call (allocated on its first use)
   void* hbuf;
+  // the pipelined HOST-buffer calls (created on their first use): two sets
+  // of five device fields, a host-to-device and a device-to-host stream, and
+  // per set the events in-copied, stepped, out-copied
+  void* pbuf;
+  cudaStream_t ps_in, ps_out;
+  cudaEvent_t pe_in[2], pe_step[2], pe_out[2];
+  int pslot;
+  bool pused[2];
   // adjoint scratch (allocated on the first adjoint call)
   void* adjbuf;
   void* a_out;  // the recomputed psi^(n+1) of mpdata_adjoint_step
@@ -294,6 +302,13 @@ auto fused_kernel_ptr() {
   return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, TAPE, KPER>;
 }
 
+// the slab instance (MPDATA_IJ_HALO: neighbours from the exchanged halo)
+template <class T, bool LIMIT, bool KPER>
+auto fused_slab_ptr() {
+  using F = FusedShape<T>;
+  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, false, KPER, 0, 1, true>;
+}
+
 template <class T, bool LIMIT, bool KPER, int OPT>
 auto fused_opt_ptr() {
   using F = FusedShape<T>;
@@ -317,6 +332,13 @@ auto fused_opt_pick(int opts) {
 // The instance for the context's limiter, vertical boundary and options.
 template <class T, bool TAPE>
 auto fused_pick(const mpdata_ctx* c) {
+  if constexpr (!TAPE) {
+    if (c->g.openij) {  // a slab (no options, no tape)
+      if (c->g.kper)
+        return c->nonosc ? fused_slab_ptr<T, true, true>() : fused_slab_ptr<T, false, true>();
+      return c->nonosc ? fused_slab_ptr<T, true, false>() : fused_slab_ptr<T, false, false>();
+    }
+  }
   if constexpr (std::is_same<T, float>::value && !TAPE) {
     if (c->opts) {
       if (c->g.kper)
@@ -913,6 +935,68 @@ int mpdata_step_host(mpdata_ctx* c, void* psi_h, const void* u_h, const void* v_
   return MPDATA_OK;
 }
 
+int mpdata_step_host_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h, const void* u_h,
+                           const void* v_h, const void* w_h, const void* g_h, int nsteps) {
+  if (!c || nsteps < 0 || !psi_in_h || !psi_out_h || !u_h || !v_h || !w_h || !g_h)
+    return MPDATA_EINVAL;
+  const size_t fbytes = (size_t)c->g.total * c->esize;
+  const size_t fpad = (fbytes + 255) & ~(size_t)255;
+  cudaError_t e;
+  if (!c->pbuf) {
+    if (cudaMalloc(&c->pbuf, 10 * fpad) != cudaSuccess) {
+      cudaGetLastError();
+      c->pbuf = nullptr;
+      return MPDATA_ENOMEM;
+    }
+    bool ok = cudaStreamCreateWithFlags(&c->ps_in, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&c->ps_out, cudaStreamNonBlocking) == cudaSuccess;
+    for (int q = 0; q < 2 && ok; ++q)
+      ok = cudaEventCreateWithFlags(&c->pe_in[q], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->pe_step[q], cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&c->pe_out[q], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      e = cudaGetLastError();
+      return cuda_fail(c, e, "pipeline streams");
+    }
+    c->pslot = 0;
+    c->pused[0] = c->pused[1] = false;
+  }
+  const int b = c->pslot;
+  char* d = (char*)c->pbuf + (size_t)b * 5 * fpad;
+  // the set's previous problem must have been copied back before its
+  // fields are overwritten
+  if (c->pused[b] && (e = cudaStreamWaitEvent(c->ps_in, c->pe_out[b], 0)) != cudaSuccess)
+    return cuda_fail(c, e, "pipeline wait");
+  const void* src[5] = {psi_in_h, u_h, v_h, w_h, g_h};
+  for (int q = 0; q < 5; ++q) {
+    e = cudaMemcpyAsync(d + q * fpad, src[q], fbytes, cudaMemcpyHostToDevice, c->ps_in);
+    if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
+  }
+  if ((e = cudaEventRecord(c->pe_in[b], c->ps_in)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(c->stream, c->pe_in[b], 0)) != cudaSuccess)
+    return cuda_fail(c, e, "pipeline events");
+  int rc = mpdata_step(c, d, d + fpad, d + 2 * fpad, d + 3 * fpad, d + 4 * fpad, nsteps);
+  if (rc) return rc;
+  if ((e = cudaEventRecord(c->pe_step[b], c->stream)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(c->ps_out, c->pe_step[b], 0)) != cudaSuccess)
+    return cuda_fail(c, e, "pipeline events");
+  e = cudaMemcpyAsync(psi_out_h, d, fbytes, cudaMemcpyDeviceToHost, c->ps_out);
+  if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
+  if ((e = cudaEventRecord(c->pe_out[b], c->ps_out)) != cudaSuccess)
+    return cuda_fail(c, e, "pipeline events");
+  c->pused[b] = true;
+  c->pslot = b ^ 1;
+  return MPDATA_OK;
+}
+
+int mpdata_host_wait(mpdata_ctx* c) {
+  if (!c) return MPDATA_EINVAL;
+  if (!c->pbuf) return MPDATA_OK;
+  cudaError_t e = cudaStreamSynchronize(c->ps_out);
+  if (e != cudaSuccess) return cuda_fail(c, e, "pipeline synchronize");
+  return MPDATA_OK;
+}
+
 int mpdata_fill_halo(mpdata_ctx* c, void* field, int kind) {
   if (!c || (kind != MPDATA_HALO_CELL && kind != MPDATA_HALO_WFACE)) return MPDATA_EINVAL;
   if (c->g.openij) return fail(c, MPDATA_EINVAL, "a slab's halo comes from the halo exchange");
@@ -1101,6 +1185,17 @@ void mpdata_destroy(mpdata_ctx* c) {
   }
   if (c->scratch) cudaFree(c->scratch);
   if (c->hbuf) cudaFree(c->hbuf);
+  if (c->pbuf) {
+    cudaStreamSynchronize(c->ps_out);
+    for (int q = 0; q < 2; ++q) {
+      if (c->pe_in[q]) cudaEventDestroy(c->pe_in[q]);
+      if (c->pe_step[q]) cudaEventDestroy(c->pe_step[q]);
+      if (c->pe_out[q]) cudaEventDestroy(c->pe_out[q]);
+    }
+    if (c->ps_in) cudaStreamDestroy(c->ps_in);
+    if (c->ps_out) cudaStreamDestroy(c->ps_out);
+    cudaFree(c->pbuf);
+  }
   delete c;
 }
 

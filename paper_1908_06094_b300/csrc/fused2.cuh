@@ -95,7 +95,7 @@ struct TileMap {
 };
 
 template <class T, int TX, int TY, bool LIMIT, bool TAPE = false, int UNROLL = 1,
-          bool KPER = false, int OPT = 0, bool MAP = (UNROLL == 1)>
+          bool KPER = false, int OPT = 0, bool MAP = (UNROLL == 1), bool OPENIJ = false>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
                                            const T* __restrict__ P0, const T* __restrict__ U,
                                            const T* __restrict__ V, const T* __restrict__ W,
@@ -136,11 +136,15 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   // covers the radius-3 ring); cells of a partial last tile past the halo
   // are clamped into it -- they feed only columns past the interior, which
   // are never written
+  // (OPENIJ: a compile-time variant, so the periodic instances carry none
+  // of the slab's code)
   auto wrapi = [&](int i) {
-    return g.openij ? min(i, g.nx + g.h - 1) : ((i % g.nx) + g.nx) % g.nx;
+    if constexpr (OPENIJ) return min(i, g.nx + g.h - 1);
+    else return ((i % g.nx) + g.nx) % g.nx;
   };
   auto wrapj = [&](int j) {
-    return g.openij ? min(j, g.ny + g.h - 1) : ((j % g.ny) + g.ny) % g.ny;
+    if constexpr (OPENIJ) return min(j, g.ny + g.h - 1);
+    else return ((j % g.ny) + g.ny) % g.ny;
   };
   const int64_t col = (int64_t)wrapj(j0 + y) * g.px + wrapi(i0 + x);
   // radius-3 ring cell of this thread (threads < NRING)
@@ -221,8 +225,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   // level, where the registers they would hold across the march cost 3.7 %
   int niU = 0, njU = 0;
   if constexpr (UNROLL > 1) {
-    niU = g.openij ? 0 : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0));
-    njU = g.openij ? 0 : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0));
+    niU = OPENIJ ? 0 : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0));
+    njU = OPENIJ ? 0 : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0));
   }
 
   // The march starts 5 levels below the chunk (stages A..E are 5 levels
@@ -450,9 +454,9 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       // the column's periodic images in the i-j halo (none on a slab: the
       // halo exchange fills a slab's halo)
       const int ni = UNROLL > 1 ? niU
-                                : (g.openij ? 0 : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0)));
+                                : (OPENIJ ? 0 : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0)));
       const int nj = UNROLL > 1 ? njU
-                                : (g.openij ? 0 : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0)));
+                                : (OPENIJ ? 0 : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0)));
       // the value and its periodic images in the halo
       auto images = [&]() {
         // the levels holding this value: t, and its k-halo images -- edge
@@ -502,14 +506,14 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
 }
 
 template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false, bool KPER = false,
-          int OPT = 0, int UNROLL = 1>
+          int OPT = 0, int UNROLL = 1, bool OPENIJ = false>
 __global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
              const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
              T* __restrict__ out, TapeOut<T> tape) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k0 = blockIdx.z * kchunk;
-  step_tile2<T, TX, TY, LIMIT, TAPE, UNROLL, KPER, OPT, true>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
+  step_tile2<T, TX, TY, LIMIT, TAPE, UNROLL, KPER, OPT, true, OPENIJ>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
                                               min(g.nz, k0 + kchunk), P0, U, V, W, G, out,
                                               smem_raw, tape);
 }

@@ -7,6 +7,7 @@
 // (the face's owner), and read by both neighbours, so the flux divergence
 // telescopes exactly and mass is conserved to the rounding of psi*G alone.
 #pragma once
+#include <type_traits>
 #include "grid.cuh"
 
 namespace mpd {
@@ -226,12 +227,39 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
   T fzm = zopen(g, k - 1) ? fl(P[nb[4]], pc, wt[nb[4]]) : zero;
   T in = (pos(fxm) - neg(fxp)) + (pos(fym) - neg(fyp)) + (pos(fzm) - neg(fzp));
   T out = (pos(fxp) - neg(fxm)) + (pos(fyp) - neg(fym)) + (pos(fzp) - neg(fzm));
-  const T ri = rcp(in + eps), ro = rcp(out + eps);
-  bu[q] = (hi - pc) * G[q] * ri;
-  bd[q] = (pc - lo) * G[q] * ro;
-  if (rin) {
-    rin[q] = ri;
-    rout[q] = ro;
+  const T gq = G[q];
+  const T nu = (hi - pc) * gq, nd = (pc - lo) * gq;  // >= +0: hi >= pc >= lo, G > 0
+  const T di = in + eps, dd = out + eps;              // > 0
+  if constexpr (std::is_same<T, double>::value && UNIT) {
+    // FP64 staged step: a beta at or above 1 is stored as 1, which the
+    // limiter reads only through min(1, beta); beta >= 1 exactly when its
+    // numerator reaches its denominator, a test on the bit patterns of two
+    // non-negative doubles (integer pipe).  A warp whose betas of one kind
+    // are all >= 1 skips that reciprocal (4 FP64 instructions); the adjoint's
+    // tape keeps both reciprocals.
+    const bool lu = dbits(nu) < dbits(di), ld = dbits(nd) < dbits(dd);
+    const unsigned live = __activemask();
+    T bu_v = 1.0, bd_v = 1.0;
+    if (rin || __any_sync(live, lu)) {
+      const T ri = rcp(di);
+      if (lu) bu_v = nu * ri;
+      if (rin) rin[q] = ri;
+    }
+    if (rin || __any_sync(live, ld)) {
+      const T ro = rcp(dd);
+      if (ld) bd_v = nd * ro;
+      if (rin) rout[q] = ro;
+    }
+    bu[q] = bu_v;
+    bd[q] = bd_v;
+  } else {
+    const T ri = rcp(di), ro = rcp(dd);
+    bu[q] = nu * ri;
+    bd[q] = nd * ro;
+    if (rin) {
+      rin[q] = ri;
+      rout[q] = ro;
+    }
   }
 }
 

@@ -110,3 +110,24 @@ class MPDATA:
         C.mpdata_step_host(self._ctx, psi_h.data_ptr(), u_h.data_ptr(), v_h.data_ptr(),
                            w_h.data_ptr(), g_h.data_ptr(), nsteps)
         return psi_h
+
+    def step_host_async(self, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps: int = 1):
+        """Pipelined HOST-buffer steps (one problem of a stream): enqueues the
+        copies in, nsteps steps and the copy of the result into psi_out_h,
+        and returns at once; call host_wait() before touching the buffers.
+        CPU tensors, pinned for the copies to overlap."""
+        for name, t in (("psi_in", psi_in_h), ("psi_out", psi_out_h), ("u", u_h), ("v", v_h),
+                        ("w", w_h), ("g", g_h)):
+            if t.is_cuda or t.dtype != self.dtype or tuple(t.shape) != self.shape \
+                    or not t.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous CPU {self.dtype} tensor of "
+                                 f"shape {self.shape}")
+        self._sync_stream()
+        C.mpdata_step_host_async(self._ctx, psi_in_h.data_ptr(), psi_out_h.data_ptr(),
+                                 u_h.data_ptr(), v_h.data_ptr(), w_h.data_ptr(), g_h.data_ptr(),
+                                 nsteps)
+        return psi_out_h
+
+    def host_wait(self):
+        """Wait for every problem enqueued by step_host_async."""
+        C.mpdata_host_wait(self._ctx)

@@ -235,11 +235,13 @@ def dist_transfer(group=None):
 
 
 def global_mass(local_mass, group=None):
-    """Sum of the ranks' FP64 masses (one all-reduce)."""
+    """Sum of the ranks' FP64 masses (one all-reduce; without a process
+    group, the one rank's mass)."""
     import torch
     import torch.distributed as dist
     t = torch.as_tensor(local_mass, dtype=torch.float64).reshape(1).clone()
-    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
     return t[0]
 
 
