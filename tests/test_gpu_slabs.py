@@ -105,6 +105,33 @@ def test_uneven_slabs_against_the_oracle(dtype, px, py, shape):
     assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= tol
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_slabs_periodic_k(dtype):
+    """Slabs of a domain periodic in k as well (2 x 2, 3 steps): equal to the
+    undivided periodic-k step bit for bit, and within the step tolerance of
+    the oracle run periodic in k."""
+    from paper_1908_06094_b300 import MPDATA, SlabDecomposition, _capi as C
+    c = rounded_inputs(synth.random_case(41, 30, 9, seed=8, cmax=0.3, kbc=1), dtype)
+    h = 3
+    dec = SlabDecomposition(c.nx, c.ny, c.nz, 2, 2, halo=h, dtype=dtype,
+                            k_bc=C.MPDATA_K_PERIODIC)
+    f = [dec.scatter(x) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    dec.step(*f, nsteps=3)
+    got = dec.gather(f[0]).double().cpu().numpy()
+    dec.close()
+    m = MPDATA(c.nx, c.ny, c.nz, halo=h, dtype=dtype, variant=0, k_bc=C.MPDATA_K_PERIODIC)
+    d = _case_fields(c, dtype, h)
+    m.step(*d, nsteps=3)
+    torch.cuda.synchronize()
+    whole = synth.interior(d[0].double().cpu().numpy(), h)
+    m.close()
+    assert np.array_equal(got, whole)
+    P = [synth.pad(x, 2) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    ref = synth.interior(oracle.run(*P, h=2, iord=2, nonosc=1, nsteps=3, kbc=1), 2)
+    tol = 3 * (F64_TOL if dtype == torch.float64 else F32_TOL)
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= tol
+
+
 def test_slab_refusals():
     """A slab context refuses what would read its halo as periodic."""
     from paper_1908_06094_b300 import MPDATA, _capi as C
