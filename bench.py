@@ -989,10 +989,11 @@ def measure_adjoint(dev, dtype, nsteps=20, ckpt=5, reps=2, cpu_seconds=0.0):
     return out
 
 
-def measure_batched(dev, steps=20, warmup=3):
+def measure_batched(dev, steps=20, warmup=3, config=None):
     """Batched configuration: 64 domains (log-uniform 32x32x16..256x256x64)
     x 8 tracers, FP32, iord 2 with the limiter, one graph-replayed persistent
-    launch per step, tile shape and chunk autotuned.  Unit: tracer-updates/s."""
+    launch per step, tile shape and chunk autotuned (or config = (shape,
+    kchunk) given).  Unit: tracer-updates/s."""
     import torch
     import synth
     from paper_1908_06094_b300 import MPDATABatch
@@ -1007,7 +1008,11 @@ def measure_batched(dev, steps=20, warmup=3):
             d[k] = torch.from_numpy(synth.pad(getattr(c, k), h)).to(dev, torch.float32).contiguous()
         doms.append(d)
     b = MPDATABatch(doms)
-    cfg = b.autotune(reps=3)
+    if config is None:
+        cfg = b.autotune(reps=3)
+    else:
+        b.set_config(*config)
+        cfg = dict(b.config(), cached=False, given=True)
     b.step(warmup, graph=True)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
