@@ -224,6 +224,9 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   // down, 0: none), formed once for the unrolled march (the batch's:
   // +2.4 % there); the single-domain march (UNROLL = 1) forms them per
   // level, where the registers they would hold across the march cost 3.7 %
+  // the column has no periodic image in the i-j halo (the single-domain
+  // march's steady levels store such a value with one store)
+  const bool noimg = OPENIJ || (gi >= g.h && gi < g.nx - g.h && gj >= g.h && gj < g.ny - g.h);
   int niU = 0, njU = 0;
   if constexpr (UNROLL > 1) {
     niU = OPENIJ ? 0 : ((gi < g.h) ? 1 : ((gi >= g.nx - g.h) ? -1 : 0));
@@ -290,12 +293,14 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     }
     // loads one plane ahead (used from the next iteration on); the plane
     // offsets are the same for every thread
-    const int64_t o5 = (int64_t)(KPER ? l5 : clampk_(t + 5)) * pxy;
-    const int64_t o4 = (int64_t)(KPER ? l4 : clampk_(t + 4)) * pxy;
-    const int64_t o3 = (int64_t)(KPER ? l3 : clampk_(t + 3)) * pxy;
+    // (steady levels, zero-flux: planes t+3 .. t+5 are inside the grid and
+    // the face t+4 is open)
+    const int64_t o5 = (int64_t)(KPER ? l5 : (S ? t + 5 : clampk_(t + 5))) * pxy;
+    const int64_t o4 = (KPER || !S) ? (int64_t)(KPER ? l4 : clampk_(t + 4)) * pxy : o5 - pxy;
+    const int64_t o3 = (KPER || !S) ? (int64_t)(KPER ? l3 : clampk_(t + 3)) * pxy : o4 - pxy;
     const T pn_next = P0[c0 + o5];
     const T un_next = U[c0 + o4], vn_next = V[c0 + o4], gn_next = G[c0 + o4];
-    const T wn_next = zface(t + 4) ? W[c0 + o4] : zero;  // closed faces
+    const T wn_next = (S || zface(t + 4)) ? W[c0 + o4] : zero;  // closed faces
     T rp_next = zero, ru_next = zero, rv_next = zero;
     if (ringer) {
       rp_next = P0[rc0 + o3];
@@ -459,6 +464,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     if ((S || t >= k0) && writes) {
       const T fzm = (S || zface(t - 1)) ? fzA : zero;
       const T r = q0 - ((fxs[s2] - fxs[s2 - 1]) + (fys[s2] - fys[s2 - EX]) + (fzB - fzm)) * rcp(g0);
+      // a steady level of a column without i-j images: one store
+      if (S && !KPER && UNROLL == 1 && noimg) {
+        out[c0 + (int64_t)t * pxy] = r;
+      } else {
       // the column's periodic images in the i-j halo (none on a slab: the
       // halo exchange fills a slab's halo)
       const int ni = UNROLL > 1 ? niU
@@ -494,6 +503,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         out[c0 + (int64_t)t * pxy] = r;
       else
         images();
+      }
     }
     // ---- shift the queues ------------------------------------------------
     p0 = p1; p1 = p2; p2 = p3; p3 = pn; pn = pn_next;
@@ -515,9 +525,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   // cap and measured 6 % slower).
   if constexpr (UNROLL == 1) {
     // the levels where every guard holds: zero-flux, t in [max(k0, 1),
-    // min(k1 - 1, nz - 3)] (no stage reaches below plane 0 or the top two
-    // planes); periodic in k, the whole chunk
-    const int tS = KPER ? k0 : max(k0, 1), tE = KPER ? k1 - 1 : min(k1 - 1, nz - 3);
+    // min(k1 - 1, nz - 6)] (no stage reaches below plane 0 or the top two
+    // planes, and the loads one plane ahead stay below the top); periodic
+    // in k, the whole chunk
+    const int tS = KPER ? k0 : max(k0, 1), tE = KPER ? k1 - 1 : min(k1 - 1, nz - 6);
     int t = t0;
     for (; t < tS && t < k1; ++t) level(t, std::false_type{});
     for (; t <= tE; ++t) level(t, std::true_type{});
