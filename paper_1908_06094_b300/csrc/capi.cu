@@ -296,10 +296,10 @@ template <class T> struct FusedShape;
 template <> struct FusedShape<double> { static constexpr int TX = 32, TY = 8, MINB = 1; };
 template <> struct FusedShape<float> { static constexpr int TX = 32, TY = 16, MINB = 1; };
 
-template <class T, bool LIMIT, bool TAPE = false, bool KPER = false>
+template <class T, bool LIMIT, bool TAPE = false, bool KPER = false, bool I32 = false>
 auto fused_kernel_ptr() {
   using F = FusedShape<T>;
-  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, TAPE, KPER>;
+  return mpd::fused2::step_kernel2<T, F::TX, F::TY, F::MINB, LIMIT, TAPE, KPER, 0, 1, false, I32>;
 }
 
 // the slab instance (MPDATA_IJ_HALO: neighbours from the exchanged halo)
@@ -345,6 +345,14 @@ auto fused_pick(const mpdata_ctx* c) {
         return c->nonosc ? fused_opt_pick<true, true>(c->opts) : fused_opt_pick<false, true>(c->opts);
       return c->nonosc ? fused_opt_pick<true, false>(c->opts) : fused_opt_pick<false, false>(c->opts);
     }
+  }
+  // fields of fewer than 2^31 elements take the 32-bit-offset instances
+  if (!TAPE && c->g.total < ((int64_t)1 << 31)) {
+    if (c->g.kper)
+      return c->nonosc ? fused_kernel_ptr<T, true, TAPE, true, true>()
+                       : fused_kernel_ptr<T, false, TAPE, true, true>();
+    return c->nonosc ? fused_kernel_ptr<T, true, TAPE, false, true>()
+                     : fused_kernel_ptr<T, false, TAPE, false, true>();
   }
   if (c->g.kper)
     return c->nonosc ? fused_kernel_ptr<T, true, TAPE, true>() : fused_kernel_ptr<T, false, TAPE, true>();

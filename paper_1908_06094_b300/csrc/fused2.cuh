@@ -96,7 +96,8 @@ struct TileMap {
 };
 
 template <class T, int TX, int TY, bool LIMIT, bool TAPE = false, int UNROLL = 1,
-          bool KPER = false, int OPT = 0, bool MAP = (UNROLL == 1), bool OPENIJ = false>
+          bool KPER = false, int OPT = 0, bool MAP = (UNROLL == 1), bool OPENIJ = false,
+          bool I32 = false>
 __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0, int k1,
                                            const T* __restrict__ P0, const T* __restrict__ U,
                                            const T* __restrict__ V, const T* __restrict__ W,
@@ -147,11 +148,14 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     if constexpr (OPENIJ) return min(j, g.ny + g.h - 1);
     else return ((j % g.ny) + g.ny) % g.ny;
   };
-  const int64_t col = (int64_t)wrapj(j0 + y) * g.px + wrapi(i0 + x);
+  // element offsets: 32-bit when the padded field has fewer than 2^31
+  // elements (I32: fewer registers and one-word address arithmetic)
+  using Ix = std::conditional_t<I32, int, int64_t>;
+  const Ix col = (Ix)wrapj(j0 + y) * (Ix)g.px + wrapi(i0 + x);
   // radius-3 ring cell of this thread (threads < NRING)
   const bool ringer = tid < L::NRING;
   int r3 = 0;
-  int64_t rcol = 0;
+  Ix rcol = 0;
   if (ringer) {
     int rx, ry, r = tid;
     if (r < RX) { rx = r - 3; ry = -3; }
@@ -159,9 +163,9 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     else if ((r -= RX) < L::EY) { rx = -3; ry = r - 2; }
     else { r -= L::EY; rx = TX + 2; ry = r - 2; }
     r3 = (ry + 3) * RX + (rx + 3);
-    rcol = (int64_t)wrapj(j0 + ry) * g.px + wrapi(i0 + rx);
+    rcol = (Ix)wrapj(j0 + ry) * (Ix)g.px + wrapi(i0 + rx);
   }
-  const int64_t pxy = g.pxy;
+  const Ix pxy = (Ix)g.pxy;
   constexpr bool kper = KPER;  // periodic in k (g.kper): a compile-time variant
   // the level of plane k: clamped (edge copy) or, periodic in k, wrapped
   // (any distance: the march runs up to 5 planes past the grid)
@@ -174,12 +178,12 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   // the face above plane k carries flux
   auto zface = [&](int k) { return kper || (k >= 0 && k < nz - 1); };
   // per-thread column pointers (plane 0); plane k is + k*pxy (warp-uniform)
-  const int64_t c0 = g.off0 + col, rc0 = g.off0 + rcol;
-  auto ld = [&](const T* f, int k, int64_t c) { return f[c + (int64_t)clampk_(k) * pxy]; };
+  const Ix c0 = (Ix)g.off0 + col, rc0 = (Ix)g.off0 + rcol;
+  auto ld = [&](const T* f, int k, Ix c) { return f[c + (Ix)clampk_(k) * pxy]; };
   // vertical face value with the closed bottom and top faces
-  auto ldw = [&](int k, int64_t c) {
-    if constexpr (KPER) return W[c + (int64_t)clampk_(k) * pxy];
-    else return (k < 0 || k >= nz - 1) ? zero : W[c + (int64_t)k * pxy];
+  auto ldw = [&](int k, Ix c) {
+    if constexpr (KPER) return W[c + (Ix)clampk_(k) * pxy];
+    else return (k < 0 || k >= nz - 1) ? zero : W[c + (Ix)k * pxy];
   };
   // shared-memory views
   T* p0s = sm + L::P0S;
@@ -295,9 +299,9 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     // offsets are the same for every thread
     // (steady levels, zero-flux: planes t+3 .. t+5 are inside the grid and
     // the face t+4 is open)
-    const int64_t o5 = (int64_t)(KPER ? l5 : (S ? t + 5 : clampk_(t + 5))) * pxy;
-    const int64_t o4 = (KPER || !S) ? (int64_t)(KPER ? l4 : clampk_(t + 4)) * pxy : o5 - pxy;
-    const int64_t o3 = (KPER || !S) ? (int64_t)(KPER ? l3 : clampk_(t + 3)) * pxy : o4 - pxy;
+    const Ix o5 = (Ix)(KPER ? l5 : (S ? t + 5 : clampk_(t + 5))) * pxy;
+    const Ix o4 = (KPER || !S) ? (Ix)(KPER ? l4 : clampk_(t + 4)) * pxy : o5 - pxy;
+    const Ix o3 = (KPER || !S) ? (Ix)(KPER ? l3 : clampk_(t + 3)) * pxy : o4 - pxy;
     const T pn_next = P0[c0 + o5];
     const T un_next = U[c0 + o4], vn_next = V[c0 + o4], gn_next = G[c0 + o4];
     const T wn_next = (S || zface(t + 4)) ? W[c0 + o4] : zero;  // closed faces
@@ -441,7 +445,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       }
       fzB = f;
       if (TAPE && t >= k0 && writes) {
-        const int64_t q = c0 + (int64_t)t * pxy;
+        const int64_t q = (int64_t)c0 + (int64_t)t * (int64_t)pxy;
         tape.p1[q] = q0;
         tape.ut[q] = utA;
         tape.vt[q] = vtA;
@@ -466,7 +470,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T r = q0 - ((fxs[s2] - fxs[s2 - 1]) + (fys[s2] - fys[s2 - EX]) + (fzB - fzm)) * rcp(g0);
       // a steady level of a column without i-j images: one store
       if (S && !KPER && UNROLL == 1 && noimg) {
-        out[c0 + (int64_t)t * pxy] = r;
+        out[c0 + (Ix)t * pxy] = r;
       } else {
       // the column's periodic images in the i-j halo (none on a slab: the
       // halo exchange fills a slab's halo)
@@ -500,7 +504,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       // a value without images takes a single store
       if (ni == 0 && nj == 0 &&
           (KPER ? t >= g.h && t < nz - g.h : (S || (t > 0 && t < nz - 1))))
-        out[c0 + (int64_t)t * pxy] = r;
+        out[c0 + (Ix)t * pxy] = r;
       else
         images();
       }
@@ -548,14 +552,14 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
 }
 
 template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false, bool KPER = false,
-          int OPT = 0, int UNROLL = 1, bool OPENIJ = false>
+          int OPT = 0, int UNROLL = 1, bool OPENIJ = false, bool I32 = false>
 __global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
              const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
              T* __restrict__ out, TapeOut<T> tape) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k0 = blockIdx.z * kchunk;
-  step_tile2<T, TX, TY, LIMIT, TAPE, UNROLL, KPER, OPT, true, OPENIJ>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
+  step_tile2<T, TX, TY, LIMIT, TAPE, UNROLL, KPER, OPT, true, OPENIJ, I32>(g, blockIdx.x * TX, blockIdx.y * TY, k0,
                                               min(g.nz, k0 + kchunk), P0, U, V, W, G, out,
                                               smem_raw, tape);
 }
