@@ -962,8 +962,19 @@ int mpdata_step_host_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h,
       ok = cudaEventCreateWithFlags(&c->pe_in[q], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&c->pe_step[q], cudaEventDisableTiming) == cudaSuccess &&
            cudaEventCreateWithFlags(&c->pe_out[q], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
+    if (!ok) {  // undo the partial set-up, so that a later call starts afresh
       e = cudaGetLastError();
+      for (int q = 0; q < 2; ++q) {
+        if (c->pe_in[q]) cudaEventDestroy(c->pe_in[q]);
+        if (c->pe_step[q]) cudaEventDestroy(c->pe_step[q]);
+        if (c->pe_out[q]) cudaEventDestroy(c->pe_out[q]);
+        c->pe_in[q] = c->pe_step[q] = c->pe_out[q] = nullptr;
+      }
+      if (c->ps_in) cudaStreamDestroy(c->ps_in);
+      if (c->ps_out) cudaStreamDestroy(c->ps_out);
+      c->ps_in = c->ps_out = nullptr;
+      cudaFree(c->pbuf);
+      c->pbuf = nullptr;
       return cuda_fail(c, e, "pipeline streams");
     }
     c->pslot = 0;

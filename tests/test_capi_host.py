@@ -83,6 +83,25 @@ def test_row_bound_of_the_mass_reduction(capi):
                                             None) == capi.MPDATA_ERANGE
 
 
+def test_later_calls_reject_bad_arguments_without_a_device(capi):
+    """The pipelined host calls, the slab calls and the FP64 probe check
+    their arguments before any device call."""
+    L = capi.lib
+    fake = 1 << 20
+    assert L.mpdata_step_host_async(None, fake, fake, fake, fake, fake, fake, 1) == \
+        capi.MPDATA_EINVAL
+    assert L.mpdata_host_wait(None) == capi.MPDATA_EINVAL
+    assert L.mpdata_set_ij_boundary(None, capi.MPDATA_IJ_HALO) == capi.MPDATA_EINVAL
+    n = ctypes.c_longlong()
+    assert L.mpdata_halo_strip_elems(None, 0, ctypes.byref(n)) == capi.MPDATA_EINVAL
+    assert L.mpdata_halo_pack(None, fake, 0, fake) == capi.MPDATA_EINVAL
+    assert L.mpdata_halo_unpack(None, fake, 0, fake) == capi.MPDATA_EINVAL
+    fl = ctypes.c_double()
+    assert L.mpdata_probe_fp64_fma(None, 1, 1, None, ctypes.byref(fl)) == capi.MPDATA_EINVAL
+    assert L.mpdata_probe_fp64_fma(fake, 0, 1, None, ctypes.byref(fl)) == capi.MPDATA_EINVAL
+    assert L.mpdata_probe_fp64_fma(fake, 1, 1, None, None) == capi.MPDATA_EINVAL
+
+
 def test_calls_reject_null_context(capi):
     L = capi.lib
     assert L.mpdata_step(None, None, None, None, None, None, 1) == capi.MPDATA_EINVAL
