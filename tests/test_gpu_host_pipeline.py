@@ -55,3 +55,17 @@ def test_stream_of_problems_equals_device_steps(dtype, nsteps):
     assert torch.equal(f[0], d[0].cpu())
     m.close()
     ref.close()
+
+
+def test_zero_steps_copies_through():
+    """nsteps = 0: the problem's psi comes back unchanged."""
+    from paper_1908_06094_b300 import MPDATA
+    c = synth.random_case(17, 13, 3, seed=3)
+    P = [synth.pad(x, 2) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    f = [_host(x, torch.float64) for x in P]
+    out = torch.empty_like(f[0]).pin_memory()
+    m = MPDATA(17, 13, 3, halo=2, dtype=torch.float64)
+    m.step_host_async(f[0], out, *f[1:], nsteps=0)
+    m.host_wait()
+    assert torch.equal(out, f[0])
+    m.close()

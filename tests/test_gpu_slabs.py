@@ -91,10 +91,11 @@ def test_slabs_equal_the_undivided_step_full_size(dtype, px, py):
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 @pytest.mark.parametrize("px,py,shape", [(3, 2, (50, 41, 7)), (1, 3, (19, 30, 5)),
-                                         (4, 1, (37, 12, 9))])
+                                         (4, 1, (37, 12, 9)), (4, 3, (12, 9, 4))])
 def test_uneven_slabs_against_the_oracle(dtype, px, py, shape):
-    """Uneven slab sizes (a ragged split), 3 steps: equal to the undivided
-    step and within the step tolerance of the oracle."""
+    """Uneven slab sizes (a ragged split) and slabs as narrow as their
+    halo (12 x 9 in 4 x 3: every slab 3 x 3), 3 steps: equal to the
+    undivided step and within the step tolerance of the oracle."""
     nx, ny, nz = shape
     c = rounded_inputs(synth.random_case(nx, ny, nz, seed=nx + ny, cmax=0.3), dtype)
     got, _, _ = _run_slabs(c, px, py, dtype, 3)
