@@ -486,8 +486,7 @@ int step_n(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G
 template <class T>
 int mass_launch(mpdata_ctx* c, const T* psi, const T* G, double* out) {
   MPD_LAUNCH(c, MPDATA_STAGE_MASS,
-             mpd::mass_partial_kernel<T><<<mpd::MASS_BLOCKS, mpd::MASS_THREADS, 0, c->stream>>>(
-                 c->g, psi, G, c->part));
+             mpd::mass_partial_launch<T>(c->g, psi, G, c->part, c->stream));
   MPD_LAUNCH(c, MPDATA_STAGE_MASS,
              mpd::mass_final_kernel<<<1, 1024, 0, c->stream>>>(c->part, mpd::MASS_BLOCKS, out));
   MPD_CHECK_LAUNCH(c, "mass kernels");

@@ -78,13 +78,22 @@ template <> struct MassAcc<float> { using type = MassAcc32; };
 // turn; the row bases are computed once per group and all 2R loads of a
 // point column are issued before its (fixed-order) accumulation.  Rows past
 // the end are skipped (a block-uniform test).
-template <class T>
+// V2: a thread takes two adjacent points of a row with one 2-element load
+// of each field (rows start on an even element: nx and h even), adding the
+// second point only inside the interior (the load past the last interior
+// point reads the first halo element, which is not added).
+template <class T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <class T, bool V2 = false>
 __global__ void __launch_bounds__(MASS_THREADS)
 mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
                     double* __restrict__ part) {
   __shared__ double sh[MASS_THREADS];
   using Acc = typename MassAcc<T>::type;
-  constexpr int R = Acc::R;
+  // (V2: half the rows a group, so a group still adds at most Acc::R points)
+  constexpr int R = V2 ? (Acc::R / 2 > 0 ? Acc::R / 2 : 1) : Acc::R;
   const int rows = g.ny * g.nz;
   // row r is (j, k) = (r % ny, r / ny); a step of gridDim.x rows moves (j, k)
   // by (dj, dk) with one carry, so only the first row takes a division
@@ -105,17 +114,38 @@ mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
         ++k;
       }
     }
-    for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
-      T a[R], b[R];
+    if constexpr (V2) {
+      using V = typename Vec2<T>::type;
+      for (int i = 2 * threadIdx.x; i < g.nx; i += 2 * blockDim.x) {
+        const bool two = i + 1 < g.nx;
+        V a[R], b[R];
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        a[q] = ok[q] ? psi[base[q] + i] : T(0);
-        b[q] = ok[q] ? G[base[q] + i] : T(0);
+        for (int q = 0; q < R; ++q) {
+          a[q] = ok[q] ? *reinterpret_cast<const V*>(psi + base[q] + i) : V{T(0), T(0)};
+          b[q] = ok[q] ? *reinterpret_cast<const V*>(G + base[q] + i) : V{T(0), T(0)};
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+          if (ok[q]) {  // rows past the end add nothing
+            acc.add(a[q].x, b[q].x);
+            if (two) acc.add(a[q].y, b[q].y);
+          }
+        }
+        acc.flush();
       }
+    } else {
+      for (int i = threadIdx.x; i < g.nx; i += blockDim.x) {
+        T a[R], b[R];
 #pragma unroll
-      for (int q = 0; q < R; ++q)
-        if (ok[q]) acc.add(a[q], b[q]);  // rows past the end add nothing
-      acc.flush();
+        for (int q = 0; q < R; ++q) {
+          a[q] = ok[q] ? psi[base[q] + i] : T(0);
+          b[q] = ok[q] ? G[base[q] + i] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          if (ok[q]) acc.add(a[q], b[q]);  // rows past the end add nothing
+        acc.flush();
+      }
     }
   }
   double b = block_fold(acc.s, sh);
@@ -129,6 +159,17 @@ mass_final_kernel(const double* __restrict__ part, int np, double* __restrict__ 
   for (int q = threadIdx.x; q < np; q += blockDim.x) s += part[q];
   double b = block_fold(s, sh);
   if (threadIdx.x == 0) *out = b;
+}
+
+// The first level of the reduction: the two-point form where every row
+// starts on an even element (nx and h even; the fields are 16-byte aligned).
+template <class T>
+inline void mass_partial_launch(const Geo& g, const T* psi, const T* G, double* part,
+                                cudaStream_t s) {
+  if (g.nx % 2 == 0 && g.h % 2 == 0)
+    mass_partial_kernel<T, true><<<MASS_BLOCKS, MASS_THREADS, 0, s>>>(g, psi, G, part);
+  else
+    mass_partial_kernel<T, false><<<MASS_BLOCKS, MASS_THREADS, 0, s>>>(g, psi, G, part);
 }
 
 }  // namespace mpd

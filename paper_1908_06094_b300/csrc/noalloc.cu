@@ -60,7 +60,7 @@ int partials_for_current_device(double** out) {
 template <class T>
 int launch(const mpd::Geo& g, const T* psi, const T* G, double* part, double* out,
            cudaStream_t s) {
-  mpd::mass_partial_kernel<T><<<mpd::MASS_BLOCKS, mpd::MASS_THREADS, 0, s>>>(g, psi, G, part);
+  mpd::mass_partial_launch<T>(g, psi, G, part, s);
   mpd::mass_final_kernel<<<1, 1024, 0, s>>>(part, mpd::MASS_BLOCKS, out);
   if (cudaGetLastError() != cudaSuccess) return MPDATA_ECUDA;
   return MPDATA_OK;
