@@ -1,10 +1,13 @@
 // fused2.cuh -- the one-kernel MPDATA step (iord = 2) with one thread per
 // column.
 //
-// Per level t of the march, five stages run on planes t+2, t+1, t+1, t, t:
+// Per level t of the march, five stages run on planes t+2, t+1, t+1, t, t-1:
 // A psi1 (donor pass), B pseudo-velocities, C limiter bounds and betas,
-// D limited face fluxes, E advance and halo images.  They are organised so
-// that almost every instruction is arithmetic:
+// D limited face fluxes, E advance and halo images.  A stage reads what an
+// earlier level wrote, except B (psi1 of plane t+2, from A) and C (Ut, Vt of
+// plane t+1, from B), so a level has two barriers: every shared ring holds
+// enough planes that a level's writes never land in a slot the same level
+// reads.  They are organised so that almost every instruction is arithmetic:
 //   * the CTA has one thread per column of the tile + 2 ring, (TX+4)(TY+4)
 //     threads; a thread keeps its own column's values (psi^n, U, V, W, G,
 //     psi1, the pseudo-velocities, the betas, the vertical fluxes) in
@@ -34,19 +37,19 @@ struct Layout {
   static constexpr int NT = SN;                                 // threads per CTA
   static constexpr int NRING = RN - SN;                         // radius-3 ring cells
   // offsets (in elements of T)
-  static constexpr int P0S = 0;             // psi^n, 2 planes, radius 3
-  static constexpr int US = P0S + 2 * RN;   // U, 2 planes, radius 3
-  static constexpr int VS = US + 2 * RN;    // V, 2 planes, radius 3
-  static constexpr int WS = VS + 2 * RN;    // W, 2 faces, radius 2
-  static constexpr int GS = WS + 2 * SN;    // G, 1 plane, radius 2
-  static constexpr int P1S = GS + SN;       // psi1, 4 planes
+  static constexpr int P0S = 0;             // psi^n, 4 planes, radius 3
+  static constexpr int US = P0S + 4 * RN;   // U, 4 planes, radius 3
+  static constexpr int VS = US + 4 * RN;    // V, 4 planes, radius 3
+  static constexpr int WS = VS + 4 * RN;    // W, 4 faces, radius 2
+  static constexpr int GS = WS + 4 * SN;    // G, 4 planes, radius 2
+  static constexpr int P1S = GS + 4 * SN;   // psi1, 4 planes
   static constexpr int UTS = P1S + 4 * SN;  // Ut, 1 plane
   static constexpr int VTS = UTS + SN;      // Vt, 1 plane
   static constexpr int BUS = VTS + SN;      // beta-up, 2 planes
   static constexpr int BDS = BUS + 2 * SN;  // beta-down, 2 planes
-  static constexpr int FXS = BDS + 2 * SN;  // x-face fluxes
-  static constexpr int FYS = FXS + SN;      // y-face fluxes
-  static constexpr int NVAL = FYS + SN;
+  static constexpr int FXS = BDS + 2 * SN;  // x-face fluxes, 2 planes
+  static constexpr int FYS = FXS + 2 * SN;  // y-face fluxes, 2 planes
+  static constexpr int NVAL = FYS + 2 * SN;
   static constexpr size_t bytes = (size_t)NVAL * sizeof(T);
 };
 
@@ -261,63 +264,81 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   T v1 = ld(V, t0 + 1, c0), v2 = ld(V, t0 + 2, c0), vn = ld(V, t0 + 3, c0);
   T w0 = ldw(t0, c0), w1 = ldw(t0 + 1, c0), w2 = ldw(t0 + 2, c0), wn = ldw(t0 + 3, c0);
   T g0 = ld(G, t0, c0), g1 = ld(G, t0 + 1, c0), g2 = ld(G, t0 + 2, c0), gn = ld(G, t0 + 3, c0);
-  T rp = zero, ru = zero, rv = zero;  // ring values of plane t+2
-  if (ringer) { rp = ld(P0, t0 + 2, rc0); ru = ld(U, t0 + 2, rc0); rv = ld(V, t0 + 2, rc0); }
+  T rp = zero, ru = zero, rv = zero;  // ring values of plane t+3
+  if (ringer) { rp = ld(P0, t0 + 3, rc0); ru = ld(U, t0 + 3, rc0); rv = ld(V, t0 + 3, rc0); }
   T q0 = zero, q1 = zero, q2 = zero;     // psi1 at t, t+1, t+2
   T utA = zero, vtA = zero, utB = zero, vtB = zero;  // Ut, Vt at t, t+1
   T wtA = zero, wtB = zero;              // Wt at faces t+1/2, t+3/2
   T buA = zero, bdA = zero, buB = zero, bdB = zero;  // betas at t, t+1
   constexpr bool kTapeR = TAPE && TapesReciprocals<T>::v;
   T riA = zero, roA = zero, riB = zero, roB = zero;  // their 1/(in+eps), 1/(out+eps) (FP64 tape)
-  T fzA = zero, fzB = zero;              // vertical fluxes at faces t-1/2, t+1/2
+  T fzAA = zero, fzA = zero, fzB = zero;  // vertical fluxes at faces t-3/2, t-1/2, t+1/2
 
-  // periodic k: the wrapped levels of planes t+3, t+4, t+5, advanced by one
+  // periodic k: the wrapped levels of planes t+4, t+5, advanced by one
   // level per plane (no division in the loop)
-  int l3 = clampk_(t0 + 3), l4 = clampk_(t0 + 4), l5 = clampk_(t0 + 5);
+  int l4 = clampk_(t0 + 4), l5 = clampk_(t0 + 5);
 
+  // Each level publishes the planes the next level's first stage reads
+  // (psi^n, U, V at t+3, W at face t+2, G at t+2), so a stage of level t
+  // reads only what level t-1 or an earlier stage of level t wrote: the
+  // slots of the planes published at level t are not read at level t.
+  // The march starts with the planes its first level reads.
   __syncthreads();  // the shared memory may still be read by a previous tile
+  {
+    const int a = t0 + 2;
+    p0s[(a & 3) * L::RN + s3] = p2;
+    us[(a & 3) * L::RN + s3] = u2;
+    vs[(a & 3) * L::RN + s3] = v2;
+    if (ringer) {
+      p0s[(a & 3) * L::RN + r3] = ld(P0, a, rc0);
+      us[(a & 3) * L::RN + r3] = ld(U, a, rc0);
+      vs[(a & 3) * L::RN + r3] = ld(V, a, rc0);
+    }
+    ws[((t0 + 1) & 3) * L::SN + s2] = w1;
+    gs[((t0 + 1) & 3) * L::SN + s2] = g1;
+  }
+  __syncthreads();
   // One level of the march.  STEADY: a level inside the chunk where every
   // stage runs and no vertical neighbour is clamped or closed, so the
   // stages' plane guards and the boundary clamps are compile-time true.
   auto level = [&](const int t, auto steady) {
     constexpr bool S = decltype(steady)::value;
-    // ---- publish plane t+2 of psi^n, U, V, face t+1 of W, plane t+1 of G --
+    // ---- publish plane t+3 of psi^n, U, V, face t+2 of W, plane t+2 of G --
+    // (read from level t+1 on: no barrier before stage A)
     {
-      const int a = t + 2;
-      p0s[(a & 1) * L::RN + s3] = p2;
-      us[(a & 1) * L::RN + s3] = u2;
-      vs[(a & 1) * L::RN + s3] = v2;
+      const int a = t + 3;
+      p0s[(a & 3) * L::RN + s3] = p3;
+      us[(a & 3) * L::RN + s3] = un;
+      vs[(a & 3) * L::RN + s3] = vn;
       if (ringer) {
-        p0s[(a & 1) * L::RN + r3] = rp;
-        us[(a & 1) * L::RN + r3] = ru;
-        vs[(a & 1) * L::RN + r3] = rv;
+        p0s[(a & 3) * L::RN + r3] = rp;
+        us[(a & 3) * L::RN + r3] = ru;
+        vs[(a & 3) * L::RN + r3] = rv;
       }
-      ws[((t + 1) & 1) * L::SN + s2] = w1;
-      gs[s2] = g1;
+      ws[((t + 2) & 3) * L::SN + s2] = w2;
+      gs[((t + 2) & 3) * L::SN + s2] = g2;
     }
     // loads one plane ahead (used from the next iteration on); the plane
     // offsets are the same for every thread
-    // (steady levels, zero-flux: planes t+3 .. t+5 are inside the grid and
+    // (steady levels, zero-flux: planes t+4 and t+5 are inside the grid and
     // the face t+4 is open)
     const Ix o5 = (Ix)(KPER ? l5 : (S ? t + 5 : clampk_(t + 5))) * pxy;
     const Ix o4 = (KPER || !S) ? (Ix)(KPER ? l4 : clampk_(t + 4)) * pxy : o5 - pxy;
-    const Ix o3 = (KPER || !S) ? (Ix)(KPER ? l3 : clampk_(t + 3)) * pxy : o4 - pxy;
     const T pn_next = P0[c0 + o5];
     const T un_next = U[c0 + o4], vn_next = V[c0 + o4], gn_next = G[c0 + o4];
     const T wn_next = (S || zface(t + 4)) ? W[c0 + o4] : zero;  // closed faces
     T rp_next = zero, ru_next = zero, rv_next = zero;
     if (ringer) {
-      rp_next = P0[rc0 + o3];
-      ru_next = U[rc0 + o3];
-      rv_next = V[rc0 + o3];
+      rp_next = P0[rc0 + o4];
+      ru_next = U[rc0 + o4];
+      rv_next = V[rc0 + o4];
     }
-    __syncthreads();
     // ---- A: psi1 on plane a = t+2 ---------------------------------------
     const int a = t + 2;
     if (S || (a >= max(klo, k0 - 3) && a <= min(khi, k1 + 1))) {
-      const T* pa = p0s + (a & 1) * L::RN + s3;
-      const T* ua = us + (a & 1) * L::RN + s3;
-      const T* va = vs + (a & 1) * L::RN + s3;
+      const T* pa = p0s + (a & 3) * L::RN + s3;
+      const T* ua = us + (a & 3) * L::RN + s3;
+      const T* va = vs + (a & 3) * L::RN + s3;
       const T fxp = donor(p2, pa[1], u2);
       const T fxm = donor(pa[-1], p2, ua[-1]);
       const T fyp = donor(p2, pa[RX], v2);
@@ -335,11 +356,11 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const int bp = S ? b + 1 : min(b + 1, khi), bm = S ? b - 1 : max(b - 1, klo);
       const T qp = (S || bp != b) ? q2 : q1;  // own psi1 at the clamped b+1
       const T qm = (S || bm != b) ? q0 : q1;  // own psi1 at the clamped b-1
-      const T* gb = gs + s2;
-      const T* vb = vs + (b & 1) * L::RN + s3;
-      const T* ub = us + (b & 1) * L::RN + s3;
-      const T* wb = ws + (b & 1) * L::SN + s2;
-      const T* wbm = ws + ((b - 1) & 1) * L::SN + s2;
+      const T* gb = gs + (b & 3) * L::SN + s2;
+      const T* vb = vs + (b & 3) * L::RN + s3;
+      const T* ub = us + (b & 3) * L::RN + s3;
+      const T* wb = ws + (b & 3) * L::SN + s2;
+      const T* wbm = ws + ((b - 1) & 3) * L::SN + s2;
       // DFL: the divergence of the Courant numbers of the cell at plane b,
       // own column (closed faces' W are 0 in the queue)
       const T dc = kDFL ? (u1 - ub[-1]) + (v1 - vb[-RX]) + (w1 - w0) : zero;
@@ -372,8 +393,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       if (inC) {  // z face (used on x in [-1, TX], y in [-1, TY])
         T res = zero;
         if (S || zface(b)) {  // a zero-flux top face is closed
-          const T* ub1 = us + ((b + 1) & 1) * L::RN + s3;
-          const T* vb1 = vs + ((b + 1) & 1) * L::RN + s3;
+          const T* ub1 = us + ((b + 1) & 3) * L::RN + s3;
+          const T* vb1 = vs + ((b + 1) & 3) * L::RN + s3;
           const T s1p = ap(P1(b + 1, 1)) + ap(P1(b, 1)), s1m = ap(P1(b + 1, -1)) + ap(P1(b, -1));
           const T s2p = ap(P1(b + 1, EX)) + ap(P1(b, EX));
           const T s2m = ap(P1(b + 1, -EX)) + ap(P1(b, -EX));
@@ -393,7 +414,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     if (LIMIT && inC && (S || (b >= max(klo, k0 - 1) && b <= min(khi, k1)))) {  // tile + 1
       const int bp = S ? b + 1 : min(b + 1, khi), bm = S ? b - 1 : max(b - 1, klo);
       const T qp = (S || bp != b) ? q2 : q1, qm = (S || bm != b) ? q0 : q1;
-      const T* pb = p0s + (b & 1) * L::RN + s3;
+      const T* pb = p0s + (b & 3) * L::RN + s3;
       const T pxm = P1(b, -1), pxp = P1(b, 1), pym = P1(b, -EX), pyp = P1(b, EX);
       const T vals[14] = {q1, p1, pb[-1], pb[1], pb[-RX], pb[RX], p0, p2,
                           pxm, pxp, pym, pyp, qm, qp};
@@ -414,7 +435,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       sm[L::BUS + (b & 1) * L::SN + s2] = buB;
       sm[L::BDS + (b & 1) * L::SN + s2] = bdB;
     }
-    __syncthreads();
+    // (no barrier: D reads the betas of plane t, written at level t-1, and
+    // its own betas of plane t+1; C and D share no other slot)
     // ---- D: limited donor fluxes of plane t and face t+1/2 ---------------
     if (inD && (S || (t >= max(klo, k0 - 1) && t <= k1 - 1))) {
       const T* bu0 = sm + L::BUS + (t & 1) * L::SN + s2;
@@ -433,10 +455,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       };
       T u = utA;  // used on x in [-1, TX-1], y in [0, TY-1]
       if (LIMIT) u = lim(u, P1(t, 1), bu0[1], bd0[1]);
-      fxs[s2] = cflux(q0, P1(t, 1), u);
+      fxs[(t & 1) * L::SN + s2] = cflux(q0, P1(t, 1), u);
       T v = vtA;  // used on x in [0, TX-1], y in [-1, TY-1]
       if (LIMIT) v = lim(v, P1(t, EX), bu0[EX], bd0[EX]);
-      fys[s2] = cflux(q0, P1(t, EX), v);
+      fys[(t & 1) * L::SN + s2] = cflux(q0, P1(t, EX), v);
       T f = zero, w = zero;
       if (S || zface(t)) {
         w = wtA;
@@ -463,14 +485,20 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         }
       }
     }
-    __syncthreads();
-    // ---- E: advance and write psi^(n+1) on plane t ------------------------
-    if ((S || t >= k0) && writes) {
-      const T fzm = (S || zface(t - 1)) ? fzA : zero;
-      const T r = q0 - ((fxs[s2] - fxs[s2 - 1]) + (fys[s2] - fys[s2 - EX]) + (fzB - fzm)) * rcp(g0);
+    // ---- E: advance and write psi^(n+1) on plane e = t-1 ------------------
+    // (one level behind D: its fluxes were written before this level's
+    // barriers, so no barrier separates D and E; psi1 and G of plane e come
+    // from the thread's own shared slots)
+    const int e = t - 1;
+    if ((S || e >= k0) && writes) {
+      const T* fx = fxs + (e & 1) * L::SN + s2;
+      const T* fy = fys + (e & 1) * L::SN + s2;
+      const T fzm = (S || zface(e - 1)) ? fzAA : zero;
+      const T r = P1(e, 0) - ((fx[0] - fx[-1]) + (fy[0] - fy[-EX]) + (fzA - fzm)) *
+                                 rcp(gs[(e & 3) * L::SN + s2]);
       // a steady level of a column without i-j images: one store
       if (S && !KPER && UNROLL == 1 && noimg) {
-        out[c0 + (Ix)t * pxy] = r;
+        out[c0 + (Ix)e * pxy] = r;
       } else {
       // the column's periodic images in the i-j halo (none on a slab: the
       // halo exchange fills a slab's halo)
@@ -480,17 +508,17 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
                                 : (OPENIJ ? 0 : ((gj < g.h) ? 1 : ((gj >= g.ny - g.h) ? -1 : 0)));
       // the value and its periodic images in the halo
       auto images = [&]() {
-        // the levels holding this value: t, and its k-halo images -- edge
+        // the levels holding this value: e, and its k-halo images -- edge
         // copies of the bottom and top levels, or under periodic k the
-        // levels t + m nz within [-h, nz + h)
-        int ilo = (t == 0) ? -g.h : t, ihi = (t == nz - 1) ? nz - 1 + g.h : t;
+        // levels e + m nz within [-h, nz + h)
+        int ilo = (e == 0) ? -g.h : e, ihi = (e == nz - 1) ? nz - 1 + g.h : e;
         if constexpr (KPER) {
-          ilo = t;
+          ilo = e;
           while (ilo - nz >= -g.h) ilo -= nz;
           ihi = nz - 1 + g.h;
         }
         for (int kk = ilo; kk <= ihi; kk += kper ? nz : 1) {
-          if (!kper && kk != t && kk >= 0 && kk < nz) continue;
+          if (!kper && kk != e && kk >= 0 && kk < nz) continue;
           const int64_t pk = g.off0 + (int64_t)kk * g.pxy;
           for (int a2 = 0; a2 <= (ni != 0); ++a2) {
             const int ii = gi + a2 * ni * g.nx;
@@ -503,8 +531,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       };
       // a value without images takes a single store
       if (ni == 0 && nj == 0 &&
-          (KPER ? t >= g.h && t < nz - g.h : (S || (t > 0 && t < nz - 1))))
-        out[c0 + (Ix)t * pxy] = r;
+          (KPER ? e >= g.h && e < nz - g.h : (S || (e > 0 && e < nz - 1))))
+        out[c0 + (Ix)e * pxy] = r;
       else
         images();
       }
@@ -520,35 +548,37 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
     utA = utB; vtA = vtB; wtA = wtB;
     buA = buB; bdA = bdB;
     if (kTapeR) { riA = riB; roA = roB; }
-    fzA = fzB;
-    if constexpr (KPER) { l3 = l4; l4 = l5; l5 = l5 + 1 == nz ? 0 : l5 + 1; }
+    fzAA = fzA; fzA = fzB;
+    if constexpr (KPER) { l4 = l5; l5 = l5 + 1 == nz ? 0 : l5 + 1; }
   };
   // The single-domain march runs its steady levels without guards (FP32
   // 512x512x128: 989 -> 945 us per launch); the batch's unrolled march
   // keeps every level guarded (its steady groups spilled at the register
   // cap and measured 6 % slower).
   if constexpr (UNROLL == 1) {
-    // the levels where every guard holds: zero-flux, t in [max(k0, 1),
-    // min(k1 - 1, nz - 6)] (no stage reaches below plane 0 or the top two
+    // the levels where every guard holds: zero-flux, t in [max(k0 + 1, 2),
+    // min(k1 - 1, nz - 6)] (stage E advances a plane of the chunk with an
+    // open face below it, no stage reaches below plane 0 or the top two
     // planes, and the loads one plane ahead stay below the top); periodic
-    // in k, the whole chunk
-    const int tS = KPER ? k0 : max(k0, 1), tE = KPER ? k1 - 1 : min(k1 - 1, nz - 6);
+    // in k, the chunk but its first level.  The last level, t = k1, runs
+    // stage E alone.
+    const int tS = KPER ? k0 + 1 : max(k0 + 1, 2), tE = KPER ? k1 - 1 : min(k1 - 1, nz - 6);
     int t = t0;
-    for (; t < tS && t < k1; ++t) level(t, std::false_type{});
+    for (; t < tS && t <= k1; ++t) level(t, std::false_type{});
     for (; t <= tE; ++t) level(t, std::true_type{});
-    for (; t < k1; ++t) level(t, std::false_type{});
+    for (; t <= k1; ++t) level(t, std::false_type{});
   } else {
-    for (int tg = t0; tg < k1; tg += UNROLL) {
+    for (int tg = t0; tg <= k1; tg += UNROLL) {
 #pragma unroll
       for (int u = 0; u < UNROLL; ++u) {
         const int t = tg + u;
-        if (t >= k1) break;  // uniform over the CTA
+        if (t > k1) break;  // uniform over the CTA
         level(t, std::false_type{});
       }
     }
   }
-  // The next level publishes into slots nobody reads after this point of
-  // the current one; its first barrier orders the rest.
+  // The next tile's march (the batch's items) starts with a barrier before
+  // it publishes its first planes.
 }
 
 template <class T, int TX, int TY, int MINB, bool LIMIT, bool TAPE = false, bool KPER = false,
