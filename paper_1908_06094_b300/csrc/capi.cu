@@ -15,6 +15,7 @@
 #include "march.cuh"
 #include "exchange.cuh"
 #include "fused2.cuh"
+#include "fusedx.cuh"
 #include "adjoint.cuh"
 
 using mpd::Geo;
@@ -32,6 +33,9 @@ struct mpdata_ctx {
   double* part;
   // fused kernel launch shape (chosen in init)
   int fused_ok, nchunks, kchunk;
+  // the two-column FP32 kernel's launch shape (x2_ok: it runs the untaped
+  // FP32 step)
+  int x2_ok, x2_nchunks, x2_kchunk;
   // level-chunk lengths of the k-marching kernels (0: not chosen yet)
   int kc_fwd, kc_rev;
   // the adjoint's accumulators (psi^n-bar, beta adjoints) are known to be
@@ -371,12 +375,72 @@ constexpr int fused_threads() {
   return (F::TX + 4) * (F::TY + 4);
 }
 
+// Split k into chunks when there are too few column tiles to load every
+// SM: an SM's time ~ (CTAs it runs) x (levels per chunk + the ~4 extra
+// planes each chunk recomputes at its start); take the cheapest split.
+// Returns the chunk count; *kchunk its length.
+int pick_chunks(const Geo& g, long ctas, int sms, int* kchunk) {
+  long best_n = 1;
+  double best_cost = 1e300;
+  for (long n = 1; n <= g.nz; ++n) {
+    const long kc = (g.nz + n - 1) / n;
+    const long nn = (g.nz + kc - 1) / kc;
+    const long per_sm = (ctas * nn + sms - 1) / sms;
+    const double cost = (double)per_sm * (kc + 4);
+    if (cost < best_cost - 1e-9) { best_cost = cost; best_n = nn; }
+  }
+  *kchunk = (int)((g.nz + best_n - 1) / best_n);
+  return (g.nz + *kchunk - 1) / *kchunk;
+}
+
+// The two-column FP32 step (fusedx.cuh): its tile (32 x 24 columns, 504
+// threads of two columns, up to 128 registers) and instances.  Zero-flux
+// only: the periodic-k instance needs more registers at this tile (it
+// spilled and ran slower than the one-column kernel).
+struct FusedX { static constexpr int TX = 32, TY = 24, MINB = 1; };
+template <bool LIMIT>
+auto fusedx_ptr() {
+  return mpd::fusedx::step_kernel_x2<FusedX::TX, FusedX::TY, FusedX::MINB, LIMIT, false>;
+}
+auto fusedx_pick(const mpdata_ctx* c) {
+  return c->nonosc ? fusedx_ptr<true>() : fusedx_ptr<false>();
+}
+constexpr int fusedx_threads() { return mpd::fusedx::PairMap<FusedX::TX, FusedX::TY>::NT; }
+constexpr size_t fusedx_smem() { return mpd::fusedx::Layout<FusedX::TX, FusedX::TY>::bytes; }
+
+// Whether the two-column kernel can run this context's untaped step: FP32,
+// no options, the periodic i-j domain, zero-flux in k, pairs of columns on 8-byte
+// boundaries (even nx and halo: even row length and interior offset) and
+// 32-bit offsets.
+void fusedx_setup(mpdata_ctx* c) {
+  const Geo& g = c->g;
+  c->x2_ok = 0;
+  if (c->dtype != MPDATA_F32 || c->opts != 0 || g.openij || g.kper || g.nx % 2 != 0 ||
+      g.h % 2 != 0 || g.total >= ((int64_t)1 << 31))
+    return;
+  auto k = fusedx_pick(c);
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fusedx_smem()) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  int occ = 0, sms = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, fusedx_threads(), fusedx_smem());
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+  cudaGetLastError();
+  if (occ < 1) return;
+  const long ctas = (long)((g.nx + FusedX::TX - 1) / FusedX::TX) * ((g.ny + FusedX::TY - 1) / FusedX::TY);
+  c->x2_nchunks = pick_chunks(g, ctas, sms, &c->x2_kchunk);
+  c->x2_ok = 1;
+}
+
 // Pick the k-chunking so that the grid covers the GPU about twice.
 template <class T>
 int fused_setup(mpdata_ctx* c) {
   using F = FusedShape<T>;
   const Geo& g = c->g;
   c->fused_ok = 0;
+  c->x2_ok = 0;
   // the periodic images a column writes need nx, ny >= 2h; a slab writes
   // none and needs only an interior as wide as the strips it sends
   const int minw = g.openij ? g.h : 2 * g.h;
@@ -396,22 +460,9 @@ int fused_setup(mpdata_ctx* c) {
   cudaGetLastError();
   if (occ < 1) return MPDATA_OK;
   const long ctas = (long)((g.nx + F::TX - 1) / F::TX) * ((g.ny + F::TY - 1) / F::TY);
-  // Split k into chunks when there are too few column tiles to load every
-  // SM: an SM's time ~ (CTAs it runs) x (levels per chunk + the ~4 extra
-  // planes each chunk recomputes at its start); take the cheapest split.
-  long best_n = 1;
-  double best_cost = 1e300;
-  for (long n = 1; n <= g.nz; ++n) {
-    const long kc = (g.nz + n - 1) / n;
-    const long nn = (g.nz + kc - 1) / kc;
-    const long per_sm = (ctas * nn + sms - 1) / sms;
-    const double cost = (double)per_sm * (kc + 4);
-    if (cost < best_cost - 1e-9) { best_cost = cost; best_n = nn; }
-  }
-  c->nchunks = (int)best_n;
-  c->kchunk = (g.nz + c->nchunks - 1) / c->nchunks;
-  c->nchunks = (g.nz + c->kchunk - 1) / c->kchunk;
+  c->nchunks = pick_chunks(g, ctas, sms, &c->kchunk);
   c->fused_ok = 1;
+  fusedx_setup(c);
   return MPDATA_OK;
 }
 
@@ -422,6 +473,22 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
                  const T* G, const mpd::fused2::TapeOut<T>* tape = nullptr) {
   using F = FusedShape<T>;
   const Geo& g = c->g;
+  if constexpr (std::is_same<T, float>::value) {
+    // the two-column kernel (the same bits) reads and writes 8-byte pairs:
+    // every field must start on an 8-byte boundary
+    auto al8 = [](const void* p) { return ((uintptr_t)p & 7) == 0; };
+    if (!tape && c->x2_ok && c->opts == 0 && !g.openij && !g.kper && al8(in) && al8(out) && al8(U) &&
+        al8(V) && al8(W) && al8(G)) {
+      dim3 gx((g.nx + FusedX::TX - 1) / FusedX::TX, (g.ny + FusedX::TY - 1) / FusedX::TY,
+              c->x2_nchunks);
+      auto kx = fusedx_pick(c);
+      MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+                 kx<<<gx, fusedx_threads(), fusedx_smem(), c->stream>>>(g, c->x2_kchunk, in, U, V,
+                                                                        W, G, out));
+      MPD_CHECK_LAUNCH(c, "fused step kernel");
+      return MPDATA_OK;
+    }
+  }
   dim3 grid((g.nx + F::TX - 1) / F::TX, (g.ny + F::TY - 1) / F::TY, c->nchunks);
   const size_t bytes = fused_smem<T>();
   const mpd::fused2::TapeOut<T> tp = tape ? *tape : mpd::fused2::TapeOut<T>{};

@@ -345,7 +345,9 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T fym = donor(pa[-RX], p2, va[-RX]);
       const T fzp = donor(p2, p3, w2);  // w2 = 0 on a zero-flux top face
       const T fzm = donor(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
-      q2 = p2 - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) * rcp(g2);
+      // psi - div * (1/G), one rounding: the negated divergence is formed
+      // exactly (every difference and sum negated) and fused in
+      q2 = fma_rn((fxm - fxp) + (fym - fyp) + (fzm - fzp), rcp(g2), p2);
       P1(a, 0) = q2;
     }
     __syncthreads();
@@ -494,8 +496,8 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T* fx = fxs + (e & 1) * L::SN + s2;
       const T* fy = fys + (e & 1) * L::SN + s2;
       const T fzm = (S || zface(e - 1)) ? fzAA : zero;
-      const T r = P1(e, 0) - ((fx[0] - fx[-1]) + (fy[0] - fy[-EX]) + (fzA - fzm)) *
-                                 rcp(gs[(e & 3) * L::SN + s2]);
+      const T r = fma_rn((fx[-1] - fx[0]) + (fy[-EX] - fy[0]) + (fzm - fzA),
+                         rcp(gs[(e & 3) * L::SN + s2]), P1(e, 0));
       // a steady level of a column without i-j images: one store
       if (S && !KPER && UNROLL == 1 && noimg) {
         out[c0 + (Ix)e * pxy] = r;

@@ -64,6 +64,10 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 __device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 
 // Sign tests on the bit pattern (integer pipe): on the B300 the FP64 pipe
 // issues 2 lanes per SM per clock, so compares and min/max of doubles are
@@ -214,19 +218,22 @@ __device__ __forceinline__ T limit_face(T Ut, T buL, T bdL, T buR, T bdR) {
 // Ut = (|U| - U^2/Gf) A - U (Vbar B1 + Wbar B2)/Gf with A = (pr-pl)/(pr+pl+eps),
 // B = (1/2)(s+ - s-)/(s+ + s- + eps), Vbar = vsum/4 (Smolarkiewicz 1984,
 // G-weighted as in Smolarkiewicz & Margolin 1998).  The factors 1/2 and 1/4
-// are applied as one exact 1/8 scaling.
+// are applied as one exact 1/8 scaling.  Every operation is explicitly
+// rounded (no contraction left to the compiler), so the two-lane form of
+// the FP32 step (fusedx.cuh) evaluates the same sequence and gives the same
+// bits.
 template <class T>
 __device__ __forceinline__ T pseudo_velocity(T U, T gsum, T pl, T pr, T s1p, T s1m, T s2p,
                                              T s2m, T vsum, T wsum) {
   const T eps = Eps<T>::v;
-  const T rG = T(2) * rcp(gsum);                       // 1/Gf
-  const T A = (pr - pl) * rcp(pr + pl + eps);
-  const T B1 = (s1p - s1m) * rcp(s1p + s1m + eps);     // 2 B1
-  const T B2 = (s2p - s2m) * rcp(s2p + s2m + eps);     // 2 B2
-  const T q = U * rG;
-  const T diff = absv(U) - U * q;                      // |U| - U^2/Gf
-  const T cross = T(0.125) * (vsum * B1 + wsum * B2);  // Vbar B1 + Wbar B2
-  return diff * A - q * cross;
+  const T rG = mul_rn(T(2), rcp(gsum));                                   // 1/Gf
+  const T A = mul_rn(sub_rn(pr, pl), rcp(add_rn(add_rn(pr, pl), eps)));
+  const T B1 = mul_rn(sub_rn(s1p, s1m), rcp(add_rn(add_rn(s1p, s1m), eps)));  // 2 B1
+  const T B2 = mul_rn(sub_rn(s2p, s2m), rcp(add_rn(add_rn(s2p, s2m), eps)));  // 2 B2
+  const T q = mul_rn(U, rG);
+  const T diff = fma_rn(-U, q, absv(U));                                  // |U| - U^2/Gf
+  const T cross = mul_rn(T(0.125), fma_rn(vsum, B1, mul_rn(wsum, B2)));   // Vbar B1 + Wbar B2
+  return fma_rn(diff, A, -mul_rn(q, cross));
 }
 
 // Corrective-pass options (bit flags; the MPDATA literature's variants).
