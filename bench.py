@@ -326,7 +326,7 @@ def job_throughput(ms_local: float, units_local: float, ws: int, device=None):
 # figure taken with ncu stays valid while these files are unchanged.
 STAGE_SOURCES = {
     "pseudo": ("march.cuh", "grid.cuh"),                # FP64 k-marching pseudo-velocity
-    "fused": ("fused2.cuh", "grid.cuh", "capi.cu"),     # FP32 fused step (+ its chunking)
+    "fused": ("fusedx.cuh", "fused2.cuh", "grid.cuh", "capi.cu"),  # FP32 fused step (+ its chunking)
     "edge": ("edge.cuh", "edge.cu", "grid.cuh"),        # edge-based flux stages
 }
 

@@ -398,12 +398,13 @@ int pick_chunks(const Geo& g, long ctas, int sms, int* kchunk) {
 // only: the periodic-k instance needs more registers at this tile (it
 // spilled and ran slower than the one-column kernel).
 struct FusedX { static constexpr int TX = 32, TY = 24, MINB = 1; };
-template <bool LIMIT>
+template <bool LIMIT, bool TAPE>
 auto fusedx_ptr() {
-  return mpd::fusedx::step_kernel_x2<FusedX::TX, FusedX::TY, FusedX::MINB, LIMIT, false>;
+  return mpd::fusedx::step_kernel_x2<FusedX::TX, FusedX::TY, FusedX::MINB, LIMIT, false, TAPE>;
 }
+template <bool TAPE = false>
 auto fusedx_pick(const mpdata_ctx* c) {
-  return c->nonosc ? fusedx_ptr<true>() : fusedx_ptr<false>();
+  return c->nonosc ? fusedx_ptr<true, TAPE>() : fusedx_ptr<false, TAPE>();
 }
 constexpr int fusedx_threads() { return mpd::fusedx::PairMap<FusedX::TX, FusedX::TY>::NT; }
 constexpr size_t fusedx_smem() { return mpd::fusedx::Layout<FusedX::TX, FusedX::TY>::bytes; }
@@ -420,6 +421,8 @@ void fusedx_setup(mpdata_ctx* c) {
     return;
   auto k = fusedx_pick(c);
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fusedx_smem()) != cudaSuccess ||
+      cudaFuncSetAttribute(fusedx_pick<true>(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)fusedx_smem()) != cudaSuccess) {
     cudaGetLastError();
     return;
@@ -477,14 +480,24 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
     // the two-column kernel (the same bits) reads and writes 8-byte pairs:
     // every field must start on an 8-byte boundary
     auto al8 = [](const void* p) { return ((uintptr_t)p & 7) == 0; };
-    if (!tape && c->x2_ok && c->opts == 0 && !g.openij && !g.kper && al8(in) && al8(out) && al8(U) &&
-        al8(V) && al8(W) && al8(G)) {
+    // (the taped step: its fields tstride elements apart from psi1, each on
+    // an 8-byte boundary)
+    const long long tstride = tape ? (long long)(tape->ut - tape->p1) : 0;
+    if (c->x2_ok && c->opts == 0 && !g.openij && !g.kper && al8(in) && al8(out) && al8(U) &&
+        al8(V) && al8(W) && al8(G) && (!tape || (al8(tape->p1) && tstride % 2 == 0))) {
       dim3 gx((g.nx + FusedX::TX - 1) / FusedX::TX, (g.ny + FusedX::TY - 1) / FusedX::TY,
               c->x2_nchunks);
-      auto kx = fusedx_pick(c);
-      MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
-                 kx<<<gx, fusedx_threads(), fusedx_smem(), c->stream>>>(g, c->x2_kchunk, in, U, V,
-                                                                        W, G, out));
+      if (tape) {
+        auto kx = fusedx_pick<true>(c);
+        MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+                   kx<<<gx, fusedx_threads(), fusedx_smem(), c->stream>>>(
+                       g, c->x2_kchunk, in, U, V, W, G, out, tape->p1, tstride));
+      } else {
+        auto kx = fusedx_pick(c);
+        MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+                   kx<<<gx, fusedx_threads(), fusedx_smem(), c->stream>>>(
+                       g, c->x2_kchunk, in, U, V, W, G, out, nullptr, 0));
+      }
       MPD_CHECK_LAUNCH(c, "fused step kernel");
       return MPDATA_OK;
     }

@@ -183,11 +183,16 @@ struct PairMap {
   }
 };
 
-template <int TX, int TY, int MINB, bool LIMIT, bool KPER>
+// TAPE: the step also writes the intermediates of its interior cells (the
+// adjoint's tape), each a padded field like psi, tstride elements apart from
+// tape (psi1): psi1, Ut, Vt, Wt, beta-up, beta-down at slots 0..5 and the
+// limited Ul, Vl, Wl at slots 8..10 (slots 6 and 7 are FP64's reciprocals).
+template <int TX, int TY, int MINB, bool LIMIT, bool KPER, bool TAPE = false>
 __global__ void __launch_bounds__(PairMap<TX, TY>::NT, MINB)
 step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __restrict__ U,
                const float* __restrict__ V, const float* __restrict__ W,
-               const float* __restrict__ G, float* __restrict__ out) {
+               const float* __restrict__ G, float* __restrict__ out,
+               float* __restrict__ tape, long long tstride) {
   using L = Layout<TX, TY>;
   using Map = PairMap<TX, TY>;
   constexpr int EX = L::EX, RX = L::RX;
@@ -440,13 +445,30 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
       f2 v = vtA;
       if (LIMIT) v = limit2(v, buA, bdA, at2(bu0 + EX), at2(bd0 + EX));
       st2(fys + (t & 1) * L::SN + s2, donor2(q0, at2(pt + EX), v));
-      f2 f = zero2;
+      f2 f = zero2, w = zero2;
       if (S || zface(t)) {
-        f2 w = wtA;
+        w = wtA;
         if (LIMIT) w = limit2(w, buA, bdA, buB, bdB);
         f = donor2(q0, q1, w);
       }
       fzB = f;
+      if constexpr (TAPE) {
+        if (t >= k0 && (wr0 || wr1)) {
+          constexpr int NF = LIMIT ? 9 : 4;
+          const f2 tv[9] = {q0, utA, vtA, wtA, buA, bdA, u, v, w};  // Wt, Wl: 0 on the top face
+          float* tq = tape + c0 + t * pxy;
+#pragma unroll
+          for (int z = 0; z < NF; ++z) {
+            float* d = tq + (long long)(z < 6 ? z : z + 2) * tstride;
+            if (wr0 && wr1) {
+              st2(d, tv[z]);
+            } else {
+              if (wr0) d[0] = tv[z].x;
+              if (wr1) d[1] = tv[z].y;
+            }
+          }
+        }
+      }
     }
     // ---- E: advance and write psi^(n+1) on plane e = t-1 ------------------
     const int e = t - 1;
