@@ -275,16 +275,21 @@ MPDATA_API int mpdata_batch_init(mpdata_batch **out, const mpdata_domain_desc *d
 MPDATA_API int mpdata_batch_step(mpdata_batch *b, int direction, int use_graph);
 
 /* Tile shape (index into the compiled shapes: FP32 32x16, 64x8, 32x8,
- * 16x16; FP64 32x8, 16x16, 16x8; one thread per column of the tile and a
- * 2-cell ring) and level-chunk length (0 = whole columns).  Setting waits
- * for the stream and drops captured graphs. */
+ * 16x16, and 32x8, 32x12 with two tracers per item (4, 5: each thread
+ * advances one column of two tracers of the domain; a field of fewer than
+ * 2^31 elements, else ERANGE); FP64 32x8, 16x16, 16x8; one thread per
+ * column of the tile and a 2-cell ring) and level-chunk length (0 = whole
+ * columns).  Setting waits for the stream and drops captured graphs.
+ * Errors: EINVAL, ERANGE (the shape cannot take this batch; the previous
+ * configuration stays), ECUDA. */
 MPDATA_API int mpdata_batch_set_config(mpdata_batch *b, int shape, int kchunk_levels);
 MPDATA_API int mpdata_batch_get_config(mpdata_batch *b, int *shape, int *kchunk_levels,
                                        int *tile_x, int *tile_y, int *threads,
                                        long long *items);
 
-/* Time every shape x chunk length (0, 32, 16, 8) over reps steps and keep
- * the fastest; *best_ms gets its time per step.  It runs steps on the
+/* Time every shape x chunk length (0, 32, 16, 8) over reps steps (the
+ * shapes that can take the batch) and keep the fastest; *best_ms gets its
+ * time per step.  It runs steps on the
  * batch's buffers, so their contents change.  Errors: EINVAL, ECUDA. */
 MPDATA_API int mpdata_batch_autotune(mpdata_batch *b, int reps, double *best_ms);
 

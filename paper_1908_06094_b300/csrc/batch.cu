@@ -25,6 +25,7 @@
 
 #include "../../include/mpdata.h"
 #include "fused2.cuh"
+#include "fusedt.cuh"
 #include "grid.cuh"
 
 using mpd::Geo;
@@ -39,6 +40,7 @@ struct BDom {
   long long item0;   // first work item of this domain
   long long tstride; // elements between consecutive tracers
   int ntr, tx, ty, nch, kchunk;
+  int nit;           // items of one tile and chunk: ntr, or (ntr + 1) / 2 tracer pairs
 };
 
 __device__ __forceinline__ int find_domain(const BDom* __restrict__ d, int nd, long long item) {
@@ -82,25 +84,64 @@ batch_kernel(const BDom* __restrict__ dom, int nd, long long nitems, int* counte
   }
 }
 
+// The same for tracer pairs (FP32, fusedt.cuh): an item is a tile and chunk
+// of two tracers of one domain.
+template <int TX, int TY, int MINB, bool LIMIT>
+__global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
+batch_kernel_t2(const BDom* __restrict__ dom, int nd, long long nitems, int* counter, int dir) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ long long s_item;
+  for (;;) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const long long it = s_item;
+    if (it >= nitems) break;
+    const int d = find_domain(dom, nd, it);
+    const BDom& b = dom[d];
+    long long r = it - b.item0;
+    const int tp = (int)(r % b.nit);
+    r /= b.nit;
+    const int ch = (int)(r % b.nch);
+    const int tile = (int)(r / b.nch);
+    const int tx = tile % b.tx, ty = tile / b.tx;
+    const int ta = 2 * tp, tb = min(2 * tp + 1, b.ntr - 1);
+    const float* src = (const float*)(dir == 0 ? b.pa : (const void*)b.pb);
+    float* dst = (float*)(dir == 0 ? b.pb : (void*)b.pa);
+    const int k0 = ch * b.kchunk;
+    mpd::fusedt::step_tile_t2<TX, TY, LIMIT>(
+        b.g, tx * TX, ty * TY, k0, min(b.g.nz, k0 + b.kchunk), src + ta * b.tstride,
+        src + tb * b.tstride, (const float*)b.u, (const float*)b.v, (const float*)b.w,
+        (const float*)b.gm, dst + ta * b.tstride, dst + tb * b.tstride, ta != tb, smem_raw);
+    // step_tile_t2 begins with a barrier (s_item is read before it)
+  }
+}
+
 // Compiled tile shapes the autotuner chooses from.
 struct Shape {
   int tx, ty, nt;
+  int pair;  // items of two tracers (FP32)
 };
 // one thread per column of the tile + 2 ring: nt = (tx+4)(ty+4)
-constexpr Shape kShapes32[] = {{32, 16, 720}, {64, 8, 816}, {32, 8, 432}, {16, 16, 400}};
-constexpr Shape kShapes64[] = {{32, 8, 432}, {16, 16, 400}, {16, 8, 240}};
-constexpr int kNShapes32 = 4, kNShapes64 = 3;
+constexpr Shape kShapes32[] = {{32, 16, 720, 0}, {64, 8, 816, 0}, {32, 8, 432, 0},
+                               {16, 16, 400, 0}, {32, 8, 432, 1},  {32, 12, 576, 1}};
+constexpr Shape kShapes64[] = {{32, 8, 432, 0}, {16, 16, 400, 0}, {16, 8, 240, 0}};
+constexpr int kNShapes32 = 6, kNShapes64 = 3;
 
 template <class T, int S> struct ShapeOf;
-#define MPD_SHAPE(TT, S, X, Y, N) \
-  template <> struct ShapeOf<TT, S> { static constexpr int TX = X, TY = Y, NT = N; };
-MPD_SHAPE(float, 0, 32, 16, 720)
-MPD_SHAPE(float, 1, 64, 8, 816)
-MPD_SHAPE(float, 2, 32, 8, 432)
-MPD_SHAPE(float, 3, 16, 16, 400)
-MPD_SHAPE(double, 0, 32, 8, 432)
-MPD_SHAPE(double, 1, 16, 16, 400)
-MPD_SHAPE(double, 2, 16, 8, 240)
+#define MPD_SHAPE(TT, S, X, Y, N, P) \
+  template <> struct ShapeOf<TT, S> {  \
+    static constexpr int TX = X, TY = Y, NT = N; \
+    static constexpr bool PAIR = P;    \
+  };
+MPD_SHAPE(float, 0, 32, 16, 720, false)
+MPD_SHAPE(float, 1, 64, 8, 816, false)
+MPD_SHAPE(float, 2, 32, 8, 432, false)
+MPD_SHAPE(float, 3, 16, 16, 400, false)
+MPD_SHAPE(float, 4, 32, 8, 432, true)
+MPD_SHAPE(float, 5, 32, 12, 576, true)
+MPD_SHAPE(double, 0, 32, 8, 432, false)
+MPD_SHAPE(double, 1, 16, 16, 400, false)
+MPD_SHAPE(double, 2, 16, 8, 240, false)
 #undef MPD_SHAPE
 
 }  // namespace
@@ -132,13 +173,17 @@ template <class T, int S, bool LIMIT>
 const void* kernel_ptr() {
   using Sh = ShapeOf<T, S>;
   constexpr int MINB = 1;
-  return reinterpret_cast<const void*>(&batch_kernel<T, Sh::TX, Sh::TY, Sh::NT, MINB, LIMIT>);
+  if constexpr (Sh::PAIR)
+    return reinterpret_cast<const void*>(&batch_kernel_t2<Sh::TX, Sh::TY, MINB, LIMIT>);
+  else
+    return reinterpret_cast<const void*>(&batch_kernel<T, Sh::TX, Sh::TY, Sh::NT, MINB, LIMIT>);
 }
 
 template <class T, int S>
 size_t smem_of() {
   using Sh = ShapeOf<T, S>;
-  return mpd::fused2::Layout<T, Sh::TX, Sh::TY>::bytes;
+  if constexpr (Sh::PAIR) return mpd::fusedt::Layout<Sh::TX, Sh::TY>::bytes;
+  else return mpd::fused2::Layout<T, Sh::TX, Sh::TY>::bytes;
 }
 
 template <class T>
@@ -148,7 +193,9 @@ void shape_info(int s, bool limit, const void** k, size_t* smem, int* nt, int* t
       case 0: *k = limit ? kernel_ptr<T, 0, true>() : kernel_ptr<T, 0, false>(); *smem = smem_of<T, 0>(); break;
       case 1: *k = limit ? kernel_ptr<T, 1, true>() : kernel_ptr<T, 1, false>(); *smem = smem_of<T, 1>(); break;
       case 2: *k = limit ? kernel_ptr<T, 2, true>() : kernel_ptr<T, 2, false>(); *smem = smem_of<T, 2>(); break;
-      default: *k = limit ? kernel_ptr<T, 3, true>() : kernel_ptr<T, 3, false>(); *smem = smem_of<T, 3>(); break;
+      case 3: *k = limit ? kernel_ptr<T, 3, true>() : kernel_ptr<T, 3, false>(); *smem = smem_of<T, 3>(); break;
+      case 4: *k = limit ? kernel_ptr<T, 4, true>() : kernel_ptr<T, 4, false>(); *smem = smem_of<T, 4>(); break;
+      default: *k = limit ? kernel_ptr<T, 5, true>() : kernel_ptr<T, 5, false>(); *smem = smem_of<T, 5>(); break;
     }
     *nt = kShapes32[s].nt; *tx = kShapes32[s].tx; *ty = kShapes32[s].ty;
   } else {
@@ -182,8 +229,7 @@ int configure(mpdata_batch* b, int shape, int kchunk_levels) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, nt, smem);
   if (e != cudaSuccess || occ < 1) return bfail(b, e, "occupancy");
   std::vector<BDom> tab(b->nd);
-  const size_t esize = b->dtype == MPDATA_F64 ? 8 : 4;
-  (void)esize;
+  const bool pair = b->dtype == MPDATA_F32 && kShapes32[shape].pair;
   long long item = 0;
   for (int d = 0; d < b->nd; ++d) {
     const mpdata_domain_desc& h = b->host[d];
@@ -197,8 +243,11 @@ int configure(mpdata_batch* b, int shape, int kchunk_levels) {
     t.ty = (h.ny + ty - 1) / ty;
     t.kchunk = kchunk_levels > 0 && kchunk_levels < h.nz ? kchunk_levels : h.nz;
     t.nch = (h.nz + t.kchunk - 1) / t.kchunk;
+    t.nit = pair ? (t.ntr + 1) / 2 : t.ntr;
+    // tracer pairs address a field with 32-bit offsets
+    if (pair && t.g.total >= ((int64_t)1 << 31)) return MPDATA_ERANGE;
     t.item0 = item;
-    item += (long long)t.tx * t.ty * t.nch * t.ntr;
+    item += (long long)t.tx * t.ty * t.nch * t.nit;
   }
   // the work counter is a 32-bit int that every CTA bumps once past the
   // last item before it exits, so it climbs to nitems + grid - 1
@@ -342,7 +391,10 @@ int mpdata_batch_autotune(mpdata_batch* b, int reps, double* best_ms) {
   int rc = MPDATA_OK;
   for (int s = 0; s < nshapes(b->dtype) && rc == MPDATA_OK; ++s)
     for (int c = 0; c < 4 && rc == MPDATA_OK; ++c) {
-      if ((rc = mpdata_batch_set_config(b, s, chunks[c]))) break;
+      if ((rc = mpdata_batch_set_config(b, s, chunks[c]))) {
+        if (rc == MPDATA_ERANGE) { rc = MPDATA_OK; break; }  // not for this batch's sizes
+        break;
+      }
       if ((rc = launch_once(b, 0))) break;  // warm-up
       cudaEventRecord(e0, b->stream);
       for (int r = 0; r < reps && rc == MPDATA_OK; ++r) rc = launch_once(b, r & 1);
