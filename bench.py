@@ -437,9 +437,15 @@ def run_ours(args, wl_name):
     stream = torch.cuda.current_stream(dev)
     npts = wl["nx"] * wl["ny"] * wl["nz"]
 
+    # the state double-buffered (mpdata_step_out), as a caller keeps it: the
+    # one-kernel step cannot run in place, and mpdata_step with nsteps = 1
+    # would add a copy back into psi
+    state = [d[0], torch.empty_like(d[0])]
+
     def step():
-        m.step(*d, nsteps=1)
-        m.mass(d[0], d[4], out=mass_out)
+        m.step_out(state[0], state[1], *d[1:])
+        state.reverse()
+        m.mass(state[0], d[4], out=mass_out)
 
     m0 = m.mass(d[0], d[4]).item()
     for _ in range(args.warmup):
@@ -736,8 +742,16 @@ def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
     npts = wl["nx"] * wl["ny"] * wl["nz"]
     out_mass = torch.empty((), dtype=torch.float64, device=dev)
     m0 = m.mass(d[0], d[4]).item()
+    # the state double-buffered, as a caller of mpdata_step_out keeps it (a
+    # one-kernel step cannot run in place: mpdata_step with nsteps = 1 would
+    # add a copy back into psi)
+    st_ = [d[0], torch.empty_like(d[0])]
+
+    def one_step():
+        m.step_out(st_[0], st_[1], *d[1:])
+        st_.reverse()
     for _ in range(warmup):
-        m.step(*d, nsteps=1)
+        one_step()
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
 
@@ -747,8 +761,8 @@ def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(steps):
-            m.step(*d, nsteps=1)
-            m.mass(d[0], d[4], out=out_mass)
+            one_step()
+            m.mass(st_[0], d[4], out=out_mass)
         e1.record(stream)
         torch.cuda.synchronize(dev)
         return e0.elapsed_time(e1)
