@@ -5,10 +5,12 @@ forward(psi0, U, V, W, G, nsteps) runs nsteps steps and keeps psi every
 ``ckpt`` steps; backward walks the segments in reverse, re-runs each
 segment once from its checkpoint with taped library steps (each keeping
 its intermediates), then applies the library's taped adjoint step to each
-step in reverse order.  The last segment, which backward needs first, is
+step in reverse order; the re-run of a segment overlaps, on a second stream
+and context, with the adjoint steps of the segment after it.  The last segment, which backward needs first, is
 taped already by the forward pass (when a gradient is wanted), so it is
 never re-run -- the segment schedule of checkpoint_sequential.  Memory:
-nsteps/ckpt checkpoints plus ckpt states and tapes (11 fields each).  G is
+nsteps/ckpt checkpoints plus two sets of ckpt states and tapes (11 fields
+each).  G is
 not differentiated.  Every step of both passes runs in the library's
 kernels; this module only orders the calls.
 """
@@ -59,31 +61,64 @@ class MPDATAFunction(torch.autograd.Function):
         u, v, w, g, *ckpts = ctx.saved_tensors
         m, nsteps, ckpt = ctx.model, ctx.nsteps, ctx.ckpt
         m._sync_stream()
+        main = torch.cuda.current_stream(m.device)
         psib = grad_out.contiguous().clone()
         # the output's halo holds copies of interior values
         C.mpdata_fold_halo_adjoint(m._ctx, m._ptr(psib, "grad"))
         ub, vb, wb = torch.zeros_like(u), torch.zeros_like(v), torch.zeros_like(w)
         nseg = len(ckpts)
-        if ctx.taped:
-            tapes, states = ctx.tapes, ctx.states
-        else:
-            tapes, states = _buffers(m, u, ckpts[0], min(ckpt, nsteps))
+        seglen = min(ckpt, nsteps)
+        # Two sets of tapes and states: while the main stream runs the
+        # adjoint steps of segment k from one set, a side stream records
+        # segment k-1 into the other (with a second context of the same
+        # grid, so the two share no scratch).  Segment k-1's adjoint steps
+        # wait for its recording; a set is recorded into again only after
+        # the adjoint steps that read it have run.
+        sets = [(ctx.tapes, ctx.states) if ctx.taped else _buffers(m, u, ckpts[0], seglen)]
+        if nseg > 1:
+            sets.append(_buffers(m, u, ckpts[0], seglen))
+        rec = m.shadow() if nseg > 1 else None
+        if rec is not None:
+            C.mpdata_set_options(rec._ctx, C.mpdata_get_options(m._ctx))
+        side = torch.cuda.Stream(m.device) if nseg > 1 else None
+        ready = main.record_event()   # checkpoints and buffers are ready
+        free = [ready, ready]         # when each set may be recorded into
+        recorded = {}
+
+        def record(seg, which, model, stream):
+            tapes, states = sets[which]
+            start = seg * ckpt
+            P = lambda t, name: model._ptr(t, name)  # noqa: E731
+            with torch.cuda.stream(stream):
+                model._sync_stream()
+                states[0].copy_(ckpts[seg])
+                for s in range(min(start + ckpt, nsteps) - start):
+                    C.mpdata_step_tape(model._ctx, P(states[s], "state"),
+                                       P(states[s + 1], "state"), P(u, "u"), P(v, "v"),
+                                       P(w, "w"), P(g, "g"), tapes[s].data_ptr())
+            return stream.record_event()
+
+        if not ctx.taped:  # the forward pass did not tape the last segment
+            recorded[nseg - 1] = record(nseg - 1, 0, m, main)
         P = lambda t, name: m._ptr(t, name)  # noqa: E731
         for seg in reversed(range(nseg)):
+            which = (nseg - 1 - seg) % 2
+            if seg - 1 >= 0:  # record the next segment meanwhile, on the side stream
+                side.wait_event(free[1 - which])
+                recorded[seg - 1] = record(seg - 1, 1 - which, rec, side)
+            if seg in recorded:
+                main.wait_event(recorded[seg])
+            m._sync_stream()
+            tapes, states = sets[which]
             start = seg * ckpt
-            end = min(start + ckpt, nsteps)
-            if not (seg == nseg - 1 and ctx.taped):  # the forward pass taped the last one
-                # record the segment once: its states and every step's tape
-                states[0].copy_(ckpts[seg])
-                for s in range(end - start):
-                    C.mpdata_step_tape(m._ctx, P(states[s], "state"), P(states[s + 1], "state"),
-                                       P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
-                                       tapes[s].data_ptr())
-            for s in reversed(range(end - start)):
+            for s in reversed(range(min(start + ckpt, nsteps) - start)):
                 C.mpdata_adjoint_step_tape(m._ctx, tapes[s].data_ptr(), P(states[s], "state"),
                                            P(u, "u"), P(v, "v"), P(w, "w"), P(g, "g"),
                                            P(psib, "psi_bar"), P(ub, "u_bar"), P(vb, "v_bar"),
                                            P(wb, "w_bar"))
+            free[which] = main.record_event()
+        if side is not None:
+            main.wait_stream(side)
         ctx.tapes = ctx.states = None
         return psib, ub, vb, wb, None, None, None, None
 

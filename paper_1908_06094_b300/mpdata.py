@@ -42,8 +42,25 @@ class MPDATA:
                 self.close()
                 raise
         self.shape = padded_shape(nx, ny, nz, halo)
+        self._k_bc, self._variant = k_bc, variant
+        self._shadow = None
+
+    def shadow(self) -> "MPDATA":
+        """A second context of the same grid and scheme (its own scratch),
+        created on first use: calls on another stream that must not share
+        this context's scratch (the adjoint's recomputed segments) use it."""
+        if self._shadow is None:
+            opts = C.mpdata_get_options(self._ctx)
+            self._shadow = MPDATA(self.nx, self.ny, self.nz, halo=self.h, iord=self.iord,
+                                  nonoscillatory=self.nonosc, dtype=self.dtype,
+                                  device=self.device, variant=self._variant, k_bc=self._k_bc,
+                                  options=opts)
+        return self._shadow
 
     def close(self):
+        if getattr(self, "_shadow", None) is not None:
+            self._shadow.close()
+            self._shadow = None
         if getattr(self, "_ctx", None):
             C.mpdata_destroy(self._ctx)
             self._ctx = None
@@ -69,6 +86,9 @@ class MPDATA:
 
     def set_variant(self, variant: int):
         C.mpdata_set_variant(self._ctx, variant)
+        self._variant = variant
+        if self._shadow is not None:
+            C.mpdata_set_variant(self._shadow._ctx, variant)
 
     def step(self, psi, u, v, w, g, nsteps: int = 1):
         """Advance psi in place by nsteps steps (asynchronous, current stream)."""
