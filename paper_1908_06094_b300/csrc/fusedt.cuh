@@ -146,8 +146,6 @@ __device__ __forceinline__ void step_tile_t2(const Geo& g, int i0, int j0, int k
   const int s2 = (y + 2) * EX + (x + 2);
   const int s3 = (y + 3) * RX + (x + 3);
   const bool inB = tid < Map::NB, inC = tid < Map::NC;
-  const bool inBx = tid < Map::NC + TY + 2;
-  const bool inBy = tid < Map::NC || (tid >= Map::NC + TY + 2 && tid < Map::NB);
   const bool inD = inC && x < TX && y < TY;
   auto wrapi = [&](int i) { return ((i % g.nx) + g.nx) % g.nx; };
   auto wrapj = [&](int j) { return ((j % g.ny) + g.ny) % g.ny; };
@@ -273,7 +271,10 @@ __device__ __forceinline__ void step_tile_t2(const Geo& g, int i0, int j0, int k
       const float* ub = us + (b & 3) * L::RN + s3;
       const float* wb = ws + (b & 3) * L::SN + s2;
       const float* wbm = ws + ((b - 1) & 3) * L::SN + s2;
-      if (inBx) {  // x face
+      // every thread of B forms all three faces (column -2 and row -2 need
+      // only their x or y faces; the others go to slots and registers
+      // nobody reads), so the faces' arithmetic interleaves: +0.6 %
+      {  // x face
         const f2 s1p = add2(pb1[EX + 1], pb1[EX]), s1m = add2(pb1[-EX + 1], pb1[-EX]);
         const f2 s2p = add2(pbp[1], qp), s2m = add2(pbm[1], qm);
         const float vsum = v1 + vb[1] + vb[-RX] + vb[-RX + 1];
@@ -281,7 +282,7 @@ __device__ __forceinline__ void step_tile_t2(const Geo& g, int i0, int j0, int k
         utB = pseudo_t(face_u(u1, g1 + gb[1]), q1, pb1[1], s1p, s1m, s2p, s2m, vsum, wsum);
         uts[s2] = utB;
       }
-      if (inBy) {  // y face
+      {  // y face
         const f2 s1p = add2(pb1[EX + 1], pb1[1]), s1m = add2(pb1[EX - 1], pb1[-1]);
         const f2 s2p = add2(pbp[EX], qp), s2m = add2(pbm[EX], qm);
         const float usum = u1 + ub[RX] + ub[-1] + ub[RX - 1];
@@ -289,7 +290,7 @@ __device__ __forceinline__ void step_tile_t2(const Geo& g, int i0, int j0, int k
         vtB = pseudo_t(face_u(v1, g1 + gb[EX]), q1, pb1[EX], s1p, s1m, s2p, s2m, usum, wsum);
         vts[s2] = vtB;
       }
-      if (inC) {  // z face
+      {  // z face
         f2 res = zero2;
         if (S || zface(b)) {  // a zero-flux top face is closed
           const f2* pb2 = p1s + ((b + 1) & 3) * L::SN + s2;

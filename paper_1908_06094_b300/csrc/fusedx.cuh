@@ -208,7 +208,7 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
   Map::cell(tid, x, y);
   const int s2 = (y + 2) * EX + (x + 2);  // radius-2 slot of the pair (even)
   const int s3 = (y + 3) * RX + (x + 4);  // radius-3 slot of the pair (even)
-  const bool inB = tid < Map::NB, inBx = tid < Map::NC, inC = tid < Map::NC;
+  const bool inB = tid < Map::NB, inC = tid < Map::NC;
   // stage D: the faces stage E reads (x faces of columns -1 .. TX-1 on the
   // tile's rows, y faces of the tile's columns on rows -1 .. TY-1)
   const bool inD = tid < Map::NTILE + TY ||
@@ -366,7 +366,11 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
       pym = at2(pb1 - EX);                 // (x, x+1) at y-1
       pxp = mk(q1.y, pb1[2]);              // (x+1, x+2)
       pxm = mk(pb1[-1], q1.x);             // (x-1, x)
-      if (inBx) {  // x faces
+      // Every thread of B forms all three faces: row -2, which needs only
+      // its y faces, forms x and z faces into a slot and a register nobody
+      // reads, and the faces' arithmetic, with no branch between them,
+      // interleaves (776 against 784 us a launch)
+      {  // x faces
         const f2 s1p = add2(mk(pyp.y, pb1[EX + 2]), pyp);
         const f2 s1m = add2(mk(pym.y, pb1[-EX + 2]), pym);
         const f2 s2p = add2(mk(qp.y, P1v(bp, 2)[0]), qp);
@@ -378,7 +382,7 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
         utB = pseudo2(u1, gsum, q1, pxp, s1p, s1m, s2p, s2m, vsum, wsum);
         st2(uts + s2, utB);
       }
-      {  // y faces (every thread of B)
+      {  // y faces
         const f2 s1p = add2(mk(pyp.y, pb1[EX + 2]), pxp);
         const f2 s1m = add2(mk(pb1[EX - 1], pyp.x), pxm);
         const f2 s2p = add2(at2(P1v(bp, EX)), qp);
@@ -390,7 +394,7 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
         vtB = pseudo2(v1, gsum, q1, pyp, s1p, s1m, s2p, s2m, usum, wsum);
         st2(vts + s2, vtB);
       }
-      if (inC) {  // z faces
+      {  // z faces
         f2 res = zero2;
         if (S || zface(b)) {  // a zero-flux top face is closed
           const float* pb2 = P1v(b + 1, 0);
