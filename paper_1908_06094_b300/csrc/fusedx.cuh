@@ -22,7 +22,8 @@
 // Requirements (checked by the caller): FP32, even nx and halo (so every
 // pair starts on an 8-byte boundary in device memory and a periodic wrap
 // never separates the two columns), fewer than 2^31 elements a field,
-// the i-j domain periodic (not a slab), no corrective-pass options, no tape.
+// the i-j domain periodic (not a slab), no corrective-pass options.  Both
+// vertical boundaries; with TAPE the step also writes the adjoint's tape.
 #pragma once
 #include <climits>
 #include <type_traits>
