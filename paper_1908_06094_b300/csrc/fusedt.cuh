@@ -195,6 +195,7 @@ __device__ __forceinline__ void step_tile_t2(const Geo& g, int i0, int j0, int k
   f2 q0 = zero2, q1 = zero2, q2 = zero2;
   f2 utA = zero2, vtA = zero2, utB = zero2, vtB = zero2, wtA = zero2, wtB = zero2;
   f2 buA = zero2, bdA = zero2, buB = zero2, bdB = zero2;
+  f2 f1z = zero2;  // the donor flux through face t+3/2 (stage A's last "+" z face)
   f2 fzAA = zero2, fzA = zero2, fzB = zero2;
 
   __syncthreads();  // the shared memory may still be read by a previous item
@@ -251,7 +252,10 @@ __device__ __forceinline__ void step_tile_t2(const Geo& g, int i0, int j0, int k
       const f2 fyp = donor_s(p2, pa[RX], v2);
       const f2 fym = donor_s(pa[-RX], p2, va[-RX]);
       const f2 fzp = donor_s(p2, p3, w2);  // w2 = 0 on a zero-flux top face
-      const f2 fzm = donor_s(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
+      // the "-" z face is the previous level's "+" z face (the same operation
+      // on the same values): stage A ran a level before every steady level
+      const f2 fzm = S ? f1z : donor_s(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
+      f1z = fzp;
       q2 = fma2(add2(add2(sub2(fxm, fxp), sub2(fym, fyp)), sub2(fzm, fzp)), splat(rcp(g2)), p2);
       p1s[(a & 3) * L::SN + s2] = q2;
     }

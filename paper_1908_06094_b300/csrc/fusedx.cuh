@@ -284,6 +284,7 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
   f2 utA = zero2, vtA = zero2, utB = zero2, vtB = zero2;  // Ut, Vt at t, t+1
   f2 wtA = zero2, wtB = zero2;            // Wt at faces t+1/2, t+3/2
   f2 buA = zero2, bdA = zero2, buB = zero2, bdB = zero2;  // betas at t, t+1
+  f2 f1z = zero2;  // the donor flux through face t+3/2 (stage A's last "+" z face)
   f2 fzAA = zero2, fzA = zero2, fzB = zero2;  // vertical fluxes at faces t-3/2 .. t+1/2
   int l4 = clampk_(t0 + 4), l5 = clampk_(t0 + 5);
 
@@ -342,7 +343,10 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
       const f2 fyp = donor2s(p2, at2(pa + RX), v2);
       const f2 fym = donor2s(at2(pa - RX), p2, at2(va - RX));
       const f2 fzp = donor2s(p2, p3, w2);  // w2 = 0 on a zero-flux top face
-      const f2 fzm = donor2s(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
+      // the "-" z face is the previous level's "+" z face (the same operation
+      // on the same values): stage A ran a level before every steady level
+      const f2 fzm = S ? f1z : donor2s(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
+      f1z = fzp;
       q2 = fma2(add2(add2(sub2(fxm, fxp), sub2(fym, fyp)), sub2(fzm, fzp)), rcp2(g2), p2);
       st2(P1v(a, 0), q2);
     }
