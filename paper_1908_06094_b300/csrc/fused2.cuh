@@ -273,6 +273,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
   constexpr bool kTapeR = TAPE && TapesReciprocals<T>::v;
   T riA = zero, roA = zero, riB = zero, roB = zero;  // their 1/(in+eps), 1/(out+eps) (FP64 tape)
   T fzAA = zero, fzA = zero, fzB = zero;  // vertical fluxes at faces t-3/2, t-1/2, t+1/2
+  T f1z = zero;  // the donor flux through face t+3/2 (stage A's last "+" z face)
 
   // periodic k: the wrapped levels of planes t+4, t+5, advanced by one
   // level per plane (no division in the loop)
@@ -344,7 +345,10 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
       const T fyp = donor(p2, pa[RX], v2);
       const T fym = donor(pa[-RX], p2, va[-RX]);
       const T fzp = donor(p2, p3, w2);  // w2 = 0 on a zero-flux top face
-      const T fzm = donor(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
+      // the "-" z face is the previous level's "+" z face (the same operation
+      // on the same values): stage A ran a level before every steady level
+      const T fzm = S ? f1z : donor(p1, p2, w1);  // w1 = 0 on a zero-flux bottom face
+      f1z = fzp;
       // psi - div * (1/G), one rounding: the negated divergence is formed
       // exactly (every difference and sum negated) and fused in
       q2 = fma_rn((fxm - fxp) + (fym - fyp) + (fzm - fzp), rcp(g2), p2);
