@@ -284,6 +284,7 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
   f2 utA = zero2, vtA = zero2, utB = zero2, vtB = zero2;  // Ut, Vt at t, t+1
   f2 wtA = zero2, wtB = zero2;            // Wt at faces t+1/2, t+3/2
   f2 buA = zero2, bdA = zero2, buB = zero2, bdB = zero2;  // betas at t, t+1
+  f2 c1z = zero2;  // stage C's last upper z flux
   f2 f1z = zero2;  // the donor flux through face t+3/2 (stage A's last "+" z face)
   f2 fzAA = zero2, fzA = zero2, fzB = zero2;  // vertical fluxes at faces t-3/2 .. t+1/2
   int l4 = clampk_(t0 + 4), l5 = clampk_(t0 + 5);
@@ -431,7 +432,10 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
       const f2 fyp = donor2(q1, pyp, vtB);
       const f2 fym = donor2(pym, q1, at2(vts + s2 - EX));
       const f2 fzp = donor2(q1, qp, wtB);  // wtB = 0 on a zero-flux top face
-      const f2 fzm = donor2(qm, q1, wtA);  // wtA = 0 on a zero-flux bottom face
+      // the lower face's flux is the previous level's upper one (the same
+      // operation on the same values): C ran a level before every steady level
+      const f2 fzm = S ? c1z : donor2(qm, q1, wtA);  // wtA = 0 on a zero-flux bottom face
+      c1z = fzp;
       const f2 in = add2(add2(sub2(pos2(fxm), neg2(fxp)), sub2(pos2(fym), neg2(fyp))),
                          sub2(pos2(fzm), neg2(fzp)));
       const f2 ou = add2(add2(sub2(pos2(fxp), neg2(fxm)), sub2(pos2(fyp), neg2(fym))),
