@@ -36,6 +36,8 @@ struct mpdata_ctx {
   // the two-column FP32 kernel's launch shape (x2_ok: it runs the untaped
   // FP32 step)
   int x2_ok, x2_nchunks, x2_kchunk;
+  // the last staged step wrote the halo of its output itself
+  bool halo_done;
   // level-chunk lengths of the k-marching kernels (0: not chosen yet)
   int kc_fwd, kc_rev;
   // the adjoint's accumulators (psi^n-bar, beta adjoints) are known to be
@@ -204,6 +206,7 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
   const Geo& g = c->g;
   const dim3 grid = cell_grid(g);
   cudaStream_t s = c->stream;
+  c->halo_done = false;
   const T* psi = psi_in;
   T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
   // FP64: the donor fluxes' kernel (bound by memory) stores 1/G for all the
@@ -242,10 +245,20 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
                      g, psi, cur, bf[0], bf[1], bf[2], G, (T*)c->bu, (T*)c->bd, nullptr,
                      nullptr)));
       if (kFin && !more && rg) {  // the last pass: limited fluxes and advance in one
-        MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-                   limadvance_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                       g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz, rg,
-                       dest));
+        // with the halo images of psi^(n+1) where one image a side covers
+        // the halo (no separate halo fill then)
+        const bool img = g.nx >= 2 * g.h && g.ny >= 2 * g.h;
+        if (img)
+          MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+                     (limadvance_kernel<T, true><<<grid, kCellBlock, 0, s>>>(
+                         g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
+                         rg, dest)));
+        else
+          MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
+                     (limadvance_kernel<T, false><<<grid, kCellBlock, 0, s>>>(
+                         g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
+                         rg, dest)));
+        c->halo_done = img;
         MPD_CHECK_LAUNCH(c, "corrective pass");
         cur = dest;
         continue;  // the last pass: nothing carries over
@@ -533,6 +546,7 @@ int step_out(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, const T
   if (use_fused(c)) return fused_launch<T>(c, in, out, U, V, W, G);
   int rc = step_staged<T>(c, in, out, U, V, W, G);
   if (rc) return rc;
+  if (c->halo_done) return MPDATA_OK;  // the last pass wrote the halo images
   return halo_launch<T>(c, out, MPDATA_HALO_CELL);
 }
 

@@ -85,8 +85,30 @@ __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
 // with the stored 1/G.  The same bits as limflux_kernel<FIN> followed by
 // advance_kernel<RG = 2>, without the limited fluxes' round trip through
 // memory (6 products a cell instead of 3: the kernel is bound by neither).
-// P and out are distinct.
+// P and out are distinct.  IMG: each cell also writes its value's images
+// in the halo of out (periodic in i and j; in k the edge copies of the
+// bottom and top levels, or the periodic images), the separate halo fill's
+// work (nx, ny >= 2h: one image a side).
 template <class T>
+__device__ __forceinline__ void put_images(const Geo& g, int i, int j, int k, T r,
+                                           T* __restrict__ out) {
+  const int ni = i < g.h ? 1 : (i >= g.nx - g.h ? -1 : 0);
+  const int nj = j < g.h ? 1 : (j >= g.ny - g.h ? -1 : 0);
+  int klo = (k == 0) ? -g.h : k, khi = (k == g.nz - 1) ? g.nz - 1 + g.h : k;
+  if (g.kper) {
+    klo = k;
+    while (klo - g.nz >= -g.h) klo -= g.nz;
+    khi = g.nz - 1 + g.h;
+  }
+  if (ni == 0 && nj == 0 && klo == k && khi == k) return;
+  for (int kk = klo; kk <= khi; kk += g.kper ? g.nz : 1) {
+    if (!g.kper && kk != k && kk >= 0 && kk < g.nz) continue;
+    for (int a = 0; a <= (ni != 0); ++a)
+      for (int b = 0; b <= (nj != 0); ++b)
+        if (kk != k || a != 0 || b != 0) out[at(g, i + a * ni * g.nx, j + b * nj * g.ny, kk)] = r;
+  }
+}
+template <class T, bool IMG = false>
 __global__ void limadvance_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ ut,
                                   const T* __restrict__ vt, const T* __restrict__ wt,
                                   const T* __restrict__ bu, const T* __restrict__ bd,
@@ -113,7 +135,9 @@ __global__ void limadvance_kernel(Geo g, const T* __restrict__ P, const T* __res
   const T fym = lf(vt[ym], fy[ym], bu[ym], bd[ym], buq, bdq);
   const T fzp = zt ? lf(wt[q], fz[q], buq, bdq, bu[zp], bd[zp]) : T(0);
   const T fzm = zb ? lf(wt[zm], fz[zm], bu[zm], bd[zm], buq, bdq) : T(0);
-  out[q] = P[q] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) * rg[q];
+  const T r = P[q] - ((fxp - fxm) + (fyp - fym) + (fzp - fzm)) * rg[q];
+  out[q] = r;
+  if constexpr (IMG) put_images(g, c.i, c.j, c.k, r, out);
 }
 
 // Antidiffusive pseudo-velocities on the "+" faces of every cell
