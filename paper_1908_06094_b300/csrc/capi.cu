@@ -246,8 +246,10 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
                      nullptr)));
       if (kFin && !more && rg) {  // the last pass: limited fluxes and advance in one
         // with the halo images of psi^(n+1) where one image a side covers
-        // the halo (no separate halo fill then)
-        const bool img = g.nx >= 2 * g.h && g.ny >= 2 * g.h;
+        // the halo and the k halo's images fall on the bottom and top levels
+        // only (no separate halo fill then; a grid of one or a few levels,
+        // whose every cell would write 2h images, keeps the fill kernel)
+        const bool img = g.nx >= 2 * g.h && g.ny >= 2 * g.h && g.nz > 2 * g.h;
         if (img)
           MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
                      (limadvance_kernel<T, true><<<grid, kCellBlock, 0, s>>>(
