@@ -123,7 +123,9 @@ MPDATA_API int mpdata_set_variant(mpdata_ctx *c, int variant);
  *        is (|U| - U^2/Gf)(psi_R - psi_L)/2 - U (Vbar N_y + Wbar N_z)/(8 Gf)
  *        with N the numerators of B.  A linear scheme, for signed fields.
  * IGA takes no other option and iord <= 2.  With an option an FP32 step
- * runs on the fused kernel (iord 2) and an FP64 step on the staged ones;
+ * runs on a fused kernel (iord 2: the two-column one with the limiter on
+ * and even nx and halo, else the one-column one) and an FP64 step on the
+ * staged ones;
  * the adjoint calls (mpdata_adjoint_step, mpdata_step_tape,
  * mpdata_adjoint_step_tape) return EINVAL. */
 enum mpdata_option { MPDATA_OPT_DFL = 1, MPDATA_OPT_ABS = 2, MPDATA_OPT_IGA = 4 };

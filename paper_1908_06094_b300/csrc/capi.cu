@@ -411,12 +411,27 @@ int pick_chunks(const Geo& g, long ctas, int sms, int* kchunk) {
 // The two-column FP32 step (fusedx.cuh): its tile (32 x 24 columns, 504
 // threads of two columns, up to 128 registers) and instances.
 struct FusedX { static constexpr int TX = 32, TY = 24, MINB = 1; };
-template <bool LIMIT, bool KPER, bool TAPE>
+template <bool LIMIT, bool KPER, bool TAPE, int OPT = 0>
 auto fusedx_ptr() {
-  return mpd::fusedx::step_kernel_x2<FusedX::TX, FusedX::TY, FusedX::MINB, LIMIT, KPER, TAPE>;
+  return mpd::fusedx::step_kernel_x2<FusedX::TX, FusedX::TY, FusedX::MINB, LIMIT, KPER, TAPE,
+                                     OPT>;
+}
+// the option instances (with the limiter; the taped step has no options)
+template <bool KPER>
+auto fusedx_opt_pick(int opts) {
+  using namespace mpd;
+  switch (opts) {
+    case kOptDFL: return fusedx_ptr<true, KPER, false, kOptDFL>();
+    case kOptABS: return fusedx_ptr<true, KPER, false, kOptABS>();
+    case kOptDFL | kOptABS: return fusedx_ptr<true, KPER, false, kOptDFL | kOptABS>();
+    default: return fusedx_ptr<true, KPER, false, kOptIGA>();
+  }
 }
 template <bool TAPE = false>
 auto fusedx_pick(const mpdata_ctx* c) {
+  if constexpr (!TAPE) {
+    if (c->opts) return c->g.kper ? fusedx_opt_pick<true>(c->opts) : fusedx_opt_pick<false>(c->opts);
+  }
   if (c->g.kper)
     return c->nonosc ? fusedx_ptr<true, true, TAPE>() : fusedx_ptr<false, true, TAPE>();
   return c->nonosc ? fusedx_ptr<true, false, TAPE>() : fusedx_ptr<false, false, TAPE>();
@@ -425,13 +440,14 @@ constexpr int fusedx_threads() { return mpd::fusedx::PairMap<FusedX::TX, FusedX:
 constexpr size_t fusedx_smem() { return mpd::fusedx::Layout<FusedX::TX, FusedX::TY>::bytes; }
 
 // Whether the two-column kernel can run this context's step (plain or
-// taped): FP32, no options, the periodic i-j domain, pairs of columns on 8-byte
+// taped): FP32, no options or options with the limiter, the periodic i-j
+// domain, pairs of columns on 8-byte
 // boundaries (even nx and halo: even row length and interior offset) and
 // 32-bit offsets.
 void fusedx_setup(mpdata_ctx* c) {
   const Geo& g = c->g;
   c->x2_ok = 0;
-  if (c->dtype != MPDATA_F32 || c->opts != 0 || g.openij || g.nx % 2 != 0 ||
+  if (c->dtype != MPDATA_F32 || (c->opts != 0 && !c->nonosc) || g.openij || g.nx % 2 != 0 ||
       g.h % 2 != 0 || g.total >= ((int64_t)1 << 31))
     return;
   auto k = fusedx_pick(c);
@@ -498,7 +514,8 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
     // (the taped step: its fields tstride elements apart from psi1, each on
     // an 8-byte boundary)
     const long long tstride = tape ? (long long)(tape->ut - tape->p1) : 0;
-    if (c->x2_ok && c->opts == 0 && !g.openij && al8(in) && al8(out) && al8(U) &&
+    if (c->x2_ok && (c->opts == 0 || (!tape && c->nonosc)) && !g.openij && al8(in) &&
+        al8(out) && al8(U) &&
         al8(V) && al8(W) && al8(G) && (!tape || (al8(tape->p1) && tstride % 2 == 0))) {
       dim3 gx((g.nx + FusedX::TX - 1) / FusedX::TX, (g.ny + FusedX::TY - 1) / FusedX::TY,
               c->x2_nchunks);
@@ -971,6 +988,7 @@ int mpdata_set_options(mpdata_ctx* c, int opts) {
       c->opts = prev;
       return fail(c, MPDATA_ECUDA, "fused kernel attribute");
     }
+    fusedx_setup(c);  // the two-column kernel's instance for these options
   }
   return MPDATA_OK;
 }

@@ -379,7 +379,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         utB = pseudo(u1, gsum, ap(q1), ap(P1(b, 1)), s1p, s1m, s2p, s2m, vsum, wsum);
         if constexpr (kDFL) {  // + the cell at x+1
           const T dr = (ub[1] - u1) + (vb[1] - vb[-RX + 1]) + (wb[1] - wbm[1]);
-          utB = utB + divergent_flow_term(u1, gsum, dc + dr);
+          utB = add_rn(utB, divergent_flow_term(u1, gsum, dc + dr));
         }
         uts[s2] = utB;
       }
@@ -392,7 +392,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
         vtB = pseudo(v1, gsum, ap(q1), ap(P1(b, EX)), s1p, s1m, s2p, s2m, usum, wsum);
         if constexpr (kDFL) {  // + the cell at y+1
           const T dr = (ub[RX] - ub[RX - 1]) + (vb[RX] - v1) + (wb[EX] - wbm[EX]);
-          vtB = vtB + divergent_flow_term(v1, gsum, dc + dr);
+          vtB = add_rn(vtB, divergent_flow_term(v1, gsum, dc + dr));
         }
         vts[s2] = vtB;
       }
@@ -409,7 +409,7 @@ __device__ __forceinline__ void step_tile2(const Geo& g, int i0, int j0, int k0,
           res = pseudo(w1, g1 + g2, ap(q1), ap(q2), s1p, s1m, s2p, s2m, usum, vsum);
           if constexpr (kDFL) {  // + the cell at plane b+1
             const T dr = (u2 - ub1[-1]) + (v2 - vb1[-RX]) + (w2 - w1);
-            res = res + divergent_flow_term(w1, g1 + g2, dc + dr);
+            res = add_rn(res, divergent_flow_term(w1, g1 + g2, dc + dr));
           }
         }
         wtB = res;

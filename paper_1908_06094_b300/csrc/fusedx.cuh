@@ -113,6 +113,39 @@ __device__ __forceinline__ f2 pseudo2(f2 U, f2 gsum, f2 pl, f2 pr, f2 s1p, f2 s1
   const f2 cross = mul2(splat(0.125f), fma2(vsum, B1, mul2(wsum, B2)));
   return fma2(diff, A, mul2(qn, cross));
 }
+// the infinite-gauge pseudo-flux of each lane: the operations of
+// pseudo_flux_iga (grid.cuh), the sign carried by -1/Gf as in pseudo2
+__device__ __forceinline__ f2 pseudo_iga2(f2 U, f2 gsum, f2 pl, f2 pr, f2 s1p, f2 s1m, f2 s2p,
+                                          f2 s2m, f2 vsum, f2 wsum) {
+  const f2 rGn = mul2(splat(-2.0f), rcp2(gsum));                          // -1/Gf
+  const f2 qn = mul2(U, rGn);
+  const f2 diff = fma2(U, qn, abs2(U));                                   // |U| - U^2/Gf
+  const f2 cross = mul2(splat(0.03125f), fma2(vsum, sub2(s1p, s1m), mul2(wsum, sub2(s2p, s2m))));
+  return fma2(diff, mul2(splat(0.5f), sub2(pr, pl)), mul2(qn, cross));
+}
+// the divergent-flow term of each lane (divergent_flow_term, grid.cuh), its
+// last product per lane: a sum consumes it
+__device__ __forceinline__ f2 dft2(f2 U, f2 gsum, f2 dsum) {
+  const f2 t = mul2(mul2(splat(-0.5f), U), dsum);
+  return mk(mul_rn(t.x, rcp(gsum.x)), mul_rn(t.y, rcp(gsum.y)));
+}
+// the options' forms (free functions, no captures): |psi1| with ABS, the
+// face's pseudo-velocity or infinite-gauge pseudo-flux, and the corrective
+// flux of a face (the donor flux of its velocity, or in the infinite gauge
+// the value itself)
+template <bool ABS>
+__device__ __forceinline__ f2 ap(f2 v) { return ABS ? abs2(v) : v; }
+template <bool IGA>
+__device__ __forceinline__ f2 pse(f2 C, f2 gsum, f2 pl, f2 pr, f2 s1p, f2 s1m, f2 s2p, f2 s2m,
+                                  f2 c1, f2 c2) {
+  if constexpr (IGA) return pseudo_iga2(C, gsum, pl, pr, s1p, s1m, s2p, s2m, c1, c2);
+  else return pseudo2(C, gsum, pl, pr, s1p, s1m, s2p, s2m, c1, c2);
+}
+template <bool IGA>
+__device__ __forceinline__ f2 cflux2(f2 L, f2 R, f2 C) {
+  if constexpr (IGA) return C;
+  else return donor2(L, R, C);
+}
 // the limiter bounds of each lane over its 14 values, folded in the order
 // of the scalar bounds()
 template <int N>
@@ -188,7 +221,7 @@ struct PairMap {
 // adjoint's tape), each a padded field like psi, tstride elements apart from
 // tape (psi1): psi1, Ut, Vt, Wt, beta-up, beta-down at slots 0..5 and the
 // limited Ul, Vl, Wl at slots 8..10 (slots 6 and 7 are FP64's reciprocals).
-template <int TX, int TY, int MINB, bool LIMIT, bool KPER, bool TAPE = false>
+template <int TX, int TY, int MINB, bool LIMIT, bool KPER, bool TAPE = false, int OPT = 0>
 __global__ void __launch_bounds__(PairMap<TX, TY>::NT, MINB)
 step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __restrict__ U,
                const float* __restrict__ V, const float* __restrict__ W,
@@ -263,6 +296,14 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
   auto st2 = [&](float* p, f2 v) { *reinterpret_cast<f2*>(p) = v; };
   // psi1 of plane k: the pair's slot, and a scalar at offset o from it
   auto P1v = [&](int k, int o) -> float* { return p1s + (k & 3) * L::SN + s2 + o; };
+  // corrective-pass options (kOpt* bits, as in the one-column kernel): ABS
+  // forms A and B from |psi1| and trades beta-up and beta-down on a face
+  // whose upwind psi1 is negative, IGA uses the infinite-gauge pseudo-fluxes
+  // (which are the corrective fluxes), DFL adds the divergent-flow term
+  constexpr bool kABS = (OPT & kOptABS) != 0, kIGA = (OPT & kOptIGA) != 0;
+  constexpr bool kDFL = (OPT & kOptDFL) != 0;
+  static_assert(!TAPE || OPT == 0, "the taped step has no options");
+  (void)kDFL;
 
   // the tile's pairs write psi^(n+1): each lane inside the grid
   const bool inT = x >= 0 && x < TX && y >= 0 && y < TY;
@@ -372,49 +413,116 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
       pym = at2(pb1 - EX);                 // (x, x+1) at y-1
       pxp = mk(q1.y, pb1[2]);              // (x+1, x+2)
       pxm = mk(pb1[-1], q1.x);             // (x-1, x)
-      // Every thread of B forms all three faces: row -2, which needs only
-      // its y faces, forms x and z faces into a slot and a register nobody
-      // reads, and the faces' arithmetic, with no branch between them,
-      // interleaves (776 against 784 us a launch)
-      {  // x faces
-        const f2 s1p = add2(mk(pyp.y, pb1[EX + 2]), pyp);
-        const f2 s1m = add2(mk(pym.y, pb1[-EX + 2]), pym);
-        const f2 s2p = add2(mk(qp.y, P1v(bp, 2)[0]), qp);
-        const f2 s2m = add2(mk(qm.y, P1v(bm, 2)[0]), qm);
-        const f2 vm = at2(vb - RX);
-        const f2 vsum = add2(add2(add2(v1, mk(v1.y, vb[2])), vm), mk(vm.y, vb[-RX + 2]));
-        const f2 wsum = add2(add2(add2(w1, mk(w1.y, wb[2])), w0), mk(w0.y, wbm[2]));
-        const f2 gsum = add2(g1, mk(g1.y, gb[2]));
-        utB = pseudo2(u1, gsum, q1, pxp, s1p, s1m, s2p, s2m, vsum, wsum);
-        st2(uts + s2, utB);
-      }
-      {  // y faces
-        const f2 s1p = add2(mk(pyp.y, pb1[EX + 2]), pxp);
-        const f2 s1m = add2(mk(pb1[EX - 1], pyp.x), pxm);
-        const f2 s2p = add2(at2(P1v(bp, EX)), qp);
-        const f2 s2m = add2(at2(P1v(bm, EX)), qm);
-        const f2 up = at2(ub + RX);
-        const f2 usum = add2(add2(add2(u1, up), mk(ub[-1], u1.x)), mk(ub[RX - 1], up.x));
-        const f2 wsum = add2(add2(add2(w1, at2(wb + EX)), w0), at2(wbm + EX));
-        const f2 gsum = add2(g1, at2(gb + EX));
-        vtB = pseudo2(v1, gsum, q1, pyp, s1p, s1m, s2p, s2m, usum, wsum);
-        st2(vts + s2, vtB);
-      }
-      {  // z faces
-        f2 res = zero2;
-        if (S || zface(b)) {  // a zero-flux top face is closed
-          const float* pb2 = P1v(b + 1, 0);
-          const float* ub1 = us + ((b + 1) & 3) * L::RN + s3;
-          const float* vb1 = vs + ((b + 1) & 3) * L::RN + s3;
-          const f2 s1p = add2(mk(q2.y, pb2[2]), pxp);
-          const f2 s1m = add2(mk(pb2[-1], q2.x), pxm);
-          const f2 s2p = add2(at2(pb2 + EX), pyp);
-          const f2 s2m = add2(at2(pb2 - EX), pym);
-          const f2 usum = add2(add2(add2(u1, u2), mk(ub[-1], u1.x)), mk(ub1[-1], u2.x));
-          const f2 vsum = add2(add2(add2(v1, v2), at2(vb - RX)), at2(vb1 - RX));
-          res = pseudo2(w1, add2(g1, g2), q1, q2, s1p, s1m, s2p, s2m, usum, vsum);
+      if constexpr (OPT == 0) {  // the basic scheme (kept apart: its code as measured)
+        // Every thread of B forms all three faces: row -2, which needs only
+        // its y faces, forms x and z faces into a slot and a register nobody
+        // reads, and the faces' arithmetic, with no branch between them,
+        // interleaves (776 against 784 us a launch)
+        {  // x faces
+          const f2 s1p = add2(mk(pyp.y, pb1[EX + 2]), pyp);
+          const f2 s1m = add2(mk(pym.y, pb1[-EX + 2]), pym);
+          const f2 s2p = add2(mk(qp.y, P1v(bp, 2)[0]), qp);
+          const f2 s2m = add2(mk(qm.y, P1v(bm, 2)[0]), qm);
+          const f2 vm = at2(vb - RX);
+          const f2 vsum = add2(add2(add2(v1, mk(v1.y, vb[2])), vm), mk(vm.y, vb[-RX + 2]));
+          const f2 wsum = add2(add2(add2(w1, mk(w1.y, wb[2])), w0), mk(w0.y, wbm[2]));
+          const f2 gsum = add2(g1, mk(g1.y, gb[2]));
+          utB = pseudo2(u1, gsum, q1, pxp, s1p, s1m, s2p, s2m, vsum, wsum);
+          st2(uts + s2, utB);
         }
-        wtB = res;
+        {  // y faces
+          const f2 s1p = add2(mk(pyp.y, pb1[EX + 2]), pxp);
+          const f2 s1m = add2(mk(pb1[EX - 1], pyp.x), pxm);
+          const f2 s2p = add2(at2(P1v(bp, EX)), qp);
+          const f2 s2m = add2(at2(P1v(bm, EX)), qm);
+          const f2 up = at2(ub + RX);
+          const f2 usum = add2(add2(add2(u1, up), mk(ub[-1], u1.x)), mk(ub[RX - 1], up.x));
+          const f2 wsum = add2(add2(add2(w1, at2(wb + EX)), w0), at2(wbm + EX));
+          const f2 gsum = add2(g1, at2(gb + EX));
+          vtB = pseudo2(v1, gsum, q1, pyp, s1p, s1m, s2p, s2m, usum, wsum);
+          st2(vts + s2, vtB);
+        }
+        {  // z faces
+          f2 res = zero2;
+          if (S || zface(b)) {  // a zero-flux top face is closed
+            const float* pb2 = P1v(b + 1, 0);
+            const float* ub1 = us + ((b + 1) & 3) * L::RN + s3;
+            const float* vb1 = vs + ((b + 1) & 3) * L::RN + s3;
+            const f2 s1p = add2(mk(q2.y, pb2[2]), pxp);
+            const f2 s1m = add2(mk(pb2[-1], q2.x), pxm);
+            const f2 s2p = add2(at2(pb2 + EX), pyp);
+            const f2 s2m = add2(at2(pb2 - EX), pym);
+            const f2 usum = add2(add2(add2(u1, u2), mk(ub[-1], u1.x)), mk(ub1[-1], u2.x));
+            const f2 vsum = add2(add2(add2(v1, v2), at2(vb - RX)), at2(vb1 - RX));
+            res = pseudo2(w1, add2(g1, g2), q1, q2, s1p, s1m, s2p, s2m, usum, vsum);
+          }
+          wtB = res;
+        }
+      } else {
+        // Every thread of B forms all three faces: row -2, which needs only
+        // its y faces, forms x and z faces into a slot and a register nobody
+        // reads, and the faces' arithmetic, with no branch between them,
+        // interleaves (776 against 784 us a launch)
+        // DFL: the divergence of the Courant numbers of the pair's cells at
+        // plane b (closed faces' W are 0 in the queue)
+        const f2 dc = kDFL ? add2(add2(sub2(u1, mk(ub[-1], u1.x)), sub2(v1, at2(vb - RX))),
+                                  sub2(w1, w0))
+                           : zero2;
+        {  // x faces
+          const f2 s1p = add2(ap<kABS>(mk(pyp.y, pb1[EX + 2])), ap<kABS>(pyp));
+          const f2 s1m = add2(ap<kABS>(mk(pym.y, pb1[-EX + 2])), ap<kABS>(pym));
+          const f2 s2p = add2(ap<kABS>(mk(qp.y, P1v(bp, 2)[0])), ap<kABS>(qp));
+          const f2 s2m = add2(ap<kABS>(mk(qm.y, P1v(bm, 2)[0])), ap<kABS>(qm));
+          const f2 vm = at2(vb - RX);
+          const f2 vsum = add2(add2(add2(v1, mk(v1.y, vb[2])), vm), mk(vm.y, vb[-RX + 2]));
+          const f2 wsum = add2(add2(add2(w1, mk(w1.y, wb[2])), w0), mk(w0.y, wbm[2]));
+          const f2 gsum = add2(g1, mk(g1.y, gb[2]));
+          utB = pse<kIGA>(u1, gsum, ap<kABS>(q1), ap<kABS>(pxp), s1p, s1m, s2p, s2m, vsum, wsum);
+          if constexpr (kDFL) {  // + the cells at x+1
+            const f2 dr = add2(add2(sub2(mk(u1.y, ub[2]), u1), sub2(mk(v1.y, vb[2]), mk(vm.y, vb[-RX + 2]))),
+                               sub2(mk(w1.y, wb[2]), mk(w0.y, wbm[2])));
+            utB = add2(utB, dft2(u1, gsum, add2(dc, dr)));
+          }
+          st2(uts + s2, utB);
+        }
+        {  // y faces
+          const f2 s1p = add2(ap<kABS>(mk(pyp.y, pb1[EX + 2])), ap<kABS>(pxp));
+          const f2 s1m = add2(ap<kABS>(mk(pb1[EX - 1], pyp.x)), ap<kABS>(pxm));
+          const f2 s2p = add2(ap<kABS>(at2(P1v(bp, EX))), ap<kABS>(qp));
+          const f2 s2m = add2(ap<kABS>(at2(P1v(bm, EX))), ap<kABS>(qm));
+          const f2 up = at2(ub + RX);
+          const f2 usum = add2(add2(add2(u1, up), mk(ub[-1], u1.x)), mk(ub[RX - 1], up.x));
+          const f2 wsum = add2(add2(add2(w1, at2(wb + EX)), w0), at2(wbm + EX));
+          const f2 gsum = add2(g1, at2(gb + EX));
+          vtB = pse<kIGA>(v1, gsum, ap<kABS>(q1), ap<kABS>(pyp), s1p, s1m, s2p, s2m, usum, wsum);
+          if constexpr (kDFL) {  // + the cells at y+1
+            const f2 dr = add2(add2(sub2(up, mk(ub[RX - 1], up.x)), sub2(at2(vb + RX), v1)),
+                               sub2(at2(wb + EX), at2(wbm + EX)));
+            vtB = add2(vtB, dft2(v1, gsum, add2(dc, dr)));
+          }
+          st2(vts + s2, vtB);
+        }
+        {  // z faces
+          f2 res = zero2;
+          if (S || zface(b)) {  // a zero-flux top face is closed
+            const float* pb2 = P1v(b + 1, 0);
+            const float* ub1 = us + ((b + 1) & 3) * L::RN + s3;
+            const float* vb1 = vs + ((b + 1) & 3) * L::RN + s3;
+            const f2 s1p = add2(ap<kABS>(mk(q2.y, pb2[2])), ap<kABS>(pxp));
+            const f2 s1m = add2(ap<kABS>(mk(pb2[-1], q2.x)), ap<kABS>(pxm));
+            const f2 s2p = add2(ap<kABS>(at2(pb2 + EX)), ap<kABS>(pyp));
+            const f2 s2m = add2(ap<kABS>(at2(pb2 - EX)), ap<kABS>(pym));
+            const f2 usum = add2(add2(add2(u1, u2), mk(ub[-1], u1.x)), mk(ub1[-1], u2.x));
+            const f2 vsum = add2(add2(add2(v1, v2), at2(vb - RX)), at2(vb1 - RX));
+            res = pse<kIGA>(w1, add2(g1, g2), ap<kABS>(q1), ap<kABS>(q2), s1p, s1m, s2p, s2m, usum, vsum);
+            if constexpr (kDFL) {  // + the cells at plane b+1
+              const f2 dr = add2(add2(sub2(u2, mk(ub1[-1], u2.x)), sub2(v2, at2(vb1 - RX))),
+                                 sub2(w2, w1));
+              res = add2(res, dft2(w1, add2(g1, g2), add2(dc, dr)));
+            }
+          }
+          wtB = res;
+        }
       }
     }
     __syncthreads();
@@ -427,14 +535,14 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
                            at2(pb + RX), p0, p2, pxm, pxp, pym, pyp, qm, qp};
       f2 hi, lo;
       bounds2(vals, hi, lo);
-      const f2 fxp = donor2(q1, pxp, utB);
-      const f2 fxm = donor2(pxm, q1, mk(uts[s2 - 1], utB.x));
-      const f2 fyp = donor2(q1, pyp, vtB);
-      const f2 fym = donor2(pym, q1, at2(vts + s2 - EX));
-      const f2 fzp = donor2(q1, qp, wtB);  // wtB = 0 on a zero-flux top face
+      const f2 fxp = cflux2<kIGA>(q1, pxp, utB);
+      const f2 fxm = cflux2<kIGA>(pxm, q1, mk(uts[s2 - 1], utB.x));
+      const f2 fyp = cflux2<kIGA>(q1, pyp, vtB);
+      const f2 fym = cflux2<kIGA>(pym, q1, at2(vts + s2 - EX));
+      const f2 fzp = cflux2<kIGA>(q1, qp, wtB);  // wtB = 0 on a zero-flux top face
       // the lower face's flux is the previous level's upper one (the same
       // operation on the same values): C ran a level before every steady level
-      const f2 fzm = S ? c1z : donor2(qm, q1, wtA);  // wtA = 0 on a zero-flux bottom face
+      const f2 fzm = S ? c1z : cflux2<kIGA>(qm, q1, wtA);  // wtA = 0 on a zero-flux bottom face
       c1z = fzp;
       const f2 in = add2(add2(sub2(pos2(fxm), neg2(fxp)), sub2(pos2(fym), neg2(fyp))),
                          sub2(pos2(fzm), neg2(fzp)));
@@ -452,17 +560,43 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
       const float* bu0 = sm + L::BUS + (t & 1) * L::SN + s2;
       const float* bd0 = sm + L::BDS + (t & 1) * L::SN + s2;
       const float* pt = P1v(t, 0);
-      f2 u = utA;
-      if (LIMIT) u = limit2(u, buA, bdA, mk(buA.y, bu0[2]), mk(bdA.y, bd0[2]));
-      st2(fxs + (t & 1) * L::SN + s2, donor2(q0, mk(q0.y, pt[2]), u));
-      f2 v = vtA;
-      if (LIMIT) v = limit2(v, buA, bdA, at2(bu0 + EX), at2(bd0 + EX));
-      st2(fys + (t & 1) * L::SN + s2, donor2(q0, at2(pt + EX), v));
-      f2 f = zero2, w = zero2;
-      if (S || zface(t)) {
-        w = wtA;
-        if (LIMIT) w = limit2(w, buA, bdA, buB, bdB);
-        f = donor2(q0, q1, w);
+      // the limited velocity of each lane; with ABS a face whose upwind psi1
+      // is negative carries its flux against its velocity: beta-up and
+      // beta-down trade places there
+      auto lim = [&](f2 C, f2 pr, f2 buR, f2 bdR) {
+        if constexpr (kABS) {
+          auto lane = [&](float c, float q, float r, float bu, float bd, float bur, float bdr) {
+            const bool sw = !ge0(ge0(c) ? q : r);
+            return limit_factor(c, sw ? bd : bu, sw ? bu : bd, sw ? bdr : bur, sw ? bur : bdr);
+          };
+          return mul2(mk(lane(C.x, q0.x, pr.x, buA.x, bdA.x, buR.x, bdR.x),
+                         lane(C.y, q0.y, pr.y, buA.y, bdA.y, buR.y, bdR.y)),
+                      C);
+        } else {
+          return limit2(C, buA, bdA, buR, bdR);
+        }
+      };
+      f2 u = utA, v = vtA, f = zero2, w = zero2;
+      if constexpr (OPT == 0) {  // the basic scheme (kept apart: its code as measured)
+        if (LIMIT) u = limit2(u, buA, bdA, mk(buA.y, bu0[2]), mk(bdA.y, bd0[2]));
+        st2(fxs + (t & 1) * L::SN + s2, donor2(q0, mk(q0.y, pt[2]), u));
+        if (LIMIT) v = limit2(v, buA, bdA, at2(bu0 + EX), at2(bd0 + EX));
+        st2(fys + (t & 1) * L::SN + s2, donor2(q0, at2(pt + EX), v));
+        if (S || zface(t)) {
+          w = wtA;
+          if (LIMIT) w = limit2(w, buA, bdA, buB, bdB);
+          f = donor2(q0, q1, w);
+        }
+      } else {
+        if (LIMIT) u = lim(u, mk(q0.y, pt[2]), mk(buA.y, bu0[2]), mk(bdA.y, bd0[2]));
+        st2(fxs + (t & 1) * L::SN + s2, cflux2<kIGA>(q0, mk(q0.y, pt[2]), u));
+        if (LIMIT) v = lim(v, at2(pt + EX), at2(bu0 + EX), at2(bd0 + EX));
+        st2(fys + (t & 1) * L::SN + s2, cflux2<kIGA>(q0, at2(pt + EX), v));
+        if (S || zface(t)) {
+          w = wtA;
+          if (LIMIT) w = lim(w, q1, buB, bdB);
+          f = cflux2<kIGA>(q0, q1, w);
+        }
       }
       fzB = f;
       if constexpr (TAPE) {

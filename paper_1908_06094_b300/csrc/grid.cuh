@@ -245,22 +245,25 @@ enum : int { kOptDFL = 1, kOptABS = 2, kOptIGA = 4 };
 // cB -> (s+ - s-)/8:
 //   Ft = (|U| - U^2/Gf) (pr - pl)/2 - U (vsum (s1p - s1m) + wsum (s2p - s2m)) / (32 Gf).
 // Ft is itself the corrective flux of the face.
+// Explicitly rounded, like pseudo_velocity.
 template <class T>
 __device__ __forceinline__ T pseudo_flux_iga(T U, T gsum, T pl, T pr, T s1p, T s1m, T s2p,
                                              T s2m, T vsum, T wsum) {
-  const T rG = T(2) * rcp(gsum);                       // 1/Gf
-  const T q = U * rG;
-  const T diff = absv(U) - U * q;                      // |U| - U^2/Gf
-  const T cross = T(0.03125) * (vsum * (s1p - s1m) + wsum * (s2p - s2m));
-  return diff * (T(0.5) * (pr - pl)) - q * cross;
+  const T rG = mul_rn(T(2), rcp(gsum));                // 1/Gf
+  const T q = mul_rn(U, rG);
+  const T diff = fma_rn(-U, q, absv(U));               // |U| - U^2/Gf
+  const T cross = mul_rn(T(0.03125), fma_rn(vsum, sub_rn(s1p, s1m),
+                                            mul_rn(wsum, sub_rn(s2p, s2m))));
+  return fma_rn(diff, mul_rn(T(0.5), sub_rn(pr, pl)), -mul_rn(q, cross));
 }
 
 // Divergent-flow term of one face (option DFL; Smolarkiewicz 1984): with
 // dsum = D_L + D_R, the divergences of the G-weighted Courant numbers of
-// the face's two cells,  -(1/4) U dsum / Gf.
+// the face's two cells,  -(1/4) U dsum / Gf.  Explicitly rounded; a caller
+// adds it with add_rn (no contraction of its last product into the sum).
 template <class T>
 __device__ __forceinline__ T divergent_flow_term(T U, T gsum, T dsum) {
-  return T(-0.5) * U * dsum * rcp(gsum);
+  return mul_rn(mul_rn(mul_rn(T(-0.5), U), dsum), rcp(gsum));
 }
 
 }  // namespace mpd

@@ -182,7 +182,7 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
     const T gs = G[q] + G[at(g, ip, j, k)];
     T r = face(cu[q], gs, pc, p(ip, j, k), s1p, s1m, s2p, s2m, vs, ws);
     if constexpr ((OPT & kOptDFL) != 0)
-      r = r + divergent_flow_term(cu[q], gs, div(i, j, k) + div(ip, j, k));
+      r = add_rn(r, divergent_flow_term(cu[q], gs, div(i, j, k) + div(ip, j, k)));
     ut[q] = r;
   }
   {  // y face between (j) and (jp)
@@ -194,7 +194,7 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
     const T gs = G[q] + G[at(g, i, jp, k)];
     T r = face(cv[q], gs, pc, p(i, jp, k), s1p, s1m, s2p, s2m, us, ws);
     if constexpr ((OPT & kOptDFL) != 0)
-      r = r + divergent_flow_term(cv[q], gs, div(i, j, k) + div(i, jp, k));
+      r = add_rn(r, divergent_flow_term(cv[q], gs, div(i, j, k) + div(i, jp, k)));
     vt[q] = r;
   }
   if (zopen(g, k)) {  // z face between (k) and (k+1); a zero-flux top face is closed
@@ -206,7 +206,7 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
     const T gs = G[q] + G[qp];
     T r = face(cw[q], gs, pc, p(i, j, kp), s1p, s1m, s2p, s2m, us, vs);
     if constexpr ((OPT & kOptDFL) != 0)
-      r = r + divergent_flow_term(cw[q], gs, div(i, j, k) + div(i, j, kp));
+      r = add_rn(r, divergent_flow_term(cw[q], gs, div(i, j, k) + div(i, j, kp)));
     wt[q] = r;
   } else {
     wt[q] = T(0);

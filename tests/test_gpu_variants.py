@@ -173,3 +173,31 @@ def test_options_off_again_restores_the_basic_step():
         m.step_out(d[0], b, *d[1:])
         assert torch.equal(a, b)
         m.close()
+
+
+def _gpu_h(c, opts, h, nsteps, kbc):
+    from paper_1908_06094_b300 import MPDATA
+    m = MPDATA(c.nx, c.ny, c.nz, halo=h, iord=2, nonoscillatory=True, dtype=torch.float32,
+               k_bc=kbc, options=opts, variant=0)
+    d = [to_dev(synth.pad(x, h, fill=np.nan), torch.float32) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    m.step(*d, nsteps=nsteps)
+    torch.cuda.synchronize()
+    out = synth.interior(d[0].double().cpu().numpy(), h)
+    m.close()
+    return out
+
+
+@pytest.mark.parametrize("kbc", [0, 1], ids=["zeroflux", "periodic_k"])
+@pytest.mark.parametrize("shape", [(40, 29, 9), (64, 26, 5)])
+@pytest.mark.parametrize("name", list(OPTS))
+def test_options_two_column_kernel_same_bits(name, shape, kbc):
+    """FP32 with the limiter and an option runs the two-column kernel where
+    nx and the halo are even: bit for bit the one-column kernel (halo 3) on
+    the same interior, 3 steps, and within the tolerance of the oracle."""
+    opts = OPTS[name]
+    c = rounded_inputs(_case(opts, shape, 91 + shape[0], kbc), torch.float32)
+    a = _gpu_h(c, opts, 2, 3, kbc)
+    b = _gpu_h(c, opts, 3, 3, kbc)
+    assert np.array_equal(a, b), int(np.count_nonzero(a != b))
+    ref = synth.interior(_oracle(c, 2, 1, opts, 3, kbc), H)
+    assert rel_err(a, ref) <= 3 * F32_TOL
