@@ -38,6 +38,7 @@ template <class T> __device__ __forceinline__ void aadd(T* p, T v) { atomicAdd(p
 template <class T>
 __global__ void rev_scale_kernel(Geo g, const T* __restrict__ ob, const T* __restrict__ G,
                                  T* __restrict__ sf) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
@@ -97,6 +98,7 @@ __global__ void rev_advance_gather_kernel(Geo g, const T* __restrict__ P,
                                           const T* __restrict__ cw, const T* __restrict__ G,
                                           const T* __restrict__ ob, const T* __restrict__ sf,
                                           T* Pin, T* Pb, Out out) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
@@ -216,6 +218,7 @@ __global__ void rev_beta_kernel(Geo g, const T* __restrict__ P0, const T* __rest
                                 const T* __restrict__ rin, const T* __restrict__ rout,
                                 T* __restrict__ bub, T* __restrict__ bdb, T* P0b,
                                 T* Pb, T* utb, T* vtb, T* wtb) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int i = c.i, j = c.j, k = c.k;
@@ -579,6 +582,7 @@ struct RevPseudoAcc {
 
 template <class T>
 __global__ void rev_pg_kernel(Geo g, const T* __restrict__ wts, T* Pb, T* ub, T* vb, T* wb) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int i = c.i, j = c.j, k = c.k, nz = g.nz;

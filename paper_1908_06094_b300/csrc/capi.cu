@@ -118,7 +118,8 @@ dim3 halo_grid(const Geo& g) {
 template <class T>
 int halo_launch(mpdata_ctx* c, T* f, int kind) {
   MPD_LAUNCH(c, MPDATA_STAGE_HALO,
-             mpd::halo_kernel<T><<<halo_grid(c->g), 256, 0, c->stream>>>(c->g, f, kind));
+             mpd::launch_pdl(mpd::halo_kernel<T>, halo_grid(c->g), 256, 0, c->stream, c->g, f,
+                             kind));
   MPD_CHECK_LAUNCH(c, "halo_kernel");
   return MPDATA_OK;
 }
@@ -176,16 +177,16 @@ void pseudo_launch(mpdata_ctx* c, const T* P, const T* U, const T* V, const T* W
     auto kern = M::march_kernel<double, Op, OPT>;
     if (!c->kc_fwd) c->kc_fwd = march_chunk(c, M::march_kernel<double, M::PseudoMerged>, true);
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-               kern<<<M::march_grid(g, c->kc_fwd), dim3(M::TX, M::TY), 0, c->stream>>>(
-                   g, P, U, V, W, G, op, c->kc_fwd));
+               mpd::launch_pdl(kern, M::march_grid(g, c->kc_fwd), dim3(M::TX, M::TY), 0, c->stream,
+                               g, P, U, V, W, G, op, c->kc_fwd));
   } else if constexpr (OPT != 0) {  // FP32 staged with options: cell-parallel kernel
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-               mpd::staged::pseudo_kernel<T, OPT><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
-                   g, P, U, V, W, G, ut, vt, wt));
+               mpd::launch_pdl(mpd::staged::pseudo_kernel<T, OPT>, cell_grid(g), kCellBlock, 0,
+                               c->stream, g, P, U, V, W, G, ut, vt, wt));
   } else {
     MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-               mpd::staged::pseudo_kernel<T><<<cell_grid(g), kCellBlock, 0, c->stream>>>(
-                   g, P, U, V, W, G, ut, vt, wt));
+               mpd::launch_pdl(mpd::staged::pseudo_kernel<T>, cell_grid(g), kCellBlock, 0,
+                               c->stream, g, P, U, V, W, G, ut, vt, wt));
   }
 }
 
@@ -216,15 +217,18 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
   T* cur = c->iord == 1 ? psi_out : (T*)c->psi1;
   if (rg) {
     MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
-               (flux_kernel<T, true><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz, G,
-                                                                rg)));
+               (mpd::launch_pdl(flux_kernel<T, true>, grid, kCellBlock, 0, s, g, psi, U, V, W, fx,
+                                fy, fz, G, rg)));
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-               (advance_kernel<T, 2><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur, rg)));
+               (mpd::launch_pdl(advance_kernel<T, 2>, grid, kCellBlock, 0, s, g, psi, fx, fy, fz, G,
+                                cur, rg)));
   } else {
     MPD_LAUNCH(c, MPDATA_STAGE_DONOR,
-               flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
+               mpd::launch_pdl(flux_kernel<T>, grid, kCellBlock, 0, s, g, psi, U, V, W, fx, fy, fz,
+                               nullptr, nullptr));
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, cur));
+               mpd::launch_pdl(advance_kernel<T>, grid, kCellBlock, 0, s, g, psi, fx, fy, fz, G,
+                               cur, nullptr));
   }
   MPD_CHECK_LAUNCH(c, "donor pass");
   // corrective passes
@@ -241,9 +245,9 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
     if (c->nonosc) {
       const T* bf[3] = {kFin ? fx : tset[0], kFin ? fy : tset[1], kFin ? fz : tset[2]};
       MPD_LAUNCH(c, MPDATA_STAGE_BETA,
-                 (beta_kernel<T, kUnit || kFin><<<grid, kCellBlock, 0, s>>>(
-                     g, psi, cur, bf[0], bf[1], bf[2], G, (T*)c->bu, (T*)c->bd, nullptr,
-                     nullptr)));
+                 (mpd::launch_pdl(beta_kernel<T, kUnit || kFin>, grid, kCellBlock, 0, s, g, psi,
+                                  cur, bf[0], bf[1], bf[2], G, (T*)c->bu, (T*)c->bd, nullptr,
+                                  nullptr)));
       if (kFin && !more && rg) {  // the last pass: limited fluxes and advance in one
         // with the halo images of psi^(n+1) where one image a side covers
         // the halo and the k halo's images fall on the bottom and top levels
@@ -252,39 +256,40 @@ int step_staged_opt(mpdata_ctx* c, const T* psi_in, T* psi_out, const T* U, cons
         const bool img = g.nx >= 2 * g.h && g.ny >= 2 * g.h && g.nz > 2 * g.h;
         if (img)
           MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-                     (limadvance_kernel<T, true><<<grid, kCellBlock, 0, s>>>(
-                         g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
-                         rg, dest)));
+                     (mpd::launch_pdl(limadvance_kernel<T, true>, grid, kCellBlock, 0, s, g, cur,
+                                      tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
+                                      rg, dest)));
         else
           MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-                     (limadvance_kernel<T, false><<<grid, kCellBlock, 0, s>>>(
-                         g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
-                         rg, dest)));
+                     (mpd::launch_pdl(limadvance_kernel<T, false>, grid, kCellBlock, 0, s, g, cur,
+                                      tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
+                                      rg, dest)));
         c->halo_done = img;
         MPD_CHECK_LAUNCH(c, "corrective pass");
         cur = dest;
         continue;  // the last pass: nothing carries over
       }
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                 (limflux_kernel<T, OPT, kFin><<<grid, kCellBlock, 0, s>>>(
-                     g, cur, tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
-                     more ? lset[0] : nullptr, more ? lset[1] : nullptr,
-                     more ? lset[2] : nullptr)));
+                 (mpd::launch_pdl(limflux_kernel<T, OPT, kFin>, grid, kCellBlock, 0, s, g, cur,
+                                  tset[0], tset[1], tset[2], (T*)c->bu, (T*)c->bd, fx, fy, fz,
+                                  more ? lset[0] : nullptr, more ? lset[1] : nullptr,
+                                  more ? lset[2] : nullptr)));
     } else if (kUnit) {  // the unlimited pseudo-fluxes themselves
       ffx = tset[0]; ffy = tset[1]; ffz = tset[2];
     } else if (kFin) {  // fx, fy, fz hold the pass's fluxes already
     } else {
       MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                 flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, tset[0], tset[1], tset[2],
-                                                             fx, fy, fz));
+                 mpd::launch_pdl(flux_kernel<T>, grid, kCellBlock, 0, s, g, cur, tset[0], tset[1],
+                                 tset[2], fx, fy, fz, nullptr, nullptr));
     }
     if (rg) {
       MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-                 (advance_kernel<T, 2><<<grid, kCellBlock, 0, s>>>(g, cur, ffx, ffy, ffz, G, dest,
-                                                                  rg)));
+                 (mpd::launch_pdl(advance_kernel<T, 2>, grid, kCellBlock, 0, s, g, cur, ffx, ffy,
+                                  ffz, G, dest, rg)));
     } else {
       MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-                 advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, cur, ffx, ffy, ffz, G, dest));
+                 mpd::launch_pdl(advance_kernel<T>, grid, kCellBlock, 0, s, g, cur, ffx, ffy, ffz,
+                                 G, dest, nullptr));
     }
     MPD_CHECK_LAUNCH(c, "corrective pass");
     cur = dest;
@@ -522,13 +527,13 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
       if (tape) {
         auto kx = fusedx_pick<true>(c);
         MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
-                   kx<<<gx, fusedx_threads(), fusedx_smem(), c->stream>>>(
-                       g, c->x2_kchunk, in, U, V, W, G, out, tape->p1, tstride));
+                   mpd::launch_pdl(kx, gx, fusedx_threads(), fusedx_smem(), c->stream, g,
+                                   c->x2_kchunk, in, U, V, W, G, out, tape->p1, tstride));
       } else {
         auto kx = fusedx_pick(c);
         MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
-                   kx<<<gx, fusedx_threads(), fusedx_smem(), c->stream>>>(
-                       g, c->x2_kchunk, in, U, V, W, G, out, nullptr, 0));
+                   mpd::launch_pdl(kx, gx, fusedx_threads(), fusedx_smem(), c->stream, g,
+                                   c->x2_kchunk, in, U, V, W, G, out, nullptr, 0));
       }
       MPD_CHECK_LAUNCH(c, "fused step kernel");
       return MPDATA_OK;
@@ -539,8 +544,8 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
   const mpd::fused2::TapeOut<T> tp = tape ? *tape : mpd::fused2::TapeOut<T>{};
   auto go = [&](auto kern) {
     MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
-               kern<<<grid, fused_threads<T>(), bytes, c->stream>>>(g, c->kchunk, in, U, V, W, G,
-                                                                   out, tp));
+               mpd::launch_pdl(kern, grid, fused_threads<T>(), bytes, c->stream, g, c->kchunk, in,
+                               U, V, W, G, out, tp));
   };
   if (tape) go(fused_pick<T, true>(c));
   else go(fused_pick<T, false>(c));
@@ -599,9 +604,10 @@ int step_n(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G
 template <class T>
 int mass_launch(mpdata_ctx* c, const T* psi, const T* G, double* out) {
   MPD_LAUNCH(c, MPDATA_STAGE_MASS,
-             mpd::mass_partial_launch<T>(c->g, psi, G, c->part, c->stream));
+             mpd::mass_partial_launch<T>(c->g, psi, G, c->part, c->stream, true));
   MPD_LAUNCH(c, MPDATA_STAGE_MASS,
-             mpd::mass_final_kernel<<<1, 1024, 0, c->stream>>>(c->part, mpd::MASS_BLOCKS, out));
+             mpd::launch_pdl(mpd::mass_final_kernel, 1, 1024, 0, c->stream, c->part,
+                             mpd::MASS_BLOCKS, out));
   MPD_CHECK_LAUNCH(c, "mass kernels");
   return MPDATA_OK;
 }
@@ -662,8 +668,10 @@ Tape<T> tape_view(const mpdata_ctx* c, const void* base, int m = 2) {
 template <class T>
 int halo_fold_launch(mpdata_ctx* c, T* f) {
   const dim3 hg = halo_grid(c->g);
-  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_fold_kernel<T><<<hg, 256, 0, c->stream>>>(c->g, f));
-  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::halo_zero_kernel<T><<<hg, 256, 0, c->stream>>>(c->g, f));
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::launch_pdl(mpd::halo_fold_kernel<T>, hg, 256, 0, c->stream,
+                                                   c->g, f));
+  MPD_LAUNCH(c, MPDATA_STAGE_HALO, mpd::launch_pdl(mpd::halo_zero_kernel<T>, hg, 256, 0, c->stream,
+                                                   c->g, f));
   MPD_CHECK_LAUNCH(c, "halo adjoint fold");
   return MPDATA_OK;
 }
@@ -685,13 +693,15 @@ int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const
   const dim3 grid = cell_grid(g);
   cudaStream_t s = c->stream;
   T *fx = (T*)c->fx, *fy = (T*)c->fy, *fz = (T*)c->fz;
-  MPD_LAUNCH(c, MPDATA_STAGE_DONOR, flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, U, V, W, fx, fy, fz));
+  MPD_LAUNCH(c, MPDATA_STAGE_DONOR, mpd::launch_pdl(flux_kernel<T>, grid, kCellBlock, 0, s, g, psi,
+                                                    U, V, W, fx, fy, fz, nullptr, nullptr));
   if (c->iord == 1) {
-    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G, out));
+    MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE, mpd::launch_pdl(advance_kernel<T>, grid, kCellBlock, 0, s,
+                                                        g, psi, fx, fy, fz, G, out, nullptr));
   } else {
     MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-               advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, psi, fx, fy, fz, G,
-                                                             tape_view<T>(c, base, 2).p1));
+               mpd::launch_pdl(advance_kernel<T>, grid, kCellBlock, 0, s, g, psi, fx, fy, fz, G,
+                               tape_view<T>(c, base, 2).p1, nullptr));
     const T *cu = U, *cv = V, *cw = W;  // the pass's input velocities
     // FP64: the pseudo-velocity stage stores the donor fluxes too, as in
     // the plain staged step (the same kernels, so the same bits)
@@ -703,22 +713,23 @@ int step_tape(mpdata_ctx* c, const T* psi, T* out, const T* U, const T* V, const
       if (c->nonosc) {
         const T* bf[3] = {kFin ? fx : tp.ut, kFin ? fy : tp.vt, kFin ? fz : tp.wt};
         MPD_LAUNCH(c, MPDATA_STAGE_BETA,
-                   (beta_kernel<T, kFin><<<grid, kCellBlock, 0, s>>>(
-                       g, psi, tp.p1, bf[0], bf[1], bf[2], G, tp.bu, tp.bd, tp.ri, tp.ro)));
+                   (mpd::launch_pdl(beta_kernel<T, kFin>, grid, kCellBlock, 0, s, g, psi, tp.p1,
+                                    bf[0], bf[1], bf[2], G, tp.bu, tp.bd, tp.ri, tp.ro)));
         MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                   (limflux_kernel<T, 0, kFin><<<grid, kCellBlock, 0, s>>>(
-                       g, tp.p1, tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, fx, fy, fz, tp.ul, tp.vl,
-                       tp.wl)));
+                   (mpd::launch_pdl(limflux_kernel<T, 0, kFin>, grid, kCellBlock, 0, s, g, tp.p1,
+                                    tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, fx, fy, fz, tp.ul, tp.vl,
+                                    tp.wl)));
         cu = tp.ul; cv = tp.vl; cw = tp.wl;
       } else {
         if (!kFin)
           MPD_LAUNCH(c, MPDATA_STAGE_LIMIT,
-                     flux_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, tp.ut, tp.vt, tp.wt,
-                                                               fx, fy, fz));
+                     mpd::launch_pdl(flux_kernel<T>, grid, kCellBlock, 0, s, g, tp.p1, tp.ut, tp.vt,
+                                     tp.wt, fx, fy, fz, nullptr, nullptr));
         cu = tp.ut; cv = tp.vt; cw = tp.wt;
       }
       MPD_LAUNCH(c, MPDATA_STAGE_ADVANCE,
-                 advance_kernel<T><<<grid, kCellBlock, 0, s>>>(g, tp.p1, fx, fy, fz, G, dest));
+                 mpd::launch_pdl(advance_kernel<T>, grid, kCellBlock, 0, s, g, tp.p1, fx, fy, fz, G,
+                                 dest, nullptr));
     }
   }
   MPD_CHECK_LAUNCH(c, "taped forward step");
@@ -770,10 +781,11 @@ int adjoint_tape(mpdata_ctx* c, const void* tape, const T* psi, const T* U, cons
                  T* Pin, T* Pb, auto out, auto add_p) {
     constexpr bool kAddP = decltype(add_p)::value;
     if (kPreS)
-      MPD_LAUNCH(c, stage, rev_scale_kernel<T><<<grid, kCellBlock, 0, s>>>(g, ob, G, sf));
+      MPD_LAUNCH(c, stage, mpd::launch_pdl(rev_scale_kernel<T>, grid, kCellBlock, 0, s, g, ob, G,
+                                           sf));
     MPD_LAUNCH(c, stage,
-               (rev_advance_gather_kernel<T, kAddP, kPreS, decltype(out)>
-                <<<grid, kCellBlock, 0, s>>>(g, P, cu_, cv_, cw_, G, ob, sf, Pin, Pb, out)));
+               (mpd::launch_pdl(rev_advance_gather_kernel<T, kAddP, kPreS, decltype(out)>, grid,
+                                kCellBlock, 0, s, g, P, cu_, cv_, cw_, G, ob, sf, Pin, Pb, out)));
   };
   using Store = std::false_type;
   using Add = std::true_type;
@@ -793,10 +805,10 @@ int adjoint_tape(mpdata_ctx* c, const void* tape, const T* psi, const T* U, cons
         adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ul, tp.vl, tp.wl, ob, nullptr, Pb,
             LimitOut<T>{tp.ut, tp.vt, tp.wt, tp.bu, tp.bd, utb, vtb, wtb, bub, bdb, au, av, aw},
             Store{});
-        MPD_LAUNCH(c, MPDATA_STAGE_BETA, rev_beta_kernel<T><<<grid, kCellBlock, 0, s>>>(
-                                             g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G, tp.bu,
-                                             tp.bd, tp.ri, tp.ro, bub, bdb, p0b, Pb, utb, vtb,
-                                             wtb));
+        MPD_LAUNCH(c, MPDATA_STAGE_BETA, mpd::launch_pdl(rev_beta_kernel<T>, grid, kCellBlock, 0, s,
+                                                         g, psi, tp.p1, tp.ut, tp.vt, tp.wt, G,
+                                                         tp.bu, tp.bd, tp.ri, tp.ro, bub, bdb, p0b,
+                                                         Pb, utb, vtb, wtb));
       } else {
         adv(MPDATA_STAGE_ADVANCE, tp.p1, tp.ut, tp.vt, tp.wt, ob, nullptr, Pb,
             VelOut<T, false>{utb, vtb, wtb, au, av, aw}, Store{});
@@ -822,17 +834,18 @@ int adjoint_tape(mpdata_ctx* c, const void* tape, const T* psi, const T* U, cons
         if (!c->kc_rev) c->kc_rev = march_chunk(c, kern, false);
         const RevPseudoAcc<T> op{utb, vtb, wtb, Pb, tu, tv, tw};
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-                   kern<<<M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s>>>(
-                       g, tp.p1, iu, iv, iw, G, op, c->kc_rev));
+                   mpd::launch_pdl(kern, M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s, g,
+                                   tp.p1, iu, iv, iw, G, op, c->kc_rev));
       } else {
         auto kern = M::march_kernel<T, RevPseudo<T>>;
         if (!c->kc_rev) c->kc_rev = march_chunk(c, kern, true);
         const RevPseudo<T> op{utb, vtb, wtb, wts, g.total, tu, tv, tw};
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-                   kern<<<M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s>>>(
-                       g, tp.p1, iu, iv, iw, G, op, c->kc_rev));
+                   mpd::launch_pdl(kern, M::march_grid(g, c->kc_rev), dim3(M::TX, M::TY), 0, s, g,
+                                   tp.p1, iu, iv, iw, G, op, c->kc_rev));
         MPD_LAUNCH(c, MPDATA_STAGE_PSEUDO,
-                   rev_pg_kernel<T><<<grid, kCellBlock, 0, s>>>(g, wts, Pb, tu, tv, tw));
+                   mpd::launch_pdl(rev_pg_kernel<T>, grid, kCellBlock, 0, s, g, wts, Pb, tu, tv,
+                                   tw));
       }
       ob = Pb;
     }
@@ -846,7 +859,7 @@ int adjoint_tape(mpdata_ctx* c, const void* tape, const T* psi, const T* U, cons
     if (e != cudaSuccess) return cuda_fail(c, e, "adjoint result copy");
   } else {  // psib's interior holds the result; its halo is cleared
     MPD_LAUNCH(c, MPDATA_STAGE_HALO,
-               mpd::halo_zero_kernel<T><<<halo_grid(g), 256, 0, s>>>(g, psib));
+               mpd::launch_pdl(mpd::halo_zero_kernel<T>, halo_grid(g), 256, 0, s, g, psib));
   }
   MPD_CHECK_LAUNCH(c, "adjoint reverse kernels");
   c->adj_zero = true;

@@ -593,6 +593,7 @@ __global__ void __launch_bounds__((TX + 4) * (TY + 4), MINB)
 step_kernel2(Geo g, int kchunk, const T* __restrict__ P0, const T* __restrict__ U,
              const T* __restrict__ V, const T* __restrict__ W, const T* __restrict__ G,
              T* __restrict__ out, TapeOut<T> tape) {
+  pdl_enter();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int k0 = blockIdx.z * kchunk;
   step_tile2<T, TX, TY, LIMIT, TAPE, UNROLL, KPER, OPT, true, OPENIJ, I32>(g, blockIdx.x * TX, blockIdx.y * TY, k0,

@@ -227,6 +227,7 @@ step_kernel_x2(Geo g, int kchunk, const float* __restrict__ P0, const float* __r
                const float* __restrict__ V, const float* __restrict__ W,
                const float* __restrict__ G, float* __restrict__ out,
                float* __restrict__ tape, long long tstride) {
+  pdl_enter();
   using L = Layout<TX, TY>;
   using Map = PairMap<TX, TY>;
   constexpr int EX = L::EX, RX = L::RX;

@@ -194,6 +194,37 @@ __device__ __forceinline__ double rcp(double b) {
   return fma(r, fma(e, e, e), r);
 }
 
+// Programmatic dependent launch.  A kernel launched with programmatic
+// stream serialization may be scheduled while the kernel before it in the
+// stream is still running; it first waits until that kernel has completed
+// and its writes are visible, then lets the next kernel of the stream be
+// scheduled the same way.  This hides the launch latency between the small
+// kernels of a step.  Launched without the attribute, the wait returns at
+// once and the trigger does nothing.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Host: launch kernel k, which begins with pdl_enter(), with programmatic
+// stream serialization.  A launch error is reported as for <<<...>>>: by
+// cudaGetLastError.
+template <class... P, class... A>
+inline void launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       A&&... a) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, k, std::forward<A>(a)...);
+}
+
 // Limited velocity on a face (non-oscillatory option):
 // min(1, bd_L, bu_R) [Ut]+ + min(1, bu_L, bd_R) [Ut]-; the betas are >= 0,
 // and only one of the two parts is non-zero.  The factor is selected before

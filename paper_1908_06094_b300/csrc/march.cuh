@@ -189,6 +189,7 @@ __global__ void __launch_bounds__(TX * TY, MarchMinB<T, Op>::v)
 march_kernel(Geo g, const T* __restrict__ P, const T* __restrict__ cu,
              const T* __restrict__ cv, const T* __restrict__ cw, const T* __restrict__ G, Op op,
              int kc) {
+  pdl_enter();
   constexpr bool kABS = (OPT & kOptABS) != 0, kDFL = (OPT & kOptDFL) != 0;
   auto lp = [&](int64_t a) { return kABS ? absv(P[a]) : P[a]; };
   // op is a per-thread copy: accumulating ops keep their flush positions in it

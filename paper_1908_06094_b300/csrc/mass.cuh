@@ -90,6 +90,7 @@ template <class T, bool V2 = false>
 __global__ void __launch_bounds__(MASS_THREADS)
 mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
                     double* __restrict__ part) {
+  pdl_enter();
   __shared__ double sh[MASS_THREADS];
   using Acc = typename MassAcc<T>::type;
   // (V2: half the rows a group, so a group still adds at most Acc::R points)
@@ -154,6 +155,7 @@ mass_partial_kernel(Geo g, const T* __restrict__ psi, const T* __restrict__ G,
 
 static __global__ void __launch_bounds__(1024)
 mass_final_kernel(const double* __restrict__ part, int np, double* __restrict__ out) {
+  pdl_enter();
   __shared__ double sh[1024];
   double s = 0.0;
   for (int q = threadIdx.x; q < np; q += blockDim.x) s += part[q];
@@ -165,11 +167,11 @@ mass_final_kernel(const double* __restrict__ part, int np, double* __restrict__ 
 // starts on an even element (nx and h even; the fields are 16-byte aligned).
 template <class T>
 inline void mass_partial_launch(const Geo& g, const T* psi, const T* G, double* part,
-                                cudaStream_t s) {
-  if (g.nx % 2 == 0 && g.h % 2 == 0)
-    mass_partial_kernel<T, true><<<MASS_BLOCKS, MASS_THREADS, 0, s>>>(g, psi, G, part);
-  else
-    mass_partial_kernel<T, false><<<MASS_BLOCKS, MASS_THREADS, 0, s>>>(g, psi, G, part);
+                                cudaStream_t s, bool pdl = false) {
+  auto k = (g.nx % 2 == 0 && g.h % 2 == 0) ? mass_partial_kernel<T, true>
+                                           : mass_partial_kernel<T, false>;
+  if (pdl) launch_pdl(k, MASS_BLOCKS, MASS_THREADS, 0, s, g, psi, G, part);
+  else k<<<MASS_BLOCKS, MASS_THREADS, 0, s>>>(g, psi, G, part);
 }
 
 }  // namespace mpd

@@ -41,6 +41,7 @@ __global__ void flux_kernel(Geo g, const T* __restrict__ P, const T* __restrict_
                             const T* __restrict__ cv, const T* __restrict__ cw,
                             T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ fz,
                             const T* __restrict__ G = nullptr, T* __restrict__ rg = nullptr) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   int64_t q = at(g, c.i, c.j, c.k);
@@ -61,6 +62,7 @@ template <class T, int RG = 0>
 __global__ void advance_kernel(Geo g, const T* P, const T* __restrict__ fx,
                                const T* __restrict__ fy, const T* __restrict__ fz,
                                const T* __restrict__ G, T* out, T* rg = nullptr) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   int64_t q = at(g, c.i, c.j, c.k);
@@ -115,6 +117,7 @@ __global__ void limadvance_kernel(Geo g, const T* __restrict__ P, const T* __res
                                   const T* __restrict__ fx, const T* __restrict__ fy,
                                   const T* __restrict__ fz, const T* __restrict__ rg,
                                   T* __restrict__ out) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
@@ -149,6 +152,7 @@ __global__ void pseudo_kernel(Geo g, const T* __restrict__ P, const T* __restric
                               const T* __restrict__ cv, const T* __restrict__ cw,
                               const T* __restrict__ G, T* __restrict__ ut, T* __restrict__ vt,
                               T* __restrict__ wt) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int i = c.i, j = c.j, k = c.k;
@@ -227,6 +231,7 @@ __global__ void beta_kernel(Geo g, const T* __restrict__ P0, const T* __restrict
                             const T* __restrict__ wt, const T* __restrict__ G,
                             T* __restrict__ bu, T* __restrict__ bd, T* __restrict__ rin,
                             T* __restrict__ rout) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const T eps = Eps<T>::v, zero = T(0);
@@ -302,6 +307,7 @@ __global__ void limflux_kernel(Geo g, const T* __restrict__ P, const T* __restri
                                const T* __restrict__ bu, const T* __restrict__ bd,
                                T* __restrict__ fx, T* __restrict__ fy, T* __restrict__ fz,
                                T* __restrict__ ul, T* __restrict__ vl, T* __restrict__ wl) {
+  pdl_enter();
   Cell c = cell_of(g);
   if (!c.ok) return;
   const int64_t q = at(g, c.i, c.j, c.k);
@@ -418,6 +424,7 @@ __device__ __forceinline__ int64_t halo_source(const Geo& g, const HaloCell& c) 
 // faces, interior included) are 0.
 template <class T>
 __global__ void halo_kernel(Geo g, T* __restrict__ f, int kind) {
+  pdl_enter();
   const bool top = kind == 1 && !g.kper;
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= halo_count(g, top)) return;
@@ -432,6 +439,7 @@ __global__ void halo_kernel(Geo g, T* __restrict__ f, int kind) {
 // (halo_zero_kernel) then clears the halo.
 template <class T>
 __global__ void halo_fold_kernel(Geo g, T* __restrict__ f) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= halo_count(g, false)) return;
   const HaloCell c = halo_cell(g, false, t);
@@ -441,6 +449,7 @@ __global__ void halo_fold_kernel(Geo g, T* __restrict__ f) {
 
 template <class T>
 __global__ void halo_zero_kernel(Geo g, T* __restrict__ f) {
+  pdl_enter();
   const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (t >= halo_count(g, false)) return;
   f[padded_at(g, halo_cell(g, false, t))] = T(0);
