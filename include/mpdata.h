@@ -79,7 +79,9 @@ enum mpdata_variant {
   MPDATA_STAGED = 1, /* one kernel per stage, intermediates in memory      */
   MPDATA_AUTO = 2    /* default: the faster of the two for the dtype on the
                         B300 (FP64: staged, since the fused kernel's halo
-                        recompute costs FP64-pipe work; FP32: fused)        */
+                        recompute costs FP64-pipe work, except the plain
+                        step of a one-level grid of at most 128 x 128
+                        columns, fused on 8 x 8 tiles; FP32: fused)         */
 };
 
 /* Create a context for one grid.

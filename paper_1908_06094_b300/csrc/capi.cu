@@ -36,6 +36,9 @@ struct mpdata_ctx {
   // the two-column FP32 kernel's launch shape (x2_ok: it runs the untaped
   // FP32 step)
   int x2_ok, x2_nchunks, x2_kchunk;
+  // the FP64 one-level grid of at most 128 x 128 columns runs its plain
+  // step on 8 x 8 tiles (s8_ok)
+  int s8_ok;
   // the last staged step wrote the halo of its output itself
   bool halo_done;
   // level-chunk lengths of the k-marching kernels (0: not chosen yet)
@@ -413,6 +416,41 @@ int pick_chunks(const Geo& g, long ctas, int sms, int* kchunk) {
   return (g.nz + *kchunk - 1) / *kchunk;
 }
 
+// The FP64 step of a small one-level grid (at most 128 x 128 columns): the
+// one-kernel step on 8 x 8 tiles.  FP64 issues 2 lanes an SM a clock, so a
+// step of a few thousand cells is bound by how many SMs share its FP64 work:
+// the staged kernels' 32 x 8 blocks, or 32 x 8 tiles, cover 16-64 SMs of a
+// 64 x 64 to 128 x 128 grid, 8 x 8 tiles 64-256 (their 2.25x ring recompute
+// included, 64 x 64: 12.4 against 18.1 us a step for the staged kernels
+// and 23.2 for 32 x 8 tiles; 128 x 128: 17.7 against 19.2; 256 x 256 is
+// faster staged, 42 against 62).
+struct FusedS { static constexpr int TX = 8, TY = 8, MINB = 1; };
+template <bool LIMIT, bool KPER>
+auto fused_small_ptr() {
+  return mpd::fused2::step_kernel2<double, FusedS::TX, FusedS::TY, FusedS::MINB, LIMIT, false,
+                                   KPER, 0, 1, false, true>;
+}
+auto fused_small_pick(const mpdata_ctx* c) {
+  if (c->g.kper) return c->nonosc ? fused_small_ptr<true, true>() : fused_small_ptr<false, true>();
+  return c->nonosc ? fused_small_ptr<true, false>() : fused_small_ptr<false, false>();
+}
+constexpr size_t fused_small_smem() {
+  return mpd::fused2::Layout<double, FusedS::TX, FusedS::TY>::bytes;
+}
+void fused_small_setup(mpdata_ctx* c) {
+  const Geo& g = c->g;
+  c->s8_ok = 0;
+  if (c->dtype != MPDATA_F64 || !c->fused_ok || g.openij || g.nz != 1 ||
+      (int64_t)g.nx * g.ny > 128 * 128)
+    return;
+  if (cudaFuncSetAttribute(fused_small_pick(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_small_smem()) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  c->s8_ok = 1;
+}
+
 // The two-column FP32 step (fusedx.cuh): its tile (32 x 24 columns, 504
 // threads of two columns, up to 128 registers) and instances.
 struct FusedX { static constexpr int TX = 32, TY = 24, MINB = 1; };
@@ -480,6 +518,7 @@ int fused_setup(mpdata_ctx* c) {
   const Geo& g = c->g;
   c->fused_ok = 0;
   c->x2_ok = 0;
+  c->s8_ok = 0;
   // the periodic images a column writes need nx, ny >= 2h; a slab writes
   // none and needs only an interior as wide as the strips it sends
   const int minw = g.openij ? g.h : 2 * g.h;
@@ -502,6 +541,7 @@ int fused_setup(mpdata_ctx* c) {
   c->nchunks = pick_chunks(g, ctas, sms, &c->kchunk);
   c->fused_ok = 1;
   fusedx_setup(c);
+  fused_small_setup(c);
   return MPDATA_OK;
 }
 
@@ -539,6 +579,17 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
       return MPDATA_OK;
     }
   }
+  if constexpr (std::is_same<T, double>::value) {
+    if (c->s8_ok && !tape && c->opts == 0) {  // a small one-level grid: 8 x 8 tiles
+      const dim3 gs((g.nx + FusedS::TX - 1) / FusedS::TX, (g.ny + FusedS::TY - 1) / FusedS::TY, 1);
+      MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+                 mpd::launch_pdl(fused_small_pick(c), gs, (FusedS::TX + 4) * (FusedS::TY + 4),
+                                 fused_small_smem(), c->stream, g, g.nz, in, U, V, W, G, out,
+                                 mpd::fused2::TapeOut<double>{}));
+      MPD_CHECK_LAUNCH(c, "fused step kernel");
+      return MPDATA_OK;
+    }
+  }
   dim3 grid((g.nx + F::TX - 1) / F::TX, (g.ny + F::TY - 1) / F::TY, c->nchunks);
   const size_t bytes = fused_smem<T>();
   const mpd::fused2::TapeOut<T> tp = tape ? *tape : mpd::fused2::TapeOut<T>{};
@@ -562,12 +613,17 @@ bool use_fused(const mpdata_ctx* c) {
   if (c->variant == MPDATA_AUTO) return c->dtype == MPDATA_F32;
   return c->variant == MPDATA_FUSED;
 }
+// The plain step of a small one-level FP64 grid runs fused on 8 x 8 tiles
+// unless the staged kernels are asked for.
+bool use_fused_plain(const mpdata_ctx* c) {
+  return use_fused(c) || (c->s8_ok && c->opts == 0 && c->variant != MPDATA_STAGED);
+}
 
 // One step psi_in -> psi_out (distinct buffers), halo of psi_out filled.
 template <class T>
 int step_out(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, const T* W,
              const T* G) {
-  if (use_fused(c)) return fused_launch<T>(c, in, out, U, V, W, G);
+  if (use_fused_plain(c)) return fused_launch<T>(c, in, out, U, V, W, G);
   int rc = step_staged<T>(c, in, out, U, V, W, G);
   if (rc) return rc;
   if (c->halo_done) return MPDATA_OK;  // the last pass wrote the halo images
@@ -577,7 +633,7 @@ int step_out(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, const T
 template <class T>
 int step_n(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G, int nsteps) {
   if (nsteps == 0) return MPDATA_OK;
-  if (!use_fused(c)) {
+  if (!use_fused_plain(c)) {
     for (int s = 0; s < nsteps; ++s) {
       int rc = step_staged<T>(c, psi, psi, U, V, W, G);
       if (rc) return rc;

@@ -313,3 +313,30 @@ def test_iord_and_halo_range(iord, h, nonosc, dtype, variant):
     ref_halo = np.pad(np.pad(inner, ((0, 0), (h, h), (h, h)), mode="wrap"),
                       ((h, h), (0, 0), (0, 0)), mode="edge")
     assert np.array_equal(got, ref_halo)
+
+
+SMALL_2D = [(64, 64, 1), (37, 29, 1), (128, 128, 1), (8, 12, 1), (129, 120, 1), (130, 128, 1)]
+
+
+@pytest.mark.parametrize("kbc", [0, 1], ids=["zeroflux", "periodic_k"])
+@pytest.mark.parametrize("nonosc", [0, 1])
+@pytest.mark.parametrize("shape", SMALL_2D, ids=[f"{a}x{b}x{c}" for a, b, c in SMALL_2D])
+def test_f64_one_level_grid_default_step(shape, nonosc, kbc):
+    """FP64 on one level: the default step (the one-kernel step on 8 x 8
+    tiles up to 128 x 128 columns, the staged kernels above) against the
+    oracle and against the staged kernels, 1 and 5 steps, the halo of the
+    result filled."""
+    nx, ny, nz = shape
+    c = synth.random_case(nx, ny, nz, seed=nx * 7 + ny, cmax=0.4, kbc=kbc)
+    P = [synth.pad(x, c.halo) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    for nsteps in (1, 5):
+        ref = oracle.run(*P, h=c.halo, iord=2, nonosc=nonosc, nsteps=nsteps, kbc=kbc)
+        got = run_library(c, torch.float64, 2, nonosc, nsteps, k_bc=kbc)
+        staged = run_library(c, torch.float64, 2, nonosc, nsteps, variant=1, k_bc=kbc)
+        assert rel_err(got, ref) <= F64_TOL * nsteps, nsteps
+        assert rel_err(got, staged) <= F64_TOL * nsteps, nsteps
+        ref_halo = ref.copy()
+        oracle.fill_halo(ref_halo, c.halo, kind=0, kbc=kbc)
+        h = c.halo
+        assert rel_err(got[:h], ref_halo[:h]) <= F64_TOL * nsteps
+        assert rel_err(got[:, :h], ref_halo[:, :h]) <= F64_TOL * nsteps
