@@ -649,10 +649,15 @@ int step_n(mpdata_ctx* c, T* psi, const T* U, const T* V, const T* W, const T* G
     if (rc) return rc;
     src = dst;
   }
-  if (src != psi) {
-    cudaError_t e = cudaMemcpyAsync(psi, src, (size_t)c->g.total * sizeof(T),
-                                    cudaMemcpyDeviceToDevice, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "copy-back");
+  if (src != psi) {  // the copy back: a kernel, so that it too overlaps its launch
+    const int64_t n = c->g.total;
+    const bool vec = (((uintptr_t)src | (uintptr_t)psi) & 15) == 0;
+    const int64_t items = vec ? n / (16 / (int64_t)sizeof(T)) + 1 : n;
+    const unsigned blocks = (unsigned)std::min<int64_t>((items + 255) / 256, 148 * 8);
+    MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+               mpd::launch_pdl(mpd::copy_kernel<T>, blocks, 256, 0, c->stream, src, psi,
+                               n, vec));
+    MPD_CHECK_LAUNCH(c, "copy-back");
   }
   return MPDATA_OK;
 }
