@@ -81,7 +81,8 @@ enum mpdata_variant {
                         B300 (FP64: staged, since the fused kernel's halo
                         recompute costs FP64-pipe work, except the plain
                         step of a one-level grid of at most 128 x 128
-                        columns, fused on 8 x 8 tiles; FP32: fused)         */
+                        columns, fused on 8 x 4 or 8 x 8 tiles; FP32:
+                        fused)                                             */
 };
 
 /* Create a context for one grid.

@@ -37,8 +37,8 @@ struct mpdata_ctx {
   // FP32 step)
   int x2_ok, x2_nchunks, x2_kchunk;
   // the FP64 one-level grid of at most 128 x 128 columns runs its plain
-  // step on 8 x 8 tiles (s8_ok)
-  int s8_ok;
+  // step on 8 x small_ty tiles (0: not)
+  int small_ty;
   // the last staged step wrote the halo of its output itself
   bool halo_done;
   // level-chunk lengths of the k-marching kernels (0: not chosen yet)
@@ -417,38 +417,57 @@ int pick_chunks(const Geo& g, long ctas, int sms, int* kchunk) {
 }
 
 // The FP64 step of a small one-level grid (at most 128 x 128 columns): the
-// one-kernel step on 8 x 8 tiles.  FP64 issues 2 lanes an SM a clock, so a
+// one-kernel step on 8 x TY tiles.  FP64 issues 2 lanes an SM a clock, so a
 // step of a few thousand cells is bound by how many SMs share its FP64 work:
 // the staged kernels' 32 x 8 blocks, or 32 x 8 tiles, cover 16-64 SMs of a
-// 64 x 64 to 128 x 128 grid, 8 x 8 tiles 64-256 (their 2.25x ring recompute
-// included, 64 x 64: 12.4 against 18.1 us a step for the staged kernels
-// and 23.2 for 32 x 8 tiles; 128 x 128: 17.7 against 19.2; 256 x 256 is
-// faster staged, 42 against 62).
-struct FusedS { static constexpr int TX = 8, TY = 8, MINB = 1; };
-template <bool LIMIT, bool KPER>
+// 64 x 64 to 128 x 128 grid, 8 x 8 tiles 64-256, 8 x 4 tiles 128-512 (their
+// ring recompute included).  Per step at 64 x 64: 8 x 4 tiles 11.8 us, 8 x 8
+// 12.4-13.3, staged kernels 18.1, 32 x 8 tiles 23.2; at 128 x 128: 8 x 8
+// tiles 17.7-19.3, 8 x 4 21.5, staged 19.2; 256 x 256 runs faster staged
+// (42 against 62).  So 8 x 4 tiles up to 64 x 64 columns, 8 x 8 up to
+// 128 x 128.
+template <int TY, bool LIMIT, bool KPER>
 auto fused_small_ptr() {
-  return mpd::fused2::step_kernel2<double, FusedS::TX, FusedS::TY, FusedS::MINB, LIMIT, false,
-                                   KPER, 0, 1, false, true>;
+  return mpd::fused2::step_kernel2<double, 8, TY, 1, LIMIT, false, KPER, 0, 1, false, true>;
 }
+template <int TY>
 auto fused_small_pick(const mpdata_ctx* c) {
-  if (c->g.kper) return c->nonosc ? fused_small_ptr<true, true>() : fused_small_ptr<false, true>();
-  return c->nonosc ? fused_small_ptr<true, false>() : fused_small_ptr<false, false>();
+  if (c->g.kper)
+    return c->nonosc ? fused_small_ptr<TY, true, true>() : fused_small_ptr<TY, false, true>();
+  return c->nonosc ? fused_small_ptr<TY, true, false>() : fused_small_ptr<TY, false, false>();
 }
+template <int TY>
 constexpr size_t fused_small_smem() {
-  return mpd::fused2::Layout<double, FusedS::TX, FusedS::TY>::bytes;
+  return mpd::fused2::Layout<double, 8, TY>::bytes;
+}
+template <int TY>
+bool fused_small_attr(const mpdata_ctx* c) {
+  if (cudaFuncSetAttribute(fused_small_pick<TY>(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)fused_small_smem<TY>()) == cudaSuccess)
+    return true;
+  cudaGetLastError();
+  return false;
 }
 void fused_small_setup(mpdata_ctx* c) {
   const Geo& g = c->g;
-  c->s8_ok = 0;
-  if (c->dtype != MPDATA_F64 || !c->fused_ok || g.openij || g.nz != 1 ||
-      (int64_t)g.nx * g.ny > 128 * 128)
+  c->small_ty = 0;
+  const int64_t cols = (int64_t)g.nx * g.ny;
+  if (c->dtype != MPDATA_F64 || !c->fused_ok || g.openij || g.nz != 1 || cols > 128 * 128)
     return;
-  if (cudaFuncSetAttribute(fused_small_pick(c), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)fused_small_smem()) != cudaSuccess) {
-    cudaGetLastError();
-    return;
-  }
-  c->s8_ok = 1;
+  if (cols <= 64 * 64) c->small_ty = fused_small_attr<4>(c) ? 4 : 0;
+  else c->small_ty = fused_small_attr<8>(c) ? 8 : 0;
+}
+template <int TY>
+int fused_small_launch(mpdata_ctx* c, const double* in, double* out, const double* U,
+                       const double* V, const double* W, const double* G) {
+  const Geo& g = c->g;
+  const dim3 gs((g.nx + 7) / 8, (g.ny + TY - 1) / TY, 1);
+  MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
+             mpd::launch_pdl(fused_small_pick<TY>(c), gs, 12 * (TY + 4), fused_small_smem<TY>(),
+                             c->stream, g, g.nz, in, U, V, W, G, out,
+                             mpd::fused2::TapeOut<double>{}));
+  MPD_CHECK_LAUNCH(c, "fused step kernel");
+  return MPDATA_OK;
 }
 
 // The two-column FP32 step (fusedx.cuh): its tile (32 x 24 columns, 504
@@ -518,7 +537,7 @@ int fused_setup(mpdata_ctx* c) {
   const Geo& g = c->g;
   c->fused_ok = 0;
   c->x2_ok = 0;
-  c->s8_ok = 0;
+  c->small_ty = 0;
   // the periodic images a column writes need nx, ny >= 2h; a slab writes
   // none and needs only an interior as wide as the strips it sends
   const int minw = g.openij ? g.h : 2 * g.h;
@@ -580,15 +599,9 @@ int fused_launch(mpdata_ctx* c, const T* in, T* out, const T* U, const T* V, con
     }
   }
   if constexpr (std::is_same<T, double>::value) {
-    if (c->s8_ok && !tape && c->opts == 0) {  // a small one-level grid: 8 x 8 tiles
-      const dim3 gs((g.nx + FusedS::TX - 1) / FusedS::TX, (g.ny + FusedS::TY - 1) / FusedS::TY, 1);
-      MPD_LAUNCH(c, MPDATA_STAGE_FUSED,
-                 mpd::launch_pdl(fused_small_pick(c), gs, (FusedS::TX + 4) * (FusedS::TY + 4),
-                                 fused_small_smem(), c->stream, g, g.nz, in, U, V, W, G, out,
-                                 mpd::fused2::TapeOut<double>{}));
-      MPD_CHECK_LAUNCH(c, "fused step kernel");
-      return MPDATA_OK;
-    }
+    if (c->small_ty && !tape && c->opts == 0)  // a small one-level grid: 8 x TY tiles
+      return c->small_ty == 4 ? fused_small_launch<4>(c, in, out, U, V, W, G)
+                              : fused_small_launch<8>(c, in, out, U, V, W, G);
   }
   dim3 grid((g.nx + F::TX - 1) / F::TX, (g.ny + F::TY - 1) / F::TY, c->nchunks);
   const size_t bytes = fused_smem<T>();
@@ -616,7 +629,7 @@ bool use_fused(const mpdata_ctx* c) {
 // The plain step of a small one-level FP64 grid runs fused on 8 x 8 tiles
 // unless the staged kernels are asked for.
 bool use_fused_plain(const mpdata_ctx* c) {
-  return use_fused(c) || (c->s8_ok && c->opts == 0 && c->variant != MPDATA_STAGED);
+  return use_fused(c) || (c->small_ty && c->opts == 0 && c->variant != MPDATA_STAGED);
 }
 
 // One step psi_in -> psi_out (distinct buffers), halo of psi_out filled.

@@ -322,10 +322,10 @@ SMALL_2D = [(64, 64, 1), (37, 29, 1), (128, 128, 1), (8, 12, 1), (129, 120, 1), 
 @pytest.mark.parametrize("nonosc", [0, 1])
 @pytest.mark.parametrize("shape", SMALL_2D, ids=[f"{a}x{b}x{c}" for a, b, c in SMALL_2D])
 def test_f64_one_level_grid_default_step(shape, nonosc, kbc):
-    """FP64 on one level: the default step (the one-kernel step on 8 x 8
-    tiles up to 128 x 128 columns, the staged kernels above) against the
-    oracle and against the staged kernels, 1 and 5 steps, the halo of the
-    result filled."""
+    """FP64 on one level: the default step (the one-kernel step on 8 x 4
+    tiles up to 64 x 64 columns, 8 x 8 up to 128 x 128, the staged kernels
+    above) against the oracle and against the staged kernels, 1 and 5
+    steps, the halo of the result filled."""
     nx, ny, nz = shape
     c = synth.random_case(nx, ny, nz, seed=nx * 7 + ny, cmax=0.4, kbc=kbc)
     P = [synth.pad(x, c.halo) for x in (c.psi, c.u, c.v, c.w, c.g)]
