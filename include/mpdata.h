@@ -179,8 +179,22 @@ MPDATA_API int mpdata_step_host_async(mpdata_ctx *c, const void *psi_in_host, vo
                                       const void *u_host, const void *v_host,
                                       const void *w_host, const void *g_host, int nsteps);
 
-/* Wait until every problem enqueued by mpdata_step_host_async has been
- * copied back.  Errors: EINVAL, ECUDA. */
+/* The same for HOST arrays of the interior alone (a library-interface
+ * addition): psi_in_host, psi_out_host, u_host, v_host, w_host and g_host
+ * each hold the nx*ny*nz interior values, i fastest, then j, then k,
+ * page-locked; psi_out_host receives the interior of the result.  Only the
+ * interior crosses the host link (one 3D copy a field into the padded
+ * device fields): the step reads no input halo and fills its output's.
+ * It shares the device buffers, streams and in-flight limit of
+ * mpdata_step_host_async.  Errors: EINVAL (also on a slab), ENOMEM, ECUDA. */
+MPDATA_API int mpdata_step_host_interior_async(mpdata_ctx *c, const void *psi_in_host,
+                                               void *psi_out_host, const void *u_host,
+                                               const void *v_host, const void *w_host,
+                                               const void *g_host, int nsteps);
+
+/* Wait until every problem enqueued by mpdata_step_host_async or
+ * mpdata_step_host_interior_async has been copied back.  Errors: EINVAL,
+ * ECUDA. */
 MPDATA_API int mpdata_host_wait(mpdata_ctx *c);
 
 /* Adjoint (reverse mode) of one step, iord 1 or 2, with or without the

@@ -80,6 +80,7 @@ SIGNATURES = {
     "mpdata_step_out": (_i, [_c, _c, _c, _c, _c, _c, _c]),
     "mpdata_step_host": (_i, [_c, _c, _c, _c, _c, _c, _i]),
     "mpdata_step_host_async": (_i, [_c, _c, _c, _c, _c, _c, _c, _i]),
+    "mpdata_step_host_interior_async": (_i, [_c, _c, _c, _c, _c, _c, _c, _i]),
     "mpdata_host_wait": (_i, [_c]),
     "mpdata_fill_halo": (_i, [_c, _c, _i]),
     "mpdata_adjoint_step": (_i, [_c] * 10),
@@ -325,6 +326,12 @@ def mpdata_halo_unpack(ctx, buf, face, field):
 def mpdata_step_host_async(ctx, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps):
     _check(lib.mpdata_step_host_async(ctx, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps),
            "mpdata_step_host_async", ctx)
+
+
+def mpdata_step_host_interior_async(ctx, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps):
+    _check(lib.mpdata_step_host_interior_async(ctx, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h,
+                                               nsteps),
+           "mpdata_step_host_interior_async", ctx)
 
 
 def mpdata_host_wait(ctx):

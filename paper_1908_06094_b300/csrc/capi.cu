@@ -1143,10 +1143,34 @@ int mpdata_step_host(mpdata_ctx* c, void* psi_h, const void* u_h, const void* v_
   return MPDATA_OK;
 }
 
-int mpdata_step_host_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h, const void* u_h,
-                           const void* v_h, const void* w_h, const void* g_h, int nsteps) {
+namespace {
+// A 3D copy between a field's interior in padded device storage and a host
+// array of the interior alone (nx*ny*nz, i fastest): rows of nx elements,
+// the padded side at its row and plane pitches.
+cudaError_t interior_copy(const mpdata_ctx* c, void* dev_field, void* host, bool to_device,
+                          cudaStream_t s) {
+  const Geo& g = c->g;
+  const size_t es = c->esize;
+  char* origin = (char*)dev_field + (size_t)g.off0 * es;
+  cudaMemcpy3DParms p = {};
+  cudaPitchedPtr dev = make_cudaPitchedPtr(origin, (size_t)g.px * es, (size_t)g.nx,
+                                           (size_t)(g.pxy / g.px));
+  cudaPitchedPtr hst = make_cudaPitchedPtr(host, (size_t)g.nx * es, (size_t)g.nx, (size_t)g.ny);
+  p.srcPtr = to_device ? hst : dev;
+  p.dstPtr = to_device ? dev : hst;
+  p.extent = make_cudaExtent((size_t)g.nx * es, (size_t)g.ny, (size_t)g.nz);
+  p.kind = to_device ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+  return cudaMemcpy3DAsync(&p, s);
+}
+
+// The pipelined host-buffer steps, with padded host fields or, interior,
+// with host arrays of the interior alone.
+int host_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h, const void* u_h,
+               const void* v_h, const void* w_h, const void* g_h, int nsteps, bool interior) {
   if (!c || nsteps < 0 || !psi_in_h || !psi_out_h || !u_h || !v_h || !w_h || !g_h)
     return MPDATA_EINVAL;
+  if (interior && c->g.openij)
+    return fail(c, MPDATA_EINVAL, "a slab takes its halo from the halo exchange");
   const size_t fbytes = (size_t)c->g.total * c->esize;
   const size_t fpad = (fbytes + 255) & ~(size_t)255;
   cudaError_t e;
@@ -1187,8 +1211,10 @@ int mpdata_step_host_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h,
   if (c->pused[b] && (e = cudaStreamWaitEvent(c->ps_in, c->pe_out[b], 0)) != cudaSuccess)
     return cuda_fail(c, e, "pipeline wait");
   const void* src[5] = {psi_in_h, u_h, v_h, w_h, g_h};
+  // (interior: the step reads no input halo, so only the interior crosses)
   for (int q = 0; q < 5; ++q) {
-    e = cudaMemcpyAsync(d + q * fpad, src[q], fbytes, cudaMemcpyHostToDevice, c->ps_in);
+    e = interior ? interior_copy(c, d + q * fpad, const_cast<void*>(src[q]), true, c->ps_in)
+                 : cudaMemcpyAsync(d + q * fpad, src[q], fbytes, cudaMemcpyHostToDevice, c->ps_in);
     if (e != cudaSuccess) return cuda_fail(c, e, "host-to-device copy");
   }
   if ((e = cudaEventRecord(c->pe_in[b], c->ps_in)) != cudaSuccess ||
@@ -1199,13 +1225,26 @@ int mpdata_step_host_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h,
   if ((e = cudaEventRecord(c->pe_step[b], c->stream)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(c->ps_out, c->pe_step[b], 0)) != cudaSuccess)
     return cuda_fail(c, e, "pipeline events");
-  e = cudaMemcpyAsync(psi_out_h, d, fbytes, cudaMemcpyDeviceToHost, c->ps_out);
+  e = interior ? interior_copy(c, d, psi_out_h, false, c->ps_out)
+               : cudaMemcpyAsync(psi_out_h, d, fbytes, cudaMemcpyDeviceToHost, c->ps_out);
   if (e != cudaSuccess) return cuda_fail(c, e, "device-to-host copy");
   if ((e = cudaEventRecord(c->pe_out[b], c->ps_out)) != cudaSuccess)
     return cuda_fail(c, e, "pipeline events");
   c->pused[b] = true;
   c->pslot = b ^ 1;
   return MPDATA_OK;
+}
+}  // namespace
+
+int mpdata_step_host_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h, const void* u_h,
+                           const void* v_h, const void* w_h, const void* g_h, int nsteps) {
+  return host_async(c, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps, false);
+}
+
+int mpdata_step_host_interior_async(mpdata_ctx* c, const void* psi_in_h, void* psi_out_h,
+                                    const void* u_h, const void* v_h, const void* w_h,
+                                    const void* g_h, int nsteps) {
+  return host_async(c, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h, nsteps, true);
 }
 
 int mpdata_host_wait(mpdata_ctx* c) {

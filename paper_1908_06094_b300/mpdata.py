@@ -148,6 +148,25 @@ class MPDATA:
                                  nsteps)
         return psi_out_h
 
+    def step_host_interior_async(self, psi_in_h, psi_out_h, u_h, v_h, w_h, g_h,
+                                 nsteps: int = 1):
+        """step_host_async for CPU tensors of the interior alone, shape
+        (nz, ny, nx): only the interior crosses the host link, and psi_out_h
+        receives the interior of the result."""
+        shape = (self.nz, self.ny, self.nx)
+        for name, t in (("psi_in", psi_in_h), ("psi_out", psi_out_h), ("u", u_h), ("v", v_h),
+                        ("w", w_h), ("g", g_h)):
+            if t.is_cuda or t.dtype != self.dtype or tuple(t.shape) != shape \
+                    or not t.is_contiguous():
+                raise ValueError(f"{name}: expected a contiguous CPU {self.dtype} tensor of "
+                                 f"shape {shape}")
+        self._sync_stream()
+        C.mpdata_step_host_interior_async(self._ctx, psi_in_h.data_ptr(), psi_out_h.data_ptr(),
+                                          u_h.data_ptr(), v_h.data_ptr(), w_h.data_ptr(),
+                                          g_h.data_ptr(), nsteps)
+        return psi_out_h
+
     def host_wait(self):
-        """Wait for every problem enqueued by step_host_async."""
+        """Wait for every problem enqueued by step_host_async or
+        step_host_interior_async."""
         C.mpdata_host_wait(self._ctx)

@@ -90,6 +90,8 @@ def test_later_calls_reject_bad_arguments_without_a_device(capi):
     fake = 1 << 20
     assert L.mpdata_step_host_async(None, fake, fake, fake, fake, fake, fake, 1) == \
         capi.MPDATA_EINVAL
+    assert L.mpdata_step_host_interior_async(None, fake, fake, fake, fake, fake, fake, 1) == \
+        capi.MPDATA_EINVAL
     assert L.mpdata_host_wait(None) == capi.MPDATA_EINVAL
     assert L.mpdata_set_ij_boundary(None, capi.MPDATA_IJ_HALO) == capi.MPDATA_EINVAL
     n = ctypes.c_longlong()

@@ -80,3 +80,31 @@ def test_noalloc_mass_rejects_bad_arguments(capi):
         capi.MPDATA_ERANGE
     assert L.mpdata_mass_noalloc(p, p, 70000, 70000, 1, 2, 0, out.data_ptr(), None) == \
         capi.MPDATA_ERANGE
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_noalloc_mass_in_a_global_mode_stream_capture(capi, dtype):
+    """The entry point's purpose: after a first (eager) call it can be
+    captured in a CUDA graph in global capture mode, which refuses any
+    allocation; the replayed graph gives the eager call's bits."""
+    nx, ny, nz, h = 61, 40, 9, 2
+    code = capi.MPDATA_F64 if dtype == torch.float64 else capi.MPDATA_F32
+    psi, g = _fields(nx, ny, nz, h, 303, dtype)
+    eager = torch.empty((), dtype=torch.float64, device="cuda")
+    capi.mpdata_mass_noalloc(psi.data_ptr(), g.data_ptr(), nx, ny, nz, h, code,
+                             eager.data_ptr())
+    torch.cuda.synchronize()
+    out = torch.full((), -1.0, dtype=torch.float64, device="cuda")
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s, capture_error_mode="global"):
+            capi.mpdata_mass_noalloc(psi.data_ptr(), g.data_ptr(), nx, ny, nz, h, code,
+                                     out.data_ptr(), s.cuda_stream)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    assert out.item() == -1.0  # captured, not run
+    graph.replay()
+    torch.cuda.synchronize()
+    assert out.item() == eager.item()
