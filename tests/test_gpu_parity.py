@@ -315,7 +315,8 @@ def test_iord_and_halo_range(iord, h, nonosc, dtype, variant):
     assert np.array_equal(got, ref_halo)
 
 
-SMALL_2D = [(64, 64, 1), (37, 29, 1), (128, 128, 1), (8, 12, 1), (129, 120, 1), (130, 128, 1)]
+SMALL_2D = [(64, 64, 1), (37, 29, 1), (128, 128, 1), (8, 12, 1), (129, 120, 1), (130, 128, 1),
+            (5, 7, 1), (4, 4, 1)]
 
 
 @pytest.mark.parametrize("kbc", [0, 1], ids=["zeroflux", "periodic_k"])
@@ -340,3 +341,15 @@ def test_f64_one_level_grid_default_step(shape, nonosc, kbc):
         h = c.halo
         assert rel_err(got[:h], ref_halo[:h]) <= F64_TOL * nsteps
         assert rel_err(got[:, :h], ref_halo[:, :h]) <= F64_TOL * nsteps
+
+
+@pytest.mark.parametrize("halo", [3, 4])
+def test_f64_one_level_grid_wider_halo(halo):
+    """The small one-level path with a halo of 3 or 4: the oracle's result,
+    the halo of the output included."""
+    c = synth.random_case(30, 22, 1, seed=77, cmax=0.4)
+    P = [synth.pad(x, halo) for x in (c.psi, c.u, c.v, c.w, c.g)]
+    ref = oracle.run(*P, h=halo, iord=2, nonosc=1, nsteps=4)
+    got = run_library(c, torch.float64, 2, 1, 4, h=halo)
+    oracle.fill_halo(ref, halo, kind=0, kbc=0)
+    assert rel_err(got, ref) <= F64_TOL * 4
