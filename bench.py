@@ -834,6 +834,8 @@ def measure_config(dev, wl_name, variant=None, steps=30, warmup=3):
             "error_vs_f64": err,
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(gbs, 1), "peak": hbm,
                          "unit": "GB/s", "frac": round(gbs / hbm, 4),
+                         "traffic": _traffic_from_profiles(dom, wl_name, _source_hash(dom)),
+                         "algorithmic_bytes": STAGE_WORDS[dom] * esize * npts,
                          "launch_ms": round(per, 5)}}
 
 
